@@ -1,0 +1,356 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: the exact
+ELBO of the implied q(u) (Cholesky), the exact GP log marginal likelihood,
+an explicitly built Fisher matrix, finite differences, textbook identities or
+library quadrature.  None of these need a GPU.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import linalg as sla
+from scipy import stats
+
+import svgp_synth as S
+from oracle import rsvgp as O
+
+
+def _spaced_state(M, D, seed, **kw):
+    p = S.random_state(M, D, seed, **kw)
+    p["Z"] = p["Z"] * 1.5
+    return p
+
+
+def _batch(B, D, seed):
+    rng = np.random.default_rng([seed, 99])
+    X = rng.normal(size=(B, D))
+    y = np.sin(X.sum(1)) + 0.1 * rng.normal(size=B)
+    return X, y
+
+
+def _msvgp_elbo(p, X, y, N):
+    """Exact M-SVGP ELBO (Section 2) for q(u) = N(m, S) with the implied
+    m = Kuu P m~ and S = Kuu - Kuu P Kuu (Section 3.2), via Cholesky."""
+    Kuu = O.se_ard(p["Z"], p["Z"], p["ell"], p["sf2"])
+    Kuf = O.se_ard(p["Z"], X, p["ell"], p["sf2"])
+    Kt = Kuu + np.diag(p["s"])
+    T = p["L"] @ p["L"].T
+    P = 2 * T - T @ Kt @ T
+    m = Kuu @ P @ p["m"]
+    Sq = Kuu - Kuu @ P @ Kuu
+    cK = sla.cho_factor(Kuu, lower=True)
+    A = sla.cho_solve(cK, Kuf)                 # Kuu^-1 k_un
+    mu = A.T @ m
+    var = p["sf2"] - np.einsum("in,in->n", Kuf, A) + np.einsum("in,in->n", A, Sq @ A)
+    noise = p["noise"]
+    En = -0.5 * np.log(2 * np.pi * noise) - ((y - mu) ** 2 + var) / (2 * noise)
+    M = Kuu.shape[0]
+    KL = 0.5 * (np.trace(sla.cho_solve(cK, Sq)) + m @ sla.cho_solve(cK, m) - M
+                + 2 * np.sum(np.log(np.diag(cK[0]))) - np.linalg.slogdet(Sq)[1])
+    return (N / X.shape[0]) * En.sum() - KL, mu, var, KL
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_bound_below_exact_elbo_of_implied_q(seed):
+    """R-SVGP(P) <= exact ELBO of the q(u) it implies; data terms identical."""
+    p = _spaced_state(10, 2, seed)
+    X, y = _batch(30, 2, seed)
+    b = O.bound(p, X, y, N=300)
+    elbo, mu, var, KL = _msvgp_elbo(p, X, y, 300)
+    np.testing.assert_allclose(b["mu"], mu, rtol=1e-7, atol=1e-9)
+    np.testing.assert_allclose(b["var"], var, rtol=1e-6, atol=1e-8)
+    assert b["KL"] >= KL - 1e-8 * abs(KL)
+    assert b["F"] <= elbo + 1e-8 * abs(elbo)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_bound_equals_exact_elbo_at_T_inverse(seed):
+    """Equality at T = K~^-1 (Section 2, Eq. (3)/(4) equality condition)."""
+    p = _spaced_state(10, 2, seed)
+    X, y = _batch(30, 2, seed)
+    Kt = O.se_ard(p["Z"], p["Z"], p["ell"], p["sf2"]) + np.diag(p["s"])
+    p["L"] = np.linalg.cholesky(np.linalg.inv(Kt))
+    b = O.bound(p, X, y, N=300)
+    elbo, _, _, KL = _msvgp_elbo(p, X, y, 300)
+    assert abs(b["F"] - elbo) <= 1e-9 * abs(elbo)
+    assert abs(b["KL"] - KL) <= 1e-8 * max(1.0, abs(KL))
+
+
+@pytest.mark.parametrize("N", [7, 23, 48])
+def test_exact_gp_limit(N):
+    """Z = X, m~ = y, S~ = noise I, T = K~^-1, full batch: bound = log N(y|0,K+noise I).
+
+    Section 3.2: with X = Z the preconditioned mean matches the GP posterior
+    mean, and q(u) is then the exact posterior, so the ELBO is tight."""
+    rng = np.random.default_rng(N)
+    X = rng.uniform(-2, 2, size=(N, 2))
+    y = np.cos(X[:, 0]) + 0.2 * rng.normal(size=N)
+    ell, sf2, noise = np.array([0.8, 1.3]), 1.4, 0.09
+    K = O.se_ard(X, X, ell, sf2)
+    Kt = K + noise * np.eye(N)
+    p = dict(Z=X.copy(), ell=ell, sf2=sf2, noise=noise, m=y.copy(), s=np.full(N, noise),
+             L=np.linalg.cholesky(np.linalg.inv(Kt)))
+    F = O.bound(p, X, y, N=N)["F"]
+    lml = stats.multivariate_normal(mean=np.zeros(N), cov=Kt).logpdf(y)
+    assert abs(F - lml) <= 1e-8 * abs(lml)
+
+
+def _sym_basis_lower(M):
+    idx = [(i, j) for j in range(M) for i in range(j, M)]   # column-wise vec of tril
+    return idx
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_prop1_natural_gradient_equals_fisher_solve(seed):
+    """Prop. 1 against F^-1 g with F built from the Gaussian Fisher formula.
+
+    Fisher of N(0, Sigma(theta)): F_ab = 1/2 tr(Sigma^-1 dSigma_a Sigma^-1 dSigma_b)
+    (textbook), theta = lower-triangular entries of L, Sigma = L L^T.
+    Gradient of KL[N(0, LL^T) || N(0, A^-1)] by central differences."""
+    rng = np.random.default_rng(seed)
+    M = 4
+    L = np.tril(rng.normal(size=(M, M)) * 0.3) + np.diag(rng.uniform(0.5, 1.5, M))
+    Q = rng.normal(size=(M, M))
+    A = Q @ Q.T + M * np.eye(M) * 0.5
+    idx = _sym_basis_lower(M)
+
+    def kl(Lm):
+        Sg = Lm @ Lm.T
+        return 0.5 * (np.trace(A @ Sg) - M - np.linalg.slogdet(A)[1] - np.linalg.slogdet(Sg)[1])
+
+    g = np.zeros(len(idx))
+    for a, (i, j) in enumerate(idx):
+        h = 1e-6
+        Lp, Lm_ = L.copy(), L.copy()
+        Lp[i, j] += h
+        Lm_[i, j] -= h
+        g[a] = (kl(Lp) - kl(Lm_)) / (2 * h)
+    Sg = L @ L.T
+    Si = np.linalg.inv(Sg)
+    dS = []
+    for (i, j) in idx:
+        E = np.zeros((M, M))
+        E[i, j] = 1.0
+        dS.append(E @ L.T + L @ E.T)
+    F = np.array([[0.5 * np.trace(Si @ da @ Si @ db) for db in dS] for da in dS])
+    ng = np.linalg.solve(F, g)
+    L1, _ = O.ng_step(L, A, 1.0)
+    nat = L - L1
+    np.testing.assert_allclose(np.array([nat[i, j] for (i, j) in idx]), ng, rtol=1e-6, atol=1e-8)
+    assert np.allclose(np.triu(nat, 1), 0.0)
+
+
+def test_tspace_natural_gradient_is_newton_schulz():
+    """Section 3.2 remark: a unit NG step in T-space is the Newton-Schulz step
+    2T - T K~ T, i.e. the preconditioner P.  The T-space Fisher is built from
+    the textbook Gaussian formula over a symmetric basis."""
+    rng = np.random.default_rng(5)
+    M = 4
+    Q = rng.normal(size=(M, M))
+    Kt = Q @ Q.T + np.eye(M)
+    L = np.tril(rng.normal(size=(M, M)) * 0.1) + np.diag(rng.uniform(0.3, 0.6, M))
+    T = L @ L.T
+    idx = [(i, j) for j in range(M) for i in range(j, M)]
+
+    def E_of(i, j):
+        E = np.zeros((M, M))
+        E[i, j] = 1.0
+        E[j, i] = 1.0
+        return E
+
+    def kl(Tm):
+        return 0.5 * (np.trace(Kt @ Tm) - M - np.linalg.slogdet(Kt)[1] - np.linalg.slogdet(Tm)[1])
+
+    g = np.array([(kl(T + 1e-6 * E_of(i, j)) - kl(T - 1e-6 * E_of(i, j))) / 2e-6 for (i, j) in idx])
+    Ti = np.linalg.inv(T)
+    F = np.array([[0.5 * np.trace(Ti @ E_of(*a) @ Ti @ E_of(*b)) for b in idx] for a in idx])
+    ng = np.linalg.solve(F, g)
+    Tnew = T.copy()
+    for a, (i, j) in enumerate(idx):
+        Tnew[i, j] -= ng[a]
+        if i != j:
+            Tnew[j, i] -= ng[a]
+    _, P = O.preconditioner(L, Kt)
+    np.testing.assert_allclose(Tnew, P, rtol=1e-6, atol=1e-8)
+    # Newton-Schulz error squaring: I - K~ P = (I - K~ T)^2
+    E0 = np.eye(M) - Kt @ T
+    np.testing.assert_allclose(np.eye(M) - Kt @ P, E0 @ E0, atol=1e-12)
+
+
+def test_ng_fixed_point_and_convergence():
+    """chol(K~^-1) is a fixed point of Prop. 1 (zero residual, Eq. (8)); NG
+    iterations from beta*I converge to it (Section 3.1, Appendix S5.3)."""
+    p = _spaced_state(16, 2, 3)
+    Kt = O.se_ard(p["Z"], p["Z"], p["ell"], p["sf2"]) + np.diag(p["s"])
+    Ls = np.linalg.cholesky(np.linalg.inv(Kt))
+    L1, r = O.ng_step(Ls, Kt, 1.0)
+    assert r < 1e-12
+    np.testing.assert_allclose(L1, Ls, atol=1e-12)
+    gam = [O.gamma_schedule(t, gamma0=1e-1, ramp=5) for t in range(200)]
+    L, it, r = O.ng_solve(1e-3 * np.eye(16), Kt, gam, eps=1e-10, max_iters=200)
+    assert r < 1e-10 and it < 200
+    np.testing.assert_allclose(L, Ls, rtol=1e-7, atol=1e-9)
+
+
+def test_stopping_rule_does_not_update_when_converged():
+    p = _spaced_state(8, 2, 4)
+    Kt = O.se_ard(p["Z"], p["Z"], p["ell"], p["sf2"]) + np.diag(p["s"])
+    Ls = np.linalg.cholesky(np.linalg.inv(Kt))
+    L, it, r = O.ng_solve(Ls, Kt, [1.0] * 5, eps=1e-6, max_iters=5)
+    assert it == 0 and r < 1e-6 and np.array_equal(L, Ls)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_gradients_match_central_differences(seed):
+    p = _spaced_state(9, 3, seed)
+    X, y = _batch(25, 3, seed)
+    N = 137.0
+    g = O.grads(p, X, y, N)
+
+    def F(pp):
+        return O.bound(pp, X, y, N)["F"]
+
+    for k in ["Z", "ell", "sf2", "noise", "m", "s"]:
+        x = np.asarray(p[k], np.float64)
+        fd = np.zeros(x.shape)
+        for idx in np.ndindex(x.shape):
+            h = 1e-6 * max(1.0, abs(float(x[idx])))
+            xp, xm = x.copy(), x.copy()
+            xp[idx] += h
+            xm[idx] -= h
+            pp, pm = dict(p), dict(p)
+            pp[k] = xp if x.ndim else float(xp)
+            pm[k] = xm if x.ndim else float(xm)
+            fd[idx] = (F(pp) - F(pm)) / (2 * h)
+        err = np.linalg.norm(fd - g[k]) / np.linalg.norm(fd)
+        assert err < 1e-6, (k, err)
+
+
+def _lsvgp_precond_bound(p, X, y, N):
+    """Preconditioned L-SVGP bound (Appendix S2) with P^(L) = K~^-1 (inverse)."""
+    Kuu = O.se_ard(p["Z"], p["Z"], p["ell"], p["sf2"])
+    Kuf = O.se_ard(p["Z"], X, p["ell"], p["sf2"])
+    Kt = Kuu + np.diag(p["s"])
+    P = np.linalg.inv(Kt)
+    mu = Kuf.T @ P @ p["m"]
+    var = p["sf2"] - np.einsum("in,in->n", Kuf, P @ Kuf)
+    noise = p["noise"]
+    En = -0.5 * np.log(2 * np.pi * noise) - ((y - mu) ** 2 + var) / (2 * noise)
+    KL = 0.5 * (-np.trace(P @ Kuu) + p["m"] @ P @ Kuu @ P @ p["m"]
+                + np.linalg.slogdet(Kt)[1] - np.sum(np.log(p["s"])))
+    return (N / X.shape[0]) * En.sum() - KL
+
+
+def test_prop2_gradient_equivalence_with_lsvgp():
+    """Prop. 2: at T = stopgrad(K~^-1) the R-SVGP(P) gradient w.r.t. xi equals
+    the preconditioned L-SVGP gradient (finite differences on the latter)."""
+    p = _spaced_state(8, 2, 11)
+    X, y = _batch(20, 2, 11)
+    N = 80.0
+    Kt = O.se_ard(p["Z"], p["Z"], p["ell"], p["sf2"]) + np.diag(p["s"])
+    p["L"] = np.linalg.cholesky(np.linalg.inv(Kt))
+    g = O.grads(p, X, y, N)
+    for k in ["Z", "ell", "sf2", "noise", "m", "s"]:
+        x = np.asarray(p[k], np.float64)
+        fd = np.zeros(x.shape)
+        for idx in np.ndindex(x.shape):
+            h = 1e-6 * max(1.0, abs(float(x[idx])))
+            xp, xm = x.copy(), x.copy()
+            xp[idx] += h
+            xm[idx] -= h
+            pp, pm = dict(p), dict(p)
+            pp[k] = xp if x.ndim else float(xp)
+            pm[k] = xm if x.ndim else float(xm)
+            fd[idx] = (_lsvgp_precond_bound(pp, X, y, N) - _lsvgp_precond_bound(pm, X, y, N)) / (2 * h)
+        err = np.linalg.norm(fd - g[k]) / np.linalg.norm(fd)
+        assert err < 1e-6, (k, err)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_prop3_variance_sandwich(seed):
+    """Prop. 3: L_n <= sigma_n^2(L) <= U_n and U_n - L_n = ||(I - K~T) k_un||^2 / sigma^2.
+
+    U_n is the oracle's sigma_n^2 (Eq. (3)); sigma_n^2(L) uses K~^-1 (Eq. (2))."""
+    p = _spaced_state(8, 2, seed)
+    X, _ = _batch(15, 2, seed)
+    y = np.zeros(15)
+    sig2 = 0.03
+    p["s"] = p["s"] + sig2                    # S~ = S~' + sigma^2 I
+    Kuu = O.se_ard(p["Z"], p["Z"], p["ell"], p["sf2"])
+    Kuf = O.se_ard(p["Z"], X, p["ell"], p["sf2"])
+    Kt = Kuu + np.diag(p["s"])
+    Km = Kt - sig2 * np.eye(8)
+    T = p["L"] @ p["L"].T
+    U = O.bound(p, X, y)["var"]
+    varL = p["sf2"] - np.einsum("in,in->n", Kuf, np.linalg.solve(Kt, Kuf))
+    Ln = np.array([p["sf2"] - (k @ k - 2 * k @ T @ Km @ k + k @ T @ Km @ Kt @ T @ k) / sig2
+                   for k in Kuf.T])
+    assert np.all(Ln <= varL + 1e-10) and np.all(varL <= U + 1e-10)
+    G = np.array([np.sum(((np.eye(8) - Kt @ T) @ k) ** 2) / sig2 for k in Kuf.T])
+    np.testing.assert_allclose(U - Ln, G, rtol=1e-8, atol=1e-10)
+
+
+def test_probit_quadrature_matches_adaptive_integral():
+    from scipy import integrate
+    from scipy.special import log_ndtr
+    mu = np.array([-1.3, 0.2, 2.1])
+    var = np.array([0.4, 1.7, 0.05])
+    y = np.array([1.0, 0.0, 1.0])
+    got = O.probit_expected_loglik(y, mu, var)
+    for n in range(3):
+        s = 2 * y[n] - 1
+        f = lambda t: stats.norm.pdf(t, mu[n], math.sqrt(var[n])) * log_ndtr(s * t)
+        ref, _ = integrate.quad(f, mu[n] - 12 * math.sqrt(var[n]), mu[n] + 12 * math.sqrt(var[n]),
+                                epsabs=1e-13, epsrel=1e-13)
+        assert abs(got[n] - ref) < 1e-6 * max(1.0, abs(ref))
+
+
+def test_predict_exact_gp_posterior():
+    """At Z = X, m~ = y, S~ = noise I, T = K~^-1 prediction is the exact GP
+    posterior (Section 3.2)."""
+    rng = np.random.default_rng(3)
+    N = 20
+    X = rng.uniform(-2, 2, size=(N, 1))
+    y = np.sin(2 * X[:, 0])
+    ell, sf2, noise = np.array([0.7]), 1.1, 0.05
+    K = O.se_ard(X, X, ell, sf2)
+    Kt = K + noise * np.eye(N)
+    p = dict(Z=X.copy(), ell=ell, sf2=sf2, noise=noise, m=y.copy(), s=np.full(N, noise),
+             L=np.linalg.cholesky(np.linalg.inv(Kt)))
+    Xs = np.linspace(-2.5, 2.5, 13)[:, None]
+    mean, var = O.predict(p, Xs, include_noise=True)
+    Ks = O.se_ard(X, Xs, ell, sf2)
+    ref_mean = Ks.T @ np.linalg.solve(Kt, y)
+    ref_var = sf2 - np.einsum("in,in->n", Ks, np.linalg.solve(Kt, Ks)) + noise
+    np.testing.assert_allclose(mean, ref_mean, atol=1e-9)
+    np.testing.assert_allclose(var, ref_var, atol=1e-9)
+
+
+def test_se_ard_special_cases():
+    """Kernel: k(x, x) = sf2; one dimension reduces to the scalar RBF."""
+    rng = np.random.default_rng(0)
+    A = rng.normal(size=(5, 1))
+    B = rng.normal(size=(4, 1))
+    K = O.se_ard(A, B, np.array([0.7]), 2.0)
+    ref = 2.0 * np.exp(-0.5 * (A - B.T) ** 2 / 0.49)
+    np.testing.assert_allclose(K, ref, rtol=1e-14)
+    np.testing.assert_allclose(np.diag(O.se_ard(A, A, np.array([0.3]), 1.7)), 1.7)
+
+
+def test_gamma_schedule_endpoints():
+    assert O.gamma_schedule(0) == pytest.approx(1e-5)
+    assert O.gamma_schedule(5) == pytest.approx(1e-5 ** 0.5)
+    assert O.gamma_schedule(10) == 1.0 and O.gamma_schedule(50) == 1.0
+
+
+def test_training_driver_improves_bound_snelson_like():
+    """Alternating NG + Adam (Section 3.1) on the 1-D workload: the bound rises.
+    (Trajectory parity is otherwise unpinned: the paper prints no values.)"""
+    prob = S.snelson_like()
+    X, y = prob.batch(0)
+    p0 = dict(Z=prob.Z0, ell=np.array([1.0]), sf2=1.0, noise=1.0, m=np.zeros(prob.M),
+              s=np.full(prob.M, 1e-4), L=1e-3 * np.eye(prob.M))
+    out, trace = O.train(p0, lambda t: (X, y), prob.N, steps=200, lr=5e-3, train_Z=False)
+    assert np.all(np.isfinite(trace))
+    assert trace[-1] > trace[0] + 50.0
