@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Benchmark: R-SVGP training steps/s at M=2048, B=4096, D=16, N=1e6.
+
+One step = one natural-gradient update of L (Prop. 1, gamma = 1, t* = 1),
+then the bound of Eq. (7), its hand-written backward (T fixed) and one Adam
+step on all of {Z, ell, sf2, noise, m~, s~} -- the alternating optimisation of
+Section 3.1 -- on a fresh minibatch resident in HBM, captured as a CUDA graph.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the same workload instead (the reference arm of this build).
+Multi-GPU runs (torchrun) are independent replicas, one per GPU (the step is
+not sharded), so the scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "train steps/s at M=2048,B=4096: BF16-TC vs FP32 plain, bound rel err ≤1e-3"
+WORKLOAD = "gp_sample_regression"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP32-plain comparison line")
+    ap.add_argument("--no-validate", action="store_true", help="skip the oracle bound check")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# CPU (oracle) leg
+# ---------------------------------------------------------------------------
+def _blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+
+        n = [d.get("num_threads", 0) for d in threadpool_info() if d.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def oracle_steps(max_seconds, max_steps):
+    """Time full oracle training steps (NG + bound + gradient + Adam)."""
+    import svgp_synth as S
+    from oracle import rsvgp as O
+
+    prob = S.gp_sample_regression()
+    M, D = prob.M, prob.D
+    p = dict(Z=prob.Z0.copy(), ell=np.ones(D), sf2=1.0, noise=1.0, m=np.zeros(M),
+             s=np.full(M, 1e-4), L=1e-3 * np.eye(M))
+    raw = {k: (O.softplus_inv(p[k]) if k in ("ell", "sf2", "noise", "s") else np.array(p[k], float))
+           for k in ("Z", "ell", "sf2", "noise", "m", "s")}
+    L = p["L"]
+    state = {}
+    times = []
+    t_start = time.perf_counter()
+    for step in range(max_steps):
+        X, y = prob.batch(step)
+        t0 = time.perf_counter()
+        c = O.constrain(raw)
+        Kt = O.se_ard(c["Z"], c["Z"], c["ell"], c["sf2"]) + np.diag(c["s"])
+        L, _ = O.ng_step(L, Kt, 1.0)
+        c["L"] = L
+        g = O.grads(c, X, y, prob.N)
+        O.bound(c, X, y, prob.N)
+        raw = O.adam_update(raw, g, state, 5e-3)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > max_seconds:
+            break
+    return times
+
+
+def cpu_baseline(seconds):
+    times = oracle_steps(seconds, 1000)
+    per = statistics.mean(times)
+    return {"value": 1.0 / per, "unit": "steps/s", "cores": _blas_threads(), "kind": "oracle",
+            "sample": f"{len(times)} full FP64 NumPy oracle training steps (NG + bound + gradient + Adam) "
+                      f"at M=2048, B=4096, D=16 on the host cores ({per:.2f} s/step)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    budget = 150.0
+    times = oracle_steps(budget, args.warmup + args.steps)
+    timed = times[min(args.warmup, max(len(times) - 1, 0)):]
+    per = statistics.mean(timed)
+    value = 1.0 / per
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
+        "steps": len(timed), "warmup": min(args.warmup, len(times) - len(timed)), "ms_per_step": per * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (GP sample via random Fourier features, seed 2)",
+        "config": {"workload": "gp_sample_regression M=2048 B=4096 D=16 N=1e6", "M": 2048, "B": 4096, "D": 16,
+                   "N": 1e6, "l2": "oracle on host"},
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": _blas_threads(), "kind": "oracle",
+                         "sample": f"{len(timed)} of the requested {args.steps} oracle steps (bounded to "
+                                   f"{budget:.0f} s of CPU work)"},
+        "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for ln in open(self.path):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def algorithmic_flops(M, B):
+    """Algorithmic FLOPs of one launch of each contraction kind."""
+    M3 = float(M) ** 3
+    return {"vt": M3, "sym": M3 / 3, "lupd": M3 / 3, "ls": M3, "out": M3 / 3,
+            "psi": float(M) * (M + 1) * B, "w": 2.0 * M * M * B}
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    from paper_2604_00697_gb300 import _lib
+    from paper_2604_00697_gb300.model import RSVGP
+    import svgp_synth as S
+
+    prob = S.gp_sample_regression()
+    M, D, B, N = prob.M, prob.D, prob.B, prob.N
+    prec = args.prec
+    if prec == "bf16" and not _lib.svgp_has_tensor_cores():
+        raise SystemExit("tensor-core path unavailable on this device")
+
+    def new_model(pr):
+        m = RSVGP(M, D, B, prec=pr)
+        m.set_state(prob.Z0, np.ones(D), 1.0, 1.0, np.zeros(M), np.full(M, 1e-4), 1e-3 * np.eye(M))
+        return m
+
+    pool = 8
+    batches = [prob.batch(1000 * rank + k) for k in range(pool)]
+    Xd = [torch.tensor(b[0], dtype=torch.float32, device="cuda") for b in batches]
+    yd = [torch.tensor(b[1], dtype=torch.float32, device="cuda") for b in batches]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
+
+    def time_model(pr, steps, warmup, profile=False):
+        m = new_model(pr)
+        # bring L near chol(K~^-1) first (untimed): NG updates with gamma = 1
+        m.ng_update(max_iters=40, gammas=[1.0] * 40)
+        torch.cuda.synchronize()
+        n0 = _lib.svgp_launch_count(m.h)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        graphs = []
+        with torch.cuda.stream(s):
+            m.train_step(Xd[0], yd[0], N)          # eager warm-up outside capture
+            torch.cuda.synchronize()
+            for k in range(pool):
+                if profile and k == 0:
+                    _lib.svgp_profile_enable(m.h, True)
+                c0 = _lib.svgp_launch_count(m.h)
+                graphs.append(m.capture(Xd[k], yd[k], N))
+                launches = _lib.svgp_launch_count(m.h) - c0
+                if profile and k == 0:
+                    _lib.svgp_profile_enable(m.h, False)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        for i in range(warmup):
+            graphs[i % pool].replay()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        prof = {}
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clk = Clocks(local)
+        clk.start()
+        t0 = time.perf_counter()
+        for i in range(steps):
+            flush.fill_(float(i))                     # evict L2 between timed steps
+            ev[i][0].record(st)
+            graphs[i % pool].replay()
+            ev[i][1].record(st)
+            if profile and i % pool == 0:
+                torch.cuda.synchronize()
+                for k, (ms, cnt) in _lib.svgp_profile_read(m.h).items():
+                    a = prof.setdefault(k, [0.0, 0])
+                    a[0] += ms
+                    a[1] += cnt
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        clocks = clk.stop()
+        dev_ms = [a.elapsed_time(b) for a, b in ev]
+        return m, dev_ms, wall, clocks, prof, launches
+
+    m, dev_ms, wall, clocks, prof, launches = time_model(prec, args.steps, args.warmup, profile=True)
+    tot_ms = sum(dev_ms)
+    if ws > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([tot_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t[0])
+    value = ws * args.steps / (tot_ms / 1e3)
+    ms_per_step = tot_ms / args.steps
+
+    # end to end through the public API with host buffers: H2D of the batch
+    # from pinned memory, the step (eager calls), D2H of the bound.
+    hX = [torch.tensor(b[0], dtype=torch.float32).pin_memory() for b in batches]
+    hy = [torch.tensor(b[1], dtype=torch.float32).pin_memory() for b in batches]
+    hout = torch.empty(1, dtype=torch.float64).pin_memory()
+    Xin = torch.empty(B, D, device="cuda")
+    yin = torch.empty(B, device="cuda")
+    for i in range(3):
+        m.train_step(Xin, yin, N)
+    torch.cuda.synchronize()
+    e2e_steps = max(5, args.steps // 2)
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        Xin.copy_(hX[i % pool], non_blocking=True)
+        yin.copy_(hy[i % pool], non_blocking=True)
+        terms = m.train_step(Xin, yin, N)
+        hout.copy_(terms[:1], non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_wall = time.perf_counter() - t0
+    e2e = {"value": ws * e2e_steps / e2e_wall, "unit": "steps/s",
+           "h2d_bytes_per_step": int(B * D * 4 + B * 4), "d2h_bytes_per_step": 8,
+           "path": "eager svgp_ng_update_T + svgp_backward + svgp_adam_step via the ctypes binding"}
+
+    ok_status = m.sync_status()
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16" if prec == "bf16" else "f32",
+        "data": "synthetic (GP sample via random Fourier features, D=16, seed 2)",
+        "config": {"workload": "gp_sample_regression M=2048 B=4096 D=16 N=1e6", "M": M, "B": B, "D": D, "N": N,
+                   "t_star": 1, "gamma": 1.0, "precision": prec, "graph": True,
+                   "l2": "flushed between timed steps (256 MB write outside the step events)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "wall_s_timed": wall, "gpu_launches": launches * args.steps, "launches_per_step": launches,
+        "clocks": clocks, "device_status": ok_status,
+    }
+    # roofline of the dominant contraction kind (events inside the graph)
+    if prof:
+        flops = algorithmic_flops(M, B)
+        tot = {k: v[0] for k, v in prof.items() if v[1] > 0}
+        dom = max(tot, key=tot.get)
+        n_l = prof[dom][1]
+        avg_ms = prof[dom][0] / n_l
+        achieved = flops[dom] / (avg_ms * 1e-3) / 1e12
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+        if prec == "bf16":
+            peak = peaks["bf16_tflops_sustained"] if peaks else 1700.0
+            src = "measured sustained" if peaks else "fallback"
+            bound = "tensor"
+        else:
+            # FP32 SIMT: 152 SMs x 128 FMA lanes x 2 flops x max clock
+            peak = 152 * 128 * 2 * (peaks["sm_max_mhz"] if peaks else 2070.0) * 1e6 / 1e12
+            src = "derived FP32 FMA peak"
+            bound = "alu"
+        step_share = {k: round(v / max(sum(tot.values()), 1e-9), 3) for k, v in tot.items()}
+        line["roofline"] = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
+                            "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": src,
+                            "traffic": None, "avg_launch_ms": avg_ms,
+                            "algorithmic_flops_per_launch": flops[dom], "contraction_share": step_share,
+                            "contraction_ms_per_step": sum(tot.values()) / max(1, args.steps)}
+    if not args.no_compare and prec == "bf16" and rank == 0:
+        m.close()
+        m2, dev2, _, _, _, _ = time_model("fp32", max(3, args.steps // 10), 2)
+        line["fp32_plain"] = {"value": len(dev2) / (sum(dev2) / 1e3), "unit": "steps/s",
+                              "ms_per_step": sum(dev2) / len(dev2),
+                              "note": "same algorithm, FP32 SIMT FMA contractions, same GPU"}
+        line["speedup_vs_fp32_plain"] = value / ws / line["fp32_plain"]["value"]
+        m2.close()
+        m = None
+    if not args.no_validate and rank == 0 and ws == 1:
+        line["validity"] = validate(prec, prob)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+
+
+def validate(prec, prob):
+    """Bound relative error vs the FP64 oracle at identical inputs (two states)."""
+    import torch
+
+    from oracle import rsvgp as O
+    from paper_2604_00697_gb300.model import RSVGP
+
+    M, D = prob.M, prob.D
+    X, y = prob.batch(0)
+    f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    X, y = f32(X), f32(y)
+    out = {}
+    p = dict(Z=f32(prob.Z0), ell=np.ones(D), sf2=1.0, noise=1.0, m=np.zeros(M), s=f32(np.full(M, 1e-4)),
+             L=f32(1e-3 * np.eye(M)))
+    m = RSVGP(M, D, prob.B, prec=prec)
+    for name in ("init", "ng40"):
+        m.set_state(p["Z"], p["ell"], p["sf2"], p["noise"], p["m"], p["s"], p["L"])
+        if name == "ng40":
+            m.ng_update(max_iters=40, gammas=[1.0] * 40)
+            p["L"] = m.L.double().cpu().numpy()
+            m.set_state(p["Z"], p["ell"], p["sf2"], p["noise"], p["m"], p["s"], p["L"])
+        F = float(m.bound(torch.tensor(X, dtype=torch.float32, device="cuda"),
+                          torch.tensor(y, dtype=torch.float32, device="cuda"), prob.N)[0])
+        ref = O.bound(p, X, y, prob.N)["F"]
+        out[name] = abs(F - ref) / abs(ref)
+    m.close()
+    out["tolerance"] = 1e-3 if prec == "bf16" else 1e-6
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * svgp.h -- C-ABI of the GB300 inverse-free SVGP (R-SVGP) training-step library.
+ *
+ * The library evaluates, on one GPU, the preconditioned inverse-free SVGP
+ * bound of Cortinovis et al. (arXiv 2604.00697), Eq. (7), its gradients with
+ * the auxiliary matrix T held fixed, and the matmul-only natural-gradient
+ * (NG) update of T = L L^T of Prop. 1 / Eq. (6).  The problem statement it
+ * follows is Section 2 (Eq. (1): SVGP ELBO over a minibatch X, y with
+ * inducing inputs Z, SE-ARD hyperparameters, likelihood parameters) and
+ * Section 3 (preconditioned mean m~, diagonal S~ = diag(s~), T = L L^T).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  * Every tensor argument is a DEVICE pointer to float32 (or float64 / int32
+ *    where stated) owned by the caller; the library never frees it.  Row-major
+ *    layouts: Z is M x D, X is B x D, L is M x M (ld = M), lower-triangular;
+ *    entries above the diagonal must be zero.
+ *  * Scalars that change during training (sf2, noise, gamma, Adam's
+ *    hyperparameters) are also device pointers, so a sequence of calls can be
+ *    captured once in a CUDA graph and replayed.
+ *  * Values are CONSTRAINED values (lengthscales, variances, s~ > 0);
+ *    gradients are dF/d(constrained value) of the bound F to be MAXIMISED.
+ *  * All calls are asynchronous on the handle's stream.  The returned status
+ *    covers argument validation and launch errors only.  Errors found on the
+ *    device (non-finite bound, a bounded wait that timed out) are recorded in
+ *    a device error word, read and cleared by svgp_sync_status().
+ *  * The handle owns its workspace (allocated once in svgp_create for M and
+ *    B_max) and is not thread-safe; use one handle per host thread/stream.
+ */
+#ifndef SVGP_H_
+#define SVGP_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct svgp_handle svgp_handle;
+
+typedef enum {
+  SVGP_OK = 0,
+  SVGP_ERR_INVALID_ARG = 1,   /* bad size, null pointer, unsupported option     */
+  SVGP_ERR_CUDA = 2,          /* a CUDA runtime/driver call failed              */
+  SVGP_ERR_OOM = 3,           /* workspace allocation failed                    */
+  SVGP_ERR_NONFINITE = 4,     /* device: bound or a reduction is NaN/Inf        */
+  SVGP_ERR_NOT_CONVERGED = 5, /* reserved: the NG loop reports via iters/resid. */
+  SVGP_ERR_TIMEOUT = 6,       /* device: a bounded pipeline wait gave up        */
+  SVGP_ERR_UNSUPPORTED = 7    /* option not built for this device / precision   */
+} svgp_status;
+
+typedef enum { SVGP_LIK_GAUSSIAN = 0, SVGP_LIK_BERNOULLI_PROBIT = 1 } svgp_lik;
+
+/* Arithmetic of the dense contractions.  SVGP_FP32: FP32 SIMT FMA kernels
+ * (no TF32).  SVGP_BF16: tcgen05 tensor-core kernels, BF16 operands with FP32
+ * accumulation in TMEM.  Scalar reductions are FP64 in both. */
+typedef enum { SVGP_FP32 = 0, SVGP_BF16 = 1 } svgp_prec;
+
+typedef struct {
+  int M;              /* number of inducing points, 1 <= M <= 8192              */
+  int D;              /* input dimension, 1 <= D <= 32                          */
+  int B_max;          /* largest minibatch / prediction block, >= 1             */
+  int lik;            /* svgp_lik; only SVGP_LIK_GAUSSIAN is built              */
+  int prec;           /* svgp_prec                                              */
+  void* cuda_stream;  /* cudaStream_t to run on; NULL = legacy default stream   */
+} svgp_config;
+
+/* Model state.  ell: D lengthscales; sf2: signal variance (1 float); noise:
+ * Gaussian observation variance (1 float); m: preconditioned variational
+ * mean m~ (M); s: diagonal of S~ (M, all > 0); L: factor of T (M x M). */
+typedef struct {
+  const float* Z;
+  const float* ell;
+  const float* sf2;
+  const float* noise;
+  const float* m;
+  const float* s;
+  const float* L;
+} svgp_params;
+
+/* Minibatch: X (B x D), y (B).  N is the dataset size; the data term is
+ * scaled by N / B (stochastic SVGP).  1 <= B <= B_max. */
+typedef struct {
+  const float* X;
+  const float* y;
+  int B;
+  double N;
+} svgp_batch;
+
+/* Gradient outputs (device, float32, same shapes as svgp_params fields). */
+typedef struct {
+  float* dZ;
+  float* dell;
+  float* dsf2;
+  float* dnoise;
+  float* dm;
+  float* ds;
+} svgp_grads;
+
+/* Layout of the float64 term vector written by svgp_bound / svgp_backward. */
+enum {
+  SVGP_T_F = 0,        /* the bound F = E - KL                                 */
+  SVGP_T_E = 1,        /* (N/B) * sum_n E_q[log p(y_n | f_n)]                  */
+  SVGP_T_KL = 2,       /* KL upper bound of Eq. (7)                            */
+  SVGP_T_TRKT = 3,     /* tr(K~ T) = tr(L^T K~ L)                              */
+  SVGP_T_TRPKUU = 4,   /* tr(P Kuu)                                            */
+  SVGP_T_QUAD = 5,     /* m~^T P Kuu P m~                                      */
+  SVGP_T_LOGDETT = 6,  /* log|T| = 2 sum_i log|L_ii|                           */
+  SVGP_T_SQERR = 7,    /* sum_n (y_n - mu_n)^2                                 */
+  SVGP_T_SUMVAR = 8,   /* sum_n sigma_n^2                                      */
+  SVGP_T_LOGDETS = 9,  /* sum_i log s~_i                                       */
+  SVGP_NTERMS = 10
+};
+
+/* Create a handle and its workspace.  On success *out owns device memory of
+ * about 10 M^2 floats + O(B_max M / 64); destroy with svgp_destroy. */
+svgp_status svgp_create(const svgp_config* cfg, svgp_handle** out);
+void svgp_destroy(svgp_handle* h);
+
+/* Change the stream later calls are issued on (e.g. a graph-capture stream). */
+svgp_status svgp_set_stream(svgp_handle* h, void* cuda_stream);
+
+/* Bound, Eq. (7) (preconditioned R-SVGP), Gaussian likelihood.
+ *   mu_n = k_nu P m~, sigma_n^2 = k_nn - k_nu P k_un, P = 2T - T K~ T,
+ *   KL <= 1/2(-tr(P Kuu) + tr(K~T) - M + m~^T P Kuu P m~ - log|T| - log|S~|).
+ * terms_dev: device float64[SVGP_NTERMS] (layout above). */
+svgp_status svgp_bound(svgp_handle* h, const svgp_params* p, const svgp_batch* b,
+                       double* terms_dev);
+
+/* Bound (as svgp_bound) plus its gradient w.r.t. Z, ell, sf2, noise, m~, s~
+ * with T held fixed (Section 3.1: T is optimised separately by NG; Prop. 2
+ * concerns exactly this gradient).  terms_dev may be NULL. */
+svgp_status svgp_backward(svgp_handle* h, const svgp_params* p, const svgp_batch* b,
+                          double* terms_dev, const svgp_grads* g);
+
+/* Natural-gradient update of L, Prop. 1 / Eq. (6), with K~ = Kuu(Z, ell, sf2)
+ * + diag(s~) taken from p (p->L is ignored; L_inout is read and updated in
+ * place).  For t = 0 .. max_iters-1:
+ *   A = L^T K~ L;  r_t = ||A - I||_F / sqrt(M)                 (Eq. (8))
+ *   if eps > 0 and r_t < eps: stop without updating            (Section 3.3)
+ *   L <- L - gamma_dev[t] * L [tril(A) - 1/2 (I + diag A)]     (Prop. 1)
+ * gamma_dev: device float[max_iters].  iters_dev (device int, may be NULL)
+ * receives the number of updates applied; residual_dev (device double, may be
+ * NULL) the last residual computed (that of L before the last update when no
+ * early stop happened).  Non-convergence is not an error: it shows as
+ * iters == max_iters with residual >= eps. */
+svgp_status svgp_ng_update_T(svgp_handle* h, const svgp_params* p, float* L_inout,
+                             const float* gamma_dev, int max_iters, double eps,
+                             int* iters_dev, double* residual_dev);
+
+/* Predictive moments at Ns test inputs Xs (Ns x D), same form as Eq. (7):
+ * mean = K*u P m~, var = sf2 - diag(K*u P Ku*) (+ noise if include_noise).
+ * 1 <= Ns <= B_max. mean, var: device float[Ns]. */
+svgp_status svgp_predict(svgp_handle* h, const svgp_params* p, const float* Xs, int Ns,
+                         float* mean, float* var, int include_noise);
+
+/* One Adam ascent step on the flat unconstrained parameter vector
+ * raw = [Z (M*D) | ell (D) | sf2 | noise | m~ (M) | s~ (M)].  Positive blocks
+ * (ell, sf2, noise, s~) are softplus-transformed; grad is the flat gradient
+ * w.r.t. constrained values in the same layout (svgp_grads may point into
+ * it).  Writes the updated raw vector and its constrained image (which
+ * svgp_params may point into).  hyper_dev: device float[10] =
+ * {lr, beta1, beta2, eps, lr multiplier for Z, ell, sf2, noise, m~, s~};
+ * beta1 applies to all blocks except Z, which uses hyper_dev[1] unless
+ * zbeta1_dev (device float, may be NULL) is given.  step_dev: device int
+ * incremented by the call (bias-correction counter).  m1, m2: moment vectors
+ * (device, same length, zero-initialised by the caller). */
+svgp_status svgp_adam_step(svgp_handle* h, float* raw, float* constrained, const float* grad,
+                           float* m1, float* m2, int* step_dev, const float* hyper_dev,
+                           const float* zbeta1_dev);
+
+/* Number of floats in the flat parameter vector for this handle. */
+int svgp_param_count(const svgp_handle* h);
+
+/* Synchronise the handle's stream, read and clear the device error word.
+ * Returns SVGP_OK, SVGP_ERR_NONFINITE, SVGP_ERR_TIMEOUT or SVGP_ERR_CUDA. */
+svgp_status svgp_sync_status(svgp_handle* h);
+
+/* Human-readable text of the last host-side error on this handle. */
+const char* svgp_last_error(const svgp_handle* h);
+const char* svgp_status_string(int status);
+
+/* 1 if this build has tensor-core (tcgen05) kernels for the current device. */
+int svgp_has_tensor_cores(void);
+
+/* Instrumentation.  Kinds of dense-contraction launches that can be timed. */
+enum {
+  SVGP_PROF_VT = 0,     /* L^T S        (S = K~ or G_P), full output           */
+  SVGP_PROF_SYM = 1,    /* (L^T S) L    symmetric output                       */
+  SVGP_PROF_LUPD = 2,   /* L Phi        NG update of L                          */
+  SVGP_PROF_LS = 3,     /* L S          full output                             */
+  SVGP_PROF_OUT = 4,    /* (L S) L^T    symmetric output (P, G_K~)              */
+  SVGP_PROF_PSI = 5,    /* Kuf Kuf^T    Kuf generated on chip                   */
+  SVGP_PROF_W = 6,      /* P Kuf        Kuf generated on chip, fused backward   */
+  SVGP_PROF_NKINDS = 7
+};
+
+/* enable != 0: from now on every launch of the kinds above is bracketed by
+ * two CUDA events recorded on the handle's stream (inside a stream capture
+ * they become event nodes of the graph).  Clears the list of records.
+ * enable == 0 stops recording.  Up to 512 launches are recorded. */
+svgp_status svgp_profile_enable(svgp_handle* h, int enable);
+
+/* After the recorded work has completed (synchronise first): total device
+ * milliseconds and launch count per kind over the current record list (for a
+ * replayed graph: of its latest replay).  ms, counts: host arrays of
+ * SVGP_PROF_NKINDS entries. */
+svgp_status svgp_profile_read(svgp_handle* h, float* ms, int* counts);
+
+/* Number of kernel launches the library has issued in this process (all
+ * handles; launches captured into a graph are counted once, at capture). */
+long long svgp_launch_count(const svgp_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SVGP_H_ */

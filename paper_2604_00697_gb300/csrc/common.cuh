@@ -1,0 +1,273 @@
+// Internal definitions shared by the kernels of the R-SVGP library.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "svgp.h"
+
+#define SVGP_MAXD 32
+
+typedef __nv_bfloat16 bf16;
+
+// Device error word bits (read by svgp_sync_status).
+enum { ERRBIT_NONFINITE = 1, ERRBIT_TIMEOUT = 2 };
+
+// Indices of the FP64 reduction slots in the workspace.
+enum {
+  RED_NG_RESID = 0,   // sum (A - I)^2 of the current NG iterate
+  RED_TRA1 = 1,       // tr(A1), A1 = L^T K~ L
+  RED_FROA1 = 2,      // ||A1||_F^2
+  RED_SPDIAG = 3,     // sum_i s_i P_ii
+  RED_PPSI = 4,       // <P, Psi>
+  RED_QUAD = 5,       // v^T Kuu v
+  RED_LOGDETL = 6,    // sum_i log|L_ii|
+  RED_SQERR = 7,      // sum_n (y_n - mu_n)^2
+  RED_LOGS = 8,       // sum_i log s_i
+  RED_SUMA_F = 9,     // sum (G_Kuf o Kuf)
+  RED_SUMA_U = 10,    // sum (G_Kuu o Kuu)
+  RED_COUNT = 16
+};
+
+// One output tile of a GEMM: rows [m0, m0+BM), cols [n0, n0+BN), and the
+// K range [k0, k1) that can hold non-zero products (triangular operands).
+struct Tile {
+  int m0, n0, k0, k1;
+};
+
+enum Region { REG_FULL = 0, REG_UPPER = 1, REG_LOWER = 2 };
+
+template <class T> __device__ __forceinline__ T to_out(float x);
+template <> __device__ __forceinline__ float to_out<float>(float x) { return x; }
+template <> __device__ __forceinline__ bf16 to_out<bf16>(float x) { return __float2bfloat16_rn(x); }
+
+__device__ __forceinline__ void store_row(float* dst, const float* v, int n) {
+#pragma unroll 4
+  for (int q = 0; q < n; ++q) dst[q] = v[q];
+}
+
+// Reduce a per-thread double over the block and add it to *dst (one atomic
+// per block).  Must be called by all threads of the block.
+__device__ __forceinline__ void block_add_double(double x, double* dst) {
+  __shared__ double red_buf[32];
+  unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  __syncthreads();
+  if (lane == 0) red_buf[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned nw = (blockDim.x + 31) >> 5;
+    double y = lane < nw ? red_buf[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+    if (lane == 0 && y != 0.0) atomicAdd(dst, y);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// GEMM epilogues.  A GEMM mainloop computes acc = sum_k A[i,k] B[j,k] for its
+// tile and hands each thread's accumulators to the epilogue one row segment
+// at a time: row(i, j0, v, n) with v[q] = acc(i, j0 + q).  Region predicates
+// (upper/lower) are applied here, per element, so every element of a
+// symmetric result is produced by exactly one tile.  Per-thread FP64 partial
+// sums are reduced by the kernel through reduce().
+// ---------------------------------------------------------------------------
+
+// Vt = L^T K~ = L^T Kuu + L^T diag(s): the diagonal of S~ is added in FP32 so
+// that it is not lost when Kuu is rounded (Section 2: S~ lower-bounds the
+// eigenvalues of K~).  Lt[i,j] = L[j,i].
+template <class OutT>
+struct EpiVt {
+  OutT* out; int ld;
+  const float* Lf; const float* s; int M;
+  const int* skip_flag;
+  __device__ bool skip() const { return skip_flag && *skip_flag; }
+  __device__ void begin_tile(int, int) {}
+  __device__ __forceinline__ void row(int i, int j0, const float* v, int n) {
+#pragma unroll 4
+    for (int q = 0; q < n; ++q) {
+      int j = j0 + q;
+      float a = v[q];
+      if (s && i < M && j < M) a = fmaf(Lf[(size_t)j * ld + i], s[j], a);
+      out[(size_t)i * ld + j] = to_out<OutT>(a);
+    }
+  }
+  __device__ void reduce() {}
+};
+
+// Symmetric result computed on the upper region (i <= j), mirrored.
+//  MODE 0 (NG):  writes Phi^T = triu(A) - 1/2 (I + diag A) (Prop. 1), zero
+//                lower part; reduces sum (A - I)^2 (Eq. (8)).
+//  MODE 1 (FWD): writes 2I - A1; reduces tr(A1), ||A1||_F^2.
+//  MODE 2 (BWD): writes A + I/2 (for T G T + T/2).
+template <class OutT, int MODE>
+struct EpiSym {
+  OutT* out; int ld; int M;
+  double* red;
+  const int* skip_flag;
+  bool offdiag;
+  double p0, p1;
+  __device__ bool skip() const { return skip_flag && *skip_flag; }
+  __device__ void begin_tile(int m0, int n0) { p0 = 0.0; p1 = 0.0; offdiag = (m0 != n0); }
+  __device__ __forceinline__ void row(int i, int j0, const float* v, int n) {
+#pragma unroll 4
+    for (int q = 0; q < n; ++q) {
+      int j = j0 + q;
+      if (i > j) continue;
+      float a = v[q];
+      bool in = (i < M) && (j < M);
+      double w = (i == j) ? 1.0 : 2.0;
+      if (MODE == 0) {
+        float val = (i < j) ? a : 0.5f * (a - 1.0f);
+        out[(size_t)i * ld + j] = to_out<OutT>(val);
+        if (i < j) out[(size_t)j * ld + i] = to_out<OutT>(0.0f);
+        if (in) { double e = (double)a - (i == j ? 1.0 : 0.0); p0 += w * e * e; }
+      } else if (MODE == 1) {
+        float val = (i == j ? 2.0f : 0.0f) - a;
+        out[(size_t)i * ld + j] = to_out<OutT>(val);
+        if (i < j) out[(size_t)j * ld + i] = to_out<OutT>(val);
+        if (in) { if (i == j) p0 += a; p1 += w * (double)a * a; }
+      } else {
+        float val = a + (i == j ? 0.5f : 0.0f);
+        out[(size_t)i * ld + j] = to_out<OutT>(val);
+        if (i < j) out[(size_t)j * ld + i] = to_out<OutT>(val);
+      }
+    }
+  }
+  __device__ void reduce() {
+    if (MODE == 0) block_add_double(p0, red + RED_NG_RESID);
+    if (MODE == 1) { block_add_double(p0, red + RED_TRA1); block_add_double(p1, red + RED_FROA1); }
+  }
+};
+
+// NG update of L (Prop. 1): acc = (L Phi)_ij on the lower region;
+// L_ij <- L_ij - gamma * acc.  The whole launch is skipped when the Frobenius
+// stopping rule (Eq. (8), Section 3.3) fired: r = sqrt(sum/M) < eps.
+struct EpiLupd {
+  float* Lf; int ld; float* Lout; int M;
+  const float* gamma; const int* done;
+  __device__ bool skip() const { return *done != 0; }
+  __device__ void begin_tile(int, int) {}
+  __device__ __forceinline__ void row(int i, int j0, const float* v, int n) {
+    float g = *gamma;
+#pragma unroll 4
+    for (int q = 0; q < n; ++q) {
+      int j = j0 + q;
+      if (j > i) continue;
+      size_t o = (size_t)i * ld + j;
+      float Ln = Lf[o] - g * v[q];
+      Lf[o] = Ln;
+      if (i < M && j < M) Lout[(size_t)i * M + j] = Ln;
+    }
+  }
+  __device__ void reduce() {}
+};
+
+// Plain store of a full result.
+template <class OutT>
+struct EpiStore {
+  OutT* out; int ld;
+  const int* skip_flag;
+  __device__ bool skip() const { return skip_flag && *skip_flag; }
+  __device__ void begin_tile(int, int) {}
+  __device__ __forceinline__ void row(int i, int j0, const float* v, int n) {
+#pragma unroll 4
+    for (int q = 0; q < n; ++q) out[(size_t)i * ld + j0 + q] = to_out<OutT>(v[q]);
+  }
+  __device__ void reduce() {}
+};
+
+// P = Y L^T = L (2I - A1) L^T on the lower region, mirrored; FP32 and
+// low-precision copies; reduces sum_i s_i P_ii and <P, Psi> (Psi may be null).
+template <class OutT>
+struct EpiP {
+  float* Pf; OutT* Plo; int ld; int M;
+  const float* s; const float* Psi; double* red;
+  double p0, p1;
+  __device__ bool skip() const { return false; }
+  __device__ void begin_tile(int, int) { p0 = 0.0; p1 = 0.0; }
+  __device__ __forceinline__ void row(int i, int j0, const float* v, int n) {
+#pragma unroll 4
+    for (int q = 0; q < n; ++q) {
+      int j = j0 + q;
+      if (j > i) continue;
+      float a = v[q];
+      Pf[(size_t)i * ld + j] = a;
+      Plo[(size_t)i * ld + j] = to_out<OutT>(a);
+      if (i != j) { Pf[(size_t)j * ld + i] = a; Plo[(size_t)j * ld + i] = to_out<OutT>(a); }
+      if (i < M && j < M) {
+        if (i == j) p0 += (double)s[i] * a;
+        if (Psi) p1 += (i == j ? 1.0 : 2.0) * (double)a * Psi[(size_t)i * ld + j];
+      }
+    }
+  }
+  __device__ void reduce() {
+    block_add_double(p0, red + RED_SPDIAG);
+    if (Psi) block_add_double(p1, red + RED_PPSI);
+  }
+};
+
+// G_K~ = -L (L^T G_P L + I/2) L^T on the lower region (acc = L S L^T part);
+// writes G_Kuu = G_K~ + P/2 - v v^T/2 (mirrored) and ds_i = G_K~_ii + 1/(2 s_i).
+struct EpiGK {
+  float* GKuu; int ld; int M;
+  const float* Pf; const float* v; const float* s; float* ds;
+  __device__ bool skip() const { return false; }
+  __device__ void begin_tile(int, int) {}
+  __device__ __forceinline__ void row(int i, int j0, const float* vv, int n) {
+#pragma unroll 4
+    for (int q = 0; q < n; ++q) {
+      int j = j0 + q;
+      if (j > i) continue;
+      float gk = -vv[q];
+      float vi = i < M ? v[i] : 0.f, vj = j < M ? v[j] : 0.f;
+      float gu = gk + 0.5f * Pf[(size_t)i * ld + j] - 0.5f * vi * vj;
+      GKuu[(size_t)i * ld + j] = gu;
+      if (i != j) GKuu[(size_t)j * ld + i] = gu;
+      if (i == j && i < M) ds[i] = gk + 0.5f / s[i];
+    }
+  }
+  __device__ void reduce() {}
+};
+
+// Psi = Kuf Kuf^T on the upper region, mirrored (FP32).
+struct EpiPsi {
+  float* Psi; int ld;
+  __device__ bool skip() const { return false; }
+  __device__ void begin_tile(int, int) {}
+  __device__ __forceinline__ void row(int i, int j0, const float* v, int n) {
+#pragma unroll 4
+    for (int q = 0; q < n; ++q) {
+      int j = j0 + q;
+      if (i > j) continue;
+      Psi[(size_t)i * ld + j] = v[q];
+      if (i != j) Psi[(size_t)j * ld + i] = v[q];
+    }
+  }
+  __device__ void reduce() {}
+};
+
+// Parameters of the Kuf generator: scaled coordinates z~ = z / ell (Mp x D,
+// padded rows zero) and x~ = x / ell (B x D), and log(sf2).  The SE-ARD value
+// is sf2 * exp(-1/2 ||z~_i - x~_n||^2) (per-dimension differences).
+struct KufGen {
+  const float* Zs; const float* Xs; int D; int M; int B; const float* sf2;
+};
+
+// Epilogue data for W = P Kuf (the data part of the backward pass): for each
+// element A_in = c * Kuf_in * (v_i g_n + W_in / noise)  (= G_Kuf o Kuf for the
+// Gaussian likelihood) accumulates per row i
+//   rowacc[i][d]     += A_in (x_nd - z_id)      (d < D)
+//   rowacc[i][D + d] += A_in (x_nd - z_id)^2
+//   rowacc[i][2D]    += A_in
+// and, when colsum != null, colsum[n] += sum_i Kuf_in W_in (for sigma_n^2).
+struct WEpi {
+  KufGen gen;
+  const float* Zraw;   // unscaled Z (Mp x D)
+  const float* Xraw;   // unscaled X (B x D)
+  const float* v; const float* g; const float* noise;
+  float c;
+  float* rowacc;       // M x (2D+1), may be null
+  float* colsum;       // B, may be null
+};

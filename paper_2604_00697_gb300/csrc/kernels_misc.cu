@@ -1,0 +1,507 @@
+// Elementwise, GEMV and reduction kernels of the R-SVGP step: SE-ARD blocks,
+// factor preparation, predictive means, Gaussian per-point terms, gradient
+// assembly, FP64 scalar finalisation and the fused Adam update.
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace {
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// z~ = z / ell, x~ = x / ell, padded to Dp = round_up(D, 4) columns and (for
+// Z) Mp rows, padding zero.
+__global__ void prep_coords_kernel(const float* __restrict__ Z, const float* __restrict__ X,
+                                   const float* __restrict__ ell, int M, int Mp, int B, int D,
+                                   float* __restrict__ Zs, float* __restrict__ Xs) {
+  int Dp = (D + 3) & ~3;
+  int tot = (Mp + B) * Dp;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
+    int r = e / Dp, d = e % Dp;
+    if (r < Mp) {
+      Zs[e] = (r < M && d < D) ? Z[(size_t)r * D + d] / ell[d] : 0.f;
+    } else {
+      int n = r - Mp;
+      Xs[(size_t)n * Dp + d] = (d < D) ? X[(size_t)n * D + d] / ell[d] : 0.f;
+    }
+  }
+}
+
+// Kuu = sf2 exp(-1/2 ||z~_i - z~_j||^2) (per-dimension differences), exact
+// sf2 on the diagonal, zero padding.  32x32 tiles, points staged in smem.
+template <class LoT>
+__global__ void kuu_kernel(const float* __restrict__ Zs, int M, int Mp, int D,
+                           const float* __restrict__ sf2p, float* __restrict__ Kf, LoT* __restrict__ Klo) {
+  __shared__ float zi[32][SVGP_MAXD + 1], zj[32][SVGP_MAXD + 1];
+  int Dp = (D + 3) & ~3;
+  int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  for (int e = threadIdx.y * 32 + threadIdx.x; e < 32 * Dp; e += 32 * blockDim.y) {
+    int r = e / Dp, d = e % Dp;
+    zi[r][d] = Zs[(size_t)(i0 + r) * Dp + d];
+    zj[r][d] = Zs[(size_t)(j0 + r) * Dp + d];
+  }
+  __syncthreads();
+  float sf2 = *sf2p;
+  for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
+    int i = i0 + rr, j = j0 + threadIdx.x;
+    float val = 0.f;
+    if (i < M && j < M) {
+      if (i == j) {
+        val = sf2;
+      } else {
+        float r2 = 0.f;
+        for (int d = 0; d < D; ++d) { float e = zi[rr][d] - zj[threadIdx.x][d]; r2 = fmaf(e, e, r2); }
+        val = sf2 * expf(-0.5f * r2);
+      }
+    }
+    Kf[(size_t)i * Mp + j] = val;
+    if (Klo) Klo[(size_t)i * Mp + j] = to_out<LoT>(val);
+  }
+}
+
+// L (M x M, ld M, lower) -> Lf (Mp x Mp FP32), Llo, Ltlo = Llo^T (operand
+// precision); strictly-upper entries forced to zero; sum log|L_ii|.
+template <class LoT>
+__global__ void prep_L_kernel(const float* __restrict__ Lin, int M, int Mp, float* __restrict__ Lf,
+                              LoT* __restrict__ Llo, LoT* __restrict__ Ltlo, double* red) {
+  __shared__ float tile[32][33];
+  int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  int tx = threadIdx.x;
+  double ld = 0.0;
+  for (int ty = threadIdx.y; ty < 32; ty += blockDim.y) {
+    int i = i0 + ty, j = j0 + tx;
+    float val = (i < M && j < M && j <= i) ? Lin[(size_t)i * M + j] : 0.f;
+    Lf[(size_t)i * Mp + j] = val;
+    if (Llo) Llo[(size_t)i * Mp + j] = to_out<LoT>(val);
+    tile[ty][tx] = val;
+    if (i == j && i < M) ld += log(fabs((double)val));
+  }
+  __syncthreads();
+  if (Ltlo) {
+    for (int ty = threadIdx.y; ty < 32; ty += blockDim.y) {
+      // Ltlo[j0 + ty][i0 + tx] = L[i0 + tx][j0 + ty]
+      Ltlo[(size_t)(j0 + ty) * Mp + i0 + tx] = to_out<LoT>(tile[tx][ty]);
+    }
+  }
+  if (blockIdx.x == blockIdx.y) block_add_double(ld, red + RED_LOGDETL);
+}
+
+// y = alpha * A (x + beta * x2)  (A: Mp x Mp FP32, rows < M); one warp per
+// row.  Optionally dot_out += sum_i y_i dotw_i.
+__global__ void gemv_kernel(const float* __restrict__ A, int Mp, int M, const float* __restrict__ x,
+                            float alpha, const float* __restrict__ x2, float beta, float* __restrict__ y,
+                            const float* __restrict__ dotw, double* dot_out) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  double part = 0.0;
+  if (warp < M) {
+    const float* row = A + (size_t)warp * Mp;
+    float acc = 0.f;
+    for (int j = lane * 4; j < M; j += 128) {
+      float4 a = *reinterpret_cast<const float4*>(row + j);
+      float xv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int jj = j + q;
+        float xx = jj < M ? x[jj] : 0.f;
+        if (x2 && jj < M) xx += beta * x2[jj];
+        xv[q] = xx;
+      }
+      acc = fmaf(a.x, xv[0], acc); acc = fmaf(a.y, xv[1], acc);
+      acc = fmaf(a.z, xv[2], acc); acc = fmaf(a.w, xv[3], acc);
+    }
+    acc = warp_sum(acc) * alpha;
+    if (lane == 0) {
+      y[warp] = acc;
+      if (dotw) part = (double)acc * dotw[warp];
+    }
+  }
+  if (dot_out) block_add_double(part, dot_out);
+}
+
+// mu_n += sum_{i in chunk} Kuf_in v_i.  grid (ceil(B/128), ceil(M/256)).
+__global__ void mu_kernel(const float* __restrict__ Zs, const float* __restrict__ Xs, int M, int B,
+                          int D, const float* __restrict__ sf2p, const float* __restrict__ v,
+                          float* __restrict__ mu) {
+  __shared__ float zs[256][SVGP_MAXD + 1];
+  __shared__ float vs[256];
+  int Dp = (D + 3) & ~3;
+  int i0 = blockIdx.y * 256;
+  int ni = min(256, M - i0);
+  for (int e = threadIdx.x; e < 256 * Dp; e += blockDim.x) {
+    int r = e / Dp, d = e % Dp;
+    zs[r][d] = r < ni ? Zs[(size_t)(i0 + r) * Dp + d] : 0.f;
+  }
+  for (int r = threadIdx.x; r < 256; r += blockDim.x) vs[r] = r < ni ? v[i0 + r] : 0.f;
+  __syncthreads();
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= B) return;
+  float x[SVGP_MAXD];
+#pragma unroll
+  for (int d = 0; d < SVGP_MAXD; ++d) x[d] = d < Dp ? Xs[(size_t)n * Dp + d] : 0.f;
+  float lsf2 = logf(*sf2p);
+  float acc = 0.f;
+  for (int r = 0; r < ni; ++r) {
+    float r2 = 0.f;
+#pragma unroll
+    for (int d = 0; d < SVGP_MAXD; ++d)
+      if (d < Dp) { float e = zs[r][d] - x[d]; r2 = fmaf(e, e, r2); }
+    acc = fmaf(expf(lsf2 - 0.5f * r2), vs[r], acc);
+  }
+  atomicAdd(mu + n, acc);
+}
+
+__global__ void pointwise_gauss_kernel(const float* __restrict__ y, const float* __restrict__ mu,
+                                       const float* __restrict__ noise, int B, float* __restrict__ g,
+                                       double* red) {
+  double part = 0.0;
+  float inv = 1.0f / *noise;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B; n += gridDim.x * blockDim.x) {
+    float r = y[n] - mu[n];
+    if (g) g[n] = r * inv;
+    part += (double)r * r;
+  }
+  block_add_double(part, red + RED_SQERR);
+}
+
+// Kg_i += sum_{n in chunk} Kuf_in g_n.  grid (Mp/128, ceil(B/256)).
+__global__ void kg_kernel(const float* __restrict__ Zs, const float* __restrict__ Xs, int M, int B,
+                          int D, const float* __restrict__ sf2p, const float* __restrict__ g,
+                          float* __restrict__ Kg) {
+  __shared__ float xs[256][SVGP_MAXD + 1];
+  __shared__ float gs[256];
+  int Dp = (D + 3) & ~3;
+  int n0 = blockIdx.y * 256;
+  int nn = min(256, B - n0);
+  for (int e = threadIdx.x; e < 256 * Dp; e += blockDim.x) {
+    int r = e / Dp, d = e % Dp;
+    xs[r][d] = r < nn ? Xs[(size_t)(n0 + r) * Dp + d] : 0.f;
+  }
+  for (int r = threadIdx.x; r < 256; r += blockDim.x) gs[r] = r < nn ? g[n0 + r] : 0.f;
+  __syncthreads();
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  float z[SVGP_MAXD];
+#pragma unroll
+  for (int d = 0; d < SVGP_MAXD; ++d) z[d] = d < Dp ? Zs[(size_t)i * Dp + d] : 0.f;
+  float lsf2 = logf(*sf2p);
+  float acc = 0.f;
+  for (int r = 0; r < nn; ++r) {
+    float r2 = 0.f;
+#pragma unroll
+    for (int d = 0; d < SVGP_MAXD; ++d)
+      if (d < Dp) { float e = xs[r][d] - z[d]; r2 = fmaf(e, e, r2); }
+    acc = fmaf(expf(lsf2 - 0.5f * r2), gs[r], acc);
+  }
+  atomicAdd(Kg + i, acc);
+}
+
+// Symmetrised G_P = c/2 (Kg m^T + m Kg^T) + c/(2 noise) Psi + Kuu/2
+//                   - (m w^T + w m^T)/2, zero padding.
+template <class LoT>
+__global__ void gp_assemble_kernel(const float* __restrict__ Kuu, const float* __restrict__ Psi,
+                                   const float* __restrict__ Kg, const float* __restrict__ m,
+                                   const float* __restrict__ w, const float* __restrict__ noise, float c,
+                                   int M, int Mp, LoT* __restrict__ out) {
+  float cn = c * 0.5f / *noise;
+  size_t tot = (size_t)Mp * Mp;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / Mp), j = (int)(e % Mp);
+    float val = 0.f;
+    if (i < M && j < M) {
+      val = 0.5f * c * (Kg[i] * m[j] + m[i] * Kg[j]) + cn * Psi[e] + 0.5f * Kuu[e]
+            - 0.5f * (m[i] * w[j] + w[i] * m[j]);
+    }
+    out[e] = to_out<LoT>(val);
+  }
+}
+
+// Kuu side of the SE-ARD chain rule: a_ij = G_Kuu_ij Kuu_ij,
+//   rowacc_u[i][d] += sum_j a_ij (z~_jd - z~_id), rowacc_u[i][D+d] += a (.)^2,
+//   rowacc_u[i][2D] += sum_j a_ij.   grid (Mp/128, Mp/256), 128 threads.
+__global__ void kuu_bwd_kernel(const float* __restrict__ GK, const float* __restrict__ Kuu,
+                               const float* __restrict__ Zs, int M, int Mp, int D,
+                               float* __restrict__ rowacc) {
+  __shared__ float zj[256][SVGP_MAXD + 1];
+  int Dp = (D + 3) & ~3;
+  int j0 = blockIdx.y * 256;
+  for (int e = threadIdx.x; e < 256 * Dp; e += blockDim.x) {
+    int r = e / Dp, d = e % Dp;
+    zj[r][d] = (j0 + r < Mp) ? Zs[(size_t)(j0 + r) * Dp + d] : 0.f;
+  }
+  __syncthreads();
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  float z[SVGP_MAXD], aZ[SVGP_MAXD], aL[SVGP_MAXD];
+#pragma unroll
+  for (int d = 0; d < SVGP_MAXD; ++d) { z[d] = d < Dp ? Zs[(size_t)i * Dp + d] : 0.f; aZ[d] = 0.f; aL[d] = 0.f; }
+  float aS = 0.f;
+  int nj = min(256, M - j0);
+  const float* gk = GK + (size_t)i * Mp + j0;
+  const float* ku = Kuu + (size_t)i * Mp + j0;
+  for (int r = 0; r < nj; ++r) {
+    float a = gk[r] * ku[r];
+    aS += a;
+#pragma unroll
+    for (int d = 0; d < SVGP_MAXD; ++d)
+      if (d < D) { float e = zj[r][d] - z[d]; float ae = a * e; aZ[d] += ae; aL[d] = fmaf(ae, e, aL[d]); }
+  }
+  float* ra = rowacc + (size_t)i * (2 * D + 1);
+  for (int d = 0; d < D; ++d) { atomicAdd(ra + d, aZ[d]); atomicAdd(ra + D + d, aL[d]); }
+  atomicAdd(ra + 2 * D, aS);
+}
+
+__global__ void logs_kernel(const float* __restrict__ s, int M, double* red) {
+  double part = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x)
+    part += log((double)s[i]);
+  block_add_double(part, red + RED_LOGS);
+}
+
+// dZ_id = (rowacc_f[i][d] + 2 rowacc_u[i][d]) / ell_d ; FP64 sums of the
+// lengthscale and signal-variance parts.
+__global__ void grad_finalize_kernel(const float* __restrict__ rf, const float* __restrict__ ru,
+                                     const float* __restrict__ ell, int M, int D, float* __restrict__ dZ,
+                                     double* acc_ell, double* red) {
+  __shared__ double sl[SVGP_MAXD];
+  __shared__ double ssf[2];
+  if (threadIdx.x < SVGP_MAXD) sl[threadIdx.x] = 0.0;
+  if (threadIdx.x < 2) ssf[threadIdx.x] = 0.0;
+  __syncthreads();
+  int W = 2 * D + 1;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+    const float* a = rf + (size_t)i * W;
+    const float* b = ru + (size_t)i * W;
+    for (int d = 0; d < D; ++d) {
+      dZ[(size_t)i * D + d] = (a[d] + 2.0f * b[d]) / ell[d];
+      atomicAdd(&sl[d], (double)a[D + d] + (double)b[D + d]);
+    }
+    atomicAdd(&ssf[0], (double)a[2 * D]);
+    atomicAdd(&ssf[1], (double)b[2 * D]);
+  }
+  __syncthreads();
+  if (threadIdx.x < D) atomicAdd(acc_ell + threadIdx.x, sl[threadIdx.x]);
+  if (threadIdx.x == 0) { atomicAdd(red + RED_SUMA_F, ssf[0]); atomicAdd(red + RED_SUMA_U, ssf[1]); }
+}
+
+// Scalar assembly of Eq. (7) in FP64 (and the scalar gradients).
+__global__ void terms_finalize_kernel(const double* __restrict__ red, const double* __restrict__ acc_ell,
+                                      const float* __restrict__ sf2p, const float* __restrict__ noisep,
+                                      const float* __restrict__ ell, int M, int D, int B, double N,
+                                      double* terms, float* dsf2, float* dnoise, float* dell,
+                                      int* errword) {
+  if (threadIdx.x != 0) return;
+  double sf2 = *sf2p, noise = *noisep, c = N / B;
+  double trA1 = red[RED_TRA1], froA1 = red[RED_FROA1];
+  double trPKt = 2.0 * trA1 - froA1;                 // tr(P K~) = tr((2I - A1) A1)
+  double trPKuu = trPKt - red[RED_SPDIAG];            // minus tr(P diag(s))
+  double quad = red[RED_QUAD];
+  double logdetT = 2.0 * red[RED_LOGDETL];
+  double logdetS = red[RED_LOGS];
+  double sqerr = red[RED_SQERR];
+  double sumvar = (double)B * sf2 - red[RED_PPSI];    // sum_n sf2 - k_n^T P k_n
+  const double LOG2PI = 1.8378770664093453;
+  double E = c * (-0.5 * B * (LOG2PI + log(noise)) - (sqerr + sumvar) / (2.0 * noise));
+  double KL = 0.5 * (-trPKuu + trA1 - M + quad - logdetT - logdetS);
+  double F = E - KL;
+  if (terms) {
+    terms[SVGP_T_F] = F; terms[SVGP_T_E] = E; terms[SVGP_T_KL] = KL; terms[SVGP_T_TRKT] = trA1;
+    terms[SVGP_T_TRPKUU] = trPKuu; terms[SVGP_T_QUAD] = quad; terms[SVGP_T_LOGDETT] = logdetT;
+    terms[SVGP_T_SQERR] = sqerr; terms[SVGP_T_SUMVAR] = sumvar; terms[SVGP_T_LOGDETS] = logdetS;
+  }
+  if (!isfinite(F)) atomicOr(errword, ERRBIT_NONFINITE);
+  if (dsf2) {
+    double h = -0.5 / noise;
+    *dsf2 = (float)(c * B * h + (red[RED_SUMA_F] + red[RED_SUMA_U]) / sf2);
+    *dnoise = (float)(c * (-0.5 * B / noise + (sqerr + sumvar) / (2.0 * noise * noise)));
+    for (int d = 0; d < D; ++d) dell[d] = (float)(acc_ell[d] / ell[d]);
+  }
+}
+
+__global__ void predict_finalize_kernel(const float* __restrict__ colsum, const float* __restrict__ sf2,
+                                        const float* __restrict__ noise, int Ns, int inc,
+                                        float* __restrict__ var) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= Ns) return;
+  float v = *sf2 - colsum[n];
+  if (inc) v += *noise;
+  var[n] = v;
+}
+
+__device__ __forceinline__ float softplus_f(float x) { return x > 20.f ? x : log1pf(expf(x)); }
+__device__ __forceinline__ float sigmoid_f(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+// Adam ascent on the flat vector [Z | ell | sf2 | noise | m | s].
+__global__ void adam_kernel(float* __restrict__ raw, float* __restrict__ cons, const float* __restrict__ grad,
+                            float* __restrict__ m1, float* __restrict__ m2, const int* __restrict__ step,
+                            const float* __restrict__ hyper, const float* __restrict__ zbeta1, int M, int D) {
+  int n = M * D + D + 2 + 2 * M;
+  int t = *step + 1;
+  float lr = hyper[0], b1 = hyper[1], b2 = hyper[2], eps = hyper[3];
+  float b1z = zbeta1 ? *zbeta1 : b1;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    int blk;
+    if (e < M * D) blk = 0;
+    else if (e < M * D + D) blk = 1;
+    else if (e == M * D + D) blk = 2;
+    else if (e == M * D + D + 1) blk = 3;
+    else if (e < M * D + D + 2 + M) blk = 4;
+    else blk = 5;
+    bool pos = (blk == 1 || blk == 2 || blk == 3 || blk == 5);
+    float x = raw[e];
+    float g = grad[e];
+    if (pos) g *= sigmoid_f(x);
+    float bb1 = blk == 0 ? b1z : b1;
+    float mm = bb1 * m1[e] + (1.f - bb1) * g;
+    float vv = b2 * m2[e] + (1.f - b2) * g * g;
+    m1[e] = mm;
+    m2[e] = vv;
+    float mh = mm / (1.f - powf(bb1, (float)t));
+    float vh = vv / (1.f - powf(b2, (float)t));
+    x += lr * hyper[4 + blk] * mh / (sqrtf(vh) + eps);
+    raw[e] = x;
+    cons[e] = pos ? softplus_f(x) : x;
+  }
+}
+
+__global__ void step_inc_kernel(int* step) { if (threadIdx.x == 0 && blockIdx.x == 0) *step += 1; }
+
+__global__ void ng_check_kernel(const double* red, int M, double eps, int* done, int* iters,
+                                double* resid) {
+  if (threadIdx.x != 0) return;
+  if (*done) return;
+  double r = sqrt(red[RED_NG_RESID] / M);
+  if (resid) *resid = r;
+  if (eps > 0.0 && r < eps) { *done = 1; return; }
+  if (iters) *iters += 1;
+}
+
+}  // namespace
+
+void k_prep_coords(const float* Z, const float* X, const float* ell, int M, int Mp, int B, int D,
+                   float* Zs, float* Xs, cudaStream_t st) {
+  int Dp = (D + 3) & ~3;
+  int tot = (Mp + B) * Dp;
+  int grid = (tot + 255) / 256;
+  if (grid > 4096) grid = 4096;
+  svgp_note_launch();
+  prep_coords_kernel<<<grid, 256, 0, st>>>(Z, X, ell, M, Mp, B, D, Zs, Xs);
+}
+
+template <class LoT>
+void k_kuu(const float* Zs, int M, int Mp, int D, const float* sf2, float* Kf, LoT* Klo, cudaStream_t st) {
+  dim3 grid(Mp / 32, Mp / 32), blk(32, 8);
+  svgp_note_launch();
+  kuu_kernel<LoT><<<grid, blk, 0, st>>>(Zs, M, Mp, D, sf2, Kf, Klo);
+}
+template void k_kuu<float>(const float*, int, int, int, const float*, float*, float*, cudaStream_t);
+template void k_kuu<bf16>(const float*, int, int, int, const float*, float*, bf16*, cudaStream_t);
+
+template <class LoT>
+void k_prep_L(const float* Lin, int M, int Mp, float* Lf, LoT* Llo, LoT* Ltlo, double* red, cudaStream_t st) {
+  dim3 grid(Mp / 32, Mp / 32), blk(32, 8);
+  svgp_note_launch();
+  prep_L_kernel<LoT><<<grid, blk, 0, st>>>(Lin, M, Mp, Lf, Llo, Ltlo, red);
+}
+template void k_prep_L<float>(const float*, int, int, float*, float*, float*, double*, cudaStream_t);
+template void k_prep_L<bf16>(const float*, int, int, float*, bf16*, bf16*, double*, cudaStream_t);
+
+void k_gemv(const float* A, int Mp, int M, const float* x, float alpha, const float* x2, float beta,
+            float* y, const float* dotw, double* dot_out, cudaStream_t st) {
+  int warps = M, blocks = (warps * 32 + 255) / 256;
+  svgp_note_launch();
+  gemv_kernel<<<blocks, 256, 0, st>>>(A, Mp, M, x, alpha, x2, beta, y, dotw, dot_out);
+}
+
+void k_mu(const float* Zs, const float* Xs, int M, int B, int D, const float* sf2, const float* v,
+          float* mu, cudaStream_t st) {
+  cudaMemsetAsync(mu, 0, sizeof(float) * B, st);
+  dim3 grid((B + 127) / 128, (M + 255) / 256);
+  svgp_note_launch();
+  mu_kernel<<<grid, 128, 0, st>>>(Zs, Xs, M, B, D, sf2, v, mu);
+}
+
+void k_pointwise_gauss(const float* y, const float* mu, const float* noise, int B, float* g,
+                       double* red, cudaStream_t st) {
+  int grid = (B + 255) / 256;
+  if (grid > 256) grid = 256;
+  svgp_note_launch();
+  pointwise_gauss_kernel<<<grid, 256, 0, st>>>(y, mu, noise, B, g, red);
+}
+
+void k_kg(const float* Zs, const float* Xs, int M, int Mp, int B, int D, const float* sf2,
+          const float* g, float* Kg, cudaStream_t st) {
+  cudaMemsetAsync(Kg, 0, sizeof(float) * Mp, st);
+  dim3 grid(Mp / 128, (B + 255) / 256);
+  svgp_note_launch();
+  kg_kernel<<<grid, 128, 0, st>>>(Zs, Xs, M, B, D, sf2, g, Kg);
+}
+
+template <class LoT>
+void k_gp_assemble(const float* Kuu, const float* Psi, const float* Kg, const float* m, const float* w,
+                   const float* noise, float c, int M, int Mp, LoT* out, cudaStream_t st) {
+  size_t tot = (size_t)Mp * Mp;
+  int grid = (int)((tot + 255) / 256);
+  if (grid > 152 * 16) grid = 152 * 16;
+  svgp_note_launch();
+  gp_assemble_kernel<LoT><<<grid, 256, 0, st>>>(Kuu, Psi, Kg, m, w, noise, c, M, Mp, out);
+}
+template void k_gp_assemble<float>(const float*, const float*, const float*, const float*, const float*,
+                                   const float*, float, int, int, float*, cudaStream_t);
+template void k_gp_assemble<bf16>(const float*, const float*, const float*, const float*, const float*,
+                                  const float*, float, int, int, bf16*, cudaStream_t);
+
+void k_kuu_bwd(const float* GKuu, const float* Kuu, const float* Zs, int M, int Mp, int D,
+               float* rowacc_u, double* red, cudaStream_t st) {
+  (void)red;
+  dim3 grid(Mp / 128, Mp / 256 + (Mp % 256 ? 1 : 0));
+  svgp_note_launch();
+  kuu_bwd_kernel<<<grid, 128, 0, st>>>(GKuu, Kuu, Zs, M, Mp, D, rowacc_u);
+}
+
+void k_logs(const float* s, int M, double* red, cudaStream_t st) {
+  svgp_note_launch();
+  logs_kernel<<<1, 256, 0, st>>>(s, M, red);
+}
+
+void k_grad_finalize(const float* rowacc_f, const float* rowacc_u, const float* ell, int M, int D,
+                     float* dZ, double* acc_ell, double* red, cudaStream_t st) {
+  int grid = (M + 255) / 256;
+  svgp_note_launch();
+  grad_finalize_kernel<<<grid, 256, 0, st>>>(rowacc_f, rowacc_u, ell, M, D, dZ, acc_ell, red);
+}
+
+void k_terms_finalize(const double* red, const double* acc_ell, const float* sf2, const float* noise,
+                      const float* ell, int M, int D, int B, double N, double* terms, float* dsf2,
+                      float* dnoise, float* dell, int* errword, cudaStream_t st) {
+  svgp_note_launch();
+  terms_finalize_kernel<<<1, 32, 0, st>>>(red, acc_ell, sf2, noise, ell, M, D, B, N, terms, dsf2, dnoise,
+                                          dell, errword);
+}
+
+void k_predict_finalize(const float* colsum, const float* sf2, const float* noise, int Ns, int inc,
+                        float* var, cudaStream_t st) {
+  svgp_note_launch();
+  predict_finalize_kernel<<<(Ns + 255) / 256, 256, 0, st>>>(colsum, sf2, noise, Ns, inc, var);
+}
+
+void k_adam(float* raw, float* cons, const float* grad, float* m1, float* m2, int* step, const float* hyper,
+            const float* zbeta1, int M, int D, cudaStream_t st) {
+  int n = M * D + D + 2 + 2 * M;
+  int grid = (n + 255) / 256;
+  if (grid > 1024) grid = 1024;
+  svgp_note_launch();
+  adam_kernel<<<grid, 256, 0, st>>>(raw, cons, grad, m1, m2, step, hyper, zbeta1, M, D);
+  svgp_note_launch();
+  step_inc_kernel<<<1, 32, 0, st>>>(step);
+}
+
+void k_ng_check(const double* red, int M, double eps, int* done, int* iters, double* resid,
+                cudaStream_t st) {
+  svgp_note_launch();
+  ng_check_kernel<<<1, 32, 0, st>>>(red, M, eps, done, iters, resid);
+}

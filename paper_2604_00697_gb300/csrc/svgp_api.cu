@@ -1,0 +1,484 @@
+// C-ABI of the R-SVGP library: handle, workspace, tile tables and the order
+// of kernels for each entry point (see include/svgp.h for the contract).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+static unsigned long long g_launches = 0;
+void svgp_note_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
+
+namespace {
+
+enum KRule { K_M0_END, K_N0_END, K_N0_M1, K_0_M1, K_0_N1, K_ALL };
+
+std::vector<Tile> make_tiles(int Mp, int BM, int BN, int region, int rule) {
+  std::vector<Tile> v;
+  for (int m0 = 0; m0 < Mp; m0 += BM)
+    for (int n0 = 0; n0 < Mp; n0 += BN) {
+      if (region == REG_UPPER && m0 > n0 + BN - 1) continue;
+      if (region == REG_LOWER && m0 + BM - 1 < n0) continue;
+      Tile t{m0, n0, 0, Mp};
+      int m1 = std::min(m0 + BM, Mp), n1 = std::min(n0 + BN, Mp);
+      switch (rule) {
+        case K_M0_END: t.k0 = m0; t.k1 = Mp; break;
+        case K_N0_END: t.k0 = n0; t.k1 = Mp; break;
+        case K_N0_M1: t.k0 = n0; t.k1 = m1; break;
+        case K_0_M1: t.k0 = 0; t.k1 = m1; break;
+        case K_0_N1: t.k0 = 0; t.k1 = n1; break;
+        default: break;
+      }
+      if (t.k1 < t.k0) t.k1 = t.k0;
+      v.push_back(t);
+    }
+  std::stable_sort(v.begin(), v.end(), [](const Tile& a, const Tile& b) { return (a.k1 - a.k0) > (b.k1 - b.k0); });
+  return v;
+}
+
+}  // namespace
+
+struct svgp_handle {
+  svgp_config cfg;
+  int M, Mp, D, Dp, Bmax, lo_bytes;
+  bool tc;
+  cudaStream_t st;
+  char err[512];
+  // matrices
+  float *Kuu_f, *Lf, *Pf, *Psi, *GKuu;
+  void *Kuu_lo, *L_lo, *Lt_lo, *V, *S, *Y, *P_lo, *GP_lo;
+  // vectors
+  float *Zs, *Xs, *v, *w, *mu, *g, *Kg, *colsum, *rowacc_f, *rowacc_u, *dm_tmp;
+  double *red, *acc_ell, *resid_tmp;
+  int *errword, *done, *iters_tmp;
+  GemmCtx gs, gt;   // SIMT and tensor-core tile tables
+  std::vector<void*> allocs;
+  // instrumentation
+  bool prof;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> rec_kind;
+};
+
+namespace {
+
+svgp_status fail(svgp_handle* h, svgp_status s, const char* msg) {
+  if (h) snprintf(h->err, sizeof(h->err), "%s", msg);
+  return s;
+}
+
+svgp_status check_launch(svgp_handle* h, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(h->err, sizeof(h->err), "%s: %s", where, cudaGetErrorString(e));
+    return SVGP_ERR_CUDA;
+  }
+  return SVGP_OK;
+}
+
+template <class T>
+bool dalloc(svgp_handle* h, T** p, size_t bytes) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, bytes) != cudaSuccess) return false;
+  cudaMemset(q, 0, bytes);
+  h->allocs.push_back(q);
+  *p = reinterpret_cast<T*>(q);
+  return true;
+}
+
+bool upload_tiles(svgp_handle* h, const std::vector<Tile>& v, Tile** out, int* n) {
+  if (!dalloc(h, out, sizeof(Tile) * std::max<size_t>(v.size(), 1))) return false;
+  cudaMemcpy(*out, v.data(), sizeof(Tile) * v.size(), cudaMemcpyHostToDevice);
+  *n = (int)v.size();
+  return true;
+}
+
+bool build_ctx(svgp_handle* h, GemmCtx& g, int BM, int BN) {
+  int Mp = h->Mp;
+  g.Mp = Mp;
+  g.st = h->st;
+  return upload_tiles(h, make_tiles(Mp, BM, BN, REG_FULL, K_M0_END), &g.tt_vt, &g.nt_vt) &&
+         upload_tiles(h, make_tiles(Mp, BM, BN, REG_UPPER, K_N0_END), &g.tt_sym_in, &g.nt_sym_in) &&
+         upload_tiles(h, make_tiles(Mp, BM, BN, REG_LOWER, K_N0_M1), &g.tt_lupd, &g.nt_lupd) &&
+         upload_tiles(h, make_tiles(Mp, BM, BN, REG_FULL, K_0_M1), &g.tt_ls, &g.nt_ls) &&
+         upload_tiles(h, make_tiles(Mp, BM, BN, REG_LOWER, K_0_N1), &g.tt_out, &g.nt_out) &&
+         upload_tiles(h, make_tiles(Mp, BM, BN, REG_UPPER, K_ALL), &g.tt_psi, &g.nt_psi);
+}
+
+bool valid_params(const svgp_params* p) {
+  return p && p->Z && p->ell && p->sf2 && p->noise && p->m && p->s && p->L;
+}
+
+// Brackets one launch with timing events while profiling is enabled.
+struct ProfScope {
+  svgp_handle* h; int idx;
+  ProfScope(svgp_handle* hh, int kind) : h(hh), idx(-1) {
+    if (!h->prof) return;
+    int n = (int)h->rec_kind.size();
+    if (2 * n + 1 >= (int)h->ev.size()) return;
+    idx = n;
+    h->rec_kind.push_back(kind);
+    cudaEventRecord(h->ev[2 * n], h->st);
+  }
+  ~ProfScope() {
+    if (idx >= 0) cudaEventRecord(h->ev[2 * idx + 1], h->st);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Precision dispatch of the M x M GEMM chain.
+// ---------------------------------------------------------------------------
+template <class T> T* lo(void* p) { return reinterpret_cast<T*>(p); }
+
+void run_vt(svgp_handle* h, const void* B, const float* s, const int* skip) {
+  ProfScope ps(h, SVGP_PROF_VT);
+  int Mp = h->Mp;
+  if (h->tc) {
+    EpiVt<bf16> e{lo<bf16>(h->V), Mp, h->Lf, s, h->M, skip};
+    tc_vt(h->gt, lo<bf16>(h->Lt_lo), (const bf16*)B, e);
+  } else {
+    EpiVt<float> e{lo<float>(h->V), Mp, h->Lf, s, h->M, skip};
+    simt_vt(h->gs, lo<float>(h->Lt_lo), (const float*)B, e);
+  }
+}
+
+template <int MODE>
+void run_sym(svgp_handle* h, const int* skip) {
+  ProfScope ps(h, SVGP_PROF_SYM);
+  int Mp = h->Mp;
+  if (h->tc) {
+    EpiSym<bf16, MODE> e{lo<bf16>(h->S), Mp, h->M, h->red, skip};
+    if constexpr (MODE == 0) tc_sym_ng(h->gt, lo<bf16>(h->V), lo<bf16>(h->Lt_lo), e);
+    if constexpr (MODE == 1) tc_sym_fwd(h->gt, lo<bf16>(h->V), lo<bf16>(h->Lt_lo), e);
+    if constexpr (MODE == 2) tc_sym_bwd(h->gt, lo<bf16>(h->V), lo<bf16>(h->Lt_lo), e);
+  } else {
+    EpiSym<float, MODE> e{lo<float>(h->S), Mp, h->M, h->red, skip};
+    if constexpr (MODE == 0) simt_sym_ng(h->gs, lo<float>(h->V), lo<float>(h->Lt_lo), e);
+    if constexpr (MODE == 1) simt_sym_fwd(h->gs, lo<float>(h->V), lo<float>(h->Lt_lo), e);
+    if constexpr (MODE == 2) simt_sym_bwd(h->gs, lo<float>(h->V), lo<float>(h->Lt_lo), e);
+  }
+}
+
+void run_ls(svgp_handle* h) {  // Y = L S
+  ProfScope ps(h, SVGP_PROF_LS);
+  if (h->tc) tc_ls(h->gt, lo<bf16>(h->L_lo), lo<bf16>(h->S), EpiStore<bf16>{lo<bf16>(h->Y), h->Mp, nullptr});
+  else simt_ls(h->gs, lo<float>(h->L_lo), lo<float>(h->S), EpiStore<float>{lo<float>(h->Y), h->Mp, nullptr});
+}
+
+void run_p(svgp_handle* h, const float* s, const float* Psi) {
+  ProfScope ps(h, SVGP_PROF_OUT);
+  if (h->tc) {
+    EpiP<bf16> e{h->Pf, lo<bf16>(h->P_lo), h->Mp, h->M, s, Psi, h->red};
+    tc_p(h->gt, lo<bf16>(h->Y), lo<bf16>(h->L_lo), e);
+  } else {
+    EpiP<float> e{h->Pf, lo<float>(h->P_lo), h->Mp, h->M, s, Psi, h->red};
+    simt_p(h->gs, lo<float>(h->Y), lo<float>(h->L_lo), e);
+  }
+}
+
+void run_psi(svgp_handle* h, const svgp_params* p, int B) {
+  ProfScope ps(h, SVGP_PROF_PSI);
+  KufGen kg{h->Zs, h->Xs, h->D, h->M, B, p->sf2};
+  EpiPsi e{h->Psi, h->Mp};
+  if (h->tc) tc_psi(h->gt, kg, B, e);
+  else simt_psi(h->gs, kg, B, e);
+}
+
+void run_w(svgp_handle* h, const WEpi& we) {
+  ProfScope ps(h, SVGP_PROF_W);
+  if (h->tc) tc_w(h->gt, lo<bf16>(h->P_lo), we);
+  else simt_w(h->gs, lo<float>(h->P_lo), we);
+}
+
+// Common prologue: scaled coordinates, Kuu, L copies, log-dets; zero sums.
+void prologue(svgp_handle* h, const svgp_params* p, const float* X, int B, const float* Lin) {
+  cudaStream_t st = h->st;
+  cudaMemsetAsync(h->red, 0, sizeof(double) * RED_COUNT, st);
+  cudaMemsetAsync(h->acc_ell, 0, sizeof(double) * SVGP_MAXD, st);
+  k_prep_coords(p->Z, X, p->ell, h->M, h->Mp, X ? B : 0, h->D, h->Zs, h->Xs, st);
+  if (h->tc) {
+    k_kuu<bf16>(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, lo<bf16>(h->Kuu_lo), st);
+    k_prep_L<bf16>(Lin, h->M, h->Mp, h->Lf, lo<bf16>(h->L_lo), lo<bf16>(h->Lt_lo), h->red, st);
+  } else {
+    k_kuu<float>(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, (float*)nullptr, st);
+    k_prep_L<float>(Lin, h->M, h->Mp, h->Lf, lo<float>(h->L_lo), lo<float>(h->Lt_lo), h->red, st);
+  }
+}
+
+// Forward pass of Eq. (7) up to the per-point Gaussian terms.
+void forward(svgp_handle* h, const svgp_params* p, const svgp_batch* b, bool psi) {
+  cudaStream_t st = h->st;
+  const void* Kb = h->tc ? h->Kuu_lo : (const void*)h->Kuu_f;
+  k_logs(p->s, h->M, h->red, st);
+  run_vt(h, Kb, p->s, nullptr);          // Vt = L^T K~
+  run_sym<1>(h, nullptr);                // A1 = L^T K~ L ; S = 2I - A1 ; tr, Frobenius
+  if (psi) run_psi(h, p, b->B);          // Psi = Kuf Kuf^T (Kuf generated on chip)
+  run_ls(h);                             // Y = L (2I - A1)
+  run_p(h, p->s, psi ? h->Psi : nullptr);  // P = Y L^T ; sum s_i P_ii ; <P, Psi>
+  k_gemv(h->Pf, h->Mp, h->M, p->m, 1.f, nullptr, 0.f, h->v, nullptr, nullptr, st);          // v = P m
+  k_gemv(h->Kuu_f, h->Mp, h->M, h->v, 1.f, nullptr, 0.f, h->w, h->v, h->red + RED_QUAD, st);  // w = Kuu v
+  if (b) {
+    k_mu(h->Zs, h->Xs, h->M, b->B, h->D, p->sf2, h->v, h->mu, st);                          // mu = Kfu v
+    k_pointwise_gauss(b->y, h->mu, p->noise, b->B, h->g, h->red, st);
+  }
+}
+
+svgp_status validate_batch(svgp_handle* h, const svgp_batch* b) {
+  if (!b || !b->X || !b->y) return fail(h, SVGP_ERR_INVALID_ARG, "batch: null pointer");
+  if (b->B < 1 || b->B > h->Bmax) return fail(h, SVGP_ERR_INVALID_ARG, "batch: B out of [1, B_max]");
+  if (!(b->N > 0)) return fail(h, SVGP_ERR_INVALID_ARG, "batch: N must be > 0");
+  return SVGP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* svgp_status_string(int s) {
+  switch (s) {
+    case SVGP_OK: return "ok";
+    case SVGP_ERR_INVALID_ARG: return "invalid argument";
+    case SVGP_ERR_CUDA: return "CUDA error";
+    case SVGP_ERR_OOM: return "out of device memory";
+    case SVGP_ERR_NONFINITE: return "non-finite value on device";
+    case SVGP_ERR_NOT_CONVERGED: return "not converged";
+    case SVGP_ERR_TIMEOUT: return "device wait timed out";
+    case SVGP_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+int svgp_has_tensor_cores(void) { return tc_available() ? 1 : 0; }
+
+svgp_status svgp_create(const svgp_config* cfg, svgp_handle** out) {
+  if (!cfg || !out) return SVGP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (cfg->M < 1 || cfg->M > 8192 || cfg->D < 1 || cfg->D > SVGP_MAXD || cfg->B_max < 1 ||
+      cfg->B_max > (1 << 22))
+    return SVGP_ERR_INVALID_ARG;
+  if (cfg->lik != SVGP_LIK_GAUSSIAN) return SVGP_ERR_UNSUPPORTED;
+  if (cfg->prec != SVGP_FP32 && cfg->prec != SVGP_BF16) return SVGP_ERR_INVALID_ARG;
+  if (cfg->prec == SVGP_BF16 && !tc_available()) return SVGP_ERR_UNSUPPORTED;
+  svgp_handle* h = new svgp_handle();
+  h->cfg = *cfg;
+  h->M = cfg->M;
+  h->Mp = (cfg->M + 127) / 128 * 128;
+  h->D = cfg->D;
+  h->Dp = (cfg->D + 3) & ~3;
+  h->Bmax = cfg->B_max;
+  h->tc = cfg->prec == SVGP_BF16;
+  h->lo_bytes = h->tc ? 2 : 4;
+  h->st = (cudaStream_t)cfg->cuda_stream;
+  h->err[0] = 0;
+  h->prof = false;
+  size_t M2 = (size_t)h->Mp * h->Mp;
+  size_t Bp = (size_t)(cfg->B_max + 127) / 128 * 128;
+  size_t lob = M2 * h->lo_bytes;
+  int W = 2 * cfg->D + 1;
+  bool ok = dalloc(h, &h->Kuu_f, M2 * 4) && dalloc(h, &h->Lf, M2 * 4) && dalloc(h, &h->Pf, M2 * 4) &&
+            dalloc(h, &h->Psi, M2 * 4) && dalloc(h, &h->GKuu, M2 * 4) && dalloc(h, &h->L_lo, lob) &&
+            dalloc(h, &h->Lt_lo, lob) && dalloc(h, &h->V, lob) && dalloc(h, &h->S, lob) &&
+            dalloc(h, &h->Y, lob) && dalloc(h, &h->GP_lo, lob) &&
+            dalloc(h, &h->Zs, sizeof(float) * h->Mp * h->Dp) && dalloc(h, &h->Xs, sizeof(float) * Bp * h->Dp) &&
+            dalloc(h, &h->v, sizeof(float) * h->Mp) && dalloc(h, &h->w, sizeof(float) * h->Mp) &&
+            dalloc(h, &h->mu, sizeof(float) * Bp) && dalloc(h, &h->g, sizeof(float) * Bp) &&
+            dalloc(h, &h->Kg, sizeof(float) * h->Mp) && dalloc(h, &h->colsum, sizeof(float) * Bp) &&
+            dalloc(h, &h->dm_tmp, sizeof(float) * h->Mp) &&
+            dalloc(h, &h->rowacc_f, sizeof(float) * h->Mp * W) && dalloc(h, &h->rowacc_u, sizeof(float) * h->Mp * W) &&
+            dalloc(h, &h->red, sizeof(double) * RED_COUNT) && dalloc(h, &h->acc_ell, sizeof(double) * SVGP_MAXD) &&
+            dalloc(h, &h->resid_tmp, sizeof(double)) && dalloc(h, &h->errword, sizeof(int)) &&
+            dalloc(h, &h->done, sizeof(int)) && dalloc(h, &h->iters_tmp, sizeof(int));
+  if (ok && h->tc) ok = dalloc(h, &h->Kuu_lo, lob) && dalloc(h, &h->P_lo, lob);
+  if (ok && !h->tc) { h->Kuu_lo = h->Kuu_f; h->P_lo = h->Pf; }
+  if (ok) ok = build_ctx(h, h->gs, 128, 128) && build_ctx(h, h->gt, 128, 128);
+  simt_init_attributes();
+  if (h->tc) tc_init_attributes();
+  if (!ok) {
+    svgp_destroy(h);
+    return SVGP_ERR_OOM;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    svgp_destroy(h);
+    return SVGP_ERR_CUDA;
+  }
+  *out = h;
+  return SVGP_OK;
+}
+
+void svgp_destroy(svgp_handle* h) {
+  if (!h) return;
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  for (void* p : h->allocs) cudaFree(p);
+  delete h;
+}
+
+svgp_status svgp_set_stream(svgp_handle* h, void* stream) {
+  if (!h) return SVGP_ERR_INVALID_ARG;
+  h->st = (cudaStream_t)stream;
+  h->gs.st = h->st;
+  h->gt.st = h->st;
+  return SVGP_OK;
+}
+
+int svgp_param_count(const svgp_handle* h) {
+  return h ? h->M * h->D + h->D + 2 + 2 * h->M : 0;
+}
+
+long long svgp_launch_count(const svgp_handle* h) {
+  (void)h;
+  return (long long)__atomic_load_n(&g_launches, __ATOMIC_RELAXED);
+}
+
+svgp_status svgp_profile_enable(svgp_handle* h, int enable) {
+  if (!h) return SVGP_ERR_INVALID_ARG;
+  if (enable && h->ev.empty()) {
+    h->ev.resize(1024);
+    for (auto& e : h->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return fail(h, SVGP_ERR_CUDA, "cudaEventCreate failed");
+  }
+  h->prof = enable != 0;
+  if (enable) h->rec_kind.clear();
+  return SVGP_OK;
+}
+
+svgp_status svgp_profile_read(svgp_handle* h, float* ms, int* counts) {
+  if (!h || !ms || !counts) return SVGP_ERR_INVALID_ARG;
+  for (int k = 0; k < SVGP_PROF_NKINDS; ++k) { ms[k] = 0.f; counts[k] = 0; }
+  for (size_t r = 0; r < h->rec_kind.size(); ++r) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, h->ev[2 * r], h->ev[2 * r + 1]) != cudaSuccess)
+      return fail(h, SVGP_ERR_CUDA, "cudaEventElapsedTime failed (work not complete?)");
+    ms[h->rec_kind[r]] += t;
+    counts[h->rec_kind[r]] += 1;
+  }
+  return SVGP_OK;
+}
+
+const char* svgp_last_error(const svgp_handle* h) { return h ? h->err : "null handle"; }
+
+svgp_status svgp_bound(svgp_handle* h, const svgp_params* p, const svgp_batch* b, double* terms_dev) {
+  if (!h) return SVGP_ERR_INVALID_ARG;
+  if (!valid_params(p)) return fail(h, SVGP_ERR_INVALID_ARG, "params: null pointer");
+  if (!terms_dev) return fail(h, SVGP_ERR_INVALID_ARG, "terms_dev is null");
+  svgp_status s = validate_batch(h, b);
+  if (s != SVGP_OK) return s;
+  prologue(h, p, b->X, b->B, p->L);
+  forward(h, p, b, true);
+  k_terms_finalize(h->red, h->acc_ell, p->sf2, p->noise, p->ell, h->M, h->D, b->B, b->N, terms_dev,
+                   nullptr, nullptr, nullptr, h->errword, h->st);
+  return check_launch(h, "svgp_bound");
+}
+
+svgp_status svgp_backward(svgp_handle* h, const svgp_params* p, const svgp_batch* b, double* terms_dev,
+                          const svgp_grads* gr) {
+  if (!h) return SVGP_ERR_INVALID_ARG;
+  if (!valid_params(p)) return fail(h, SVGP_ERR_INVALID_ARG, "params: null pointer");
+  if (!gr || !gr->dZ || !gr->dell || !gr->dsf2 || !gr->dnoise || !gr->dm || !gr->ds)
+    return fail(h, SVGP_ERR_INVALID_ARG, "grads: null pointer");
+  svgp_status s = validate_batch(h, b);
+  if (s != SVGP_OK) return s;
+  cudaStream_t st = h->st;
+  const int M = h->M, Mp = h->Mp, W = 2 * h->D + 1;
+  const float c = (float)(b->N / b->B);
+  prologue(h, p, b->X, b->B, p->L);
+  forward(h, p, b, true);
+  // backward, T fixed (Section 3.1)
+  k_kg(h->Zs, h->Xs, M, Mp, b->B, h->D, p->sf2, h->g, h->Kg, st);                      // Kuf g
+  if (h->tc) k_gp_assemble<bf16>(h->Kuu_f, h->Psi, h->Kg, p->m, h->w, p->noise, c, M, Mp, lo<bf16>(h->GP_lo), st);
+  else k_gp_assemble<float>(h->Kuu_f, h->Psi, h->Kg, p->m, h->w, p->noise, c, M, Mp, lo<float>(h->GP_lo), st);
+  run_vt(h, h->GP_lo, nullptr, nullptr); // X1t = L^T G_P
+  run_sym<2>(h, nullptr);                // S = L^T G_P L + I/2
+  run_ls(h);                             // Y = L S
+  if (ProfScope ps(h, SVGP_PROF_OUT); h->tc) {  // G_K~ = -Y L^T -> G_Kuu, ds
+    EpiGK e{h->GKuu, Mp, M, h->Pf, h->v, p->s, gr->ds};
+    tc_gk(h->gt, lo<bf16>(h->Y), lo<bf16>(h->L_lo), e);
+  } else {
+    EpiGK e{h->GKuu, Mp, M, h->Pf, h->v, p->s, gr->ds};
+    simt_gk(h->gs, lo<float>(h->Y), lo<float>(h->L_lo), e);
+  }
+  cudaMemsetAsync(h->rowacc_f, 0, sizeof(float) * Mp * W, st);
+  cudaMemsetAsync(h->rowacc_u, 0, sizeof(float) * Mp * W, st);
+  WEpi we{KufGen{h->Zs, h->Xs, h->D, M, b->B, p->sf2}, nullptr, nullptr, h->v, h->g, p->noise, c,
+          h->rowacc_f, nullptr};
+  run_w(h, we);                                                                        // data part of dZ, dell, dsf2
+  k_kuu_bwd(h->GKuu, h->Kuu_f, h->Zs, M, Mp, h->D, h->rowacc_u, h->red, st);          // Kuu part
+  k_gemv(h->Pf, Mp, M, h->Kg, c, h->w, -1.0f / c, gr->dm, nullptr, nullptr, st);      // dm = P (c Kg - w)
+  k_grad_finalize(h->rowacc_f, h->rowacc_u, p->ell, M, h->D, gr->dZ, h->acc_ell, h->red, st);
+  k_terms_finalize(h->red, h->acc_ell, p->sf2, p->noise, p->ell, M, h->D, b->B, b->N, terms_dev, gr->dsf2,
+                   gr->dnoise, gr->dell, h->errword, st);
+  return check_launch(h, "svgp_backward");
+}
+
+svgp_status svgp_ng_update_T(svgp_handle* h, const svgp_params* p, float* L_inout, const float* gamma_dev,
+                             int max_iters, double eps, int* iters_dev, double* residual_dev) {
+  if (!h) return SVGP_ERR_INVALID_ARG;
+  if (!p || !p->Z || !p->ell || !p->sf2 || !p->s || !L_inout || !gamma_dev)
+    return fail(h, SVGP_ERR_INVALID_ARG, "ng_update_T: null pointer");
+  if (max_iters < 0 || max_iters > 100000) return fail(h, SVGP_ERR_INVALID_ARG, "ng_update_T: max_iters");
+  cudaStream_t st = h->st;
+  int* iters = iters_dev ? iters_dev : h->iters_tmp;
+  double* resid = residual_dev ? residual_dev : h->resid_tmp;
+  cudaMemsetAsync(h->done, 0, sizeof(int), st);
+  cudaMemsetAsync(iters, 0, sizeof(int), st);
+  prologue(h, p, nullptr, 0, L_inout);
+  const void* Kb = h->tc ? h->Kuu_lo : (const void*)h->Kuu_f;
+  for (int t = 0; t < max_iters; ++t) {
+    cudaMemsetAsync(h->red + RED_NG_RESID, 0, sizeof(double), st);
+    run_vt(h, Kb, p->s, h->done);                // Vt = L^T K~ (skipped once converged)
+    run_sym<0>(h, h->done);                      // A, Phi^T, ||A - I||^2
+    k_ng_check(h->red, h->M, eps, h->done, iters, resid, st);   // Eq. (8) stopping rule
+    EpiLupd e{h->Lf, h->Mp, L_inout, h->M, gamma_dev + t, h->done};
+    {
+      ProfScope ps(h, SVGP_PROF_LUPD);           // L <- L - gamma L Phi  (Prop. 1)
+      if (h->tc) tc_lupd(h->gt, lo<bf16>(h->L_lo), lo<bf16>(h->S), e);
+      else simt_lupd(h->gs, lo<float>(h->L_lo), lo<float>(h->S), e);
+    }
+    if (t + 1 < max_iters) {
+      if (h->tc) k_prep_L<bf16>(L_inout, h->M, h->Mp, h->Lf, lo<bf16>(h->L_lo), lo<bf16>(h->Lt_lo), h->red + RED_COUNT - 1, st);
+      else k_prep_L<float>(L_inout, h->M, h->Mp, h->Lf, lo<float>(h->L_lo), lo<float>(h->Lt_lo), h->red + RED_COUNT - 1, st);
+    }
+  }
+  return check_launch(h, "svgp_ng_update_T");
+}
+
+svgp_status svgp_predict(svgp_handle* h, const svgp_params* p, const float* Xs, int Ns, float* mean, float* var,
+                         int include_noise) {
+  if (!h) return SVGP_ERR_INVALID_ARG;
+  if (!valid_params(p) || !Xs || !mean || !var) return fail(h, SVGP_ERR_INVALID_ARG, "predict: null pointer");
+  if (Ns < 1 || Ns > h->Bmax) return fail(h, SVGP_ERR_INVALID_ARG, "predict: Ns out of [1, B_max]");
+  cudaStream_t st = h->st;
+  prologue(h, p, Xs, Ns, p->L);
+  forward(h, p, nullptr, false);
+  k_mu(h->Zs, h->Xs, h->M, Ns, h->D, p->sf2, h->v, mean, st);
+  cudaMemsetAsync(h->colsum, 0, sizeof(float) * Ns, st);
+  WEpi we{KufGen{h->Zs, h->Xs, h->D, h->M, Ns, p->sf2}, nullptr, nullptr, nullptr, nullptr, nullptr, 0.f,
+          nullptr, h->colsum};
+  run_w(h, we);
+  k_predict_finalize(h->colsum, p->sf2, p->noise, Ns, include_noise, var, st);
+  return check_launch(h, "svgp_predict");
+}
+
+svgp_status svgp_adam_step(svgp_handle* h, float* raw, float* constrained, const float* grad, float* m1, float* m2,
+                           int* step_dev, const float* hyper_dev, const float* zbeta1_dev) {
+  if (!h) return SVGP_ERR_INVALID_ARG;
+  if (!raw || !constrained || !grad || !m1 || !m2 || !step_dev || !hyper_dev)
+    return fail(h, SVGP_ERR_INVALID_ARG, "adam: null pointer");
+  k_adam(raw, constrained, grad, m1, m2, step_dev, hyper_dev, zbeta1_dev, h->M, h->D, h->st);
+  return check_launch(h, "svgp_adam_step");
+}
+
+svgp_status svgp_sync_status(svgp_handle* h) {
+  if (!h) return SVGP_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(h, SVGP_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+  int e = 0;
+  if (cudaMemcpy(&e, h->errword, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SVGP_ERR_CUDA;
+  cudaMemset(h->errword, 0, sizeof(int));
+  if (e & ERRBIT_TIMEOUT) return fail(h, SVGP_ERR_TIMEOUT, "a device pipeline wait timed out");
+  if (e & ERRBIT_NONFINITE) return fail(h, SVGP_ERR_NONFINITE, "non-finite bound");
+  return SVGP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,161 @@
+"""Device state and training step of one R-SVGP model on top of the C-ABI.
+
+PyTorch supplies device memory, streams and CUDA-graph capture; every step of
+the computation runs in ``libsvgp.so``.  The training step follows the
+alternating optimisation of Section 3.1: natural-gradient update(s) of L given
+K~, then one Adam step on xi = {Z, ell, sf2, noise, m~, s~} with L fixed.
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+from . import _lib as C
+
+PREC = {"fp32": C.SVGP_FP32, "bf16": C.SVGP_BF16}
+
+
+def _softplus_inv(x: torch.Tensor) -> torch.Tensor:
+    x = x.double()
+    return (x + torch.log(-torch.expm1(-x))).float()
+
+
+class RSVGP:
+    """One model: flat constrained/raw parameter vectors, L, Adam moments.
+
+    Flat layout (shared with svgp_adam_step): [Z (M*D) | ell (D) | sf2 | noise |
+    m~ (M) | s~ (M)].  ``params`` points into the constrained vector.
+    """
+
+    def __init__(self, M: int, D: int, B_max: int, prec: str = "bf16", device: str = "cuda"):
+        if not torch.cuda.is_available():
+            raise RuntimeError("RSVGP needs a CUDA device (no CPU fallback)")
+        self.M, self.D, self.B_max = M, D, B_max
+        self.prec = prec
+        self.dev = torch.device(device)
+        self.h = C.svgp_create(M, D, B_max, PREC[prec], cuda_stream=torch.cuda.current_stream().cuda_stream)
+        self.n = C.svgp_param_count(self.h)
+        f32 = dict(device=self.dev, dtype=torch.float32)
+        self.cons = torch.zeros(self.n, **f32)
+        self.raw = torch.zeros(self.n, **f32)
+        self.grad = torch.zeros(self.n, **f32)
+        self.m1 = torch.zeros(self.n, **f32)
+        self.m2 = torch.zeros(self.n, **f32)
+        self.step = torch.zeros(1, device=self.dev, dtype=torch.int32)
+        self.hyper = torch.tensor([5e-3, 0.9, 0.999, 1e-8, 1, 1, 1, 1, 1, 1], **f32)
+        self.L = torch.zeros(M, M, **f32)
+        self.gamma = torch.ones(64, **f32)
+        self.terms = torch.zeros(C.SVGP_NTERMS, device=self.dev, dtype=torch.float64)
+        self.iters = torch.zeros(1, device=self.dev, dtype=torch.int32)
+        self.resid = torch.zeros(1, device=self.dev, dtype=torch.float64)
+        o = 0
+        self.sl = {}
+        for name, size in (("Z", M * D), ("ell", D), ("sf2", 1), ("noise", 1), ("m", M), ("s", M)):
+            self.sl[name] = slice(o, o + size)
+            o += size
+        self.params = C.svgp_params(*[self.cons[self.sl[k]].data_ptr() for k in ("Z", "ell", "sf2", "noise", "m", "s")],
+                                    self.L.data_ptr())
+        self.grads = C.svgp_grads(*[self.grad[self.sl[k]].data_ptr() for k in ("Z", "ell", "sf2", "noise", "m", "s")])
+
+    def close(self):
+        if self.h:
+            C.svgp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- state ---------------------------------------------------------------
+    def set_state(self, Z, ell, sf2, noise, m, s, L):
+        def t(x):
+            return torch.as_tensor(x, dtype=torch.float32).reshape(-1).to(self.dev)
+
+        for k, v in (("Z", Z), ("ell", ell), ("sf2", [sf2]), ("noise", [noise]), ("m", m), ("s", s)):
+            self.cons[self.sl[k]] = t(v)
+        self.L.copy_(torch.as_tensor(L, dtype=torch.float32).reshape(self.M, self.M))
+        raw = self.cons.clone()
+        for k in ("ell", "sf2", "noise", "s"):
+            raw[self.sl[k]] = _softplus_inv(self.cons[self.sl[k]])
+        self.raw.copy_(raw)
+        self.m1.zero_()
+        self.m2.zero_()
+        self.step.zero_()
+
+    def get(self, name):
+        v = self.cons[self.sl[name]]
+        return v.reshape(self.M, self.D) if name == "Z" else v
+
+    def grad_of(self, name):
+        v = self.grad[self.sl[name]]
+        return v.reshape(self.M, self.D) if name == "Z" else v
+
+    def _sync_stream(self):
+        C.svgp_set_stream(self.h, torch.cuda.current_stream().cuda_stream)
+
+    @staticmethod
+    def batch(X: torch.Tensor, y: torch.Tensor, N: float):
+        return C.svgp_batch(X.data_ptr(), y.data_ptr(), X.shape[0], float(N))
+
+    # -- entry points ----------------------------------------------------------
+    def bound(self, X, y, N):
+        self._sync_stream()
+        C.svgp_bound(self.h, self.params, self.batch(X, y, N), self.terms.data_ptr())
+        return self.terms
+
+    def backward(self, X, y, N):
+        self._sync_stream()
+        C.svgp_backward(self.h, self.params, self.batch(X, y, N), self.terms.data_ptr(), self.grads)
+        return self.terms
+
+    def ng_update(self, max_iters=1, eps=0.0, gammas=None):
+        self._sync_stream()
+        if gammas is not None:
+            g = torch.as_tensor(gammas, dtype=torch.float32)
+            self.gamma[: g.numel()] = g.to(self.dev)
+        if max_iters > self.gamma.numel():
+            raise ValueError("max_iters larger than the gamma buffer")
+        C.svgp_ng_update_T(self.h, self.params, self.L.data_ptr(), self.gamma.data_ptr(), max_iters, eps,
+                           self.iters.data_ptr(), self.resid.data_ptr())
+
+    def predict(self, Xs, include_noise=False):
+        self._sync_stream()
+        mean = torch.empty(Xs.shape[0], device=self.dev)
+        var = torch.empty(Xs.shape[0], device=self.dev)
+        C.svgp_predict(self.h, self.params, Xs.data_ptr(), Xs.shape[0], mean.data_ptr(), var.data_ptr(),
+                       include_noise)
+        return mean, var
+
+    def adam_step(self):
+        self._sync_stream()
+        C.svgp_adam_step(self.h, self.raw.data_ptr(), self.cons.data_ptr(), self.grad.data_ptr(),
+                         self.m1.data_ptr(), self.m2.data_ptr(), self.step.data_ptr(), self.hyper.data_ptr())
+
+    def train_step(self, X, y, N, t_star=1, eps=0.0):
+        """NG update(s) of L given K~ (Prop. 1), then bound + gradient + Adam."""
+        self.ng_update(max_iters=t_star, eps=eps)
+        self.backward(X, y, N)
+        self.adam_step()
+        return self.terms
+
+    def capture(self, X, y, N, t_star=1, eps=0.0):
+        """Capture one training step on (X, y) into a CUDA graph."""
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.train_step(X, y, N, t_star=t_star, eps=eps)
+        self._sync_stream()
+        return g
+
+    def sync_status(self):
+        return C.svgp_sync_status(self.h)
+
+
+def paper_init(M, D, Z0, sf2=1.0, noise=1.0, ell=1.0, alpha=1e-4, beta=1e-3):
+    """Initial state of Appendix S5.3: m~ = 0, s~ = alpha 1, L = beta I."""
+    import numpy as np
+
+    return dict(Z=np.asarray(Z0, np.float64), ell=np.full(D, ell), sf2=sf2, noise=noise,
+                m=np.zeros(M), s=np.full(M, alpha), L=beta * np.eye(M))

@@ -1,0 +1,242 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle.
+
+Bound, gradients, NG update, prediction and Adam are compared on the same
+seeded float32 inputs.  Tolerances: relative bound error <= 1e-6 (FP32 SIMT)
+and <= 1e-3 (BF16 tensor cores); per-block relative gradient error <= 1e-4
+(FP32) and <= 1e-2 (BF16).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from _helpers import BLOCKS, TOL, chol_inv, f32, make_case, rel, round_state, small_case
+from oracle import rsvgp as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PRECS = ["fp32", "bf16"]
+
+
+def _model(p, M, D, B, prec):
+    from paper_2604_00697_gb300 import _lib
+    from paper_2604_00697_gb300.model import RSVGP
+
+    if prec == "bf16" and not _lib.svgp_has_tensor_cores():
+        pytest.fail("tensor-core path not available on this device")
+    m = RSVGP(M, D, B, prec=prec)
+    m.set_state(p["Z"], p["ell"], p["sf2"], p["noise"], p["m"], p["s"], p["L"])
+    return m
+
+
+def _dev(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float32, device="cuda")
+
+
+def _check_bound_and_grads(p, X, y, N, prec, grads=True):
+    M, D = p["Z"].shape
+    B = X.shape[0]
+    m = _model(p, M, D, B, prec)
+    Xd, yd = _dev(X), _dev(y)
+    ref = O.bound(p, X, y, N)
+    if grads:
+        terms = m.backward(Xd, yd, N)
+    else:
+        terms = m.bound(Xd, yd, N)
+    torch.cuda.synchronize()
+    assert m.sync_status() == 0
+    t = terms.cpu().numpy()
+    F = t[0]
+    err = abs(F - ref["F"]) / abs(ref["F"])
+    assert err <= TOL[prec]["bound"], (prec, F, ref["F"], err, t, ref["KL"], ref["E"])
+    out = {"bound_err": err}
+    if grads:
+        g = O.grads(p, X, y, N)
+        for k in BLOCKS:
+            gg = m.grad_of(k).double().cpu().numpy().reshape(np.shape(g[k]))
+            e = rel(gg, g[k])
+            out[k] = e
+            assert e <= TOL[prec]["grad"], (prec, k, e)
+    m.close()
+    return out
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("state", ["init", "chol"])
+def test_snelson_like_bound_and_grads(prec, state):
+    p, X, y, N = make_case("snelson_like", state)
+    _check_bound_and_grads(p, X, y, N, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("M,D,B,seed", [(200, 3, 300, 0), (130, 5, 129, 1), (1, 2, 7, 2), (257, 1, 1, 3)])
+def test_ragged_random_state(prec, M, D, B, seed):
+    p, X, y, N = small_case(M, D, B, seed)
+    _check_bound_and_grads(p, X, y, N, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("state", ["init", "chol"])
+def test_sinusoid_regression_M512(prec, state):
+    p, X, y, N = make_case("sinusoid_regression", state)
+    _check_bound_and_grads(p, X, y, N, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("state", ["init", "chol"])
+def test_gp_sample_full_size(prec, state):
+    """M=2048, B=4096, D=16, N=1e6: the benchmark's workload."""
+    p, X, y, N = make_case("gp_sample_regression", state)
+    _check_bound_and_grads(p, X, y, N, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("M,D,seed", [(16, 1, 0), (200, 3, 1), (512, 8, 2)])
+def test_ng_step_matches_oracle(prec, M, D, seed):
+    p, _, _, _ = small_case(M, D, 4, seed)
+    p["L"] = f32(0.5 * chol_inv(p) + 0.02 * np.tril(np.random.default_rng(seed).normal(size=(M, M))) / math.sqrt(M))
+    Kt = O.se_ard(p["Z"], p["Z"], p["ell"], p["sf2"]) + np.diag(p["s"])
+    L1, r = O.ng_step(p["L"], Kt, 0.7)
+    m = _model(p, M, D, 4, prec)
+    m.ng_update(max_iters=1, eps=0.0, gammas=[0.7])
+    torch.cuda.synchronize()
+    Lg = m.L.double().cpu().numpy()
+    tol = 1e-5 if prec == "fp32" else 2e-2
+    assert rel(Lg, L1) <= tol
+    assert abs(float(m.resid[0]) - r) <= tol * max(r, 1.0)
+    assert int(m.iters[0]) == 1
+    assert np.all(np.triu(Lg, 1) == 0.0)
+    m.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_ng_converges_to_fixed_point_with_stopping_rule(prec):
+    M, D = 96, 2
+    p, _, _, _ = small_case(M, D, 4, 7)
+    p["s"] = f32(np.full(M, 0.2))
+    Kt = O.se_ard(p["Z"], p["Z"], p["ell"], p["sf2"]) + np.diag(p["s"])
+    Ls = np.linalg.cholesky(np.linalg.inv(Kt))
+    p["L"] = f32(1e-3 * np.eye(M))
+    eps = 1e-4 if prec == "fp32" else 3e-2
+    m = _model(p, M, D, 4, prec)
+    gam = [O.gamma_schedule(t, gamma0=1e-1, ramp=5) for t in range(60)]
+    m.ng_update(max_iters=60, eps=eps, gammas=gam)
+    torch.cuda.synchronize()
+    it, r = int(m.iters[0]), float(m.resid[0])
+    assert r < eps and it < 60
+    Lo, ito, ro = O.ng_solve(p["L"], Kt, gam, eps=eps, max_iters=60)
+    assert abs(it - ito) <= (0 if prec == "fp32" else 3)
+    assert rel(m.L.double().cpu().numpy(), Ls) <= (1e-3 if prec == "fp32" else 5e-2)
+    m.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("Ns", [1, 300])
+def test_predict_matches_oracle(prec, Ns):
+    M, D = 150, 3
+    p, _, _, _ = small_case(M, D, 4, 9, state="chol")
+    Xs = f32(np.random.default_rng(4).normal(size=(Ns, D)))
+    mean, var = O.predict(p, Xs, include_noise=True)
+    m = _model(p, M, D, Ns, prec)
+    gm, gv = m.predict(_dev(Xs), include_noise=True)
+    torch.cuda.synchronize()
+    tol = 1e-4 if prec == "fp32" else 2e-2
+    assert rel(gm.double().cpu().numpy(), mean) <= tol
+    assert rel(gv.double().cpu().numpy(), var) <= tol
+    m.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32"])
+def test_adam_step_matches_oracle(prec):
+    M, D = 40, 3
+    p, X, y, N = small_case(M, D, 50, 12)
+    g = O.grads(p, X, y, N)
+    g = {k: f32(np.asarray(v)) for k, v in g.items()}
+    m = _model(p, M, D, 50, prec)
+    for k in BLOCKS:
+        m.grad[m.sl[k]] = _dev(np.reshape(g[k], -1))
+    raw0 = m.raw.double().cpu().numpy().copy()
+    m.adam_step()
+    torch.cuda.synchronize()
+    raw = {k: raw0[m.sl[k]].reshape(np.shape(p[k])) for k in BLOCKS}
+    new = O.adam_update(raw, g, {}, 5e-3)
+    cons = O.constrain(new)
+    for k in BLOCKS:
+        gv = m.cons[m.sl[k]].double().cpu().numpy().reshape(np.shape(p[k]))
+        assert rel(gv, cons[k]) <= 1e-5, k
+    assert int(m.step[0]) == 1
+    m.close()
+
+
+def test_short_training_trajectory_fp32():
+    """20 alternating NG + Adam steps (Section 3.1) on the 1-D workload."""
+    import svgp_synth as S
+
+    prob = S.snelson_like()
+    X, y = prob.batch(0)
+    X, y = f32(X), f32(y)
+    p0 = round_state(dict(Z=prob.Z0, ell=np.array([1.0]), sf2=1.0, noise=1.0, m=np.zeros(prob.M),
+                          s=np.full(prob.M, 1e-4), L=1e-3 * np.eye(prob.M)))
+    _, trace = O.train(p0, lambda t: (X, y), prob.N, steps=20, lr=5e-3, train_Z=True)
+    m = _model(p0, prob.M, 1, prob.B, "fp32")
+    Xd, yd = _dev(X), _dev(y)
+    got = []
+    for _ in range(20):
+        m.ng_update(max_iters=1, gammas=[1.0])
+        got.append(float(m.backward(Xd, yd, prob.N)[0]))
+        m.adam_step()
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(got, trace, rtol=1e-4)
+    m.close()
+
+
+def test_nonfinite_input_is_reported():
+    from paper_2604_00697_gb300 import _lib
+
+    p, X, y, N = small_case(20, 2, 30, 1)
+    X = X.copy()
+    X[3, 1] = np.nan
+    m = _model(p, 20, 2, 30, "fp32")
+    m.bound(_dev(X), _dev(y), N)
+    assert m.sync_status() == _lib.SVGP_ERR_NONFINITE
+    assert m.sync_status() == 0      # cleared after reading
+    m.close()
+
+
+def test_invalid_arguments_are_rejected():
+    from paper_2604_00697_gb300 import _lib
+
+    with pytest.raises(_lib.SvgpError):
+        _lib.svgp_create(0, 2, 10, _lib.SVGP_FP32)
+    with pytest.raises(_lib.SvgpError):
+        _lib.svgp_create(10, 33, 10, _lib.SVGP_FP32)
+    p, X, y, N = small_case(20, 2, 30, 1)
+    m = _model(p, 20, 2, 10, "fp32")
+    with pytest.raises(_lib.SvgpError):
+        m.bound(_dev(X), _dev(y), N)     # B = 30 > B_max = 10
+    m.close()
+
+
+def test_graph_captured_step_matches_eager():
+    import svgp_synth as S
+
+    p, X, y, N = make_case("sinusoid_regression", "init")
+    M, D = p["Z"].shape
+    B = X.shape[0]
+    ms = []
+    for _ in range(2):
+        m = _model(p, M, D, B, "fp32")
+        ms.append(m)
+    Xd, yd = _dev(X), _dev(y)
+    a, b = ms
+    g = b.capture(Xd, yd, N)
+    b.set_state(p["Z"], p["ell"], p["sf2"], p["noise"], p["m"], p["s"], p["L"])
+    for _ in range(3):
+        a.train_step(Xd, yd, N)
+        g.replay()
+    torch.cuda.synchronize()
+    assert torch.allclose(a.cons, b.cons, rtol=1e-5, atol=1e-7) and torch.allclose(a.L, b.L, rtol=1e-5, atol=1e-9)
+    assert abs(float(a.terms[0]) - float(b.terms[0])) <= 1e-9 * abs(float(a.terms[0]))
+    for m in ms:
+        m.close()
