@@ -50,14 +50,16 @@ __device__ __forceinline__ void store_row(float* dst, const float* v, int n) {
 // per block).  Must be called by all threads of the block.
 __device__ __forceinline__ void block_add_double(double x, double* dst) {
   __shared__ double red_buf[32];
-  unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const unsigned nthr = blockDim.x * blockDim.y * blockDim.z;
+  unsigned lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   __syncthreads();
   if (lane == 0) red_buf[warp] = x;
   __syncthreads();
   if (warp == 0) {
-    unsigned nw = (blockDim.x + 31) >> 5;
+    unsigned nw = (nthr + 31) >> 5;
     double y = lane < nw ? red_buf[lane] : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);

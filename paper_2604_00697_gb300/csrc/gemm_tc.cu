@@ -1,16 +1,333 @@
-// tcgen05 BF16 GEMMs (placeholder until the tensor-core mainloop lands).
+// tcgen05 BF16 GEMMs for sm_103a: acc[i,j] = sum_k A[i,k] B[j,k], both
+// operands K-major BF16 (row-major, k contiguous), FP32 accumulation in TMEM.
+//
+// One 128 x 128 output tile per CTA, 192 threads:
+//   warp 0      TMA producer: 128B-swizzled 128x64 tiles of A and B into a
+//               STAGES-deep shared-memory ring (mbarrier full/empty pairs);
+//   warp 1      TMEM allocator and MMA issuer: one elected thread issues
+//               tcgen05.mma.cta_group::1.kind::f16 (M=128, N=128, K=16) x 4 per
+//               k-block and frees the stage with tcgen05.commit;
+//   warps 2..5  epilogue: tcgen05.ld 32x32b.x32 of their 32 TMEM lanes, then
+//               the shared epilogue functors (common.cuh) write the results.
+// Every mbarrier wait is bounded by a %globaltimer deadline; on expiry the
+// CTA raises ERRBIT_TIMEOUT, drains its own copies and frees TMEM.
+#include <cuda.h>
+
 #include "common.cuh"
 #include "internal.h"
 
-bool tc_available() { return false; }
-void tc_init_attributes() {}
-bool tc_vt(const GemmCtx&, const bf16*, const bf16*, EpiVt<bf16>) { return false; }
-bool tc_sym_ng(const GemmCtx&, const bf16*, const bf16*, EpiSym<bf16, 0>) { return false; }
-bool tc_sym_fwd(const GemmCtx&, const bf16*, const bf16*, EpiSym<bf16, 1>) { return false; }
-bool tc_sym_bwd(const GemmCtx&, const bf16*, const bf16*, EpiSym<bf16, 2>) { return false; }
-bool tc_lupd(const GemmCtx&, const bf16*, const bf16*, EpiLupd) { return false; }
-bool tc_ls(const GemmCtx&, const bf16*, const bf16*, EpiStore<bf16>) { return false; }
-bool tc_p(const GemmCtx&, const bf16*, const bf16*, EpiP<bf16>) { return false; }
-bool tc_gk(const GemmCtx&, const bf16*, const bf16*, EpiGK) { return false; }
+namespace {
+
+constexpr int BM = 128;
+constexpr int BN = 128;
+constexpr int BK = 64;                      // one 128-byte swizzle atom of BF16
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;        // 16 KB
+constexpr int B_BYTES = BN * BK * 2;        // 16 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s per wait
+
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: true on completion, false when the deadline passed.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  unsigned long long t0 = gtimer();
+  while (!mbar_try(bar, parity)) {
+    if (gtimer() - t0 > WAIT_NS) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), version 1 (sm_100 family).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;                 // LBO (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;       // SBO
+  d |= (uint64_t)1 << 46;                 // descriptor version
+  d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D=F32, A=B=BF16, both K-major, M=128, N=BN.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem_d), "l"(ad), "l"(bd), "r"(IDESC), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+template <class Epi>
+__global__ void __launch_bounds__(192, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const Tile* __restrict__ tiles, Epi epi, int* errword) {
+  if (epi.skip()) return;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = base;
+  unsigned char* sB = base + STAGES * A_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
+  // bars[0..S) full, bars[S..2S) empty, bars[2S] tmem_full
+  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars + 2 * STAGES + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * STAGES + 2);
+  volatile int* consumed = abort_flag + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const Tile tl = tiles[blockIdx.x];
+  const int nk = (tl.k1 - tl.k0) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&bars[s]), 1);
+      mbar_init(smem_u32(&bars[STAGES + s]), 1);
+    }
+    mbar_init(smem_u32(&bars[2 * STAGES]), 1);
+    *abort_flag = 0;
+    *consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32((const void*)tmem_slot)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      int s = kb % STAGES;
+      uint32_t ph = (kb / STAGES) & 1;
+      if (!mbar_wait(smem_u32(&bars[STAGES + s]), ph ^ 1)) { *abort_flag = 1; break; }
+      if (*abort_flag) break;
+      uint32_t fb = smem_u32(&bars[s]);
+      mbar_expect_tx(fb, STAGE_BYTES);
+      int k = tl.k0 + kb * BK;
+      tma_load_2d(smem_u32(sA + s * A_BYTES), &tmA, k, tl.m0, fb);
+      tma_load_2d(smem_u32(sB + s * B_BYTES), &tmB, k, tl.n0, fb);
+      issued = kb + 1;
+    }
+    // On abort, wait (bounded) for copies that nobody consumed.
+    if (*abort_flag) {
+      for (int kb = *consumed; kb < issued; ++kb) mbar_wait(smem_u32(&bars[kb % STAGES]), (kb / STAGES) & 1);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    for (int kb = 0; kb < nk; ++kb) {
+      int s = kb % STAGES;
+      uint32_t ph = (kb / STAGES) & 1;
+      if (!mbar_wait(smem_u32(&bars[s]), ph)) { *abort_flag = 1; break; }
+      fence_after();
+      uint64_t ad = sw128_desc(smem_u32(sA + s * A_BYTES));
+      uint64_t bd = sw128_desc(smem_u32(sB + s * B_BYTES));
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk)
+        mma_bf16(tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), (kb | kk) != 0);
+      mma_commit(smem_u32(&bars[STAGES + s]));
+      *consumed = kb + 1;
+    }
+    if (nk > 0) mma_commit(smem_u32(&bars[2 * STAGES]));
+  }
+  __syncwarp();
+
+  // ---------------- epilogue ----------------
+  epi.begin_tile(tl.m0, tl.n0);
+  if (warp >= 2) {
+    const int quad = warp & 3;
+    const int row = quad * 32 + lane;
+    bool ok = true;
+    if (nk > 0) {
+      ok = mbar_wait(smem_u32(&bars[2 * STAGES]), 0);
+      fence_after();
+    }
+    if (!ok) *abort_flag = 1;
+    float v[32];
+    for (int c = 0; c < BN / 32; ++c) {
+      if (nk > 0 && ok) {
+        tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32), v);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) v[q] = 0.f;
+      }
+      if (ok) epi.row(tl.m0 + row, tl.n0 + c * 32, v, 32);
+    }
+  }
+  epi.reduce();
+  fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(errword, ERRBIT_TIMEOUT);
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side: tensor maps and launches.
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2-D BF16 row-major [rows][cols] (ld = cols), box 64 (k) x 128 (rows).
+bool make_map(CUtensorMap* m, const void* ptr, int rows, int cols) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {BK, 128};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+
+template <class Epi>
+bool launch(const GemmCtx& g, const Tile* tiles, int ntiles, const bf16* A, const bf16* B, const Epi& e) {
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, g.Mp, g.Mp) || !make_map(&mb, B, g.Mp, g.Mp)) return false;
+  svgp_note_launch();
+  tc_gemm_kernel<Epi><<<ntiles, 192, SMEM_BYTES, g.st>>>(ma, mb, tiles, e, g.err);
+  return true;
+}
+
+template <class Epi>
+void set_attr() {
+  cudaFuncSetAttribute(tc_gemm_kernel<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+}
+
+}  // namespace
+
+bool tc_available() {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3 && encode_fn() != nullptr;
+}
+
+void tc_init_attributes() {
+  set_attr<EpiVt<bf16>>();
+  set_attr<EpiSym<bf16, 0>>();
+  set_attr<EpiSym<bf16, 1>>();
+  set_attr<EpiSym<bf16, 2>>();
+  set_attr<EpiLupd>();
+  set_attr<EpiStore<bf16>>();
+  set_attr<EpiP<bf16>>();
+  set_attr<EpiGK>();
+}
+
+bool tc_vt(const GemmCtx& g, const bf16* Lt, const bf16* K, EpiVt<bf16> e) {
+  return launch(g, g.tt_vt, g.nt_vt, Lt, K, e);
+}
+bool tc_sym_ng(const GemmCtx& g, const bf16* V, const bf16* Lt, EpiSym<bf16, 0> e) {
+  return launch(g, g.tt_sym_in, g.nt_sym_in, V, Lt, e);
+}
+bool tc_sym_fwd(const GemmCtx& g, const bf16* V, const bf16* Lt, EpiSym<bf16, 1> e) {
+  return launch(g, g.tt_sym_in, g.nt_sym_in, V, Lt, e);
+}
+bool tc_sym_bwd(const GemmCtx& g, const bf16* V, const bf16* Lt, EpiSym<bf16, 2> e) {
+  return launch(g, g.tt_sym_in, g.nt_sym_in, V, Lt, e);
+}
+bool tc_lupd(const GemmCtx& g, const bf16* L, const bf16* PhiT, EpiLupd e) {
+  return launch(g, g.tt_lupd, g.nt_lupd, L, PhiT, e);
+}
+bool tc_ls(const GemmCtx& g, const bf16* L, const bf16* S, EpiStore<bf16> e) {
+  return launch(g, g.tt_ls, g.nt_ls, L, S, e);
+}
+bool tc_p(const GemmCtx& g, const bf16* Y, const bf16* L, EpiP<bf16> e) {
+  return launch(g, g.tt_out, g.nt_out, Y, L, e);
+}
+bool tc_gk(const GemmCtx& g, const bf16* Y, const bf16* L, EpiGK e) {
+  return launch(g, g.tt_out, g.nt_out, Y, L, e);
+}
+// The Kuf-producer tensor-core kernels are not built yet: callers use the
+// FP32 SIMT kernels for Psi and W.
 bool tc_psi(const GemmCtx&, const KufGen&, int, EpiPsi) { return false; }
 bool tc_w(const GemmCtx&, const bf16*, const WEpi&) { return false; }

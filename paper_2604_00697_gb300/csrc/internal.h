@@ -7,6 +7,7 @@
 struct GemmCtx {
   int Mp;
   cudaStream_t st;
+  int* err;       // device error word of the handle
   // Tables (device memory).  Regions and K ranges (L lower, Lt = L^T upper):
   //  vt     : full,  K [m0, Mp)          Lt S       (S symmetric)
   //  sym_in : upper, K [n0, Mp)          V Lt^T     = L^T S L

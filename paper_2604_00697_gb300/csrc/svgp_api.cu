@@ -100,6 +100,7 @@ bool build_ctx(svgp_handle* h, GemmCtx& g, int BM, int BN) {
   int Mp = h->Mp;
   g.Mp = Mp;
   g.st = h->st;
+  g.err = h->errword;
   return upload_tiles(h, make_tiles(Mp, BM, BN, REG_FULL, K_M0_END), &g.tt_vt, &g.nt_vt) &&
          upload_tiles(h, make_tiles(Mp, BM, BN, REG_UPPER, K_N0_END), &g.tt_sym_in, &g.nt_sym_in) &&
          upload_tiles(h, make_tiles(Mp, BM, BN, REG_LOWER, K_N0_M1), &g.tt_lupd, &g.nt_lupd) &&
@@ -121,10 +122,12 @@ struct ProfScope {
     if (2 * n + 1 >= (int)h->ev.size()) return;
     idx = n;
     h->rec_kind.push_back(kind);
-    cudaEventRecord(h->ev[2 * n], h->st);
+    // External record: inside a stream capture this becomes an event-record
+    // node of the graph, so replays re-record it.
+    cudaEventRecordWithFlags(h->ev[2 * n], h->st, cudaEventRecordExternal);
   }
   ~ProfScope() {
-    if (idx >= 0) cudaEventRecord(h->ev[2 * idx + 1], h->st);
+    if (idx >= 0) cudaEventRecordWithFlags(h->ev[2 * idx + 1], h->st, cudaEventRecordExternal);
   }
 };
 
@@ -183,14 +186,12 @@ void run_psi(svgp_handle* h, const svgp_params* p, int B) {
   ProfScope ps(h, SVGP_PROF_PSI);
   KufGen kg{h->Zs, h->Xs, h->D, h->M, B, p->sf2};
   EpiPsi e{h->Psi, h->Mp};
-  if (h->tc) tc_psi(h->gt, kg, B, e);
-  else simt_psi(h->gs, kg, B, e);
+  if (!(h->tc && tc_psi(h->gt, kg, B, e))) simt_psi(h->gs, kg, B, e);
 }
 
 void run_w(svgp_handle* h, const WEpi& we) {
   ProfScope ps(h, SVGP_PROF_W);
-  if (h->tc) tc_w(h->gt, lo<bf16>(h->P_lo), we);
-  else simt_w(h->gs, lo<float>(h->P_lo), we);
+  if (!(h->tc && tc_w(h->gt, lo<bf16>(h->P_lo), we))) simt_w(h->gs, h->Pf, we);
 }
 
 // Common prologue: scaled coordinates, Kuu, L copies, log-dets; zero sums.
