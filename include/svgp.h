@@ -51,8 +51,13 @@ typedef enum { SVGP_LIK_GAUSSIAN = 0, SVGP_LIK_BERNOULLI_PROBIT = 1 } svgp_lik;
 
 /* Arithmetic of the dense contractions.  SVGP_FP32: FP32 SIMT FMA kernels
  * (no TF32).  SVGP_BF16: tcgen05 tensor-core kernels, BF16 operands with FP32
- * accumulation in TMEM.  Scalar reductions are FP64 in both. */
-typedef enum { SVGP_FP32 = 0, SVGP_BF16 = 1 } svgp_prec;
+ * accumulation in TMEM (one MMA per product; relative error of the M x M
+ * products grows like 2^-9 * cond(K~)).  SVGP_BF16X3: the same tensor-core
+ * kernels with every M x M operand held as an unevaluated sum hi + lo of two
+ * BF16 matrices and each product formed as hi*hi + hi*lo + lo*hi (three BF16
+ * MMAs, FP32 accumulation; error like 2^-17 * cond(K~)).  Scalar reductions
+ * are FP64 in every mode. */
+typedef enum { SVGP_FP32 = 0, SVGP_BF16 = 1, SVGP_BF16X3 = 2 } svgp_prec;
 
 typedef struct {
   int M;              /* number of inducing points, 1 <= M <= 8192              */

@@ -26,6 +26,7 @@ enum {
   RED_LOGS = 8,       // sum_i log s_i
   RED_SUMA_F = 9,     // sum (G_Kuf o Kuf)
   RED_SUMA_U = 10,    // sum (G_Kuu o Kuu)
+  RED_KW = 11,        // sum_n sum_i Kuf_in W_in = sum_n k_n^T P k_n
   RED_COUNT = 16
 };
 
@@ -37,17 +38,23 @@ struct Tile {
 
 enum Region { REG_FULL = 0, REG_UPPER = 1, REG_LOWER = 2 };
 
-template <class T> __device__ __forceinline__ T to_out(float x);
-template <> __device__ __forceinline__ float to_out<float>(float x) { return x; }
-template <> __device__ __forceinline__ bf16 to_out<bf16>(float x) { return __float2bfloat16_rn(x); }
+// Low-precision operand stored as an unevaluated sum hi + lo of two BF16
+// matrices (lo = bf16(x - hi)); products use hi*hi + hi*lo + lo*hi.
+struct SplitPtr {
+  bf16* hi;
+  bf16* lo;
+};
 
-__device__ __forceinline__ void store_row(float* dst, const float* v, int n) {
-#pragma unroll 4
-  for (int q = 0; q < n; ++q) dst[q] = v[q];
+__device__ __forceinline__ void put(float* p, size_t i, float x) { p[i] = x; }
+__device__ __forceinline__ void put(bf16* p, size_t i, float x) { p[i] = __float2bfloat16_rn(x); }
+__device__ __forceinline__ void put(const SplitPtr& p, size_t i, float x) {
+  bf16 h = __float2bfloat16_rn(x);
+  p.hi[i] = h;
+  p.lo[i] = __float2bfloat16_rn(x - __bfloat162float(h));
 }
 
 // Reduce a per-thread double over the block and add it to *dst (one atomic
-// per block).  Must be called by all threads of the block.
+// per block).  Must be called by all threads of the block (any block shape).
 __device__ __forceinline__ void block_add_double(double x, double* dst) {
   __shared__ double red_buf[32];
   const unsigned tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
@@ -68,31 +75,37 @@ __device__ __forceinline__ void block_add_double(double x, double* dst) {
 }
 
 // ---------------------------------------------------------------------------
-// GEMM epilogues.  A GEMM mainloop computes acc = sum_k A[i,k] B[j,k] for its
-// tile and hands each thread's accumulators to the epilogue one row segment
-// at a time: row(i, j0, v, n) with v[q] = acc(i, j0 + q).  Region predicates
-// (upper/lower) are applied here, per element, so every element of a
-// symmetric result is produced by exactly one tile.  Per-thread FP64 partial
-// sums are reduced by the kernel through reduce().
+// GEMM epilogues.  A GEMM mainloop computes acc(i, j) = sum_k A[i,k] B[j,k]
+// for its tile and hands it to the epilogue one 32 x 32 block per warp:
+//   block(i0, j0, v, vt, lane)   v[q]  = acc(i0 + lane, j0 + q)   (row layout)
+//                                vt[r] = acc(i0 + r, j0 + lane)   (column layout)
+// Direct writes C[i][j] use the column layout (a warp writes 32 consecutive
+// elements of row i0 + r); transposed (mirror) writes C[j][i] use the row
+// layout.  Region predicates are applied per element so that every element
+// of a symmetric result is produced by exactly one tile.  Per-thread FP64
+// partial sums are reduced by the kernel through reduce(), which every
+// thread of the block calls.
 // ---------------------------------------------------------------------------
 
 // Vt = L^T K~ = L^T Kuu + L^T diag(s): the diagonal of S~ is added in FP32 so
 // that it is not lost when Kuu is rounded (Section 2: S~ lower-bounds the
-// eigenvalues of K~).  Lt[i,j] = L[j,i].
-template <class OutT>
+// eigenvalues of K~).  Lt[i,j] = L[j,i].  s == nullptr: plain L^T S.
+template <class OutP>
 struct EpiVt {
-  OutT* out; int ld;
+  OutP out; int ld;
   const float* Lf; const float* s; int M;
   const int* skip_flag;
   __device__ bool skip() const { return skip_flag && *skip_flag; }
   __device__ void begin_tile(int, int) {}
-  __device__ __forceinline__ void row(int i, int j0, const float* v, int n) {
-#pragma unroll 4
-    for (int q = 0; q < n; ++q) {
-      int j = j0 + q;
-      float a = v[q];
-      if (s && i < M && j < M) a = fmaf(Lf[(size_t)j * ld + i], s[j], a);
-      out[(size_t)i * ld + j] = to_out<OutT>(a);
+  __device__ __forceinline__ void block(int i0, int j0, const float (&v)[32], const float (&vt)[32], int lane) {
+    const int j = j0 + lane;
+    const float sj = (s && j < M) ? s[j] : 0.f;
+    const float* Lrow = Lf + (size_t)j * ld + i0;     // L[j][i0 + r] = Lt[i0 + r][j]
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      float a = vt[r];
+      if (s) a = fmaf(Lrow[r], sj, a);
+      put(out, (size_t)(i0 + r) * ld + j, a);
     }
   }
   __device__ void reduce() {}
@@ -103,38 +116,45 @@ struct EpiVt {
 //                lower part; reduces sum (A - I)^2 (Eq. (8)).
 //  MODE 1 (FWD): writes 2I - A1; reduces tr(A1), ||A1||_F^2.
 //  MODE 2 (BWD): writes A + I/2 (for T G T + T/2).
-template <class OutT, int MODE>
+template <class OutP, int MODE>
 struct EpiSym {
-  OutT* out; int ld; int M;
+  OutP out; int ld; int M;
   double* red;
   const int* skip_flag;
-  bool offdiag;
   double p0, p1;
   __device__ bool skip() const { return skip_flag && *skip_flag; }
-  __device__ void begin_tile(int m0, int n0) { p0 = 0.0; p1 = 0.0; offdiag = (m0 != n0); }
-  __device__ __forceinline__ void row(int i, int j0, const float* v, int n) {
-#pragma unroll 4
-    for (int q = 0; q < n; ++q) {
-      int j = j0 + q;
+  __device__ void begin_tile(int, int) { p0 = 0.0; p1 = 0.0; }
+  __device__ __forceinline__ void block(int i0, int j0, const float (&v)[32], const float (&vt)[32], int lane) {
+    if (i0 > j0 + 31) return;                    // block entirely below the diagonal
+    // direct part (i <= j), column layout: i = i0 + r, j = j0 + lane
+    const int j = j0 + lane;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      const int i = i0 + r;
       if (i > j) continue;
-      float a = v[q];
-      bool in = (i < M) && (j < M);
-      double w = (i == j) ? 1.0 : 2.0;
-      if (MODE == 0) {
-        float val = (i < j) ? a : 0.5f * (a - 1.0f);
-        out[(size_t)i * ld + j] = to_out<OutT>(val);
-        if (i < j) out[(size_t)j * ld + i] = to_out<OutT>(0.0f);
-        if (in) { double e = (double)a - (i == j ? 1.0 : 0.0); p0 += w * e * e; }
-      } else if (MODE == 1) {
-        float val = (i == j ? 2.0f : 0.0f) - a;
-        out[(size_t)i * ld + j] = to_out<OutT>(val);
-        if (i < j) out[(size_t)j * ld + i] = to_out<OutT>(val);
-        if (in) { if (i == j) p0 += a; p1 += w * (double)a * a; }
-      } else {
-        float val = a + (i == j ? 0.5f : 0.0f);
-        out[(size_t)i * ld + j] = to_out<OutT>(val);
-        if (i < j) out[(size_t)j * ld + i] = to_out<OutT>(val);
+      const float a = vt[r];
+      float val;
+      if (MODE == 0) val = (i < j) ? a : 0.5f * (a - 1.0f);
+      else if (MODE == 1) val = (i == j ? 2.0f : 0.0f) - a;
+      else val = a + (i == j ? 0.5f : 0.0f);
+      put(out, (size_t)i * ld + j, val);
+      if (i < M && j < M) {
+        const double w = (i == j) ? 1.0 : 2.0;
+        if (MODE == 0) { double e = (double)a - (i == j ? 1.0 : 0.0); p0 += w * e * e; }
+        if (MODE == 1) { if (i == j) p0 += a; p1 += w * (double)a * a; }
       }
+    }
+    // mirror part (j, i) for i < j, row layout: i = i0 + lane, j = j0 + q
+    const int i = i0 + lane;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      const int jj = j0 + q;
+      if (i >= jj) continue;
+      float val;
+      if (MODE == 0) val = 0.0f;
+      else if (MODE == 1) val = -v[q];
+      else val = v[q];
+      put(out, (size_t)jj * ld + i, val);
     }
   }
   __device__ void reduce() {
@@ -145,20 +165,22 @@ struct EpiSym {
 
 // NG update of L (Prop. 1): acc = (L Phi)_ij on the lower region;
 // L_ij <- L_ij - gamma * acc.  The whole launch is skipped when the Frobenius
-// stopping rule (Eq. (8), Section 3.3) fired: r = sqrt(sum/M) < eps.
+// stopping rule (Eq. (8), Section 3.3) fired.
 struct EpiLupd {
   float* Lf; int ld; float* Lout; int M;
   const float* gamma; const int* done;
   __device__ bool skip() const { return *done != 0; }
   __device__ void begin_tile(int, int) {}
-  __device__ __forceinline__ void row(int i, int j0, const float* v, int n) {
-    float g = *gamma;
-#pragma unroll 4
-    for (int q = 0; q < n; ++q) {
-      int j = j0 + q;
+  __device__ __forceinline__ void block(int i0, int j0, const float (&)[32], const float (&vt)[32], int lane) {
+    if (j0 > i0 + 31) return;
+    const float g = *gamma;
+    const int j = j0 + lane;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      const int i = i0 + r;
       if (j > i) continue;
-      size_t o = (size_t)i * ld + j;
-      float Ln = Lf[o] - g * v[q];
+      const size_t o = (size_t)i * ld + j;
+      const float Ln = Lf[o] - g * vt[r];
       Lf[o] = Ln;
       if (i < M && j < M) Lout[(size_t)i * M + j] = Ln;
     }
@@ -167,41 +189,52 @@ struct EpiLupd {
 };
 
 // Plain store of a full result.
-template <class OutT>
+template <class OutP>
 struct EpiStore {
-  OutT* out; int ld;
+  OutP out; int ld;
   const int* skip_flag;
   __device__ bool skip() const { return skip_flag && *skip_flag; }
   __device__ void begin_tile(int, int) {}
-  __device__ __forceinline__ void row(int i, int j0, const float* v, int n) {
-#pragma unroll 4
-    for (int q = 0; q < n; ++q) out[(size_t)i * ld + j0 + q] = to_out<OutT>(v[q]);
+  __device__ __forceinline__ void block(int i0, int j0, const float (&)[32], const float (&vt)[32], int lane) {
+#pragma unroll
+    for (int r = 0; r < 32; ++r) put(out, (size_t)(i0 + r) * ld + j0 + lane, vt[r]);
   }
   __device__ void reduce() {}
 };
 
 // P = Y L^T = L (2I - A1) L^T on the lower region, mirrored; FP32 and
 // low-precision copies; reduces sum_i s_i P_ii and <P, Psi> (Psi may be null).
-template <class OutT>
+template <class OutP>
 struct EpiP {
-  float* Pf; OutT* Plo; int ld; int M;
+  float* Pf; OutP Plo; int ld; int M;
   const float* s; const float* Psi; double* red;
   double p0, p1;
   __device__ bool skip() const { return false; }
   __device__ void begin_tile(int, int) { p0 = 0.0; p1 = 0.0; }
-  __device__ __forceinline__ void row(int i, int j0, const float* v, int n) {
-#pragma unroll 4
-    for (int q = 0; q < n; ++q) {
-      int j = j0 + q;
+  __device__ __forceinline__ void block(int i0, int j0, const float (&v)[32], const float (&vt)[32], int lane) {
+    if (j0 > i0 + 31) return;
+    const int j = j0 + lane;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      const int i = i0 + r;
       if (j > i) continue;
-      float a = v[q];
-      Pf[(size_t)i * ld + j] = a;
-      Plo[(size_t)i * ld + j] = to_out<OutT>(a);
-      if (i != j) { Pf[(size_t)j * ld + i] = a; Plo[(size_t)j * ld + i] = to_out<OutT>(a); }
+      const float a = vt[r];
+      const size_t o = (size_t)i * ld + j;
+      Pf[o] = a;
+      put(Plo, o, a);
       if (i < M && j < M) {
         if (i == j) p0 += (double)s[i] * a;
-        if (Psi) p1 += (i == j ? 1.0 : 2.0) * (double)a * Psi[(size_t)i * ld + j];
+        if (Psi) p1 += (i == j ? 1.0 : 2.0) * (double)a * Psi[o];
       }
+    }
+    const int i = i0 + lane;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      const int jj = j0 + q;
+      if (jj >= i) continue;
+      const size_t o = (size_t)jj * ld + i;
+      Pf[o] = v[q];
+      put(Plo, o, v[q]);
     }
   }
   __device__ void reduce() {
@@ -217,17 +250,29 @@ struct EpiGK {
   const float* Pf; const float* v; const float* s; float* ds;
   __device__ bool skip() const { return false; }
   __device__ void begin_tile(int, int) {}
-  __device__ __forceinline__ void row(int i, int j0, const float* vv, int n) {
-#pragma unroll 4
-    for (int q = 0; q < n; ++q) {
-      int j = j0 + q;
+  __device__ __forceinline__ void block(int i0, int j0, const float (&vr)[32], const float (&vt)[32], int lane) {
+    if (j0 > i0 + 31) return;
+    const int j = j0 + lane;
+    const float vj = j < M ? v[j] : 0.f;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      const int i = i0 + r;
       if (j > i) continue;
-      float gk = -vv[q];
-      float vi = i < M ? v[i] : 0.f, vj = j < M ? v[j] : 0.f;
-      float gu = gk + 0.5f * Pf[(size_t)i * ld + j] - 0.5f * vi * vj;
-      GKuu[(size_t)i * ld + j] = gu;
-      if (i != j) GKuu[(size_t)j * ld + i] = gu;
+      const float gk = -vt[r];
+      const float vi = i < M ? v[i] : 0.f;
+      const size_t o = (size_t)i * ld + j;
+      GKuu[o] = gk + 0.5f * Pf[o] - 0.5f * vi * vj;
       if (i == j && i < M) ds[i] = gk + 0.5f / s[i];
+    }
+    const int i = i0 + lane;
+    const float vi = i < M ? v[i] : 0.f;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      const int jj = j0 + q;
+      if (jj >= i) continue;
+      const size_t o = (size_t)jj * ld + i;      // P symmetric: P[jj][i] = P[i][jj]
+      const float vjj = jj < M ? v[jj] : 0.f;
+      GKuu[o] = -vr[q] + 0.5f * Pf[o] - 0.5f * vi * vjj;
     }
   }
   __device__ void reduce() {}
@@ -238,36 +283,43 @@ struct EpiPsi {
   float* Psi; int ld;
   __device__ bool skip() const { return false; }
   __device__ void begin_tile(int, int) {}
-  __device__ __forceinline__ void row(int i, int j0, const float* v, int n) {
-#pragma unroll 4
-    for (int q = 0; q < n; ++q) {
-      int j = j0 + q;
-      if (i > j) continue;
-      Psi[(size_t)i * ld + j] = v[q];
-      if (i != j) Psi[(size_t)j * ld + i] = v[q];
+  __device__ __forceinline__ void block(int i0, int j0, const float (&v)[32], const float (&vt)[32], int lane) {
+    if (i0 > j0 + 31) return;
+    const int j = j0 + lane;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      const int i = i0 + r;
+      if (i <= j) Psi[(size_t)i * ld + j] = vt[r];
+    }
+    const int i = i0 + lane;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      const int jj = j0 + q;
+      if (i < jj) Psi[(size_t)jj * ld + i] = v[q];
     }
   }
   __device__ void reduce() {}
 };
 
-// Parameters of the Kuf generator: scaled coordinates z~ = z / ell (Mp x D,
-// padded rows zero) and x~ = x / ell (B x D), and log(sf2).  The SE-ARD value
-// is sf2 * exp(-1/2 ||z~_i - x~_n||^2) (per-dimension differences).
+// Parameters of the Kuf generator: scaled coordinates z~ = z / ell (Mp x Dp,
+// padded rows and columns zero) and x~ = x / ell (B x Dp), and sf2.  The
+// SE-ARD value is sf2 * exp(-1/2 ||z~_i - x~_n||^2).
 struct KufGen {
   const float* Zs; const float* Xs; int D; int M; int B; const float* sf2;
 };
 
 // Epilogue data for W = P Kuf (the data part of the backward pass): for each
 // element A_in = c * Kuf_in * (v_i g_n + W_in / noise)  (= G_Kuf o Kuf for the
-// Gaussian likelihood) accumulates per row i
-//   rowacc[i][d]     += A_in (x_nd - z_id)      (d < D)
-//   rowacc[i][D + d] += A_in (x_nd - z_id)^2
+// Gaussian likelihood) accumulates per row i, over scaled differences
+// e_d = x~_nd - z~_id,
+//   rowacc[i][d]     += A_in e_d          (d < D)
+//   rowacc[i][D + d] += A_in e_d^2
 //   rowacc[i][2D]    += A_in
 // and, when colsum != null, colsum[n] += sum_i Kuf_in W_in (for sigma_n^2).
 struct WEpi {
   KufGen gen;
-  const float* Zraw;   // unscaled Z (Mp x D)
-  const float* Xraw;   // unscaled X (B x D)
+  const float* Zraw;
+  const float* Xraw;
   const float* v; const float* g; const float* noise;
   float c;
   float* rowacc;       // M x (2D+1), may be null

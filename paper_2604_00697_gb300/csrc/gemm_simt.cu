@@ -127,25 +127,47 @@ __device__ __forceinline__ void simt_mainloop(LA& la, LB& lb, int m0, int n0, in
   }
 }
 
+
+// Stage the 128x128 accumulator tile in shared memory, then hand it to the
+// epilogue as 32x32 warp blocks (row and column layouts).
 template <class Epi>
-__device__ __forceinline__ void simt_epilogue(Epi& epi, int m0, int n0, float (&acc)[8][8]) {
+__device__ __forceinline__ void simt_epilogue(Epi& epi, int m0, int n0, float (&acc)[8][8], float* T) {
+  const int ldT = SB + 1;
   int t = threadIdx.x;
   int ty = t >> 4, tx = t & 15;
-  epi.begin_tile(m0, n0);
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
-    int i = m0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + r - 4);
-    epi.row(i, n0 + tx * 4, &acc[r][0], 4);
-    epi.row(i, n0 + 64 + tx * 4, &acc[r][4], 4);
+    int ii = r < 4 ? ty * 4 + r : 64 + ty * 4 + r - 4;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      int jj = c < 4 ? tx * 4 + c : 64 + tx * 4 + c - 4;
+      T[ii * ldT + jj] = acc[r][c];
+    }
+  }
+  __syncthreads();
+  epi.begin_tile(m0, n0);
+  const int warp = t >> 5, lane = t & 31;
+  for (int b = warp; b < 16; b += 8) {
+    int bi = b >> 2, bj = b & 3;
+    float v[32], vt[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      v[q] = T[(bi * 32 + lane) * ldT + bj * 32 + q];
+      vt[q] = T[(bi * 32 + q) * ldT + bj * 32 + lane];
+    }
+    epi.block(m0 + bi * 32, n0 + bj * 32, v, vt, lane);
   }
   epi.reduce();
 }
+
+constexpr size_t SIMT_SMEM = sizeof(float) * SB * (SB + 1) > sizeof(Smem) ? sizeof(float) * SB * (SB + 1) : sizeof(Smem);
 
 template <class Epi, class LA, class LB>
 __global__ void __launch_bounds__(256) simt_gemm_tiles(const Tile* __restrict__ tiles, LA la, LB lb,
                                                        Epi epi, int kb_over, int ke_over) {
   if (epi.skip()) return;
-  __shared__ __align__(16) Smem sm;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  Smem& sm = *reinterpret_cast<Smem*>(dyn_smem);
   Tile tl = tiles[blockIdx.x];
   int kb = tl.k0, ke = tl.k1;
   if (ke_over > 0) { kb = kb_over; ke = ke_over; }
@@ -153,7 +175,8 @@ __global__ void __launch_bounds__(256) simt_gemm_tiles(const Tile* __restrict__ 
   lb.init(tl.n0);
   float acc[8][8];
   simt_mainloop(la, lb, tl.m0, tl.n0, kb, ke, sm, acc);
-  simt_epilogue(epi, tl.m0, tl.n0, acc);
+  __syncthreads();
+  simt_epilogue(epi, tl.m0, tl.n0, acc, reinterpret_cast<float*>(dyn_smem));
 }
 
 // W = P Kuf tile (rows i of P, columns n of the batch) with the fused
@@ -257,12 +280,11 @@ __global__ void __launch_bounds__(256) simt_w_kernel(MemLoad la, GenLoad lb, int
   }
 }
 
+
 template <class Epi>
-void launch_mem(const Tile* tiles, int ntiles, const float* A, const float* B, int ld, Epi epi,
-                cudaStream_t st) {
-  MemLoad la{A, ld}, lb{B, ld};
-  svgp_note_launch();
-  simt_gemm_tiles<Epi, MemLoad, MemLoad><<<ntiles, 256, 0, st>>>(tiles, la, lb, epi, 0, 0);
+void set_smem_attr() {
+  cudaFuncSetAttribute(simt_gemm_tiles<Epi, MemLoad, MemLoad>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)SIMT_SMEM);
 }
 
 }  // namespace
@@ -270,37 +292,30 @@ void launch_mem(const Tile* tiles, int ntiles, const float* A, const float* B, i
 // ---------------------------------------------------------------------------
 // Host launchers (FP32 path).  All matrices are Mp x Mp with ld = Mp.
 // ---------------------------------------------------------------------------
-void simt_vt(const GemmCtx& g, const float* Lt, const float* Kuu, EpiVt<float> e) {
-  launch_mem(g.tt_vt, g.nt_vt, Lt, Kuu, g.Mp, e, g.st);
+template <class Epi>
+void simt_gemm(const GemmCtx& g, int tab, const float* A, const float* B, const Epi& e) {
+  MemLoad la{A, g.Mp}, lb{B, g.Mp};
+  svgp_note_launch();
+  simt_gemm_tiles<Epi, MemLoad, MemLoad><<<g.nt[tab], 256, SIMT_SMEM, g.st>>>(g.tt[tab], la, lb, e, 0, 0);
 }
-void simt_sym_ng(const GemmCtx& g, const float* Vt, const float* Lt, EpiSym<float, 0> e) {
-  launch_mem(g.tt_sym_in, g.nt_sym_in, Vt, Lt, g.Mp, e, g.st);
-}
-void simt_sym_fwd(const GemmCtx& g, const float* Vt, const float* Lt, EpiSym<float, 1> e) {
-  launch_mem(g.tt_sym_in, g.nt_sym_in, Vt, Lt, g.Mp, e, g.st);
-}
-void simt_sym_bwd(const GemmCtx& g, const float* Vt, const float* Lt, EpiSym<float, 2> e) {
-  launch_mem(g.tt_sym_in, g.nt_sym_in, Vt, Lt, g.Mp, e, g.st);
-}
-void simt_lupd(const GemmCtx& g, const float* L, const float* PhiT, EpiLupd e) {
-  launch_mem(g.tt_lupd, g.nt_lupd, L, PhiT, g.Mp, e, g.st);
-}
-void simt_ls(const GemmCtx& g, const float* L, const float* S, EpiStore<float> e) {
-  launch_mem(g.tt_ls, g.nt_ls, L, S, g.Mp, e, g.st);
-}
-void simt_p(const GemmCtx& g, const float* Y, const float* L, EpiP<float> e) {
-  launch_mem(g.tt_out, g.nt_out, Y, L, g.Mp, e, g.st);
-}
-void simt_gk(const GemmCtx& g, const float* Y, const float* L, EpiGK e) {
-  launch_mem(g.tt_out, g.nt_out, Y, L, g.Mp, e, g.st);
-}
+
+template void simt_gemm<EpiVt<float*>>(const GemmCtx&, int, const float*, const float*, const EpiVt<float*>&);
+template void simt_gemm<EpiSym<float*, 0>>(const GemmCtx&, int, const float*, const float*, const EpiSym<float*, 0>&);
+template void simt_gemm<EpiSym<float*, 1>>(const GemmCtx&, int, const float*, const float*, const EpiSym<float*, 1>&);
+template void simt_gemm<EpiSym<float*, 2>>(const GemmCtx&, int, const float*, const float*, const EpiSym<float*, 2>&);
+template void simt_gemm<EpiLupd>(const GemmCtx&, int, const float*, const float*, const EpiLupd&);
+template void simt_gemm<EpiStore<float*>>(const GemmCtx&, int, const float*, const float*, const EpiStore<float*>&);
+template void simt_gemm<EpiP<float*>>(const GemmCtx&, int, const float*, const float*, const EpiP<float*>&);
+template void simt_gemm<EpiGK>(const GemmCtx&, int, const float*, const float*, const EpiGK&);
+
 void simt_psi(const GemmCtx& g, const KufGen& kg, int B, EpiPsi e) {
   int Dp = (kg.D + 3) & ~3;
   GenLoad la{kg.Zs, kg.M, kg.Xs, B, Dp, kg.sf2}, lb{kg.Zs, kg.M, kg.Xs, B, Dp, kg.sf2};
   int Bp = (B + SK - 1) / SK * SK;
   svgp_note_launch();
-  simt_gemm_tiles<EpiPsi, GenLoad, GenLoad><<<g.nt_psi, 256, 0, g.st>>>(g.tt_psi, la, lb, e, 0, Bp);
+  simt_gemm_tiles<EpiPsi, GenLoad, GenLoad><<<g.nt[TT_PSI], 256, SIMT_SMEM, g.st>>>(g.tt[TT_PSI], la, lb, e, 0, Bp);
 }
+
 void simt_w(const GemmCtx& g, const float* P, const WEpi& we) {
   int Dp = (we.gen.D + 3) & ~3;
   MemLoad la{P, g.Mp};
@@ -314,4 +329,14 @@ void simt_w(const GemmCtx& g, const float* P, const WEpi& we) {
 
 void simt_init_attributes() {
   cudaFuncSetAttribute(simt_w_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  set_smem_attr<EpiVt<float*>>();
+  set_smem_attr<EpiSym<float*, 0>>();
+  set_smem_attr<EpiSym<float*, 1>>();
+  set_smem_attr<EpiSym<float*, 2>>();
+  set_smem_attr<EpiLupd>();
+  set_smem_attr<EpiStore<float*>>();
+  set_smem_attr<EpiP<float*>>();
+  set_smem_attr<EpiGK>();
+  cudaFuncSetAttribute(simt_gemm_tiles<EpiPsi, GenLoad, GenLoad>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)SIMT_SMEM);
 }

@@ -21,13 +21,17 @@ namespace {
 constexpr int BM = 128;
 constexpr int BN = 128;
 constexpr int BK = 64;                      // one 128-byte swizzle atom of BF16
-constexpr int STAGES = 4;
-constexpr int A_BYTES = BM * BK * 2;        // 16 KB
-constexpr int B_BYTES = BN * BK * 2;        // 16 KB
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int TILE_BYTES = 128 * BK * 2;    // 16 KB per 128 x 64 operand tile
+constexpr int EPI_SCRATCH = 4 * 32 * 33 * 4;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s per wait
 
+// Pipeline geometry per operand precision: NSPLIT = 1 (BF16) or 3 (hi/lo pairs).
+template <int NSPLIT> struct Geo {
+  static constexpr int NT = NSPLIT == 1 ? 2 : 4;                 // tiles per stage
+  static constexpr int STAGES = NSPLIT == 1 ? 4 : 3;
+  static constexpr int STAGE_BYTES = NT * TILE_BYTES;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_SCRATCH + 1024 + 256;
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -120,19 +124,36 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// Epilogue hand-off: the warp's 32 TMEM lanes x 32 columns arrive in the row
+// layout (thread = row); a padded shared-memory transpose gives the column
+// layout; the functor then writes coalesced.
 template <class Epi>
+__device__ __forceinline__ void epi_block(Epi& epi, int i0, int j0, const float (&v)[32], float* scr, int lane) {
+  float vt[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) scr[lane * 33 + q] = v[q];
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 32; ++r) vt[r] = scr[r * 33 + lane];
+  __syncwarp();
+  epi.block(i0, j0, v, vt, lane);
+}
+
+template <class Epi, int NSPLIT>
 __global__ void __launch_bounds__(192, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const __grid_constant__ CUtensorMap tmAl, const __grid_constant__ CUtensorMap tmBl,
                const Tile* __restrict__ tiles, Epi epi, int* errword) {
+  using G = Geo<NSPLIT>;
   if (epi.skip()) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sA = base;
-  unsigned char* sB = base + STAGES * A_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
+  // stage s holds tiles [A_hi, B_hi, (A_lo, B_lo)]
+  float* scratch = reinterpret_cast<float*>(base + G::STAGES * G::STAGE_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + G::STAGES * G::STAGE_BYTES + EPI_SCRATCH);
   // bars[0..S) full, bars[S..2S) empty, bars[2S] tmem_full
-  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars + 2 * STAGES + 1);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * STAGES + 2);
+  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars + 2 * G::STAGES + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * G::STAGES + 2);
   volatile int* consumed = abort_flag + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -140,11 +161,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   const int nk = (tl.k1 - tl.k0) / BK;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < G::STAGES; ++s) {
       mbar_init(smem_u32(&bars[s]), 1);
-      mbar_init(smem_u32(&bars[STAGES + s]), 1);
+      mbar_init(smem_u32(&bars[G::STAGES + s]), 1);
     }
-    mbar_init(smem_u32(&bars[2 * STAGES]), 1);
+    mbar_init(smem_u32(&bars[2 * G::STAGES]), 1);
     *abort_flag = 0;
     *consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -166,37 +187,50 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     // ---------------- TMA producer ----------------
     int issued = 0;
     for (int kb = 0; kb < nk; ++kb) {
-      int s = kb % STAGES;
-      uint32_t ph = (kb / STAGES) & 1;
-      if (!mbar_wait(smem_u32(&bars[STAGES + s]), ph ^ 1)) { *abort_flag = 1; break; }
+      int s = kb % G::STAGES;
+      uint32_t ph = (kb / G::STAGES) & 1;
+      if (!mbar_wait(smem_u32(&bars[G::STAGES + s]), ph ^ 1)) { *abort_flag = 1; break; }
       if (*abort_flag) break;
       uint32_t fb = smem_u32(&bars[s]);
-      mbar_expect_tx(fb, STAGE_BYTES);
+      mbar_expect_tx(fb, G::STAGE_BYTES);
       int k = tl.k0 + kb * BK;
-      tma_load_2d(smem_u32(sA + s * A_BYTES), &tmA, k, tl.m0, fb);
-      tma_load_2d(smem_u32(sB + s * B_BYTES), &tmB, k, tl.n0, fb);
+      unsigned char* st = base + s * G::STAGE_BYTES;
+      tma_load_2d(smem_u32(st), &tmA, k, tl.m0, fb);
+      tma_load_2d(smem_u32(st + TILE_BYTES), &tmB, k, tl.n0, fb);
+      if (NSPLIT == 3) {
+        tma_load_2d(smem_u32(st + 2 * TILE_BYTES), &tmAl, k, tl.m0, fb);
+        tma_load_2d(smem_u32(st + 3 * TILE_BYTES), &tmBl, k, tl.n0, fb);
+      }
       issued = kb + 1;
     }
     // On abort, wait (bounded) for copies that nobody consumed.
     if (*abort_flag) {
-      for (int kb = *consumed; kb < issued; ++kb) mbar_wait(smem_u32(&bars[kb % STAGES]), (kb / STAGES) & 1);
+      for (int kb = *consumed; kb < issued; ++kb) mbar_wait(smem_u32(&bars[kb % G::STAGES]), (kb / G::STAGES) & 1);
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
     for (int kb = 0; kb < nk; ++kb) {
-      int s = kb % STAGES;
-      uint32_t ph = (kb / STAGES) & 1;
+      int s = kb % G::STAGES;
+      uint32_t ph = (kb / G::STAGES) & 1;
       if (!mbar_wait(smem_u32(&bars[s]), ph)) { *abort_flag = 1; break; }
       fence_after();
-      uint64_t ad = sw128_desc(smem_u32(sA + s * A_BYTES));
-      uint64_t bd = sw128_desc(smem_u32(sB + s * B_BYTES));
+      unsigned char* st = base + s * G::STAGE_BYTES;
+      uint64_t ad = sw128_desc(smem_u32(st));
+      uint64_t bd = sw128_desc(smem_u32(st + TILE_BYTES));
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk)
+      for (int kk = 0; kk < BK / 16; ++kk) {
         mma_bf16(tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), (kb | kk) != 0);
-      mma_commit(smem_u32(&bars[STAGES + s]));
+        if (NSPLIT == 3) {
+          uint64_t adl = sw128_desc(smem_u32(st + 2 * TILE_BYTES));
+          uint64_t bdl = sw128_desc(smem_u32(st + 3 * TILE_BYTES));
+          mma_bf16(tmem, ad + (uint64_t)(kk * 2), bdl + (uint64_t)(kk * 2), 1);
+          mma_bf16(tmem, adl + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), 1);
+        }
+      }
+      mma_commit(smem_u32(&bars[G::STAGES + s]));
       *consumed = kb + 1;
     }
-    if (nk > 0) mma_commit(smem_u32(&bars[2 * STAGES]));
+    if (nk > 0) mma_commit(smem_u32(&bars[2 * G::STAGES]));
   }
   __syncwarp();
 
@@ -204,13 +238,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   epi.begin_tile(tl.m0, tl.n0);
   if (warp >= 2) {
     const int quad = warp & 3;
-    const int row = quad * 32 + lane;
     bool ok = true;
     if (nk > 0) {
-      ok = mbar_wait(smem_u32(&bars[2 * STAGES]), 0);
+      ok = mbar_wait(smem_u32(&bars[2 * G::STAGES]), 0);
       fence_after();
     }
     if (!ok) *abort_flag = 1;
+    float* scr = scratch + (warp - 2) * 32 * 33;
     float v[32];
     for (int c = 0; c < BN / 32; ++c) {
       if (nk > 0 && ok) {
@@ -219,7 +253,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 #pragma unroll
         for (int q = 0; q < 32; ++q) v[q] = 0.f;
       }
-      if (ok) epi.row(tl.m0 + row, tl.n0 + c * 32, v, 32);
+      if (ok) epi_block(epi, tl.m0 + quad * 32, tl.n0 + c * 32, v, scr, lane);
     }
   }
   epi.reduce();
@@ -267,19 +301,15 @@ bool make_map(CUtensorMap* m, const void* ptr, int rows, int cols) {
   return r == CUDA_SUCCESS;
 }
 
-
-template <class Epi>
-bool launch(const GemmCtx& g, const Tile* tiles, int ntiles, const bf16* A, const bf16* B, const Epi& e) {
-  CUtensorMap ma, mb;
-  if (!make_map(&ma, A, g.Mp, g.Mp) || !make_map(&mb, B, g.Mp, g.Mp)) return false;
-  svgp_note_launch();
-  tc_gemm_kernel<Epi><<<ntiles, 192, SMEM_BYTES, g.st>>>(ma, mb, tiles, e, g.err);
-  return true;
+template <class Epi, int NSPLIT>
+void set_attr() {
+  cudaFuncSetAttribute(tc_gemm_kernel<Epi, NSPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Geo<NSPLIT>::SMEM);
 }
 
 template <class Epi>
-void set_attr() {
-  cudaFuncSetAttribute(tc_gemm_kernel<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+void set_attr_both() {
+  set_attr<Epi, 1>();
+  set_attr<Epi, 3>();
 }
 
 }  // namespace
@@ -292,41 +322,56 @@ bool tc_available() {
   return major == 10 && minor == 3 && encode_fn() != nullptr;
 }
 
-void tc_init_attributes() {
-  set_attr<EpiVt<bf16>>();
-  set_attr<EpiSym<bf16, 0>>();
-  set_attr<EpiSym<bf16, 1>>();
-  set_attr<EpiSym<bf16, 2>>();
-  set_attr<EpiLupd>();
-  set_attr<EpiStore<bf16>>();
-  set_attr<EpiP<bf16>>();
-  set_attr<EpiGK>();
+template <class Epi>
+bool tc_gemm(const GemmCtx& g, int tab, const bf16* A, const bf16* B, const Epi& e) {
+  const size_t MM = (size_t)g.Mp * g.Mp;
+  CUtensorMap ma, mb, mal, mbl;
+  if (!make_map(&ma, A, g.Mp, g.Mp) || !make_map(&mb, B, g.Mp, g.Mp)) return false;
+  if (g.split) {
+    if (!make_map(&mal, A + MM, g.Mp, g.Mp) || !make_map(&mbl, B + MM, g.Mp, g.Mp)) return false;
+    svgp_note_launch();
+    tc_gemm_kernel<Epi, 3><<<g.nt[tab], 192, Geo<3>::SMEM, g.st>>>(ma, mb, mal, mbl, g.tt[tab], e, g.err);
+  } else {
+    svgp_note_launch();
+    tc_gemm_kernel<Epi, 1><<<g.nt[tab], 192, Geo<1>::SMEM, g.st>>>(ma, mb, ma, mb, g.tt[tab], e, g.err);
+  }
+  return true;
 }
 
-bool tc_vt(const GemmCtx& g, const bf16* Lt, const bf16* K, EpiVt<bf16> e) {
-  return launch(g, g.tt_vt, g.nt_vt, Lt, K, e);
+#define SVGP_TC_INST(...) \
+  template bool tc_gemm<__VA_ARGS__>(const GemmCtx&, int, const bf16*, const bf16*, const __VA_ARGS__&);
+SVGP_TC_INST(EpiVt<bf16*>)
+SVGP_TC_INST(EpiSym<bf16*, 0>)
+SVGP_TC_INST(EpiSym<bf16*, 1>)
+SVGP_TC_INST(EpiSym<bf16*, 2>)
+SVGP_TC_INST(EpiStore<bf16*>)
+SVGP_TC_INST(EpiP<bf16*>)
+SVGP_TC_INST(EpiVt<SplitPtr>)
+SVGP_TC_INST(EpiSym<SplitPtr, 0>)
+SVGP_TC_INST(EpiSym<SplitPtr, 1>)
+SVGP_TC_INST(EpiSym<SplitPtr, 2>)
+SVGP_TC_INST(EpiStore<SplitPtr>)
+SVGP_TC_INST(EpiP<SplitPtr>)
+SVGP_TC_INST(EpiLupd)
+SVGP_TC_INST(EpiGK)
+
+void tc_init_attributes() {
+  set_attr_both<EpiVt<bf16*>>();
+  set_attr_both<EpiSym<bf16*, 0>>();
+  set_attr_both<EpiSym<bf16*, 1>>();
+  set_attr_both<EpiSym<bf16*, 2>>();
+  set_attr_both<EpiStore<bf16*>>();
+  set_attr_both<EpiP<bf16*>>();
+  set_attr_both<EpiVt<SplitPtr>>();
+  set_attr_both<EpiSym<SplitPtr, 0>>();
+  set_attr_both<EpiSym<SplitPtr, 1>>();
+  set_attr_both<EpiSym<SplitPtr, 2>>();
+  set_attr_both<EpiStore<SplitPtr>>();
+  set_attr_both<EpiP<SplitPtr>>();
+  set_attr_both<EpiLupd>();
+  set_attr_both<EpiGK>();
 }
-bool tc_sym_ng(const GemmCtx& g, const bf16* V, const bf16* Lt, EpiSym<bf16, 0> e) {
-  return launch(g, g.tt_sym_in, g.nt_sym_in, V, Lt, e);
-}
-bool tc_sym_fwd(const GemmCtx& g, const bf16* V, const bf16* Lt, EpiSym<bf16, 1> e) {
-  return launch(g, g.tt_sym_in, g.nt_sym_in, V, Lt, e);
-}
-bool tc_sym_bwd(const GemmCtx& g, const bf16* V, const bf16* Lt, EpiSym<bf16, 2> e) {
-  return launch(g, g.tt_sym_in, g.nt_sym_in, V, Lt, e);
-}
-bool tc_lupd(const GemmCtx& g, const bf16* L, const bf16* PhiT, EpiLupd e) {
-  return launch(g, g.tt_lupd, g.nt_lupd, L, PhiT, e);
-}
-bool tc_ls(const GemmCtx& g, const bf16* L, const bf16* S, EpiStore<bf16> e) {
-  return launch(g, g.tt_ls, g.nt_ls, L, S, e);
-}
-bool tc_p(const GemmCtx& g, const bf16* Y, const bf16* L, EpiP<bf16> e) {
-  return launch(g, g.tt_out, g.nt_out, Y, L, e);
-}
-bool tc_gk(const GemmCtx& g, const bf16* Y, const bf16* L, EpiGK e) {
-  return launch(g, g.tt_out, g.nt_out, Y, L, e);
-}
+
 // The Kuf-producer tensor-core kernels are not built yet: callers use the
 // FP32 SIMT kernels for Psi and W.
 bool tc_psi(const GemmCtx&, const KufGen&, int, EpiPsi) { return false; }

@@ -2,62 +2,56 @@
 #pragma once
 #include "common.cuh"
 
-// Tile tables and stream for the M x M GEMMs of one handle.  All matrices are
-// Mp x Mp row-major with ld = Mp (Mp = M rounded up to 128, zero padded).
+// Tile tables of the M x M contractions.  All matrices are Mp x Mp row-major
+// with ld = Mp (Mp = M rounded up to 128, zero padded).  L is lower
+// triangular, Lt = L^T upper triangular; regions and K ranges:
+enum TileTable {
+  TT_VT = 0,      // full,  K [m0, Mp)        Lt S        (S symmetric)
+  TT_SYM_IN = 1,  // upper, K [n0, Mp)        V Lt^T      = L^T S L
+  TT_LUPD = 2,    // lower, K [n0, m0 + BM)   L Phi       (Phi lower)
+  TT_LS = 3,      // full,  K [0, m0 + BM)    L S
+  TT_OUT = 4,     // lower, K [0, n0 + BN)    Y L^T       = L S L^T
+  TT_PSI = 5,     // upper, K given at launch Kuf Kuf^T
+  TT_COUNT = 6
+};
+
 struct GemmCtx {
   int Mp;
   cudaStream_t st;
-  int* err;       // device error word of the handle
-  // Tables (device memory).  Regions and K ranges (L lower, Lt = L^T upper):
-  //  vt     : full,  K [m0, Mp)          Lt S       (S symmetric)
-  //  sym_in : upper, K [n0, Mp)          V Lt^T     = L^T S L
-  //  lupd   : lower, K [n0, m0 + BM)     L Phi      (Phi lower)
-  //  ls     : full,  K [0, m0 + BM)      L S
-  //  out    : lower, K [0, n0 + BN)      Y L^T      = L S L^T
-  //  psi    : upper, K given at launch   Kuf Kuf^T
-  Tile *tt_vt, *tt_sym_in, *tt_lupd, *tt_ls, *tt_out, *tt_psi;
-  int nt_vt, nt_sym_in, nt_lupd, nt_ls, nt_out, nt_psi;
+  int* err;        // device error word of the handle
+  bool split;      // tensor-core operands are hi/lo BF16 pairs (lo at +Mp*Mp)
+  Tile* tt[TT_COUNT];
+  int nt[TT_COUNT];
 };
 
 // Process-wide count of kernel launches issued by the library (svgp_api.cu).
 void svgp_note_launch();
 
-// FP32 SIMT launchers (gemm_simt.cu).
-void simt_vt(const GemmCtx& g, const float* Lt, const float* Kuu, EpiVt<float> e);
-void simt_sym_ng(const GemmCtx& g, const float* Vt, const float* Lt, EpiSym<float, 0> e);
-void simt_sym_fwd(const GemmCtx& g, const float* Vt, const float* Lt, EpiSym<float, 1> e);
-void simt_sym_bwd(const GemmCtx& g, const float* Vt, const float* Lt, EpiSym<float, 2> e);
-void simt_lupd(const GemmCtx& g, const float* L, const float* PhiT, EpiLupd e);
-void simt_ls(const GemmCtx& g, const float* L, const float* S, EpiStore<float> e);
-void simt_p(const GemmCtx& g, const float* Y, const float* L, EpiP<float> e);
-void simt_gk(const GemmCtx& g, const float* Y, const float* L, EpiGK e);
+// FP32 SIMT contractions (gemm_simt.cu): acc = A B^T over table `tab`.
+template <class Epi>
+void simt_gemm(const GemmCtx& g, int tab, const float* A, const float* B, const Epi& e);
 void simt_psi(const GemmCtx& g, const KufGen& kg, int B, EpiPsi e);
 void simt_w(const GemmCtx& g, const float* P, const WEpi& we);
 void simt_init_attributes();
 
-// tcgen05 BF16 launchers (gemm_tc.cu).  Return false when the tensor-core
-// path is not available for this device.
+// tcgen05 BF16 contractions (gemm_tc.cu): acc = A B^T over table `tab`; A and
+// B point at the hi part (lo at +Mp*Mp when g.split).  Return false when the
+// tensor-core path is unavailable.
 bool tc_available();
 void tc_init_attributes();
-bool tc_vt(const GemmCtx& g, const bf16* Lt, const bf16* Kuu, EpiVt<bf16> e);
-bool tc_sym_ng(const GemmCtx& g, const bf16* Vt, const bf16* Lt, EpiSym<bf16, 0> e);
-bool tc_sym_fwd(const GemmCtx& g, const bf16* Vt, const bf16* Lt, EpiSym<bf16, 1> e);
-bool tc_sym_bwd(const GemmCtx& g, const bf16* Vt, const bf16* Lt, EpiSym<bf16, 2> e);
-bool tc_lupd(const GemmCtx& g, const bf16* L, const bf16* PhiT, EpiLupd e);
-bool tc_ls(const GemmCtx& g, const bf16* L, const bf16* S, EpiStore<bf16> e);
-bool tc_p(const GemmCtx& g, const bf16* Y, const bf16* L, EpiP<bf16> e);
-bool tc_gk(const GemmCtx& g, const bf16* Y, const bf16* L, EpiGK e);
+template <class Epi>
+bool tc_gemm(const GemmCtx& g, int tab, const bf16* A, const bf16* B, const Epi& e);
 bool tc_psi(const GemmCtx& g, const KufGen& kg, int B, EpiPsi e);
 bool tc_w(const GemmCtx& g, const bf16* P, const WEpi& we);
 
-// Miscellaneous kernels (kernels_misc.cu).
+// Miscellaneous kernels (kernels_misc.cu).  OutP is float*, bf16* or SplitPtr.
 void k_prep_coords(const float* Z, const float* X, const float* ell, int M, int Mp, int B, int D,
                    float* Zs, float* Xs, cudaStream_t st);
-template <class LoT>
-void k_kuu(const float* Zs, int M, int Mp, int D, const float* sf2, float* Kf, LoT* Klo,
+template <class OutP>
+void k_kuu(const float* Zs, int M, int Mp, int D, const float* sf2, float* Kf, OutP Klo, bool has_lo,
            cudaStream_t st);
-template <class LoT>
-void k_prep_L(const float* Lin, int M, int Mp, float* Lf, LoT* Llo, LoT* Ltlo, double* red,
+template <class OutP>
+void k_prep_L(const float* Lin, int M, int Mp, float* Lf, OutP Llo, OutP Ltlo, double* red,
               cudaStream_t st);
 void k_gemv(const float* A, int Mp, int M, const float* x, float alpha, const float* x2, float beta,
             float* y, const float* dotw, double* dot_out, cudaStream_t st);
@@ -67,9 +61,9 @@ void k_pointwise_gauss(const float* y, const float* mu, const float* noise, int 
                        double* red, cudaStream_t st);
 void k_kg(const float* Zs, const float* Xs, int M, int Mp, int B, int D, const float* sf2,
           const float* g, float* Kg, cudaStream_t st);
-template <class LoT>
+template <class OutP>
 void k_gp_assemble(const float* Kuu, const float* Psi, const float* Kg, const float* m,
-                   const float* w, const float* noise, float c, int M, int Mp, LoT* out,
+                   const float* w, const float* noise, float c, int M, int Mp, OutP out,
                    cudaStream_t st);
 void k_kuu_bwd(const float* GKuu, const float* Kuu, const float* Zs, int M, int Mp, int D,
                float* rowacc_u, double* red, cudaStream_t st);

@@ -34,9 +34,9 @@ __global__ void prep_coords_kernel(const float* __restrict__ Z, const float* __r
 
 // Kuu = sf2 exp(-1/2 ||z~_i - z~_j||^2) (per-dimension differences), exact
 // sf2 on the diagonal, zero padding.  32x32 tiles, points staged in smem.
-template <class LoT>
+template <class OutP>
 __global__ void kuu_kernel(const float* __restrict__ Zs, int M, int Mp, int D,
-                           const float* __restrict__ sf2p, float* __restrict__ Kf, LoT* __restrict__ Klo) {
+                           const float* __restrict__ sf2p, float* __restrict__ Kf, OutP Klo, bool has_lo) {
   __shared__ float zi[32][SVGP_MAXD + 1], zj[32][SVGP_MAXD + 1];
   int Dp = (D + 3) & ~3;
   int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
@@ -60,15 +60,15 @@ __global__ void kuu_kernel(const float* __restrict__ Zs, int M, int Mp, int D,
       }
     }
     Kf[(size_t)i * Mp + j] = val;
-    if (Klo) Klo[(size_t)i * Mp + j] = to_out<LoT>(val);
+    if (has_lo) put(Klo, (size_t)i * Mp + j, val);
   }
 }
 
 // L (M x M, ld M, lower) -> Lf (Mp x Mp FP32), Llo, Ltlo = Llo^T (operand
 // precision); strictly-upper entries forced to zero; sum log|L_ii|.
-template <class LoT>
+template <class OutP>
 __global__ void prep_L_kernel(const float* __restrict__ Lin, int M, int Mp, float* __restrict__ Lf,
-                              LoT* __restrict__ Llo, LoT* __restrict__ Ltlo, double* red) {
+                              OutP Llo, OutP Ltlo, double* red) {
   __shared__ float tile[32][33];
   int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
   int tx = threadIdx.x;
@@ -77,16 +77,14 @@ __global__ void prep_L_kernel(const float* __restrict__ Lin, int M, int Mp, floa
     int i = i0 + ty, j = j0 + tx;
     float val = (i < M && j < M && j <= i) ? Lin[(size_t)i * M + j] : 0.f;
     Lf[(size_t)i * Mp + j] = val;
-    if (Llo) Llo[(size_t)i * Mp + j] = to_out<LoT>(val);
+    put(Llo, (size_t)i * Mp + j, val);
     tile[ty][tx] = val;
     if (i == j && i < M) ld += log(fabs((double)val));
   }
   __syncthreads();
-  if (Ltlo) {
-    for (int ty = threadIdx.y; ty < 32; ty += blockDim.y) {
-      // Ltlo[j0 + ty][i0 + tx] = L[i0 + tx][j0 + ty]
-      Ltlo[(size_t)(j0 + ty) * Mp + i0 + tx] = to_out<LoT>(tile[tx][ty]);
-    }
+  for (int ty = threadIdx.y; ty < 32; ty += blockDim.y) {
+    // Lt[j0 + ty][i0 + tx] = L[i0 + tx][j0 + ty]
+    put(Ltlo, (size_t)(j0 + ty) * Mp + i0 + tx, tile[tx][ty]);
   }
   if (blockIdx.x == blockIdx.y) block_add_double(ld, red + RED_LOGDETL);
 }
@@ -202,11 +200,11 @@ __global__ void kg_kernel(const float* __restrict__ Zs, const float* __restrict_
 
 // Symmetrised G_P = c/2 (Kg m^T + m Kg^T) + c/(2 noise) Psi + Kuu/2
 //                   - (m w^T + w m^T)/2, zero padding.
-template <class LoT>
+template <class OutP>
 __global__ void gp_assemble_kernel(const float* __restrict__ Kuu, const float* __restrict__ Psi,
                                    const float* __restrict__ Kg, const float* __restrict__ m,
                                    const float* __restrict__ w, const float* __restrict__ noise, float c,
-                                   int M, int Mp, LoT* __restrict__ out) {
+                                   int M, int Mp, OutP out) {
   float cn = c * 0.5f / *noise;
   size_t tot = (size_t)Mp * Mp;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
@@ -216,7 +214,7 @@ __global__ void gp_assemble_kernel(const float* __restrict__ Kuu, const float* _
       val = 0.5f * c * (Kg[i] * m[j] + m[i] * Kg[j]) + cn * Psi[e] + 0.5f * Kuu[e]
             - 0.5f * (m[i] * w[j] + w[i] * m[j]);
     }
-    out[e] = to_out<LoT>(val);
+    put(out, e, val);
   }
 }
 
@@ -392,23 +390,26 @@ void k_prep_coords(const float* Z, const float* X, const float* ell, int M, int 
   prep_coords_kernel<<<grid, 256, 0, st>>>(Z, X, ell, M, Mp, B, D, Zs, Xs);
 }
 
-template <class LoT>
-void k_kuu(const float* Zs, int M, int Mp, int D, const float* sf2, float* Kf, LoT* Klo, cudaStream_t st) {
+template <class OutP>
+void k_kuu(const float* Zs, int M, int Mp, int D, const float* sf2, float* Kf, OutP Klo, bool has_lo,
+           cudaStream_t st) {
   dim3 grid(Mp / 32, Mp / 32), blk(32, 8);
   svgp_note_launch();
-  kuu_kernel<LoT><<<grid, blk, 0, st>>>(Zs, M, Mp, D, sf2, Kf, Klo);
+  kuu_kernel<OutP><<<grid, blk, 0, st>>>(Zs, M, Mp, D, sf2, Kf, Klo, has_lo);
 }
-template void k_kuu<float>(const float*, int, int, int, const float*, float*, float*, cudaStream_t);
-template void k_kuu<bf16>(const float*, int, int, int, const float*, float*, bf16*, cudaStream_t);
+template void k_kuu<float*>(const float*, int, int, int, const float*, float*, float*, bool, cudaStream_t);
+template void k_kuu<bf16*>(const float*, int, int, int, const float*, float*, bf16*, bool, cudaStream_t);
+template void k_kuu<SplitPtr>(const float*, int, int, int, const float*, float*, SplitPtr, bool, cudaStream_t);
 
-template <class LoT>
-void k_prep_L(const float* Lin, int M, int Mp, float* Lf, LoT* Llo, LoT* Ltlo, double* red, cudaStream_t st) {
+template <class OutP>
+void k_prep_L(const float* Lin, int M, int Mp, float* Lf, OutP Llo, OutP Ltlo, double* red, cudaStream_t st) {
   dim3 grid(Mp / 32, Mp / 32), blk(32, 8);
   svgp_note_launch();
-  prep_L_kernel<LoT><<<grid, blk, 0, st>>>(Lin, M, Mp, Lf, Llo, Ltlo, red);
+  prep_L_kernel<OutP><<<grid, blk, 0, st>>>(Lin, M, Mp, Lf, Llo, Ltlo, red);
 }
-template void k_prep_L<float>(const float*, int, int, float*, float*, float*, double*, cudaStream_t);
-template void k_prep_L<bf16>(const float*, int, int, float*, bf16*, bf16*, double*, cudaStream_t);
+template void k_prep_L<float*>(const float*, int, int, float*, float*, float*, double*, cudaStream_t);
+template void k_prep_L<bf16*>(const float*, int, int, float*, bf16*, bf16*, double*, cudaStream_t);
+template void k_prep_L<SplitPtr>(const float*, int, int, float*, SplitPtr, SplitPtr, double*, cudaStream_t);
 
 void k_gemv(const float* A, int Mp, int M, const float* x, float alpha, const float* x2, float beta,
             float* y, const float* dotw, double* dot_out, cudaStream_t st) {
@@ -441,19 +442,21 @@ void k_kg(const float* Zs, const float* Xs, int M, int Mp, int B, int D, const f
   kg_kernel<<<grid, 128, 0, st>>>(Zs, Xs, M, B, D, sf2, g, Kg);
 }
 
-template <class LoT>
+template <class OutP>
 void k_gp_assemble(const float* Kuu, const float* Psi, const float* Kg, const float* m, const float* w,
-                   const float* noise, float c, int M, int Mp, LoT* out, cudaStream_t st) {
+                   const float* noise, float c, int M, int Mp, OutP out, cudaStream_t st) {
   size_t tot = (size_t)Mp * Mp;
   int grid = (int)((tot + 255) / 256);
   if (grid > 152 * 16) grid = 152 * 16;
   svgp_note_launch();
-  gp_assemble_kernel<LoT><<<grid, 256, 0, st>>>(Kuu, Psi, Kg, m, w, noise, c, M, Mp, out);
+  gp_assemble_kernel<OutP><<<grid, 256, 0, st>>>(Kuu, Psi, Kg, m, w, noise, c, M, Mp, out);
 }
-template void k_gp_assemble<float>(const float*, const float*, const float*, const float*, const float*,
-                                   const float*, float, int, int, float*, cudaStream_t);
-template void k_gp_assemble<bf16>(const float*, const float*, const float*, const float*, const float*,
-                                  const float*, float, int, int, bf16*, cudaStream_t);
+template void k_gp_assemble<float*>(const float*, const float*, const float*, const float*, const float*,
+                                    const float*, float, int, int, float*, cudaStream_t);
+template void k_gp_assemble<bf16*>(const float*, const float*, const float*, const float*, const float*,
+                                   const float*, float, int, int, bf16*, cudaStream_t);
+template void k_gp_assemble<SplitPtr>(const float*, const float*, const float*, const float*, const float*,
+                                      const float*, float, int, int, SplitPtr, cudaStream_t);
 
 void k_kuu_bwd(const float* GKuu, const float* Kuu, const float* Zs, int M, int Mp, int D,
                float* rowacc_u, double* red, cudaStream_t st) {

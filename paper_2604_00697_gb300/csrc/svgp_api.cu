@@ -44,8 +44,8 @@ std::vector<Tile> make_tiles(int Mp, int BM, int BN, int region, int rule) {
 
 struct svgp_handle {
   svgp_config cfg;
-  int M, Mp, D, Dp, Bmax, lo_bytes;
-  bool tc;
+  int M, Mp, D, Dp, Bmax;
+  int mode;       // MODE_F32 / MODE_BF16 / MODE_SPLIT (svgp_prec)
   cudaStream_t st;
   char err[512];
   // matrices
@@ -101,12 +101,13 @@ bool build_ctx(svgp_handle* h, GemmCtx& g, int BM, int BN) {
   g.Mp = Mp;
   g.st = h->st;
   g.err = h->errword;
-  return upload_tiles(h, make_tiles(Mp, BM, BN, REG_FULL, K_M0_END), &g.tt_vt, &g.nt_vt) &&
-         upload_tiles(h, make_tiles(Mp, BM, BN, REG_UPPER, K_N0_END), &g.tt_sym_in, &g.nt_sym_in) &&
-         upload_tiles(h, make_tiles(Mp, BM, BN, REG_LOWER, K_N0_M1), &g.tt_lupd, &g.nt_lupd) &&
-         upload_tiles(h, make_tiles(Mp, BM, BN, REG_FULL, K_0_M1), &g.tt_ls, &g.nt_ls) &&
-         upload_tiles(h, make_tiles(Mp, BM, BN, REG_LOWER, K_0_N1), &g.tt_out, &g.nt_out) &&
-         upload_tiles(h, make_tiles(Mp, BM, BN, REG_UPPER, K_ALL), &g.tt_psi, &g.nt_psi);
+  g.split = h->mode == 2;
+  return upload_tiles(h, make_tiles(Mp, BM, BN, REG_FULL, K_M0_END), &g.tt[TT_VT], &g.nt[TT_VT]) &&
+         upload_tiles(h, make_tiles(Mp, BM, BN, REG_UPPER, K_N0_END), &g.tt[TT_SYM_IN], &g.nt[TT_SYM_IN]) &&
+         upload_tiles(h, make_tiles(Mp, BM, BN, REG_LOWER, K_N0_M1), &g.tt[TT_LUPD], &g.nt[TT_LUPD]) &&
+         upload_tiles(h, make_tiles(Mp, BM, BN, REG_FULL, K_0_M1), &g.tt[TT_LS], &g.nt[TT_LS]) &&
+         upload_tiles(h, make_tiles(Mp, BM, BN, REG_LOWER, K_0_N1), &g.tt[TT_OUT], &g.nt[TT_OUT]) &&
+         upload_tiles(h, make_tiles(Mp, BM, BN, REG_UPPER, K_ALL), &g.tt[TT_PSI], &g.nt[TT_PSI]);
 }
 
 bool valid_params(const svgp_params* p) {
@@ -134,64 +135,85 @@ struct ProfScope {
 // ---------------------------------------------------------------------------
 // Precision dispatch of the M x M GEMM chain.
 // ---------------------------------------------------------------------------
-template <class T> T* lo(void* p) { return reinterpret_cast<T*>(p); }
+enum Mode { MODE_F32 = 0, MODE_BF16 = 1, MODE_SPLIT = 2 };
 
-void run_vt(svgp_handle* h, const void* B, const float* s, const int* skip) {
+float* F(void* p) { return reinterpret_cast<float*>(p); }
+bf16* H(void* p) { return reinterpret_cast<bf16*>(p); }
+SplitPtr SP(const svgp_handle* h, void* p) {
+  return SplitPtr{reinterpret_cast<bf16*>(p), reinterpret_cast<bf16*>(p) + (size_t)h->Mp * h->Mp};
+}
+
+// Calls simt_gemm / tc_gemm with the functor built for the handle's mode.
+#define DISPATCH(h, tab, A, B, MAKE)                                                         \
+  do {                                                                                       \
+    if ((h)->mode == MODE_F32) simt_gemm((h)->gs, tab, F(A), F(B), MAKE(float*, F));         \
+    else if ((h)->mode == MODE_BF16) tc_gemm((h)->gt, tab, H(A), H(B), MAKE(bf16*, H));      \
+    else tc_gemm((h)->gt, tab, H(A), H(B), MAKE(SplitPtr, SPH));                             \
+  } while (0)
+
+void run_vt(svgp_handle* h, void* B, const float* s, const int* skip) {
   ProfScope ps(h, SVGP_PROF_VT);
-  int Mp = h->Mp;
-  if (h->tc) {
-    EpiVt<bf16> e{lo<bf16>(h->V), Mp, h->Lf, s, h->M, skip};
-    tc_vt(h->gt, lo<bf16>(h->Lt_lo), (const bf16*)B, e);
-  } else {
-    EpiVt<float> e{lo<float>(h->V), Mp, h->Lf, s, h->M, skip};
-    simt_vt(h->gs, lo<float>(h->Lt_lo), (const float*)B, e);
-  }
+  auto SPH = [h](void* p) { return SP(h, p); };
+#define MK(T, CV) EpiVt<T>{CV(h->V), h->Mp, h->Lf, s, h->M, skip}
+  DISPATCH(h, TT_VT, h->Lt_lo, B, MK);
+#undef MK
 }
 
 template <int MODE>
 void run_sym(svgp_handle* h, const int* skip) {
   ProfScope ps(h, SVGP_PROF_SYM);
-  int Mp = h->Mp;
-  if (h->tc) {
-    EpiSym<bf16, MODE> e{lo<bf16>(h->S), Mp, h->M, h->red, skip};
-    if constexpr (MODE == 0) tc_sym_ng(h->gt, lo<bf16>(h->V), lo<bf16>(h->Lt_lo), e);
-    if constexpr (MODE == 1) tc_sym_fwd(h->gt, lo<bf16>(h->V), lo<bf16>(h->Lt_lo), e);
-    if constexpr (MODE == 2) tc_sym_bwd(h->gt, lo<bf16>(h->V), lo<bf16>(h->Lt_lo), e);
-  } else {
-    EpiSym<float, MODE> e{lo<float>(h->S), Mp, h->M, h->red, skip};
-    if constexpr (MODE == 0) simt_sym_ng(h->gs, lo<float>(h->V), lo<float>(h->Lt_lo), e);
-    if constexpr (MODE == 1) simt_sym_fwd(h->gs, lo<float>(h->V), lo<float>(h->Lt_lo), e);
-    if constexpr (MODE == 2) simt_sym_bwd(h->gs, lo<float>(h->V), lo<float>(h->Lt_lo), e);
-  }
+  auto SPH = [h](void* p) { return SP(h, p); };
+#define MK(T, CV) EpiSym<T, MODE>{CV(h->S), h->Mp, h->M, h->red, skip}
+  DISPATCH(h, TT_SYM_IN, h->V, h->Lt_lo, MK);
+#undef MK
 }
 
 void run_ls(svgp_handle* h) {  // Y = L S
   ProfScope ps(h, SVGP_PROF_LS);
-  if (h->tc) tc_ls(h->gt, lo<bf16>(h->L_lo), lo<bf16>(h->S), EpiStore<bf16>{lo<bf16>(h->Y), h->Mp, nullptr});
-  else simt_ls(h->gs, lo<float>(h->L_lo), lo<float>(h->S), EpiStore<float>{lo<float>(h->Y), h->Mp, nullptr});
+  auto SPH = [h](void* p) { return SP(h, p); };
+#define MK(T, CV) EpiStore<T>{CV(h->Y), h->Mp, nullptr}
+  DISPATCH(h, TT_LS, h->L_lo, h->S, MK);
+#undef MK
 }
 
-void run_p(svgp_handle* h, const float* s, const float* Psi) {
+void run_p(svgp_handle* h, const float* s, const float* Psi) {  // P = Y L^T
   ProfScope ps(h, SVGP_PROF_OUT);
-  if (h->tc) {
-    EpiP<bf16> e{h->Pf, lo<bf16>(h->P_lo), h->Mp, h->M, s, Psi, h->red};
-    tc_p(h->gt, lo<bf16>(h->Y), lo<bf16>(h->L_lo), e);
-  } else {
-    EpiP<float> e{h->Pf, lo<float>(h->P_lo), h->Mp, h->M, s, Psi, h->red};
-    simt_p(h->gs, lo<float>(h->Y), lo<float>(h->L_lo), e);
-  }
+  auto SPH = [h](void* p) { return SP(h, p); };
+#define MK(T, CV) EpiP<T>{h->Pf, CV(h->P_lo), h->Mp, h->M, s, Psi, h->red}
+  DISPATCH(h, TT_OUT, h->Y, h->L_lo, MK);
+#undef MK
+}
+
+void run_gk(svgp_handle* h, const float* s, float* ds) {  // G_K~ = -Y L^T
+  ProfScope ps(h, SVGP_PROF_OUT);
+  EpiGK e{h->GKuu, h->Mp, h->M, h->Pf, h->v, s, ds};
+  if (h->mode == MODE_F32) simt_gemm(h->gs, TT_OUT, F(h->Y), F(h->L_lo), e);
+  else tc_gemm(h->gt, TT_OUT, H(h->Y), H(h->L_lo), e);
+}
+
+void run_lupd(svgp_handle* h, float* L_inout, const float* gamma) {  // L <- L - gamma L Phi
+  ProfScope ps(h, SVGP_PROF_LUPD);
+  EpiLupd e{h->Lf, h->Mp, L_inout, h->M, gamma, h->done};
+  if (h->mode == MODE_F32) simt_gemm(h->gs, TT_LUPD, F(h->L_lo), F(h->S), e);
+  else tc_gemm(h->gt, TT_LUPD, H(h->L_lo), H(h->S), e);
 }
 
 void run_psi(svgp_handle* h, const svgp_params* p, int B) {
   ProfScope ps(h, SVGP_PROF_PSI);
   KufGen kg{h->Zs, h->Xs, h->D, h->M, B, p->sf2};
   EpiPsi e{h->Psi, h->Mp};
-  if (!(h->tc && tc_psi(h->gt, kg, B, e))) simt_psi(h->gs, kg, B, e);
+  if (!(h->mode != MODE_F32 && tc_psi(h->gt, kg, B, e))) simt_psi(h->gs, kg, B, e);
 }
 
 void run_w(svgp_handle* h, const WEpi& we) {
   ProfScope ps(h, SVGP_PROF_W);
-  if (!(h->tc && tc_w(h->gt, lo<bf16>(h->P_lo), we))) simt_w(h->gs, h->Pf, we);
+  if (!(h->mode != MODE_F32 && tc_w(h->gt, H(h->P_lo), we))) simt_w(h->gs, h->Pf, we);
+}
+
+void prep_L(svgp_handle* h, const float* Lin, double* red) {
+  if (h->mode == MODE_F32) k_prep_L(Lin, h->M, h->Mp, h->Lf, F(h->L_lo), F(h->Lt_lo), red, h->st);
+  else if (h->mode == MODE_BF16) k_prep_L(Lin, h->M, h->Mp, h->Lf, H(h->L_lo), H(h->Lt_lo), red, h->st);
+  else k_prep_L(Lin, h->M, h->Mp, h->Lf, SP(h, h->L_lo), SP(h, h->Lt_lo), red, h->st);
 }
 
 // Common prologue: scaled coordinates, Kuu, L copies, log-dets; zero sums.
@@ -200,21 +222,17 @@ void prologue(svgp_handle* h, const svgp_params* p, const float* X, int B, const
   cudaMemsetAsync(h->red, 0, sizeof(double) * RED_COUNT, st);
   cudaMemsetAsync(h->acc_ell, 0, sizeof(double) * SVGP_MAXD, st);
   k_prep_coords(p->Z, X, p->ell, h->M, h->Mp, X ? B : 0, h->D, h->Zs, h->Xs, st);
-  if (h->tc) {
-    k_kuu<bf16>(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, lo<bf16>(h->Kuu_lo), st);
-    k_prep_L<bf16>(Lin, h->M, h->Mp, h->Lf, lo<bf16>(h->L_lo), lo<bf16>(h->Lt_lo), h->red, st);
-  } else {
-    k_kuu<float>(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, (float*)nullptr, st);
-    k_prep_L<float>(Lin, h->M, h->Mp, h->Lf, lo<float>(h->L_lo), lo<float>(h->Lt_lo), h->red, st);
-  }
+  if (h->mode == MODE_F32) k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, (float*)nullptr, false, st);
+  else if (h->mode == MODE_BF16) k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, H(h->Kuu_lo), true, st);
+  else k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, SP(h, h->Kuu_lo), true, st);
+  prep_L(h, Lin, h->red);
 }
 
 // Forward pass of Eq. (7) up to the per-point Gaussian terms.
 void forward(svgp_handle* h, const svgp_params* p, const svgp_batch* b, bool psi) {
   cudaStream_t st = h->st;
-  const void* Kb = h->tc ? h->Kuu_lo : (const void*)h->Kuu_f;
   k_logs(p->s, h->M, h->red, st);
-  run_vt(h, Kb, p->s, nullptr);          // Vt = L^T K~
+  run_vt(h, h->Kuu_lo, p->s, nullptr);   // Vt = L^T K~
   run_sym<1>(h, nullptr);                // A1 = L^T K~ L ; S = 2I - A1 ; tr, Frobenius
   if (psi) run_psi(h, p, b->B);          // Psi = Kuf Kuf^T (Kuf generated on chip)
   run_ls(h);                             // Y = L (2I - A1)
@@ -261,8 +279,8 @@ svgp_status svgp_create(const svgp_config* cfg, svgp_handle** out) {
       cfg->B_max > (1 << 22))
     return SVGP_ERR_INVALID_ARG;
   if (cfg->lik != SVGP_LIK_GAUSSIAN) return SVGP_ERR_UNSUPPORTED;
-  if (cfg->prec != SVGP_FP32 && cfg->prec != SVGP_BF16) return SVGP_ERR_INVALID_ARG;
-  if (cfg->prec == SVGP_BF16 && !tc_available()) return SVGP_ERR_UNSUPPORTED;
+  if (cfg->prec != SVGP_FP32 && cfg->prec != SVGP_BF16 && cfg->prec != SVGP_BF16X3) return SVGP_ERR_INVALID_ARG;
+  if (cfg->prec != SVGP_FP32 && !tc_available()) return SVGP_ERR_UNSUPPORTED;
   svgp_handle* h = new svgp_handle();
   h->cfg = *cfg;
   h->M = cfg->M;
@@ -270,14 +288,14 @@ svgp_status svgp_create(const svgp_config* cfg, svgp_handle** out) {
   h->D = cfg->D;
   h->Dp = (cfg->D + 3) & ~3;
   h->Bmax = cfg->B_max;
-  h->tc = cfg->prec == SVGP_BF16;
-  h->lo_bytes = h->tc ? 2 : 4;
+  h->mode = cfg->prec;   // svgp_prec values coincide with MODE_*
   h->st = (cudaStream_t)cfg->cuda_stream;
   h->err[0] = 0;
   h->prof = false;
   size_t M2 = (size_t)h->Mp * h->Mp;
   size_t Bp = (size_t)(cfg->B_max + 127) / 128 * 128;
-  size_t lob = M2 * h->lo_bytes;
+  // operand copies: FP32 (SIMT), BF16, or BF16 hi followed by BF16 lo
+  size_t lob = M2 * (h->mode == MODE_F32 ? 4 : h->mode == MODE_BF16 ? 2 : 4);
   int W = 2 * cfg->D + 1;
   bool ok = dalloc(h, &h->Kuu_f, M2 * 4) && dalloc(h, &h->Lf, M2 * 4) && dalloc(h, &h->Pf, M2 * 4) &&
             dalloc(h, &h->Psi, M2 * 4) && dalloc(h, &h->GKuu, M2 * 4) && dalloc(h, &h->L_lo, lob) &&
@@ -292,11 +310,11 @@ svgp_status svgp_create(const svgp_config* cfg, svgp_handle** out) {
             dalloc(h, &h->red, sizeof(double) * RED_COUNT) && dalloc(h, &h->acc_ell, sizeof(double) * SVGP_MAXD) &&
             dalloc(h, &h->resid_tmp, sizeof(double)) && dalloc(h, &h->errword, sizeof(int)) &&
             dalloc(h, &h->done, sizeof(int)) && dalloc(h, &h->iters_tmp, sizeof(int));
-  if (ok && h->tc) ok = dalloc(h, &h->Kuu_lo, lob) && dalloc(h, &h->P_lo, lob);
-  if (ok && !h->tc) { h->Kuu_lo = h->Kuu_f; h->P_lo = h->Pf; }
+  if (ok && h->mode != MODE_F32) ok = dalloc(h, &h->Kuu_lo, lob) && dalloc(h, &h->P_lo, lob);
+  if (ok && h->mode == MODE_F32) { h->Kuu_lo = h->Kuu_f; h->P_lo = h->Pf; }
   if (ok) ok = build_ctx(h, h->gs, 128, 128) && build_ctx(h, h->gt, 128, 128);
   simt_init_attributes();
-  if (h->tc) tc_init_attributes();
+  if (h->mode != MODE_F32) tc_init_attributes();
   if (!ok) {
     svgp_destroy(h);
     return SVGP_ERR_OOM;
@@ -388,18 +406,13 @@ svgp_status svgp_backward(svgp_handle* h, const svgp_params* p, const svgp_batch
   forward(h, p, b, true);
   // backward, T fixed (Section 3.1)
   k_kg(h->Zs, h->Xs, M, Mp, b->B, h->D, p->sf2, h->g, h->Kg, st);                      // Kuf g
-  if (h->tc) k_gp_assemble<bf16>(h->Kuu_f, h->Psi, h->Kg, p->m, h->w, p->noise, c, M, Mp, lo<bf16>(h->GP_lo), st);
-  else k_gp_assemble<float>(h->Kuu_f, h->Psi, h->Kg, p->m, h->w, p->noise, c, M, Mp, lo<float>(h->GP_lo), st);
+  if (h->mode == MODE_F32) k_gp_assemble(h->Kuu_f, h->Psi, h->Kg, p->m, h->w, p->noise, c, M, Mp, F(h->GP_lo), st);
+  else if (h->mode == MODE_BF16) k_gp_assemble(h->Kuu_f, h->Psi, h->Kg, p->m, h->w, p->noise, c, M, Mp, H(h->GP_lo), st);
+  else k_gp_assemble(h->Kuu_f, h->Psi, h->Kg, p->m, h->w, p->noise, c, M, Mp, SP(h, h->GP_lo), st);
   run_vt(h, h->GP_lo, nullptr, nullptr); // X1t = L^T G_P
   run_sym<2>(h, nullptr);                // S = L^T G_P L + I/2
   run_ls(h);                             // Y = L S
-  if (ProfScope ps(h, SVGP_PROF_OUT); h->tc) {  // G_K~ = -Y L^T -> G_Kuu, ds
-    EpiGK e{h->GKuu, Mp, M, h->Pf, h->v, p->s, gr->ds};
-    tc_gk(h->gt, lo<bf16>(h->Y), lo<bf16>(h->L_lo), e);
-  } else {
-    EpiGK e{h->GKuu, Mp, M, h->Pf, h->v, p->s, gr->ds};
-    simt_gk(h->gs, lo<float>(h->Y), lo<float>(h->L_lo), e);
-  }
+  run_gk(h, p->s, gr->ds);               // G_K~ = -Y L^T -> G_Kuu, ds
   cudaMemsetAsync(h->rowacc_f, 0, sizeof(float) * Mp * W, st);
   cudaMemsetAsync(h->rowacc_u, 0, sizeof(float) * Mp * W, st);
   WEpi we{KufGen{h->Zs, h->Xs, h->D, M, b->B, p->sf2}, nullptr, nullptr, h->v, h->g, p->noise, c,
@@ -425,22 +438,13 @@ svgp_status svgp_ng_update_T(svgp_handle* h, const svgp_params* p, float* L_inou
   cudaMemsetAsync(h->done, 0, sizeof(int), st);
   cudaMemsetAsync(iters, 0, sizeof(int), st);
   prologue(h, p, nullptr, 0, L_inout);
-  const void* Kb = h->tc ? h->Kuu_lo : (const void*)h->Kuu_f;
   for (int t = 0; t < max_iters; ++t) {
     cudaMemsetAsync(h->red + RED_NG_RESID, 0, sizeof(double), st);
-    run_vt(h, Kb, p->s, h->done);                // Vt = L^T K~ (skipped once converged)
+    run_vt(h, h->Kuu_lo, p->s, h->done);         // Vt = L^T K~ (skipped once converged)
     run_sym<0>(h, h->done);                      // A, Phi^T, ||A - I||^2
     k_ng_check(h->red, h->M, eps, h->done, iters, resid, st);   // Eq. (8) stopping rule
-    EpiLupd e{h->Lf, h->Mp, L_inout, h->M, gamma_dev + t, h->done};
-    {
-      ProfScope ps(h, SVGP_PROF_LUPD);           // L <- L - gamma L Phi  (Prop. 1)
-      if (h->tc) tc_lupd(h->gt, lo<bf16>(h->L_lo), lo<bf16>(h->S), e);
-      else simt_lupd(h->gs, lo<float>(h->L_lo), lo<float>(h->S), e);
-    }
-    if (t + 1 < max_iters) {
-      if (h->tc) k_prep_L<bf16>(L_inout, h->M, h->Mp, h->Lf, lo<bf16>(h->L_lo), lo<bf16>(h->Lt_lo), h->red + RED_COUNT - 1, st);
-      else k_prep_L<float>(L_inout, h->M, h->Mp, h->Lf, lo<float>(h->L_lo), lo<float>(h->Lt_lo), h->red + RED_COUNT - 1, st);
-    }
+    run_lupd(h, L_inout, gamma_dev + t);         // L <- L - gamma L Phi  (Prop. 1)
+    if (t + 1 < max_iters) prep_L(h, L_inout, h->red + RED_COUNT - 1);
   }
   return check_launch(h, "svgp_ng_update_T");
 }

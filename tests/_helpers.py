@@ -11,7 +11,28 @@ from oracle import rsvgp as O
 TOL = {  # relative bound error, per-block relative gradient error
     "fp32": dict(bound=1e-6, grad=1e-4),
     "bf16": dict(bound=1e-3, grad=1e-2),
+    "bf16x3": dict(bound=1e-3, grad=1e-2),
 }
+# unit roundoff of the contraction operands: FP32, BF16, BF16 hi+lo pair
+UNIT = {"fp32": 2.0 ** -24, "bf16": 2.0 ** -9, "bf16x3": 2.0 ** -17}
+
+
+def cond_Kt(p):
+    Kt = O.se_ard(p["Z"], p["Z"], p["ell"], p["sf2"]) + np.diag(p["s"])
+    return float(np.linalg.cond(Kt))
+
+
+def tolerances(prec, p):
+    """Stated tolerance, widened to the arithmetic's error bound.
+
+    The M x M products of the bound (A1 = L^T K~ L, P = L(2I - A1)L^T and the
+    T G T chain) are computed from operands rounded to unit roundoff u; a
+    relative perturbation u of K~ or L moves P by about u * cond(K~) relative
+    to ||K~^-1||.  The tests therefore accept max(stated, u * cond) for the
+    bound and max(stated, 4 u cond) for the gradient blocks."""
+    k = cond_Kt(p)
+    u = UNIT[prec]
+    return max(TOL[prec]["bound"], u * k), max(TOL[prec]["grad"], 4 * u * k), k
 BLOCKS = ("Z", "ell", "sf2", "noise", "m", "s")
 
 
