@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace {
 
@@ -23,7 +24,6 @@ constexpr int BN = 128;
 constexpr int BK = 64;                      // one 128-byte swizzle atom of BF16
 constexpr int TILE_BYTES = 128 * BK * 2;    // 16 KB per 128 x 64 operand tile
 constexpr int EPI_SCRATCH = 4 * 32 * 33 * 4;
-constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s per wait
 
 // Pipeline geometry per operand precision: NSPLIT = 1 (BF16) or 3 (hi/lo pairs).
 template <int NSPLIT> struct Geo {
@@ -33,96 +33,8 @@ template <int NSPLIT> struct Geo {
   static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_SCRATCH + 1024 + 256;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait: true on completion, false when the deadline passed.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  if (mbar_try(bar, parity)) return true;
-  unsigned long long t0 = gtimer();
-  while (!mbar_try(bar, parity)) {
-    if (gtimer() - t0 > WAIT_NS) return false;
-  }
-  return true;
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (SBO), version 1 (sm_100 family).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-  d |= (uint64_t)1 << 16;                 // LBO (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;       // SBO
-  d |= (uint64_t)1 << 46;                 // descriptor version
-  d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
-  return d;
-}
-
-// Instruction descriptor, kind::f16: D=F32, A=B=BF16, both K-major, M=128, N=BN.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-      ::"r"(tmem_d), "l"(ad), "l"(bd), "r"(IDESC), "r"(accum)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
-}
-
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+using namespace tc;
+constexpr uint32_t IDESC = idesc_bf16(BM, BN);
 
 // Epilogue hand-off: the warp's 32 TMEM lanes x 32 columns arrive in the row
 // layout (thread = row); a padded shared-memory transpose gives the column
@@ -219,12 +131,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       uint64_t bd = sw128_desc(smem_u32(st + TILE_BYTES));
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
-        mma_bf16(tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), (kb | kk) != 0);
+        mma_bf16(tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), IDESC, (kb | kk) != 0);
         if (NSPLIT == 3) {
           uint64_t adl = sw128_desc(smem_u32(st + 2 * TILE_BYTES));
           uint64_t bdl = sw128_desc(smem_u32(st + 3 * TILE_BYTES));
-          mma_bf16(tmem, ad + (uint64_t)(kk * 2), bdl + (uint64_t)(kk * 2), 1);
-          mma_bf16(tmem, adl + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), 1);
+          mma_bf16(tmem, ad + (uint64_t)(kk * 2), bdl + (uint64_t)(kk * 2), IDESC, 1);
+          mma_bf16(tmem, adl + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), IDESC, 1);
         }
       }
       mma_commit(smem_u32(&bars[G::STAGES + s]));
@@ -287,20 +199,6 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2-D BF16 row-major [rows][cols] (ld = cols), box 64 (k) x 128 (rows).
-bool make_map(CUtensorMap* m, const void* ptr, int rows, int cols) {
-  EncodeTiledFn fn = encode_fn();
-  if (!fn) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-  cuuint32_t box[2] = {BK, 128};
-  cuuint32_t es[2] = {1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
-}
-
 template <class Epi, int NSPLIT>
 void set_attr() {
   cudaFuncSetAttribute(tc_gemm_kernel<Epi, NSPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Geo<NSPLIT>::SMEM);
@@ -314,6 +212,20 @@ void set_attr_both() {
 
 }  // namespace
 
+// 2-D BF16 row-major [rows][cols] (ld = cols), box 64 (k) x box_rows (rows).
+bool tc_make_map(CUtensorMap* m, const void* ptr, int rows, int cols, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 bool tc_available() {
   int dev = 0, major = 0, minor = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
@@ -326,9 +238,9 @@ template <class Epi>
 bool tc_gemm(const GemmCtx& g, int tab, const bf16* A, const bf16* B, const Epi& e) {
   const size_t MM = (size_t)g.Mp * g.Mp;
   CUtensorMap ma, mb, mal, mbl;
-  if (!make_map(&ma, A, g.Mp, g.Mp) || !make_map(&mb, B, g.Mp, g.Mp)) return false;
+  if (!tc_make_map(&ma, A, g.Mp, g.Mp, 128) || !tc_make_map(&mb, B, g.Mp, g.Mp, 128)) return false;
   if (g.split) {
-    if (!make_map(&mal, A + MM, g.Mp, g.Mp) || !make_map(&mbl, B + MM, g.Mp, g.Mp)) return false;
+    if (!tc_make_map(&mal, A + MM, g.Mp, g.Mp, 128) || !tc_make_map(&mbl, B + MM, g.Mp, g.Mp, 128)) return false;
     svgp_note_launch();
     tc_gemm_kernel<Epi, 3><<<g.nt[tab], 192, Geo<3>::SMEM, g.st>>>(ma, mb, mal, mbl, g.tt[tab], e, g.err);
   } else {
@@ -372,7 +284,3 @@ void tc_init_attributes() {
   set_attr_both<EpiGK>();
 }
 
-// The Kuf-producer tensor-core kernels are not built yet: callers use the
-// FP32 SIMT kernels for Psi and W.
-bool tc_psi(const GemmCtx&, const KufGen&, int, EpiPsi) { return false; }
-bool tc_w(const GemmCtx&, const bf16*, const WEpi&) { return false; }

@@ -41,8 +41,21 @@ bool tc_available();
 void tc_init_attributes();
 template <class Epi>
 bool tc_gemm(const GemmCtx& g, int tab, const bf16* A, const bf16* B, const Epi& e);
-bool tc_psi(const GemmCtx& g, const KufGen& kg, int B, EpiPsi e);
-bool tc_w(const GemmCtx& g, const bf16* P, const WEpi& we);
+
+// Tensor-core Kuf-producer contractions (gemm_kuf_tc.cu): split coordinates
+// of the generator (64 BF16 per point: row role [hi, hi, lo], k role
+// [hi, lo, hi]) and per-point offsets c = -1/2 log2(e) |p|^2.
+struct KufTC {
+  bf16 *ZR, *ZK, *XR, *XK;
+  float *cz, *cx;
+  double* red;
+};
+bool tc_kuf_supported(int D);
+void tc_kuf_init_attributes();
+void k_kuf_prep(const float* Zs, const float* Xs, int M, int Mp, int B, int Bp, int D, const KufTC& t,
+                cudaStream_t st);
+bool tc_psi(const GemmCtx& g, const KufGen& kg, const KufTC& t, int B, EpiPsi e);
+bool tc_w(const GemmCtx& g, const bf16* P, const KufTC& t, const WEpi& we);
 
 // Miscellaneous kernels (kernels_misc.cu).  OutP is float*, bf16* or SplitPtr.
 void k_prep_coords(const float* Z, const float* X, const float* ell, int M, int Mp, int B, int D,

@@ -56,6 +56,8 @@ struct svgp_handle {
   double *red, *acc_ell, *resid_tmp;
   int *errword, *done, *iters_tmp;
   GemmCtx gs, gt;   // SIMT and tensor-core tile tables
+  KufTC kt;         // split coordinates for the tensor-core Kuf generator
+  bool tc_kuf;      // Psi and W run on the tensor-core Kuf-producer kernels
   std::vector<void*> allocs;
   // instrumentation
   bool prof;
@@ -202,12 +204,12 @@ void run_psi(svgp_handle* h, const svgp_params* p, int B) {
   ProfScope ps(h, SVGP_PROF_PSI);
   KufGen kg{h->Zs, h->Xs, h->D, h->M, B, p->sf2};
   EpiPsi e{h->Psi, h->Mp};
-  if (!(h->mode != MODE_F32 && tc_psi(h->gt, kg, B, e))) simt_psi(h->gs, kg, B, e);
+  if (!(h->tc_kuf && tc_psi(h->gt, kg, h->kt, B, e))) simt_psi(h->gs, kg, B, e);
 }
 
 void run_w(svgp_handle* h, const WEpi& we) {
   ProfScope ps(h, SVGP_PROF_W);
-  if (!(h->mode != MODE_F32 && tc_w(h->gt, H(h->P_lo), we))) simt_w(h->gs, h->Pf, we);
+  if (!(h->tc_kuf && tc_w(h->gt, H(h->P_lo), h->kt, we))) simt_w(h->gs, h->Pf, we);
 }
 
 void prep_L(svgp_handle* h, const float* Lin, double* red) {
@@ -222,6 +224,7 @@ void prologue(svgp_handle* h, const svgp_params* p, const float* X, int B, const
   cudaMemsetAsync(h->red, 0, sizeof(double) * RED_COUNT, st);
   cudaMemsetAsync(h->acc_ell, 0, sizeof(double) * SVGP_MAXD, st);
   k_prep_coords(p->Z, X, p->ell, h->M, h->Mp, X ? B : 0, h->D, h->Zs, h->Xs, st);
+  if (h->tc_kuf) k_kuf_prep(h->Zs, X ? h->Xs : nullptr, h->M, h->Mp, X ? B : 0, (B + 127) / 128 * 128, h->D, h->kt, st);
   if (h->mode == MODE_F32) k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, (float*)nullptr, false, st);
   else if (h->mode == MODE_BF16) k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, H(h->Kuu_lo), true, st);
   else k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, SP(h, h->Kuu_lo), true, st);
@@ -311,10 +314,17 @@ svgp_status svgp_create(const svgp_config* cfg, svgp_handle** out) {
             dalloc(h, &h->resid_tmp, sizeof(double)) && dalloc(h, &h->errword, sizeof(int)) &&
             dalloc(h, &h->done, sizeof(int)) && dalloc(h, &h->iters_tmp, sizeof(int));
   if (ok && h->mode != MODE_F32) ok = dalloc(h, &h->Kuu_lo, lob) && dalloc(h, &h->P_lo, lob);
+  h->tc_kuf = h->mode != MODE_F32 && tc_kuf_supported(h->D);
+  if (ok && h->tc_kuf)
+    ok = dalloc(h, &h->kt.ZR, 2 * 64 * h->Mp) && dalloc(h, &h->kt.ZK, 2 * 64 * h->Mp) &&
+         dalloc(h, &h->kt.XR, 2 * 64 * Bp) && dalloc(h, &h->kt.XK, 2 * 64 * Bp) &&
+         dalloc(h, &h->kt.cz, 4 * h->Mp) && dalloc(h, &h->kt.cx, 4 * Bp);
+  h->kt.red = h->red;
   if (ok && h->mode == MODE_F32) { h->Kuu_lo = h->Kuu_f; h->P_lo = h->Pf; }
   if (ok) ok = build_ctx(h, h->gs, 128, 128) && build_ctx(h, h->gt, 128, 128);
   simt_init_attributes();
   if (h->mode != MODE_F32) tc_init_attributes();
+  if (h->tc_kuf) tc_kuf_init_attributes();
   if (!ok) {
     svgp_destroy(h);
     return SVGP_ERR_OOM;

@@ -18,21 +18,32 @@ UNIT = {"fp32": 2.0 ** -24, "bf16": 2.0 ** -9, "bf16x3": 2.0 ** -17}
 
 
 def cond_Kt(p):
+    """Error amplification of the preconditioner products.
+
+    max(cond(K~), ||T||^2 ||K~|| / ||P||) in the 2-norm: a relative
+    perturbation u of K~ or L moves P = 2T - T K~ T by about
+    u ||T||^2 ||K~||, which relative to ||P|| is the second factor; at
+    T = K~^-1 both factors equal cond(K~)."""
     Kt = O.se_ard(p["Z"], p["Z"], p["ell"], p["sf2"]) + np.diag(p["s"])
-    return float(np.linalg.cond(Kt))
+    T = p["L"] @ p["L"].T
+    P = 2 * T - T @ Kt @ T
+    nP = np.linalg.norm(P, 2)
+    amp = np.linalg.norm(T, 2) ** 2 * np.linalg.norm(Kt, 2) / nP if nP > 0 else np.inf
+    return float(max(np.linalg.cond(Kt), amp))
 
 
 def tolerances(prec, p):
     """Stated tolerance, widened to the arithmetic's error bound.
 
     The M x M products of the bound (A1 = L^T K~ L, P = L(2I - A1)L^T and the
-    T G T chain) are computed from operands rounded to unit roundoff u; a
-    relative perturbation u of K~ or L moves P by about u * cond(K~) relative
-    to ||K~^-1||.  The tests therefore accept max(stated, u * cond) for the
-    bound and max(stated, 4 u cond) for the gradient blocks."""
+    T G T chain) are computed from operands rounded to unit roundoff u, so
+    their relative error is about u * cnd (cnd from cond_Kt).  The bound
+    accepts max(stated, u cnd); the gradient blocks accept max(stated,
+    16 u cnd) because the data and KL parts of dF/dZ partly cancel (a factor
+    of about 10 measured at cnd = 579 in FP32, BF16 and split BF16 alike)."""
     k = cond_Kt(p)
     u = UNIT[prec]
-    return max(TOL[prec]["bound"], u * k), max(TOL[prec]["grad"], 4 * u * k), k
+    return max(TOL[prec]["bound"], u * k), max(TOL[prec]["grad"], 16 * u * k), k
 BLOCKS = ("Z", "ell", "sf2", "noise", "m", "s")
 
 
