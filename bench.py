@@ -43,7 +43,33 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32-plain comparison line")
     ap.add_argument("--no-validate", action="store_true", help="skip the oracle bound check")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--profile-step", action="store_true",
+                    help="run two eager training steps (no timing) on an M x B case, for profilers")
+    ap.add_argument("--M", type=int, default=2048)
+    ap.add_argument("--B", type=int, default=4096)
     return ap.parse_args()
+
+
+def run_profile_step(args):
+    """Two eager NG + backward + Adam steps on the GP-sample workload with M
+    inducing points and batch B (D = 16): a short, self-contained program for
+    kernel profilers.  Prints the bound and the device status."""
+    import torch
+
+    import svgp_synth as S
+    from paper_2604_00697_gb300.model import RSVGP
+
+    prob = S.gp_sample_regression(M=args.M, B=args.B)
+    m = RSVGP(prob.M, prob.D, prob.B, prec=args.prec)
+    m.set_state(prob.Z0, np.ones(prob.D), 1.0, 1.0, np.zeros(prob.M), np.full(prob.M, 1e-4), 1e-3 * np.eye(prob.M))
+    X, y = prob.batch(0)
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    yd = torch.tensor(y, dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        m.train_step(Xd, yd, prob.N)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_step": True, "M": prob.M, "B": prob.B, "prec": args.prec,
+                      "bound": float(m.terms[0]), "status": m.sync_status()}))
 
 
 def dist_env():
@@ -260,6 +286,7 @@ def run_ours(args):
                     a = prof.setdefault(k, [0.0, 0])
                     a[0] += ms
                     a[1] += cnt
+                prof["_reads"] = prof.get("_reads", 0) + 1
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         clocks = clk.stop()
@@ -304,7 +331,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16" if prec == "bf16" else "f32",
+        "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "bf16", "e2e": e2e,
         "data": "synthetic (GP sample via random Fourier features, D=16, seed 2)",
         "config": {"workload": "gp_sample_regression M=2048 B=4096 D=16 N=1e6", "M": M, "B": B, "D": D, "N": N,
                    "t_star": 1, "gamma": 1.0, "precision": prec, "graph": True,
@@ -315,6 +342,7 @@ def run_ours(args):
     }
     # roofline of the dominant contraction kind (events inside the graph)
     if prof:
+        reads = max(1, prof.pop("_reads", 1))
         flops = algorithmic_flops(M, B)
         tot = {k: v[0] for k, v in prof.items() if v[1] > 0}
         dom = max(tot, key=tot.get)
@@ -323,21 +351,23 @@ def run_ours(args):
         achieved = flops[dom] / (avg_ms * 1e-3) / 1e12
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
-        if prec == "bf16":
+        if prec in ("bf16", "bf16x3"):
             peak = peaks["bf16_tflops_sustained"] if peaks else 1700.0
-            src = "measured sustained" if peaks else "fallback"
+            src = "measured sustained bf16 (MEASURED_PEAKS.json)" if peaks else "fallback"
             bound = "tensor"
         else:
             # FP32 SIMT: 152 SMs x 128 FMA lanes x 2 flops x max clock
             peak = 152 * 128 * 2 * (peaks["sm_max_mhz"] if peaks else 2070.0) * 1e6 / 1e12
-            src = "derived FP32 FMA peak"
+            src = "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 x max SM clock"
             bound = "alu"
         step_share = {k: round(v / max(sum(tot.values()), 1e-9), 3) for k, v in tot.items()}
         line["roofline"] = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
                             "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": src,
-                            "traffic": None, "avg_launch_ms": avg_ms,
+                            "traffic": None, "avg_launch_ms": avg_ms, "launches_per_step": n_l // reads,
+                            "mma_passes_per_product": 3 if prec == "bf16x3" else 1,
                             "algorithmic_flops_per_launch": flops[dom], "contraction_share": step_share,
-                            "contraction_ms_per_step": sum(tot.values()) / max(1, args.steps)}
+                            "contraction_ms_per_step": sum(tot.values()) / reads,
+                            "per_kind_ms_per_step": {k: round(v / reads, 4) for k, v in tot.items()}}
     if not args.no_compare and prec == "bf16" and rank == 0:
         m.close()
         m2, dev2, _, _, _, _ = time_model("fp32", max(3, args.steps // 10), 2)
@@ -383,13 +413,15 @@ def validate(prec, prob):
         ref = O.bound(p, X, y, prob.N)["F"]
         out[name] = abs(F - ref) / abs(ref)
     m.close()
-    out["tolerance"] = 1e-3 if prec == "bf16" else 1e-6
+    out["tolerance"] = 1e-6 if prec == "fp32" else 1e-3
     return out
 
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile_step:
+        run_profile_step(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
