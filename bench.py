@@ -204,6 +204,21 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def reduce_timing(tot_ms, steps, ws):
+    """Max over ranks of the timed milliseconds; whole-job steps/s.
+
+    Each rank is an independent replica that ran `steps` steps, so the job
+    processed ws * steps steps in the slowest rank's time."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([float(tot_ms)], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t[0])
+    return tot_ms, ws * steps / (tot_ms / 1e3)
+
+
 def algorithmic_flops(M, B):
     """Algorithmic FLOPs of one launch of each contraction kind."""
     M3 = float(M) ** 3
@@ -294,14 +309,7 @@ def run_ours(args):
         return m, dev_ms, wall, clocks, prof, launches
 
     m, dev_ms, wall, clocks, prof, launches = time_model(prec, args.steps, args.warmup, profile=True)
-    tot_ms = sum(dev_ms)
-    if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([tot_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t[0])
-    value = ws * args.steps / (tot_ms / 1e3)
+    tot_ms, value = reduce_timing(sum(dev_ms), args.steps, ws)
     ms_per_step = tot_ms / args.steps
 
     # end to end through the public API with host buffers: H2D of the batch

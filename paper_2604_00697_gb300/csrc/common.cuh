@@ -97,19 +97,33 @@ struct EpiVt {
   const int* skip_flag;
   __device__ bool skip() const { return skip_flag && *skip_flag; }
   __device__ void begin_tile(int, int) {}
-  __device__ __forceinline__ void block(int i0, int j0, const float (&v)[32], const float (&vt)[32], int lane) {
-    const int j = j0 + lane;
-    const float sj = (s && j < M) ? s[j] : 0.f;
-    const float* Lrow = Lf + (size_t)j * ld + i0;     // L[j][i0 + r] = Lt[i0 + r][j]
+  // Row layout (thread = row i): add Lt[i][j] s[j] = L[j][i] s[j]; the reads
+  // L[j0 + q][i0 + lane] are coalesced across the warp.
+  __device__ __forceinline__ void pre(int i0, int j0, float (&v)[32], int lane) {
+    if (!s) return;
+    const int i = i0 + lane;
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-      float a = vt[r];
-      if (s) a = fmaf(Lrow[r], sj, a);
-      put(out, (size_t)(i0 + r) * ld + j, a);
+    for (int q = 0; q < 32; ++q) {
+      const int j = j0 + q;
+      if (i < M && j < M) v[q] = fmaf(Lf[(size_t)j * ld + i], s[j], v[q]);
     }
+  }
+  __device__ __forceinline__ void block(int i0, int j0, const float (&)[32], const float (&vt)[32], int lane) {
+    const int j = j0 + lane;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) put(out, (size_t)(i0 + r) * ld + j, vt[r]);
   }
   __device__ void reduce() {}
 };
+
+// Optional row-layout step of a functor (called before the transpose).
+template <class E>
+__device__ __forceinline__ auto call_pre(E& e, int i0, int j0, float (&v)[32], int lane, int)
+    -> decltype(e.pre(i0, j0, v, lane), void()) {
+  e.pre(i0, j0, v, lane);
+}
+template <class E>
+__device__ __forceinline__ void call_pre(E&, int, int, float (&)[32], int, long) {}
 
 // Symmetric result computed on the upper region (i <= j), mirrored.
 //  MODE 0 (NG):  writes Phi^T = triu(A) - 1/2 (I + diag A) (Prop. 1), zero

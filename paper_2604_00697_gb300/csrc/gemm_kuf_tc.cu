@@ -128,17 +128,19 @@ __device__ __forceinline__ void epi_block32(Epi& epi, int i0, int j0, const floa
   epi.block(i0, j0, v, vt, lane);
 }
 
-// Fused epilogue of W = P Kuf for one accumulator row i over 128 columns n.
+// Fused epilogue of W = P Kuf for one accumulator row i over 128 columns n
+// (DP: compile-time bound on the padded input dimension).
+template <int DP>
 __device__ __forceinline__ void w_epilogue(uint32_t tacc, int i, int n0, const WEpi& we, float* colbuf, int lane,
                                            double& kw) {
   const int D = we.gen.D, Dp = (D + 3) & ~3;
   const bool row_ok = i < we.gen.M;
-  float z[SVGP_MAXD];
+  float z[DP];
 #pragma unroll
-  for (int d = 0; d < SVGP_MAXD; ++d) z[d] = (d < Dp && row_ok) ? we.gen.Zs[(size_t)i * Dp + d] : 0.f;
-  float accZ[SVGP_MAXD], accL[SVGP_MAXD], accS = 0.f;
+  for (int d = 0; d < DP; ++d) z[d] = (d < Dp && row_ok) ? we.gen.Zs[(size_t)i * Dp + d] : 0.f;
+  float accZ[DP], accL[DP], accS = 0.f;
 #pragma unroll
-  for (int d = 0; d < SVGP_MAXD; ++d) { accZ[d] = 0.f; accL[d] = 0.f; }
+  for (int d = 0; d < DP; ++d) { accZ[d] = 0.f; accL[d] = 0.f; }
   const float lsf2 = log2f(*we.gen.sf2);
   const float inv_noise = we.noise ? 1.0f / *we.noise : 0.f;
   const float vi = (row_ok && we.v) ? we.v[i] : 0.f;
@@ -151,10 +153,10 @@ __device__ __forceinline__ void w_epilogue(uint32_t tacc, int i, int n0, const W
       float prod = 0.f;
       if (n < we.gen.B && row_ok) {
         const float* xn = we.gen.Xs + (size_t)n * Dp;
-        float e[SVGP_MAXD];
+        float e[DP];
         float r2 = 0.f;
 #pragma unroll
-        for (int d = 0; d < SVGP_MAXD; ++d) {
+        for (int d = 0; d < DP; ++d) {
           e[d] = 0.f;
           if (d < Dp) { e[d] = __ldg(xn + d) - z[d]; r2 = fmaf(e[d], e[d], r2); }
         }
@@ -164,7 +166,7 @@ __device__ __forceinline__ void w_epilogue(uint32_t tacc, int i, int n0, const W
           const float a = we.c * kuf * fmaf(vi, we.g[n], w[q] * inv_noise);
           accS += a;
 #pragma unroll
-          for (int d = 0; d < SVGP_MAXD; ++d) {
+          for (int d = 0; d < DP; ++d) {
             if (d < D) { const float ae = a * e[d]; accZ[d] += ae; accL[d] = fmaf(ae, e[d], accL[d]); }
           }
         }
@@ -181,7 +183,7 @@ __device__ __forceinline__ void w_epilogue(uint32_t tacc, int i, int n0, const W
   if (we.rowacc && row_ok) {
     float* ra = we.rowacc + (size_t)i * (2 * D + 1);
 #pragma unroll
-    for (int d = 0; d < SVGP_MAXD; ++d)
+    for (int d = 0; d < DP; ++d)
       if (d < D) { atomicAdd(ra + d, accZ[d]); atomicAdd(ra + D + d, accL[d]); }
     atomicAdd(ra + 2 * D, accS);
   }
@@ -422,7 +424,11 @@ kuf_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // row-coordinate s
           epi_block32(epsi, m0 + quad * 32, n0 + c * 32, v, scr, lane);
         }
       } else {
-        w_epilogue(tacc, m0 + quad * 32 + lane, n0, we, colbuf, lane, kw);
+        const int i = m0 + quad * 32 + lane;
+        if (we.gen.D <= 4) w_epilogue<4>(tacc, i, n0, we, colbuf, lane, kw);
+        else if (we.gen.D <= 8) w_epilogue<8>(tacc, i, n0, we, colbuf, lane, kw);
+        else if (we.gen.D <= 16) w_epilogue<16>(tacc, i, n0, we, colbuf, lane, kw);
+        else w_epilogue<24>(tacc, i, n0, we, colbuf, lane, kw);
       }
     }
   }

@@ -151,10 +151,13 @@ __device__ __forceinline__ void simt_epilogue(Epi& epi, int m0, int n0, float (&
     int bi = b >> 2, bj = b & 3;
     float v[32], vt[32];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      v[q] = T[(bi * 32 + lane) * ldT + bj * 32 + q];
-      vt[q] = T[(bi * 32 + q) * ldT + bj * 32 + lane];
-    }
+    for (int q = 0; q < 32; ++q) v[q] = T[(bi * 32 + lane) * ldT + bj * 32 + q];
+    call_pre(epi, m0 + bi * 32, n0 + bj * 32, v, lane, 0);
+#pragma unroll
+    for (int q = 0; q < 32; ++q) T[(bi * 32 + lane) * ldT + bj * 32 + q] = v[q];   // this warp's block only
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < 32; ++q) vt[q] = T[(bi * 32 + q) * ldT + bj * 32 + lane];
     epi.block(m0 + bi * 32, n0 + bj * 32, v, vt, lane);
   }
   epi.reduce();

@@ -40,7 +40,8 @@ constexpr uint32_t IDESC = idesc_bf16(BM, BN);
 // layout (thread = row); a padded shared-memory transpose gives the column
 // layout; the functor then writes coalesced.
 template <class Epi>
-__device__ __forceinline__ void epi_block(Epi& epi, int i0, int j0, const float (&v)[32], float* scr, int lane) {
+__device__ __forceinline__ void epi_block(Epi& epi, int i0, int j0, float (&v)[32], float* scr, int lane) {
+  call_pre(epi, i0, j0, v, lane, 0);
   float vt[32];
 #pragma unroll
   for (int q = 0; q < 32; ++q) scr[lane * 33 + q] = v[q];

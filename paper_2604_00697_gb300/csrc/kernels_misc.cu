@@ -121,34 +121,51 @@ __global__ void gemv_kernel(const float* __restrict__ A, int Mp, int M, const fl
   if (dot_out) block_add_double(part, dot_out);
 }
 
+constexpr float HALF_LOG2E = 0.72134752044448170f;   // log2(e) / 2
+
+__device__ __forceinline__ float ex2f(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Calls KERNEL<DP> with DP the smallest of 4, 8, 16, 32 not below D.
+#define SVGP_DP_DISPATCH(D, ...)                              \
+  do {                                                        \
+    if ((D) <= 4) { constexpr int DP = 4; __VA_ARGS__; }      \
+    else if ((D) <= 8) { constexpr int DP = 8; __VA_ARGS__; } \
+    else if ((D) <= 16) { constexpr int DP = 16; __VA_ARGS__; } \
+    else { constexpr int DP = 32; __VA_ARGS__; }              \
+  } while (0)
+
 // mu_n += sum_{i in chunk} Kuf_in v_i.  grid (ceil(B/128), ceil(M/256)).
+template <int DP>
 __global__ void mu_kernel(const float* __restrict__ Zs, const float* __restrict__ Xs, int M, int B,
                           int D, const float* __restrict__ sf2p, const float* __restrict__ v,
                           float* __restrict__ mu) {
-  __shared__ float zs[256][SVGP_MAXD + 1];
+  __shared__ float zs[256][DP + 1];
   __shared__ float vs[256];
-  int Dp = (D + 3) & ~3;
+  const int Dp = (D + 3) & ~3;
   int i0 = blockIdx.y * 256;
   int ni = min(256, M - i0);
-  for (int e = threadIdx.x; e < 256 * Dp; e += blockDim.x) {
-    int r = e / Dp, d = e % Dp;
-    zs[r][d] = r < ni ? Zs[(size_t)(i0 + r) * Dp + d] : 0.f;
+  for (int e = threadIdx.x; e < 256 * DP; e += blockDim.x) {
+    int r = e / DP, d = e % DP;
+    zs[r][d] = (r < ni && d < Dp) ? Zs[(size_t)(i0 + r) * Dp + d] : 0.f;
   }
   for (int r = threadIdx.x; r < 256; r += blockDim.x) vs[r] = r < ni ? v[i0 + r] : 0.f;
   __syncthreads();
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= B) return;
-  float x[SVGP_MAXD];
+  float x[DP];
 #pragma unroll
-  for (int d = 0; d < SVGP_MAXD; ++d) x[d] = d < Dp ? Xs[(size_t)n * Dp + d] : 0.f;
-  float lsf2 = logf(*sf2p);
+  for (int d = 0; d < DP; ++d) x[d] = d < Dp ? Xs[(size_t)n * Dp + d] : 0.f;
+  const float l2sf2 = log2f(*sf2p);
   float acc = 0.f;
   for (int r = 0; r < ni; ++r) {
     float r2 = 0.f;
 #pragma unroll
-    for (int d = 0; d < SVGP_MAXD; ++d)
-      if (d < Dp) { float e = zs[r][d] - x[d]; r2 = fmaf(e, e, r2); }
-    acc = fmaf(expf(lsf2 - 0.5f * r2), vs[r], acc);
+    for (int d = 0; d < DP; ++d) { float e = zs[r][d] - x[d]; r2 = fmaf(e, e, r2); }
+    acc = fmaf(ex2f(fmaf(-HALF_LOG2E, r2, l2sf2)), vs[r], acc);
   }
   atomicAdd(mu + n, acc);
 }
@@ -167,33 +184,33 @@ __global__ void pointwise_gauss_kernel(const float* __restrict__ y, const float*
 }
 
 // Kg_i += sum_{n in chunk} Kuf_in g_n.  grid (Mp/128, ceil(B/256)).
+template <int DP>
 __global__ void kg_kernel(const float* __restrict__ Zs, const float* __restrict__ Xs, int M, int B,
                           int D, const float* __restrict__ sf2p, const float* __restrict__ g,
                           float* __restrict__ Kg) {
-  __shared__ float xs[256][SVGP_MAXD + 1];
+  __shared__ float xs[256][DP + 1];
   __shared__ float gs[256];
-  int Dp = (D + 3) & ~3;
+  const int Dp = (D + 3) & ~3;
   int n0 = blockIdx.y * 256;
   int nn = min(256, B - n0);
-  for (int e = threadIdx.x; e < 256 * Dp; e += blockDim.x) {
-    int r = e / Dp, d = e % Dp;
-    xs[r][d] = r < nn ? Xs[(size_t)(n0 + r) * Dp + d] : 0.f;
+  for (int e = threadIdx.x; e < 256 * DP; e += blockDim.x) {
+    int r = e / DP, d = e % DP;
+    xs[r][d] = (r < nn && d < Dp) ? Xs[(size_t)(n0 + r) * Dp + d] : 0.f;
   }
   for (int r = threadIdx.x; r < 256; r += blockDim.x) gs[r] = r < nn ? g[n0 + r] : 0.f;
   __syncthreads();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
-  float z[SVGP_MAXD];
+  float z[DP];
 #pragma unroll
-  for (int d = 0; d < SVGP_MAXD; ++d) z[d] = d < Dp ? Zs[(size_t)i * Dp + d] : 0.f;
-  float lsf2 = logf(*sf2p);
+  for (int d = 0; d < DP; ++d) z[d] = d < Dp ? Zs[(size_t)i * Dp + d] : 0.f;
+  const float l2sf2 = log2f(*sf2p);
   float acc = 0.f;
   for (int r = 0; r < nn; ++r) {
     float r2 = 0.f;
 #pragma unroll
-    for (int d = 0; d < SVGP_MAXD; ++d)
-      if (d < Dp) { float e = xs[r][d] - z[d]; r2 = fmaf(e, e, r2); }
-    acc = fmaf(expf(lsf2 - 0.5f * r2), gs[r], acc);
+    for (int d = 0; d < DP; ++d) { float e = xs[r][d] - z[d]; r2 = fmaf(e, e, r2); }
+    acc = fmaf(ex2f(fmaf(-HALF_LOG2E, r2, l2sf2)), gs[r], acc);
   }
   atomicAdd(Kg + i, acc);
 }
@@ -220,37 +237,47 @@ __global__ void gp_assemble_kernel(const float* __restrict__ Kuu, const float* _
 
 // Kuu side of the SE-ARD chain rule: a_ij = G_Kuu_ij Kuu_ij,
 //   rowacc_u[i][d] += sum_j a_ij (z~_jd - z~_id), rowacc_u[i][D+d] += a (.)^2,
-//   rowacc_u[i][2D] += sum_j a_ij.   grid (Mp/128, Mp/256), 128 threads.
+//   rowacc_u[i][2D] += sum_j a_ij.
+// One warp per row i; lanes stride over j so the G_Kuu and Kuu reads are
+// coalesced; the row's sums are reduced by warp shuffles and stored once.
+template <int DP>
 __global__ void kuu_bwd_kernel(const float* __restrict__ GK, const float* __restrict__ Kuu,
                                const float* __restrict__ Zs, int M, int Mp, int D,
                                float* __restrict__ rowacc) {
-  __shared__ float zj[256][SVGP_MAXD + 1];
-  int Dp = (D + 3) & ~3;
-  int j0 = blockIdx.y * 256;
-  for (int e = threadIdx.x; e < 256 * Dp; e += blockDim.x) {
-    int r = e / Dp, d = e % Dp;
-    zj[r][d] = (j0 + r < Mp) ? Zs[(size_t)(j0 + r) * Dp + d] : 0.f;
-  }
-  __syncthreads();
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (i >= M) return;
-  float z[SVGP_MAXD], aZ[SVGP_MAXD], aL[SVGP_MAXD];
+  const int Dp = (D + 3) & ~3;
+  float z[DP], aZ[DP], aL[DP];
 #pragma unroll
-  for (int d = 0; d < SVGP_MAXD; ++d) { z[d] = d < Dp ? Zs[(size_t)i * Dp + d] : 0.f; aZ[d] = 0.f; aL[d] = 0.f; }
+  for (int d = 0; d < DP; ++d) { z[d] = d < Dp ? Zs[(size_t)i * Dp + d] : 0.f; aZ[d] = 0.f; aL[d] = 0.f; }
   float aS = 0.f;
-  int nj = min(256, M - j0);
-  const float* gk = GK + (size_t)i * Mp + j0;
-  const float* ku = Kuu + (size_t)i * Mp + j0;
-  for (int r = 0; r < nj; ++r) {
-    float a = gk[r] * ku[r];
+  const float* gk = GK + (size_t)i * Mp;
+  const float* ku = Kuu + (size_t)i * Mp;
+  for (int j = lane; j < M; j += 32) {
+    const float a = gk[j] * ku[j];
     aS += a;
+    const float* zj = Zs + (size_t)j * Dp;
 #pragma unroll
-    for (int d = 0; d < SVGP_MAXD; ++d)
-      if (d < D) { float e = zj[r][d] - z[d]; float ae = a * e; aZ[d] += ae; aL[d] = fmaf(ae, e, aL[d]); }
+    for (int d = 0; d < DP; ++d) {
+      if (d < Dp) { const float e = __ldg(zj + d) - z[d]; const float ae = a * e; aZ[d] += ae; aL[d] = fmaf(ae, e, aL[d]); }
+    }
   }
-  float* ra = rowacc + (size_t)i * (2 * D + 1);
-  for (int d = 0; d < D; ++d) { atomicAdd(ra + d, aZ[d]); atomicAdd(ra + D + d, aL[d]); }
-  atomicAdd(ra + 2 * D, aS);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    aS += __shfl_xor_sync(0xffffffffu, aS, o);
+#pragma unroll
+    for (int d = 0; d < DP; ++d) {
+      aZ[d] += __shfl_xor_sync(0xffffffffu, aZ[d], o);
+      aL[d] += __shfl_xor_sync(0xffffffffu, aL[d], o);
+    }
+  }
+  if (lane == 0) {
+    float* ra = rowacc + (size_t)i * (2 * D + 1);
+#pragma unroll
+    for (int d = 0; d < DP; ++d)
+      if (d < D) { ra[d] = aZ[d]; ra[D + d] = aL[d]; }
+    ra[2 * D] = aS;
+  }
 }
 
 __global__ void logs_kernel(const float* __restrict__ s, int M, double* red) {
@@ -261,29 +288,40 @@ __global__ void logs_kernel(const float* __restrict__ s, int M, double* red) {
 }
 
 // dZ_id = (rowacc_f[i][d] + 2 rowacc_u[i][d]) / ell_d ; FP64 sums of the
-// lengthscale and signal-variance parts.
+// lengthscale and signal-variance parts (warp shuffles, then one shared
+// atomic per warp and one global atomic per block and value).
 __global__ void grad_finalize_kernel(const float* __restrict__ rf, const float* __restrict__ ru,
                                      const float* __restrict__ ell, int M, int D, float* __restrict__ dZ,
                                      double* acc_ell, double* red) {
-  __shared__ double sl[SVGP_MAXD];
-  __shared__ double ssf[2];
-  if (threadIdx.x < SVGP_MAXD) sl[threadIdx.x] = 0.0;
-  if (threadIdx.x < 2) ssf[threadIdx.x] = 0.0;
+  __shared__ double sl[SVGP_MAXD + 2];
+  if (threadIdx.x < SVGP_MAXD + 2) sl[threadIdx.x] = 0.0;
   __syncthreads();
-  int W = 2 * D + 1;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
-    const float* a = rf + (size_t)i * W;
-    const float* b = ru + (size_t)i * W;
-    for (int d = 0; d < D; ++d) {
+  const int W = 2 * D + 1;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool live = i < M;
+  const float* a = rf + (size_t)i * W;
+  const float* b = ru + (size_t)i * W;
+  for (int d = 0; d < D; ++d) {
+    double x = 0.0;
+    if (live) {
       dZ[(size_t)i * D + d] = (a[d] + 2.0f * b[d]) / ell[d];
-      atomicAdd(&sl[d], (double)a[D + d] + (double)b[D + d]);
+      x = (double)a[D + d] + (double)b[D + d];
     }
-    atomicAdd(&ssf[0], (double)a[2 * D]);
-    atomicAdd(&ssf[1], (double)b[2 * D]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) atomicAdd(&sl[d], x);
   }
+  double xf = live ? (double)a[2 * D] : 0.0, xu = live ? (double)b[2 * D] : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    xf += __shfl_xor_sync(0xffffffffu, xf, o);
+    xu += __shfl_xor_sync(0xffffffffu, xu, o);
+  }
+  if (lane == 0) { atomicAdd(&sl[SVGP_MAXD], xf); atomicAdd(&sl[SVGP_MAXD + 1], xu); }
   __syncthreads();
   if (threadIdx.x < D) atomicAdd(acc_ell + threadIdx.x, sl[threadIdx.x]);
-  if (threadIdx.x == 0) { atomicAdd(red + RED_SUMA_F, ssf[0]); atomicAdd(red + RED_SUMA_U, ssf[1]); }
+  if (threadIdx.x == 0) { atomicAdd(red + RED_SUMA_F, sl[SVGP_MAXD]); atomicAdd(red + RED_SUMA_U, sl[SVGP_MAXD + 1]); }
 }
 
 // Scalar assembly of Eq. (7) in FP64 (and the scalar gradients).
@@ -423,7 +461,7 @@ void k_mu(const float* Zs, const float* Xs, int M, int B, int D, const float* sf
   cudaMemsetAsync(mu, 0, sizeof(float) * B, st);
   dim3 grid((B + 127) / 128, (M + 255) / 256);
   svgp_note_launch();
-  mu_kernel<<<grid, 128, 0, st>>>(Zs, Xs, M, B, D, sf2, v, mu);
+  SVGP_DP_DISPATCH(D, mu_kernel<DP><<<grid, 128, 0, st>>>(Zs, Xs, M, B, D, sf2, v, mu));
 }
 
 void k_pointwise_gauss(const float* y, const float* mu, const float* noise, int B, float* g,
@@ -439,7 +477,7 @@ void k_kg(const float* Zs, const float* Xs, int M, int Mp, int B, int D, const f
   cudaMemsetAsync(Kg, 0, sizeof(float) * Mp, st);
   dim3 grid(Mp / 128, (B + 255) / 256);
   svgp_note_launch();
-  kg_kernel<<<grid, 128, 0, st>>>(Zs, Xs, M, B, D, sf2, g, Kg);
+  SVGP_DP_DISPATCH(D, kg_kernel<DP><<<grid, 128, 0, st>>>(Zs, Xs, M, B, D, sf2, g, Kg));
 }
 
 template <class OutP>
@@ -461,14 +499,14 @@ template void k_gp_assemble<SplitPtr>(const float*, const float*, const float*, 
 void k_kuu_bwd(const float* GKuu, const float* Kuu, const float* Zs, int M, int Mp, int D,
                float* rowacc_u, double* red, cudaStream_t st) {
   (void)red;
-  dim3 grid(Mp / 128, Mp / 256 + (Mp % 256 ? 1 : 0));
+  const int grid = (M + 7) / 8;     // 8 warps per block, one warp per row
   svgp_note_launch();
-  kuu_bwd_kernel<<<grid, 128, 0, st>>>(GKuu, Kuu, Zs, M, Mp, D, rowacc_u);
+  SVGP_DP_DISPATCH(D, kuu_bwd_kernel<DP><<<grid, 256, 0, st>>>(GKuu, Kuu, Zs, M, Mp, D, rowacc_u));
 }
 
 void k_logs(const float* s, int M, double* red, cudaStream_t st) {
   svgp_note_launch();
-  logs_kernel<<<1, 256, 0, st>>>(s, M, red);
+  logs_kernel<<<(M + 255) / 256, 256, 0, st>>>(s, M, red);
 }
 
 void k_grad_finalize(const float* rowacc_f, const float* rowacc_u, const float* ell, int M, int D,

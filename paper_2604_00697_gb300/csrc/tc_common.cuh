@@ -42,14 +42,20 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: true on completion, false when the deadline passed.
+// Bounded wait: true on completion, false when the deadline passed.  The
+// deadline is counted in SM clock cycles (clock64 is cheap to read; the
+// global timer is not) and checked once per 64 polls: 2^32 cycles is about
+// 2 s at the GB300's maximum SM clock.
+constexpr long long WAIT_CYCLES = 1ll << 32;
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   if (mbar_try(bar, parity)) return true;
-  unsigned long long t0 = gtimer();
-  while (!mbar_try(bar, parity)) {
-    if (gtimer() - t0 > WAIT_NS) return false;
+  const long long t0 = clock64();
+  for (;;) {
+#pragma unroll 1
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try(bar, parity)) return true;
+    if (clock64() - t0 > WAIT_CYCLES) return false;
   }
-  return true;
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
