@@ -214,6 +214,31 @@ svgp_status svgp_profile_read(svgp_handle* h, float* ms, int* counts);
  * handles; launches captured into a graph are counted once, at capture). */
 long long svgp_launch_count(const svgp_handle* h);
 
+/* Prediction without any device allocation.  (The paper has no counterpart:
+ * this entry point exists for callers, not for the method.)
+ *
+ * Some callers cannot call cudaMalloc: code that runs while a framework
+ * captures a CUDA graph, plug-ins and embedded runtimes that own a fixed
+ * memory budget, or services that must not touch the allocator on a latency
+ * path.  A handle allocates its workspace in svgp_create, so those callers
+ * cannot use svgp_predict.  This function computes the same mean and
+ * variance as svgp_predict on an SVGP_FP32 handle, with the same FP32
+ * kernels, but takes no handle and allocates nothing: its scratch is one
+ * array in the library's device memory of about 2.7 MB, which every GPU
+ * that loads the library holds until the process exits.
+ *
+ * Limits: 1 <= M <= 256, 1 <= D <= 32, 1 <= Ns <= 4096; larger sizes return
+ * SVGP_ERR_INVALID_ARG.  Arguments are as for svgp_predict (device pointers;
+ * p->L is the M x M factor of T); cuda_stream is the stream to run on (NULL:
+ * legacy default stream).  The first call on a device performs a one-time
+ * set-up on the host (it looks up the array's device address), so make that
+ * first call before any stream capture.  Every call uses the same array and
+ * clears what must start at zero; calls that overlap on the GPU (on different
+ * streams, or from different host threads) race and must be serialised by
+ * the caller.  Returns SVGP_ERR_CUDA when a launch fails. */
+svgp_status svgp_predict_noalloc(const svgp_params* p, int M, int D, const float* Xs, int Ns, float* mean,
+                                 float* var, int include_noise, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -201,3 +201,18 @@ def svgp_launch_count(h=None):
     lib.svgp_launch_count.argtypes = [c_void_p]
     lib.svgp_launch_count.restype = ctypes.c_longlong
     return int(lib.svgp_launch_count(h))
+
+
+EXPORTED += ["svgp_predict_noalloc"]
+
+
+def svgp_predict_noalloc(params, M, D, Xs_ptr, Ns, mean_ptr, var_ptr, include_noise=False, cuda_stream=None):
+    """Prediction without a handle or any device allocation (fixed scratch)."""
+    lib = load()
+    fn = lib.svgp_predict_noalloc
+    fn.argtypes = [POINTER(svgp_params), c_int, c_int, c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p]
+    fn.restype = c_int
+    st = fn(byref(params), M, D, c_void_p(Xs_ptr), Ns, c_void_p(mean_ptr), c_void_p(var_ptr),
+            int(bool(include_noise)), c_void_p(cuda_stream))
+    if st != SVGP_OK:
+        raise SvgpError(st, lib.svgp_status_string(st).decode())
