@@ -82,10 +82,22 @@ __device__ __forceinline__ void block_add_double(double x, double* dst) {
 // Direct writes C[i][j] use the column layout (a warp writes 32 consecutive
 // elements of row i0 + r); transposed (mirror) writes C[j][i] use the row
 // layout.  Region predicates are applied per element so that every element
-// of a symmetric result is produced by exactly one tile.  Per-thread FP64
-// partial sums are reduced by the kernel through reduce(), which every
-// thread of the block calls.
+// of a symmetric result is produced by exactly one tile.  Every global read
+// of an epilogue is issued as a batch of 32 independent loads before any
+// store (the compiler cannot reorder loads across stores it cannot prove
+// disjoint).  Per-thread partial sums are FP32 (a thread adds at most a few
+// hundred terms; FP64 arithmetic is slow on this part) and the block-level
+// reduction in reduce() is FP64; every thread of the block calls it.
 // ---------------------------------------------------------------------------
+
+// Optional row-layout step of a functor (called before the transpose).
+template <class E>
+__device__ __forceinline__ auto call_pre(E& e, int i0, int j0, float (&v)[32], int lane, int)
+    -> decltype(e.pre(i0, j0, v, lane), void()) {
+  e.pre(i0, j0, v, lane);
+}
+template <class E>
+__device__ __forceinline__ void call_pre(E&, int, int, float (&)[32], int, long) {}
 
 // Vt = L^T K~ = L^T Kuu + L^T diag(s): the diagonal of S~ is added in FP32 so
 // that it is not lost when Kuu is rounded (Section 2: S~ lower-bounds the
@@ -102,11 +114,16 @@ struct EpiVt {
   __device__ __forceinline__ void pre(int i0, int j0, float (&v)[32], int lane) {
     if (!s) return;
     const int i = i0 + lane;
+    float lv[32], sv[32];
 #pragma unroll
     for (int q = 0; q < 32; ++q) {
       const int j = j0 + q;
-      if (i < M && j < M) v[q] = fmaf(Lf[(size_t)j * ld + i], s[j], v[q]);
+      const bool in = (i < M) && (j < M);
+      lv[q] = in ? __ldg(Lf + (size_t)j * ld + i) : 0.f;
+      sv[q] = in ? __ldg(s + j) : 0.f;
     }
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = fmaf(lv[q], sv[q], v[q]);
   }
   __device__ __forceinline__ void block(int i0, int j0, const float (&)[32], const float (&vt)[32], int lane) {
     const int j = j0 + lane;
@@ -115,15 +132,6 @@ struct EpiVt {
   }
   __device__ void reduce() {}
 };
-
-// Optional row-layout step of a functor (called before the transpose).
-template <class E>
-__device__ __forceinline__ auto call_pre(E& e, int i0, int j0, float (&v)[32], int lane, int)
-    -> decltype(e.pre(i0, j0, v, lane), void()) {
-  e.pre(i0, j0, v, lane);
-}
-template <class E>
-__device__ __forceinline__ void call_pre(E&, int, int, float (&)[32], int, long) {}
 
 // Symmetric result computed on the upper region (i <= j), mirrored.
 //  MODE 0 (NG):  writes Phi^T = triu(A) - 1/2 (I + diag A) (Prop. 1), zero
@@ -135,9 +143,9 @@ struct EpiSym {
   OutP out; int ld; int M;
   double* red;
   const int* skip_flag;
-  double p0, p1;
+  float p0, p1;
   __device__ bool skip() const { return skip_flag && *skip_flag; }
-  __device__ void begin_tile(int, int) { p0 = 0.0; p1 = 0.0; }
+  __device__ void begin_tile(int, int) { p0 = 0.f; p1 = 0.f; }
   __device__ __forceinline__ void block(int i0, int j0, const float (&v)[32], const float (&vt)[32], int lane) {
     if (i0 > j0 + 31) return;                    // block entirely below the diagonal
     // direct part (i <= j), column layout: i = i0 + r, j = j0 + lane
@@ -153,9 +161,9 @@ struct EpiSym {
       else val = a + (i == j ? 0.5f : 0.0f);
       put(out, (size_t)i * ld + j, val);
       if (i < M && j < M) {
-        const double w = (i == j) ? 1.0 : 2.0;
-        if (MODE == 0) { double e = (double)a - (i == j ? 1.0 : 0.0); p0 += w * e * e; }
-        if (MODE == 1) { if (i == j) p0 += a; p1 += w * (double)a * a; }
+        const float w = (i == j) ? 1.f : 2.f;
+        if (MODE == 0) { const float e = a - (i == j ? 1.f : 0.f); p0 = fmaf(w * e, e, p0); }
+        if (MODE == 1) { if (i == j) p0 += a; p1 = fmaf(w * a, a, p1); }
       }
     }
     // mirror part (j, i) for i < j, row layout: i = i0 + lane, j = j0 + q
@@ -189,13 +197,15 @@ struct EpiLupd {
     if (j0 > i0 + 31) return;
     const float g = *gamma;
     const int j = j0 + lane;
+    float old[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) old[r] = (j <= i0 + r) ? Lf[(size_t)(i0 + r) * ld + j] : 0.f;
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
       const int i = i0 + r;
       if (j > i) continue;
-      const size_t o = (size_t)i * ld + j;
-      const float Ln = Lf[o] - g * vt[r];
-      Lf[o] = Ln;
+      const float Ln = old[r] - g * vt[r];
+      Lf[(size_t)i * ld + j] = Ln;
       if (i < M && j < M) Lout[(size_t)i * M + j] = Ln;
     }
   }
@@ -222,12 +232,19 @@ template <class OutP>
 struct EpiP {
   float* Pf; OutP Plo; int ld; int M;
   const float* s; const float* Psi; double* red;
-  double p0, p1;
+  float p0, p1;
   __device__ bool skip() const { return false; }
-  __device__ void begin_tile(int, int) { p0 = 0.0; p1 = 0.0; }
+  __device__ void begin_tile(int, int) { p0 = 0.f; p1 = 0.f; }
   __device__ __forceinline__ void block(int i0, int j0, const float (&v)[32], const float (&vt)[32], int lane) {
     if (j0 > i0 + 31) return;
     const int j = j0 + lane;
+    float ps[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      const int i = i0 + r;
+      ps[r] = (Psi && j <= i && i < M && j < M) ? __ldg(Psi + (size_t)i * ld + j) : 0.f;
+    }
+    const float sj = (j < M) ? __ldg(s + j) : 0.f;
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
       const int i = i0 + r;
@@ -237,8 +254,8 @@ struct EpiP {
       Pf[o] = a;
       put(Plo, o, a);
       if (i < M && j < M) {
-        if (i == j) p0 += (double)s[i] * a;
-        if (Psi) p1 += (i == j ? 1.0 : 2.0) * (double)a * Psi[o];
+        if (i == j) p0 = fmaf(sj, a, p0);
+        p1 = fmaf((i == j ? 1.f : 2.f) * a, ps[r], p1);
       }
     }
     const int i = i0 + lane;
@@ -266,27 +283,39 @@ struct EpiGK {
   __device__ void begin_tile(int, int) {}
   __device__ __forceinline__ void block(int i0, int j0, const float (&vr)[32], const float (&vt)[32], int lane) {
     if (j0 > i0 + 31) return;
+    // column layout loads (direct part): P[i0 + r][j], v[i0 + r]
     const int j = j0 + lane;
-    const float vj = j < M ? v[j] : 0.f;
+    const float vj = j < M ? __ldg(v + j) : 0.f;
+    float pc[32], vi_c[32];
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
       const int i = i0 + r;
-      if (j > i) continue;
-      const float gk = -vt[r];
-      const float vi = i < M ? v[i] : 0.f;
-      const size_t o = (size_t)i * ld + j;
-      GKuu[o] = gk + 0.5f * Pf[o] - 0.5f * vi * vj;
-      if (i == j && i < M) ds[i] = gk + 0.5f / s[i];
+      pc[r] = (j <= i) ? __ldg(Pf + (size_t)i * ld + j) : 0.f;
+      vi_c[r] = i < M ? __ldg(v + i) : 0.f;
     }
+    // row layout loads (mirror part): P[j0 + q][i], v[j0 + q]
     const int i = i0 + lane;
-    const float vi = i < M ? v[i] : 0.f;
+    const float vi = i < M ? __ldg(v + i) : 0.f;
+    float pr[32], vq[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      const int jj = j0 + q;
+      pr[q] = (jj < i) ? __ldg(Pf + (size_t)jj * ld + i) : 0.f;
+      vq[q] = jj < M ? __ldg(v + jj) : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      const int ii = i0 + r;
+      if (j > ii) continue;
+      const float gk = -vt[r];
+      GKuu[(size_t)ii * ld + j] = gk + 0.5f * pc[r] - 0.5f * vi_c[r] * vj;
+      if (ii == j && ii < M) ds[ii] = gk + 0.5f / s[ii];
+    }
 #pragma unroll
     for (int q = 0; q < 32; ++q) {
       const int jj = j0 + q;
       if (jj >= i) continue;
-      const size_t o = (size_t)jj * ld + i;      // P symmetric: P[jj][i] = P[i][jj]
-      const float vjj = jj < M ? v[jj] : 0.f;
-      GKuu[o] = -vr[q] + 0.5f * Pf[o] - 0.5f * vi * vjj;
+      GKuu[(size_t)jj * ld + i] = -vr[q] + 0.5f * pr[q] - 0.5f * vi * vq[q];
     }
   }
   __device__ void reduce() {}

@@ -132,7 +132,7 @@ __device__ __forceinline__ void epi_block32(Epi& epi, int i0, int j0, const floa
 // (DP: compile-time bound on the padded input dimension).
 template <int DP>
 __device__ __forceinline__ void w_epilogue(uint32_t tacc, int i, int n0, const WEpi& we, float* colbuf, int lane,
-                                           double& kw) {
+                                           float& kw) {
   const int D = we.gen.D, Dp = (D + 3) & ~3;
   const bool row_ok = i < we.gen.M;
   float z[DP];
@@ -403,7 +403,7 @@ kuf_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // row-coordinate s
   __syncwarp();
 
   // ---------------- epilogue (transform warps) ----------------
-  double kw = 0.0;
+  float kw = 0.f;
   if (KIND == KIND_W && we.colsum) {
     // colbuf aliases the epilogue scratch: all threads clear it first
     for (int e = threadIdx.x; e < 128; e += blockDim.x) colbuf[e] = 0.f;
