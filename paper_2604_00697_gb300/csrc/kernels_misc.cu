@@ -238,30 +238,42 @@ __global__ void gp_assemble_kernel(const float* __restrict__ Kuu, const float* _
 // Kuu side of the SE-ARD chain rule: a_ij = G_Kuu_ij Kuu_ij,
 //   rowacc_u[i][d] += sum_j a_ij (z~_jd - z~_id), rowacc_u[i][D+d] += a (.)^2,
 //   rowacc_u[i][2D] += sum_j a_ij.
-// One warp per row i; lanes stride over j so the G_Kuu and Kuu reads are
-// coalesced; the row's sums are reduced by warp shuffles and stored once.
+// One warp per row i (8 rows per block); lanes stride over j so the G_Kuu and
+// Kuu reads are coalesced; z~_j comes from 256-point chunks staged in shared
+// memory (padded rows, conflict-free); the row's sums are reduced by warp
+// shuffles and stored once.
 template <int DP>
-__global__ void kuu_bwd_kernel(const float* __restrict__ GK, const float* __restrict__ Kuu,
-                               const float* __restrict__ Zs, int M, int Mp, int D,
-                               float* __restrict__ rowacc) {
-  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (i >= M) return;
+__global__ void __launch_bounds__(256) kuu_bwd_kernel(const float* __restrict__ GK, const float* __restrict__ Kuu,
+                                                     const float* __restrict__ Zs, int M, int Mp, int D,
+                                                     float* __restrict__ rowacc) {
+  __shared__ float zc[256][DP + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + warp;
+  const bool live = i < M;
   const int Dp = (D + 3) & ~3;
   float z[DP], aZ[DP], aL[DP];
 #pragma unroll
-  for (int d = 0; d < DP; ++d) { z[d] = d < Dp ? Zs[(size_t)i * Dp + d] : 0.f; aZ[d] = 0.f; aL[d] = 0.f; }
+  for (int d = 0; d < DP; ++d) { z[d] = (live && d < Dp) ? Zs[(size_t)i * Dp + d] : 0.f; aZ[d] = 0.f; aL[d] = 0.f; }
   float aS = 0.f;
-  const float* gk = GK + (size_t)i * Mp;
-  const float* ku = Kuu + (size_t)i * Mp;
-  for (int j = lane; j < M; j += 32) {
-    const float a = gk[j] * ku[j];
-    aS += a;
-    const float* zj = Zs + (size_t)j * Dp;
+  const float* gk = GK + (size_t)(live ? i : 0) * Mp;
+  const float* ku = Kuu + (size_t)(live ? i : 0) * Mp;
+  for (int j0 = 0; j0 < M; j0 += 256) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < 256 * DP; e += blockDim.x) {
+      const int r = e / DP, d = e % DP;
+      zc[r][d] = (j0 + r < M && d < Dp) ? Zs[(size_t)(j0 + r) * Dp + d] : 0.f;
+    }
+    __syncthreads();
+    if (!live) continue;
+    const int jn = min(256, M - j0);
+    for (int jj = lane; jj < jn; jj += 32) {
+      const float a = gk[j0 + jj] * ku[j0 + jj];
+      aS += a;
 #pragma unroll
-    for (int d = 0; d < DP; ++d) {
-      if (d < Dp) { const float e = __ldg(zj + d) - z[d]; const float ae = a * e; aZ[d] += ae; aL[d] = fmaf(ae, e, aL[d]); }
+      for (int d = 0; d < DP; ++d) { const float e = zc[jj][d] - z[d]; const float ae = a * e; aZ[d] += ae; aL[d] = fmaf(ae, e, aL[d]); }
     }
   }
+  if (!live) return;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     aS += __shfl_xor_sync(0xffffffffu, aS, o);
