@@ -26,7 +26,6 @@ enum {
   RED_LOGS = 8,       // sum_i log s_i
   RED_SUMA_F = 9,     // sum (G_Kuf o Kuf)
   RED_SUMA_U = 10,    // sum (G_Kuu o Kuu)
-  RED_KW = 11,        // sum_n sum_i Kuf_in W_in = sum_n k_n^T P k_n
   RED_COUNT = 16
 };
 

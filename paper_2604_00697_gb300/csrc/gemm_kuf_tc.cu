@@ -15,8 +15,9 @@
 //      c = -1/2 log2(e) |p|^2 and log2(sf2), and store BF16 (or hi/lo BF16)
 //      values into the 128-byte-swizzled operand buffer of the main MMA;
 //   3. one thread issues the main tcgen05 MMA on the generated tile(s).
-// Warp roles (192 threads): 0 TMA producer, 1 TMEM allocator + MMA issuer,
-// 2..5 transform and then epilogue.  All waits are bounded.
+// Warp roles (320 threads): 0 TMA producer, 1 TMEM allocator + MMA issuer,
+// 2..9 transform and then epilogue (warp w covers TMEM lanes 32 (w mod 4) ..
+// +31 and one half of the columns).  All waits are bounded.
 #include "common.cuh"
 #include "internal.h"
 #include "tc_common.cuh"
@@ -28,7 +29,10 @@ using namespace tc;
 constexpr int KB = 64;                        // k-block (one swizzle atom of BF16)
 constexpr int GT = 128 * KB * 2;              // 16 KB: 128-row operand tile
 constexpr int CT = 64 * KB * 2;               // 8 KB: 64-row coordinate tile
-constexpr int EPI_SCR = 4 * 32 * 33 * 4;
+constexpr int NTW = 8;                        // transform / epilogue warps
+constexpr int KUF_THREADS = 64 + 32 * NTW;
+constexpr int STASH_LD = 129;                 // padded row stride (floats) of the W stash
+constexpr int STASH_BYTES = 128 * STASH_LD * 4;
 constexpr float LOG2E = 1.4426950408889634f;
 
 enum { KIND_PSI = 0, KIND_W = 1 };
@@ -43,8 +47,14 @@ struct KGeo {
   static constexpr int OFF_GB = OFF_GA + (KIND == KIND_PSI ? NS * GT : 0);
   static constexpr int STAGE = OFF_GB + NS * GT;
   static constexpr int STATIC = (KIND == KIND_PSI ? 2 : 1) * GT;         // row-coordinate tiles
+  // W: FP32 copy of the generated Kuf block whose inducing rows are the output
+  // rows (see w_epilogue).  The epilogues stage through the (then idle)
+  // pipeline buffers.
+  static constexpr int EPI = KIND == KIND_PSI ? 0 : STASH_BYTES;
+  static_assert(STAGES * STAGE >= 4 * (256 + 128 * 48) && STAGES * STAGE >= NTW * 32 * 33 * 4, "epilogue staging");
   static constexpr int NBAR = 3 * STAGES + 6;
-  static constexpr int SMEM = 1024 + STATIC + STAGES * STAGE + EPI_SCR + 8 * NBAR + 64;
+  static constexpr int SMEM = 1024 + STATIC + STAGES * STAGE + EPI + 8 * NBAR + 64;
+  static_assert(SMEM <= 232448, "shared memory budget");
   static constexpr uint32_t TMEM_COLS = KIND == KIND_PSI ? 512 : 256;
   // TMEM columns: accumulator [0,128); S buffers of 64 columns after it
   __host__ __device__ static constexpr uint32_t S_A(int b) { return 128 + 64 * b; }
@@ -60,7 +70,6 @@ struct KufArgs {
   int nkb;                  // number of k-blocks
   const float* sf2;
   int* errword;
-  double* red;              // W: receives sum_n sum_i Kuf_in W_in in RED_KW (may be null)
 };
 
 __device__ __forceinline__ float ex2(float x) {
@@ -74,28 +83,62 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// Transform 64 cross-term values of one row into the generated tile(s).
+// 2^t on the FMA pipe (offloads the MUFU unit): t = j + f with j = rint(t)
+// taken by the 1.5 * 2^23 rounding trick and |f| <= 1/2; 2^f from its Taylor
+// series sum_k (f ln 2)^k / k! to degree DEG (relative truncation error below
+// 3.3e-6 for DEG = 5 and 1.7e-7 for DEG = 6); 2^j enters through the exponent
+// field.  t is clamped to >= -125, so underflowing values come out as 2^-125
+// instead of 0.
+template <int DEG>
+__device__ __forceinline__ float ex2_poly(float t) {
+  t = fmaxf(t, -125.f);
+  const float r = t + 12582912.f;
+  const float f = t - (r - 12582912.f);
+  float p = DEG >= 6 ? 1.5403530393381606e-4f : 1.3333558146428443e-3f;
+  if (DEG >= 6) p = fmaf(p, f, 1.3333558146428443e-3f);
+  p = fmaf(p, f, 9.6181291076284772e-3f);
+  p = fmaf(p, f, 5.5504108664821580e-2f);
+  p = fmaf(p, f, 2.4022650695910071e-1f);
+  p = fmaf(p, f, 6.9314718055994531e-1f);
+  p = fmaf(p, f, 1.0f);
+  const int j = __float_as_int(r) - 0x4B400000;
+  return __int_as_float(__float_as_int(p) + (j << 23));
+}
+
+// Elements q (of each group of 8 generated values) whose exponential runs on
+// the FMA pipe instead of the MUFU unit.
+constexpr int POLY_MASK = 0;
+
+// Transform 32 cross-term values s[q] = p_row . q_k (k = kbase + q) of one row
+// into BF16 (hi, and lo = value - hi for NSPLIT = 3) operand values at
+// columns kcol0 + q of the 128-byte-swizzled tile(s).  ck[q] holds the k-point
+// constants.  When stash != null the FP32 values also go to
+// stash[(kcol0 + q) * STASH_LD + row].
 template <int NSPLIT>
-__device__ __forceinline__ void gen_row(const float (&s)[64], float crow, const float* __restrict__ ck, int kbase,
-                                        int nk, bool row_ok, unsigned char* hi, unsigned char* lo, int row) {
+__device__ __forceinline__ void gen32(const float (&s)[32], float crow, const float (&ck)[32], int kbase, int nk,
+                                      bool row_ok, unsigned char* hi, unsigned char* lo, int row, int kcol0,
+                                      float* stash) {
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
+  for (int c = 0; c < 4; ++c) {
     float v[8];
-    const float4 c0 = __ldg(reinterpret_cast<const float4*>(ck + kbase + c * 8));
-    const float4 c1 = __ldg(reinterpret_cast<const float4*>(ck + kbase + c * 8 + 4));
-    const float cc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int k = kbase + c * 8 + q;
-      const float t = fmaf(s[c * 8 + q], LOG2E, crow + cc[q]);
-      v[q] = (row_ok && k < nk) ? ex2(t) : 0.f;
+      const float t = fmaf(s[c * 8 + q], LOG2E, crow + ck[c * 8 + q]);
+      const float e = ((POLY_MASK >> q) & 1) ? ex2_poly<NSPLIT == 3 ? 6 : 5>(t) : ex2(t);
+      v[q] = (row_ok && k < nk) ? e : 0.f;
+    }
+    if (stash) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) stash[(kcol0 + c * 8 + q) * STASH_LD + row] = v[q];
     }
     uint4 ph;
     ph.x = pack_bf16(v[0], v[1]);
     ph.y = pack_bf16(v[2], v[3]);
     ph.z = pack_bf16(v[4], v[5]);
     ph.w = pack_bf16(v[6], v[7]);
-    const uint32_t off = (uint32_t)(row * 128 + (((c ^ (row & 7)) & 7) << 4));
+    const int chunk = (kcol0 >> 3) + c;
+    const uint32_t off = (uint32_t)(row * 128 + (((chunk ^ (row & 7)) & 7) << 4));
     *reinterpret_cast<uint4*>(hi + off) = ph;
     if (NSPLIT == 3) {
       const __nv_bfloat162* hp = reinterpret_cast<const __nv_bfloat162*>(&ph);
@@ -128,69 +171,106 @@ __device__ __forceinline__ void epi_block32(Epi& epi, int i0, int j0, const floa
   epi.block(i0, j0, v, vt, lane);
 }
 
-// Fused epilogue of W = P Kuf for one accumulator row i over 128 columns n
-// (DP: compile-time bound on the padded input dimension).
+// Fused epilogue of W = P Kuf for the 128 x 128 output block (rows i = m0 + r,
+// columns n = n0 + 0..127), run by the 128 epilogue threads, thread r owning
+// accumulator row r.  Kuf_in comes from the FP32 stash the transform filled
+// while generating the k-blocks that cover rows [m0, m0 + 128), so nothing is
+// recomputed.  Gradient mode (rowacc): with A_in = c Kuf_in (v_i g_n + W_in /
+// noise), the sums
+//   S0_i = sum_n A_in,  S1_id = sum_n A_in x~_nd,  S2_id = sum_n A_in x~_nd^2
+// are accumulated in FP32 from x~ and x~^2 staged in shared memory, and turned
+// into the differences form
+//   sum_n A_in e_d   = S1 - z~_d S0,
+//   sum_n A_in e_d^2 = S2 - 2 z~_d S1 + z~_d^2 S0          (e_d = x~_nd - z~_id)
+// before they are added to rowacc.  Variance mode (colsum): colsum[n] +=
+// sum_i Kuf_in W_in.  The pipeline stage buffers (free once the accumulator is
+// final) hold the staged data.
 template <int DP>
-__device__ __forceinline__ void w_epilogue(uint32_t tacc, int i, int n0, const WEpi& we, float* colbuf, int lane,
-                                           float& kw) {
-  const int D = we.gen.D, Dp = (D + 3) & ~3;
-  const bool row_ok = i < we.gen.M;
-  float z[DP];
-#pragma unroll
-  for (int d = 0; d < DP; ++d) z[d] = (d < Dp && row_ok) ? we.gen.Zs[(size_t)i * Dp + d] : 0.f;
-  float accZ[DP], accL[DP], accS = 0.f;
-#pragma unroll
-  for (int d = 0; d < DP; ++d) { accZ[d] = 0.f; accL[d] = 0.f; }
-  const float lsf2 = log2f(*we.gen.sf2);
-  const float inv_noise = we.noise ? 1.0f / *we.noise : 0.f;
-  const float vi = (row_ok && we.v) ? we.v[i] : 0.f;
-  for (int c = 0; c < 4; ++c) {
-    float w[32];
-    tmem_ld32(tacc + (uint32_t)(c * 32), w);
-#pragma unroll 4
-    for (int q = 0; q < 32; ++q) {
-      const int n = n0 + c * 32 + q;
-      float prod = 0.f;
-      if (n < we.gen.B && row_ok) {
-        const float* xn = we.gen.Xs + (size_t)n * Dp;
-        float e[DP];
-        float r2 = 0.f;
-#pragma unroll
-        for (int d = 0; d < DP; ++d) {
-          e[d] = 0.f;
-          if (d < Dp) { e[d] = __ldg(xn + d) - z[d]; r2 = fmaf(e[d], e[d], r2); }
-        }
-        const float kuf = ex2(lsf2 - 0.5f * LOG2E * r2);
-        prod = kuf * w[q];
-        if (we.rowacc) {
-          const float a = we.c * kuf * fmaf(vi, we.g[n], w[q] * inv_noise);
-          accS += a;
-#pragma unroll
-          for (int d = 0; d < DP; ++d) {
-            if (d < D) { const float ae = a * e[d]; accZ[d] += ae; accL[d] = fmaf(ae, e[d], accL[d]); }
-          }
-        }
+__device__ __forceinline__ void w_epilogue(uint32_t tacc, int m0, int n0, int r, int half, const WEpi& we,
+                                           const float* __restrict__ stash, float* ebuf, bool ok) {
+  constexpr int XW = 2 * DP;
+  float* colbuf = ebuf;              // column sums (variance mode)
+  float* gq = ebuf + 128;            // g_n
+  float* xq = ebuf + 256;            // [128][XW]: x~_n (d < D), then x~_n^2; zero padded
+  const int D = we.gen.D, Dp = (D + 3) & ~3, B = we.gen.B;
+  const int lane = r & 31, tid = half * 128 + r;
+  if (ok) {
+    if (we.rowacc) {
+      for (int e = tid; e < 128 * DP; e += 32 * NTW) {
+        const int n = e / DP, d = e - n * DP;
+        const float x = (n0 + n < B && d < D) ? we.gen.Xs[(size_t)(n0 + n) * Dp + d] : 0.f;
+        xq[n * XW + d] = x;
+        xq[n * XW + DP + d] = x * x;
       }
-      kw += prod;
-      if (we.colsum) {
-        float sv = prod;
+      if (tid < 128) gq[tid] = (n0 + tid < B) ? we.g[n0 + tid] : 0.f;
+    }
+    if (tid < 128) colbuf[tid] = 0.f;
+  }
+  asm volatile("bar.sync 1, %0;" ::"n"(32 * NTW) : "memory");
+  if (!ok) return;
+  const float* krow = stash + r * STASH_LD;
+  if (we.rowacc) {
+    const int i = m0 + r;
+    const bool row_ok = i < we.gen.M;
+    const float inv_noise = 1.0f / *we.noise;
+    const float cv = row_ok ? we.c * we.v[i] : 0.f;
+    const float cn = we.c * inv_noise;
+    float S0 = 0.f, S1[DP], S2[DP];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
-        if (lane == 0) atomicAdd(colbuf + c * 32 + q, sv);
+    for (int d = 0; d < DP; ++d) { S1[d] = 0.f; S2[d] = 0.f; }
+    for (int ch = 2 * half; ch < 2 * half + 2; ++ch) {
+      float w[32];
+      tmem_ld32(tacc + (uint32_t)(ch * 32), w);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int n = ch * 32 + q;
+        const float a = krow[n] * fmaf(cv, gq[n], cn * w[q]);
+        S0 += a;
+        const float4* xv = reinterpret_cast<const float4*>(xq + n * XW);
+#pragma unroll
+        for (int d4 = 0; d4 < DP / 4; ++d4) {
+          const float4 x = xv[d4], x2 = xv[DP / 4 + d4];
+          S1[4 * d4 + 0] = fmaf(a, x.x, S1[4 * d4 + 0]);
+          S1[4 * d4 + 1] = fmaf(a, x.y, S1[4 * d4 + 1]);
+          S1[4 * d4 + 2] = fmaf(a, x.z, S1[4 * d4 + 2]);
+          S1[4 * d4 + 3] = fmaf(a, x.w, S1[4 * d4 + 3]);
+          S2[4 * d4 + 0] = fmaf(a, x2.x, S2[4 * d4 + 0]);
+          S2[4 * d4 + 1] = fmaf(a, x2.y, S2[4 * d4 + 1]);
+          S2[4 * d4 + 2] = fmaf(a, x2.z, S2[4 * d4 + 2]);
+          S2[4 * d4 + 3] = fmaf(a, x2.w, S2[4 * d4 + 3]);
+        }
       }
     }
-  }
-  if (we.rowacc && row_ok) {
-    float* ra = we.rowacc + (size_t)i * (2 * D + 1);
+    if (row_ok) {
+      float* ra = we.rowacc + (size_t)i * (2 * D + 1);
+      const float* zi = we.gen.Zs + (size_t)i * Dp;
 #pragma unroll
-    for (int d = 0; d < DP; ++d)
-      if (d < D) { atomicAdd(ra + d, accZ[d]); atomicAdd(ra + D + d, accL[d]); }
-    atomicAdd(ra + 2 * D, accS);
+      for (int d = 0; d < DP; ++d) {
+        if (d < D) {
+          const float z = zi[d];
+          atomicAdd(ra + d, fmaf(-z, S0, S1[d]));
+          atomicAdd(ra + D + d, fmaf(z, fmaf(z, S0, -2.0f * S1[d]), S2[d]));
+        }
+      }
+      atomicAdd(ra + 2 * D, S0);
+    }
+  } else if (we.colsum) {
+    for (int ch = 2 * half; ch < 2 * half + 2; ++ch) {
+      float w[32];
+      tmem_ld32(tacc + (uint32_t)(ch * 32), w);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        float sv = krow[ch * 32 + q] * w[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+        if (lane == 0) atomicAdd(colbuf + ch * 32 + q, sv);
+      }
+    }
   }
 }
 
 template <int KIND, int NSPLIT>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(KUF_THREADS, 1)
 kuf_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // row-coordinate splits (PSI: z, W: x)
               const __grid_constant__ CUtensorMap tmK,       // k-coordinate splits (PSI: x, W: z)
               const __grid_constant__ CUtensorMap tmP,       // W: P hi
@@ -203,11 +283,11 @@ kuf_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // row-coordinate s
   unsigned char* sRowB = base + GT;                              // PSI: z rows of J
   unsigned char* stg = base + G::STATIC;
   float* scratch = reinterpret_cast<float*>(stg + G::STAGES * G::STAGE);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(scratch) + EPI_SCR);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(scratch) + G::EPI);
   volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars + G::NBAR);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   volatile int* consumed = abort_flag + 1;
-  float* colbuf = reinterpret_cast<float*>(scratch);             // W colsum (after the mainloop)
+  float* stash = scratch;                                        // W: Kuf[m0 + r][n0 + n] at r * STASH_LD + n
   constexpr int S = G::STAGES;
   auto BAR = [&](int idx) { return smem_u32(&bars[idx]); };
   const int B_STATIC = 0, B_LD = 1, B_EMPTY = 1 + S, B_GEN = 1 + 2 * S, B_SFULL = 1 + 3 * S, B_SEMPTY = 3 + 3 * S,
@@ -230,11 +310,11 @@ kuf_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // row-coordinate s
     for (int s = 0; s < S; ++s) {
       mbar_init(BAR(B_LD + s), 1);
       mbar_init(BAR(B_EMPTY + s), 1);
-      mbar_init(BAR(B_GEN + s), 4);
+      mbar_init(BAR(B_GEN + s), NTW);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(BAR(B_SFULL + b), 1);
-      mbar_init(BAR(B_SEMPTY + b), 4);
+      mbar_init(BAR(B_SEMPTY + b), NTW);
     }
     mbar_init(BAR(B_ACC), 1);
     *abort_flag = 0;
@@ -346,8 +426,9 @@ kuf_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // row-coordinate s
     mma_commit(BAR(B_ACC));
   } else if (warp >= 2) {
     // ---------------- transform ----------------
-    const int quad = warp & 3;
-    const int row = quad * 32 + lane;
+    // warp (quad, half): TMEM lanes / tile rows quad*32 .. +31, k columns half*32 .. +31
+    const int quad = warp & 3, half = (warp - 2) >> 2;
+    const int row = quad * 32 + lane, kcol0 = half * 32;
     const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
     const float lsf2 = log2f(*ka.sf2);
     float crA = 0.f, crB = 0.f;
@@ -364,36 +445,33 @@ kuf_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // row-coordinate s
     for (int kb = 0; kb < nkb; ++kb) {
       if (*abort_flag) break;
       const int s = kb % S, b = kb & 1;
+      const int kbase = kb * KB + kcol0;
+      float ck[32];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 c4 = __ldg(reinterpret_cast<const float4*>(ka.ck + kbase + 4 * q));
+        ck[4 * q] = c4.x; ck[4 * q + 1] = c4.y; ck[4 * q + 2] = c4.z; ck[4 * q + 3] = c4.w;
+      }
       if (!mbar_wait(BAR(B_SFULL + b), (kb >> 1) & 1)) { *abort_flag = 1; break; }
       fence_after();
-      float sa[64], sbv[64];
-      {
-        float t0[32], t1[32];
-        if (KIND == KIND_PSI) {
-          tmem_ld32(tmem + lane_off + G::S_A(b), t0);
-          tmem_ld32(tmem + lane_off + G::S_A(b) + 32, t1);
-#pragma unroll
-          for (int q = 0; q < 32; ++q) { sa[q] = t0[q]; sa[32 + q] = t1[q]; }
-        }
-        if (KIND == KIND_W || !diag) {
-          tmem_ld32(tmem + lane_off + G::S_B(b), t0);
-          tmem_ld32(tmem + lane_off + G::S_B(b) + 32, t1);
-#pragma unroll
-          for (int q = 0; q < 32; ++q) { sbv[q] = t0[q]; sbv[32 + q] = t1[q]; }
-        }
-      }
+      float sa[32], sbv[32];
+      if (KIND == KIND_PSI) tmem_ld32(tmem + lane_off + G::S_A(b) + kcol0, sa);
+      if (KIND == KIND_W || !diag) tmem_ld32(tmem + lane_off + G::S_B(b) + kcol0, sbv);
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(BAR(B_SEMPTY + b));
       // the generated buffers of stage s are free once the main MMA of kb - S finished
       if (!mbar_wait(BAR(B_EMPTY + s), ((kb / S) & 1) ^ 1)) { *abort_flag = 1; break; }
       unsigned char* st = stg + s * G::STAGE;
-      const int kbase = kb * KB;
       if (KIND == KIND_PSI) {
-        gen_row<NSPLIT>(sa, crA, ka.ck, kbase, ka.nk, okA, st + G::OFF_GA, st + G::OFF_GA + GT, row);
-        if (!diag) gen_row<NSPLIT>(sbv, crB, ka.ck, kbase, ka.nk, okB, st + G::OFF_GB, st + G::OFF_GB + GT, row);
+        gen32<NSPLIT>(sa, crA, ck, kbase, ka.nk, okA, st + G::OFF_GA, st + G::OFF_GA + GT, row, kcol0, nullptr);
+        if (!diag)
+          gen32<NSPLIT>(sbv, crB, ck, kbase, ka.nk, okB, st + G::OFF_GB, st + G::OFF_GB + GT, row, kcol0, nullptr);
       } else {
-        gen_row<NSPLIT>(sbv, crB, ka.ck, kbase, ka.nk, okB, st + G::OFF_GB, st + G::OFF_GB + GT, row);
+        // the k-blocks covering the output rows [m0, m0 + 128) also fill the stash
+        const int kb0 = kb * KB;
+        float* sh = (kb0 >= m0 && kb0 < m0 + 128) ? stash + (size_t)(kb0 - m0) * STASH_LD : nullptr;
+        gen32<NSPLIT>(sbv, crB, ck, kbase, ka.nk, okB, st + G::OFF_GB, st + G::OFF_GB + GT, row, kcol0, sh);
       }
       fence_proxy_async();
       __syncwarp();
@@ -403,40 +481,37 @@ kuf_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // row-coordinate s
   __syncwarp();
 
   // ---------------- epilogue (transform warps) ----------------
-  float kw = 0.f;
-  if (KIND == KIND_W && we.colsum) {
-    // colbuf aliases the epilogue scratch: all threads clear it first
-    for (int e = threadIdx.x; e < 128; e += blockDim.x) colbuf[e] = 0.f;
-  }
-  __syncthreads();
   if (warp >= 2) {
     const int quad = warp & 3;
     bool ok = mbar_wait(BAR(B_ACC), 0);
     fence_after();
     if (!ok) *abort_flag = 1;
-    if (ok && !*abort_flag) {
-      const uint32_t tacc = tmem + ((uint32_t)(quad * 32) << 16);
-      if (KIND == KIND_PSI) {
-        float* scr = scratch + (warp - 2) * 32 * 33;
-        for (int c = 0; c < 4; ++c) {
+    ok = ok && !*abort_flag;
+    const uint32_t tacc = tmem + ((uint32_t)(quad * 32) << 16);
+    const int half = (warp - 2) >> 2;
+    if (KIND == KIND_PSI) {
+      if (ok) {
+        float* scr = reinterpret_cast<float*>(stg) + (warp - 2) * 32 * 33;
+        for (int c = 2 * half; c < 2 * half + 2; ++c) {
           float v[32];
           tmem_ld32(tacc + (uint32_t)(c * 32), v);
           epi_block32(epsi, m0 + quad * 32, n0 + c * 32, v, scr, lane);
         }
-      } else {
-        const int i = m0 + quad * 32 + lane;
-        if (we.gen.D <= 4) w_epilogue<4>(tacc, i, n0, we, colbuf, lane, kw);
-        else if (we.gen.D <= 8) w_epilogue<8>(tacc, i, n0, we, colbuf, lane, kw);
-        else if (we.gen.D <= 16) w_epilogue<16>(tacc, i, n0, we, colbuf, lane, kw);
-        else w_epilogue<24>(tacc, i, n0, we, colbuf, lane, kw);
       }
+    } else {
+      const int r = quad * 32 + lane;
+      float* ebuf = reinterpret_cast<float*>(stg);
+      if (we.gen.D <= 4) w_epilogue<4>(tacc, m0, n0, r, half, we, stash, ebuf, ok);
+      else if (we.gen.D <= 8) w_epilogue<8>(tacc, m0, n0, r, half, we, stash, ebuf, ok);
+      else if (we.gen.D <= 16) w_epilogue<16>(tacc, m0, n0, r, half, we, stash, ebuf, ok);
+      else w_epilogue<24>(tacc, m0, n0, r, half, we, stash, ebuf, ok);
     }
   }
-  if (KIND == KIND_W && ka.red) block_add_double(kw, ka.red + RED_KW);
   fence_before();
   __syncthreads();
-  if (KIND == KIND_W && we.colsum && threadIdx.x < 128) {
+  if (KIND == KIND_W && we.colsum && threadIdx.x < 128 && !*abort_flag) {
     const int n = n0 + threadIdx.x;
+    const float* colbuf = reinterpret_cast<const float*>(stg);
     if (n < we.gen.B) atomicAdd(we.colsum + n, colbuf[threadIdx.x]);
   }
   if (threadIdx.x == 0 && *abort_flag) atomicOr(ka.errword, ERRBIT_TIMEOUT);
@@ -511,13 +586,13 @@ bool tc_psi(const GemmCtx& g, const KufGen& kg, const KufTC& t, int B, EpiPsi e)
   const int Bp = (B + 127) / 128 * 128;
   CUtensorMap mr, mk;
   if (!tc_make_map(&mr, t.ZR, g.Mp, 64, 128) || !tc_make_map(&mk, t.XK, Bp, 64, 64)) return false;
-  KufArgs ka{t.cz, t.cz, t.cx, kg.M, kg.M, B, Bp / KB, kg.sf2, g.err, nullptr};
+  KufArgs ka{t.cz, t.cz, t.cx, kg.M, kg.M, B, Bp / KB, kg.sf2, g.err};
   WEpi we{};
   svgp_note_launch();
   if (g.split)
-    kuf_tc_kernel<KIND_PSI, 3><<<g.nt[TT_PSI], 192, KGeo<KIND_PSI, 3>::SMEM, g.st>>>(mr, mk, mr, mr, g.tt[TT_PSI], ka, e, we);
+    kuf_tc_kernel<KIND_PSI, 3><<<g.nt[TT_PSI], KUF_THREADS, KGeo<KIND_PSI, 3>::SMEM, g.st>>>(mr, mk, mr, mr, g.tt[TT_PSI], ka, e, we);
   else
-    kuf_tc_kernel<KIND_PSI, 1><<<g.nt[TT_PSI], 192, KGeo<KIND_PSI, 1>::SMEM, g.st>>>(mr, mk, mr, mr, g.tt[TT_PSI], ka, e, we);
+    kuf_tc_kernel<KIND_PSI, 1><<<g.nt[TT_PSI], KUF_THREADS, KGeo<KIND_PSI, 1>::SMEM, g.st>>>(mr, mk, mr, mr, g.tt[TT_PSI], ka, e, we);
   return true;
 }
 
@@ -534,13 +609,13 @@ bool tc_w(const GemmCtx& g, const bf16* P, const KufTC& t, const WEpi& we) {
   } else {
     mpl = mp;
   }
-  KufArgs ka{t.cz, t.cx, t.cz, we.gen.M, B, we.gen.M, g.Mp / KB, we.gen.sf2, g.err, t.red};
+  KufArgs ka{t.cz, t.cx, t.cz, we.gen.M, B, we.gen.M, g.Mp / KB, we.gen.sf2, g.err};
   EpiPsi ep{nullptr, 0};
   dim3 grid(Bp / 128, g.Mp / 128);
   svgp_note_launch();
   if (g.split)
-    kuf_tc_kernel<KIND_W, 3><<<grid, 192, KGeo<KIND_W, 3>::SMEM, g.st>>>(mr, mk, mp, mpl, nullptr, ka, ep, we);
+    kuf_tc_kernel<KIND_W, 3><<<grid, KUF_THREADS, KGeo<KIND_W, 3>::SMEM, g.st>>>(mr, mk, mp, mpl, nullptr, ka, ep, we);
   else
-    kuf_tc_kernel<KIND_W, 1><<<grid, 192, KGeo<KIND_W, 1>::SMEM, g.st>>>(mr, mk, mp, mpl, nullptr, ka, ep, we);
+    kuf_tc_kernel<KIND_W, 1><<<grid, KUF_THREADS, KGeo<KIND_W, 1>::SMEM, g.st>>>(mr, mk, mp, mpl, nullptr, ka, ep, we);
   return true;
 }

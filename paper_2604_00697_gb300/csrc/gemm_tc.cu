@@ -1,16 +1,23 @@
 // tcgen05 BF16 GEMMs for sm_103a: acc[i,j] = sum_k A[i,k] B[j,k], both
 // operands K-major BF16 (row-major, k contiguous), FP32 accumulation in TMEM.
 //
-// One 128 x 128 output tile per CTA, 192 threads:
-//   warp 0      TMA producer: 128B-swizzled 128x64 tiles of A and B into a
-//               STAGES-deep shared-memory ring (mbarrier full/empty pairs);
-//   warp 1      TMEM allocator and MMA issuer: one elected thread issues
-//               tcgen05.mma.cta_group::1.kind::f16 (M=128, N=128, K=16) x 4 per
-//               k-block and frees the stage with tcgen05.commit;
-//   warps 2..5  epilogue: tcgen05.ld 32x32b.x32 of their 32 TMEM lanes, then
-//               the shared epilogue functors (common.cuh) write the results.
-// Every mbarrier wait is bounded by a %globaltimer deadline; on expiry the
-// CTA raises ERRBIT_TIMEOUT, drains its own copies and frees TMEM.
+// Persistent kernel: one CTA per SM walks the tile table (128 x 128 output
+// tiles, sorted by decreasing K length) with stride gridDim.x.  192 threads:
+//   warp 0      TMA producer: 128B-swizzled 128x64 tiles of A and B (and of
+//               their lo parts for split operands) into a STAGES-deep
+//               shared-memory ring (mbarrier full/empty pairs) that runs
+//               continuously across tiles;
+//   warp 1      TMEM allocator and MMA issuer: one thread issues
+//               tcgen05.mma.cta_group::1.kind::f16 (M=128, N=128, K=16) into
+//               one of two TMEM accumulators (256 columns), frees stages with
+//               tcgen05.commit and signals the finished accumulator;
+//   warps 2..5  epilogue: tcgen05.ld 32x32b.x32 of their 32 TMEM lanes,
+//               transpose 32x32 blocks through padded shared memory, run the
+//               shared epilogue functors (common.cuh), then release the
+//               accumulator -- so the epilogue of tile t overlaps the
+//               mainloop of tile t+1.
+// Every mbarrier wait is bounded; on expiry the CTA raises ERRBIT_TIMEOUT,
+// stops issuing, drains its own copies and frees TMEM.
 #include <cuda.h>
 
 #include "common.cuh"
@@ -24,13 +31,15 @@ constexpr int BN = 128;
 constexpr int BK = 64;                      // one 128-byte swizzle atom of BF16
 constexpr int TILE_BYTES = 128 * BK * 2;    // 16 KB per 128 x 64 operand tile
 constexpr int EPI_SCRATCH = 4 * 32 * 33 * 4;
+constexpr uint32_t TMEM_COLS = 2 * BN;      // two accumulators
 
 // Pipeline geometry per operand precision: NSPLIT = 1 (BF16) or 3 (hi/lo pairs).
 template <int NSPLIT> struct Geo {
-  static constexpr int NT = NSPLIT == 1 ? 2 : 4;                 // tiles per stage
-  static constexpr int STAGES = NSPLIT == 1 ? 4 : 3;
+  static constexpr int NT = NSPLIT == 1 ? 2 : 4;                 // operand tiles per stage
+  static constexpr int STAGES = NSPLIT == 1 ? 6 : 3;
   static constexpr int STAGE_BYTES = NT * TILE_BYTES;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_SCRATCH + 1024 + 256;
+  static constexpr int NBAR = 2 * STAGES + 4;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_SCRATCH + 1024 + 8 * NBAR + 64;
 };
 
 using namespace tc;
@@ -56,41 +65,39 @@ template <class Epi, int NSPLIT>
 __global__ void __launch_bounds__(192, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmAl, const __grid_constant__ CUtensorMap tmBl,
-               const Tile* __restrict__ tiles, Epi epi, int* errword) {
+               const Tile* __restrict__ tiles, int ntiles, Epi epi, int* errword) {
   using G = Geo<NSPLIT>;
+  constexpr int S = G::STAGES;
   if (epi.skip()) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   // stage s holds tiles [A_hi, B_hi, (A_lo, B_lo)]
-  float* scratch = reinterpret_cast<float*>(base + G::STAGES * G::STAGE_BYTES);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + G::STAGES * G::STAGE_BYTES + EPI_SCRATCH);
-  // bars[0..S) full, bars[S..2S) empty, bars[2S] tmem_full
-  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars + 2 * G::STAGES + 1);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * G::STAGES + 2);
+  float* scratch = reinterpret_cast<float*>(base + S * G::STAGE_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + S * G::STAGE_BYTES + EPI_SCRATCH);
+  // bars: [0,S) full, [S,2S) empty, 2S+b acc_full[b], 2S+2+b acc_empty[b]
+  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars + G::NBAR);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   volatile int* consumed = abort_flag + 1;
+  auto BAR = [&](int i) { return smem_u32(&bars[i]); };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const Tile tl = tiles[blockIdx.x];
-  const int nk = (tl.k1 - tl.k0) / BK;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < G::STAGES; ++s) {
-      mbar_init(smem_u32(&bars[s]), 1);
-      mbar_init(smem_u32(&bars[G::STAGES + s]), 1);
+    for (int s = 0; s < S; ++s) {
+      mbar_init(BAR(s), 1);
+      mbar_init(BAR(S + s), 1);
     }
-    mbar_init(smem_u32(&bars[2 * G::STAGES]), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(BAR(2 * S + b), 1);       // acc_full: one tcgen05.commit (or arrive)
+      mbar_init(BAR(2 * S + 2 + b), 4);   // acc_empty: one arrive per epilogue warp
+    }
     *abort_flag = 0;
     *consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
   }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32((const void*)tmem_slot)),
-                 "r"(BN)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
+  if (warp == 1) tmem_alloc(smem_u32((const void*)tmem_slot), TMEM_COLS);
   fence_before();
   __syncthreads();
   fence_after();
@@ -98,84 +105,105 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
-    int issued = 0;
-    for (int kb = 0; kb < nk; ++kb) {
-      int s = kb % G::STAGES;
-      uint32_t ph = (kb / G::STAGES) & 1;
-      if (!mbar_wait(smem_u32(&bars[G::STAGES + s]), ph ^ 1)) { *abort_flag = 1; break; }
-      if (*abort_flag) break;
-      uint32_t fb = smem_u32(&bars[s]);
-      mbar_expect_tx(fb, G::STAGE_BYTES);
-      int k = tl.k0 + kb * BK;
-      unsigned char* st = base + s * G::STAGE_BYTES;
-      tma_load_2d(smem_u32(st), &tmA, k, tl.m0, fb);
-      tma_load_2d(smem_u32(st + TILE_BYTES), &tmB, k, tl.n0, fb);
-      if (NSPLIT == 3) {
-        tma_load_2d(smem_u32(st + 2 * TILE_BYTES), &tmAl, k, tl.m0, fb);
-        tma_load_2d(smem_u32(st + 3 * TILE_BYTES), &tmBl, k, tl.n0, fb);
+    int g = 0;          // running k-block counter over all tiles of this CTA
+    for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+      const Tile tl = tiles[t];
+      const int nk = (tl.k1 - tl.k0) / BK;
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = g % S;
+        if (!mbar_wait(BAR(S + s), ((g / S) & 1) ^ 1)) { *abort_flag = 1; break; }
+        if (*abort_flag) break;
+        const uint32_t fb = BAR(s);
+        mbar_expect_tx(fb, G::STAGE_BYTES);
+        const int k = tl.k0 + kb * BK;
+        unsigned char* st = base + s * G::STAGE_BYTES;
+        tma_load_2d(smem_u32(st), &tmA, k, tl.m0, fb);
+        tma_load_2d(smem_u32(st + TILE_BYTES), &tmB, k, tl.n0, fb);
+        if (NSPLIT == 3) {
+          tma_load_2d(smem_u32(st + 2 * TILE_BYTES), &tmAl, k, tl.m0, fb);
+          tma_load_2d(smem_u32(st + 3 * TILE_BYTES), &tmBl, k, tl.n0, fb);
+        }
       }
-      issued = kb + 1;
     }
     // On abort, wait (bounded) for copies that nobody consumed.
     if (*abort_flag) {
-      for (int kb = *consumed; kb < issued; ++kb) mbar_wait(smem_u32(&bars[kb % G::STAGES]), (kb / G::STAGES) & 1);
+      for (int q = *consumed; q < g; ++q) mbar_wait(BAR(q % S), (q / S) & 1);
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
-    for (int kb = 0; kb < nk; ++kb) {
-      int s = kb % G::STAGES;
-      uint32_t ph = (kb / G::STAGES) & 1;
-      if (!mbar_wait(smem_u32(&bars[s]), ph)) { *abort_flag = 1; break; }
+    int g = 0, lt = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+      const Tile tl = tiles[t];
+      const int nk = (tl.k1 - tl.k0) / BK;
+      const int b = lt & 1;
+      if (!mbar_wait(BAR(2 * S + 2 + b), ((lt >> 1) & 1) ^ 1)) { *abort_flag = 1; break; }
       fence_after();
-      unsigned char* st = base + s * G::STAGE_BYTES;
-      uint64_t ad = sw128_desc(smem_u32(st));
-      uint64_t bd = sw128_desc(smem_u32(st + TILE_BYTES));
+      const uint32_t acc = tmem + (uint32_t)(b * BN);
+      bool ok = true;
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = g % S;
+        if (!mbar_wait(BAR(s), (g / S) & 1)) { ok = false; break; }
+        fence_after();
+        unsigned char* st = base + s * G::STAGE_BYTES;
+        const uint64_t ad = sw128_desc(smem_u32(st));
+        const uint64_t bd = sw128_desc(smem_u32(st + TILE_BYTES));
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
-        mma_bf16(tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), IDESC, (kb | kk) != 0);
-        if (NSPLIT == 3) {
-          uint64_t adl = sw128_desc(smem_u32(st + 2 * TILE_BYTES));
-          uint64_t bdl = sw128_desc(smem_u32(st + 3 * TILE_BYTES));
-          mma_bf16(tmem, ad + (uint64_t)(kk * 2), bdl + (uint64_t)(kk * 2), IDESC, 1);
-          mma_bf16(tmem, adl + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), IDESC, 1);
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint64_t o = (uint64_t)(kk * 2);
+          mma_bf16(acc, ad + o, bd + o, IDESC, (kb | kk) != 0);
+          if (NSPLIT == 3) {
+            const uint64_t adl = sw128_desc(smem_u32(st + 2 * TILE_BYTES));
+            const uint64_t bdl = sw128_desc(smem_u32(st + 3 * TILE_BYTES));
+            mma_bf16(acc, ad + o, bdl + o, IDESC, 1);
+            mma_bf16(acc, adl + o, bd + o, IDESC, 1);
+          }
         }
+        mma_commit(BAR(S + s));
+        *consumed = g + 1;
       }
-      mma_commit(smem_u32(&bars[G::STAGES + s]));
-      *consumed = kb + 1;
+      if (!ok) { *abort_flag = 1; mma_commit(BAR(2 * S + b)); break; }
+      if (nk > 0) mma_commit(BAR(2 * S + b));
+      else mbar_arrive(BAR(2 * S + b));
+      if (*abort_flag) break;
     }
-    if (nk > 0) mma_commit(smem_u32(&bars[2 * G::STAGES]));
+  } else if (warp >= 2) {
+    // ---------------- epilogue ----------------
+    const int quad = warp & 3;
+    float* scr = scratch + (warp - 2) * 32 * 33;
+    epi.begin_tile(0, 0);
+    int lt = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+      const Tile tl = tiles[t];
+      const int nk = (tl.k1 - tl.k0) / BK;
+      const int b = lt & 1;
+      if (!mbar_wait(BAR(2 * S + b), (lt >> 1) & 1)) { *abort_flag = 1; break; }
+      fence_after();
+      if (*abort_flag) break;
+      const uint32_t acc = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * BN);
+      float v[32];
+      for (int c = 0; c < BN / 32; ++c) {
+        if (nk > 0) {
+          tmem_ld32(acc + (uint32_t)(c * 32), v);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) v[q] = 0.f;
+        }
+        epi_block(epi, tl.m0 + quad * 32, tl.n0 + c * 32, v, scr, lane);
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(BAR(2 * S + 2 + b));
+    }
   }
   __syncwarp();
-
-  // ---------------- epilogue ----------------
-  epi.begin_tile(tl.m0, tl.n0);
-  if (warp >= 2) {
-    const int quad = warp & 3;
-    bool ok = true;
-    if (nk > 0) {
-      ok = mbar_wait(smem_u32(&bars[2 * G::STAGES]), 0);
-      fence_after();
-    }
-    if (!ok) *abort_flag = 1;
-    float* scr = scratch + (warp - 2) * 32 * 33;
-    float v[32];
-    for (int c = 0; c < BN / 32; ++c) {
-      if (nk > 0 && ok) {
-        tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32), v);
-      } else {
-#pragma unroll
-        for (int q = 0; q < 32; ++q) v[q] = 0.f;
-      }
-      if (ok) epi_block(epi, tl.m0 + quad * 32, tl.n0 + c * 32, v, scr, lane);
-    }
-  }
+  if (warp < 2) epi.begin_tile(0, 0);     // zero partials of the non-epilogue warps
   epi.reduce();
   fence_before();
   __syncthreads();
   if (threadIdx.x == 0 && *abort_flag) atomicOr(errword, ERRBIT_TIMEOUT);
   if (warp == 1) {
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+    tmem_dealloc(tmem, TMEM_COLS);
   }
 }
 
@@ -211,6 +239,17 @@ void set_attr_both() {
   set_attr<Epi, 3>();
 }
 
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
 }  // namespace
 
 // 2-D BF16 row-major [rows][cols] (ld = cols), box 64 (k) x box_rows (rows).
@@ -238,15 +277,17 @@ bool tc_available() {
 template <class Epi>
 bool tc_gemm(const GemmCtx& g, int tab, const bf16* A, const bf16* B, const Epi& e) {
   const size_t MM = (size_t)g.Mp * g.Mp;
+  const int nt = g.nt[tab];
+  const int grid = nt < num_sms() ? nt : num_sms();
   CUtensorMap ma, mb, mal, mbl;
   if (!tc_make_map(&ma, A, g.Mp, g.Mp, 128) || !tc_make_map(&mb, B, g.Mp, g.Mp, 128)) return false;
   if (g.split) {
     if (!tc_make_map(&mal, A + MM, g.Mp, g.Mp, 128) || !tc_make_map(&mbl, B + MM, g.Mp, g.Mp, 128)) return false;
     svgp_note_launch();
-    tc_gemm_kernel<Epi, 3><<<g.nt[tab], 192, Geo<3>::SMEM, g.st>>>(ma, mb, mal, mbl, g.tt[tab], e, g.err);
+    tc_gemm_kernel<Epi, 3><<<grid, 192, Geo<3>::SMEM, g.st>>>(ma, mb, mal, mbl, g.tt[tab], nt, e, g.err);
   } else {
     svgp_note_launch();
-    tc_gemm_kernel<Epi, 1><<<g.nt[tab], 192, Geo<1>::SMEM, g.st>>>(ma, mb, ma, mb, g.tt[tab], e, g.err);
+    tc_gemm_kernel<Epi, 1><<<grid, 192, Geo<1>::SMEM, g.st>>>(ma, mb, ma, mb, g.tt[tab], nt, e, g.err);
   }
   return true;
 }
@@ -284,4 +325,3 @@ void tc_init_attributes() {
   set_attr_both<EpiLupd>();
   set_attr_both<EpiGK>();
 }
-

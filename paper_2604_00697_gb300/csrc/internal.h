@@ -48,7 +48,6 @@ bool tc_gemm(const GemmCtx& g, int tab, const bf16* A, const bf16* B, const Epi&
 struct KufTC {
   bf16 *ZR, *ZK, *XR, *XK;
   float *cz, *cx;
-  double* red;
 };
 bool tc_kuf_supported(int D);
 void tc_kuf_init_attributes();

@@ -34,16 +34,16 @@ __global__ void prep_coords_kernel(const float* __restrict__ Z, const float* __r
 
 // Kuu = sf2 exp(-1/2 ||z~_i - z~_j||^2) (per-dimension differences), exact
 // sf2 on the diagonal, zero padding.  32x32 tiles, points staged in smem.
-template <class OutP>
+template <class OutP, int DP>
 __global__ void kuu_kernel(const float* __restrict__ Zs, int M, int Mp, int D,
                            const float* __restrict__ sf2p, float* __restrict__ Kf, OutP Klo, bool has_lo) {
-  __shared__ float zi[32][SVGP_MAXD + 1], zj[32][SVGP_MAXD + 1];
+  __shared__ float zi[32][DP + 1], zj[32][DP + 1];
   int Dp = (D + 3) & ~3;
   int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
-  for (int e = threadIdx.y * 32 + threadIdx.x; e < 32 * Dp; e += 32 * blockDim.y) {
-    int r = e / Dp, d = e % Dp;
-    zi[r][d] = Zs[(size_t)(i0 + r) * Dp + d];
-    zj[r][d] = Zs[(size_t)(j0 + r) * Dp + d];
+  for (int e = threadIdx.y * 32 + threadIdx.x; e < 32 * DP; e += 32 * blockDim.y) {
+    int r = e / DP, d = e % DP;
+    zi[r][d] = d < Dp ? Zs[(size_t)(i0 + r) * Dp + d] : 0.f;
+    zj[r][d] = d < Dp ? Zs[(size_t)(j0 + r) * Dp + d] : 0.f;
   }
   __syncthreads();
   float sf2 = *sf2p;
@@ -55,7 +55,8 @@ __global__ void kuu_kernel(const float* __restrict__ Zs, int M, int Mp, int D,
         val = sf2;
       } else {
         float r2 = 0.f;
-        for (int d = 0; d < D; ++d) { float e = zi[rr][d] - zj[threadIdx.x][d]; r2 = fmaf(e, e, r2); }
+#pragma unroll
+        for (int d = 0; d < DP; ++d) { float e = zi[rr][d] - zj[threadIdx.x][d]; r2 = fmaf(e, e, r2); }
         val = sf2 * expf(-0.5f * r2);
       }
     }
@@ -71,6 +72,9 @@ __global__ void prep_L_kernel(const float* __restrict__ Lin, int M, int Mp, floa
                               OutP Llo, OutP Ltlo, double* red) {
   __shared__ float tile[32][33];
   int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  // Blocks strictly above the diagonal stay zero in L (and below it in L^T):
+  // nothing else ever writes there, and the buffers start zeroed.
+  if (j0 > i0 + 31) return;
   int tx = threadIdx.x;
   double ld = 0.0;
   for (int ty = threadIdx.y; ty < 32; ty += blockDim.y) {
@@ -79,7 +83,7 @@ __global__ void prep_L_kernel(const float* __restrict__ Lin, int M, int Mp, floa
     Lf[(size_t)i * Mp + j] = val;
     put(Llo, (size_t)i * Mp + j, val);
     tile[ty][tx] = val;
-    if (i == j && i < M) ld += log(fabs((double)val));
+    if (i == j && i < M) ld += (double)logf(fabsf(val));
   }
   __syncthreads();
   for (int ty = threadIdx.y; ty < 32; ty += blockDim.y) {
@@ -138,36 +142,51 @@ __device__ __forceinline__ float ex2f(float x) {
     else { constexpr int DP = 32; __VA_ARGS__; }              \
   } while (0)
 
-// mu_n += sum_{i in chunk} Kuf_in v_i.  grid (ceil(B/128), ceil(M/256)).
+// mu_n += sum_{i in chunk} Kuf_in v_i.  grid (ceil(B/512), ceil(M/64)).
 template <int DP>
 __global__ void mu_kernel(const float* __restrict__ Zs, const float* __restrict__ Xs, int M, int B,
                           int D, const float* __restrict__ sf2p, const float* __restrict__ v,
                           float* __restrict__ mu) {
-  __shared__ float zs[256][DP + 1];
-  __shared__ float vs[256];
+  __shared__ float zs[64][DP + 1];
+  __shared__ float vs[64];
   const int Dp = (D + 3) & ~3;
-  int i0 = blockIdx.y * 256;
-  int ni = min(256, M - i0);
-  for (int e = threadIdx.x; e < 256 * DP; e += blockDim.x) {
+  int i0 = blockIdx.y * 64;
+  int ni = min(64, M - i0);
+  for (int e = threadIdx.x; e < 64 * DP; e += blockDim.x) {
     int r = e / DP, d = e % DP;
     zs[r][d] = (r < ni && d < Dp) ? Zs[(size_t)(i0 + r) * Dp + d] : 0.f;
   }
-  for (int r = threadIdx.x; r < 256; r += blockDim.x) vs[r] = r < ni ? v[i0 + r] : 0.f;
+  for (int r = threadIdx.x; r < 64; r += blockDim.x) vs[r] = r < ni ? v[i0 + r] : 0.f;
   __syncthreads();
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= B) return;
-  float x[DP];
+  // four points per thread: each shared-memory z~_i row feeds four distances
+  constexpr int NP = 4;
+  const int nb = blockIdx.x * blockDim.x * NP + threadIdx.x;
+  float x[NP][DP];
 #pragma unroll
-  for (int d = 0; d < DP; ++d) x[d] = d < Dp ? Xs[(size_t)n * Dp + d] : 0.f;
-  const float l2sf2 = log2f(*sf2p);
-  float acc = 0.f;
-  for (int r = 0; r < ni; ++r) {
-    float r2 = 0.f;
+  for (int p = 0; p < NP; ++p) {
+    const int n = nb + p * blockDim.x;
 #pragma unroll
-    for (int d = 0; d < DP; ++d) { float e = zs[r][d] - x[d]; r2 = fmaf(e, e, r2); }
-    acc = fmaf(ex2f(fmaf(-HALF_LOG2E, r2, l2sf2)), vs[r], acc);
+    for (int d = 0; d < DP; ++d) x[p][d] = (n < B && d < Dp) ? Xs[(size_t)n * Dp + d] : 0.f;
   }
-  atomicAdd(mu + n, acc);
+  const float l2sf2 = log2f(*sf2p);
+  float acc[NP] = {0.f, 0.f, 0.f, 0.f};
+  for (int r = 0; r < ni; ++r) {
+    float r2[NP] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int d = 0; d < DP; ++d) {
+      const float zd = zs[r][d];
+#pragma unroll
+      for (int p = 0; p < NP; ++p) { const float e = zd - x[p][d]; r2[p] = fmaf(e, e, r2[p]); }
+    }
+    const float vr = vs[r];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) acc[p] = fmaf(ex2f(fmaf(-HALF_LOG2E, r2[p], l2sf2)), vr, acc[p]);
+  }
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const int n = nb + p * blockDim.x;
+    if (n < B) atomicAdd(mu + n, acc[p]);
+  }
 }
 
 __global__ void pointwise_gauss_kernel(const float* __restrict__ y, const float* __restrict__ mu,
@@ -183,36 +202,51 @@ __global__ void pointwise_gauss_kernel(const float* __restrict__ y, const float*
   block_add_double(part, red + RED_SQERR);
 }
 
-// Kg_i += sum_{n in chunk} Kuf_in g_n.  grid (Mp/128, ceil(B/256)).
+// Kg_i += sum_{n in chunk} Kuf_in g_n.  grid (ceil(M/512), ceil(B/64)).
 template <int DP>
 __global__ void kg_kernel(const float* __restrict__ Zs, const float* __restrict__ Xs, int M, int B,
                           int D, const float* __restrict__ sf2p, const float* __restrict__ g,
                           float* __restrict__ Kg) {
-  __shared__ float xs[256][DP + 1];
-  __shared__ float gs[256];
+  __shared__ float xs[64][DP + 1];
+  __shared__ float gs[64];
   const int Dp = (D + 3) & ~3;
-  int n0 = blockIdx.y * 256;
-  int nn = min(256, B - n0);
-  for (int e = threadIdx.x; e < 256 * DP; e += blockDim.x) {
+  int n0 = blockIdx.y * 64;
+  int nn = min(64, B - n0);
+  for (int e = threadIdx.x; e < 64 * DP; e += blockDim.x) {
     int r = e / DP, d = e % DP;
     xs[r][d] = (r < nn && d < Dp) ? Xs[(size_t)(n0 + r) * Dp + d] : 0.f;
   }
-  for (int r = threadIdx.x; r < 256; r += blockDim.x) gs[r] = r < nn ? g[n0 + r] : 0.f;
+  for (int r = threadIdx.x; r < 64; r += blockDim.x) gs[r] = r < nn ? g[n0 + r] : 0.f;
   __syncthreads();
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M) return;
-  float z[DP];
+  // four inducing points per thread
+  constexpr int NP = 4;
+  const int ib = blockIdx.x * blockDim.x * NP + threadIdx.x;
+  float z[NP][DP];
 #pragma unroll
-  for (int d = 0; d < DP; ++d) z[d] = d < Dp ? Zs[(size_t)i * Dp + d] : 0.f;
-  const float l2sf2 = log2f(*sf2p);
-  float acc = 0.f;
-  for (int r = 0; r < nn; ++r) {
-    float r2 = 0.f;
+  for (int p = 0; p < NP; ++p) {
+    const int i = ib + p * blockDim.x;
 #pragma unroll
-    for (int d = 0; d < DP; ++d) { float e = xs[r][d] - z[d]; r2 = fmaf(e, e, r2); }
-    acc = fmaf(ex2f(fmaf(-HALF_LOG2E, r2, l2sf2)), gs[r], acc);
+    for (int d = 0; d < DP; ++d) z[p][d] = (i < M && d < Dp) ? Zs[(size_t)i * Dp + d] : 0.f;
   }
-  atomicAdd(Kg + i, acc);
+  const float l2sf2 = log2f(*sf2p);
+  float acc[NP] = {0.f, 0.f, 0.f, 0.f};
+  for (int r = 0; r < nn; ++r) {
+    float r2[NP] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int d = 0; d < DP; ++d) {
+      const float xd = xs[r][d];
+#pragma unroll
+      for (int p = 0; p < NP; ++p) { const float e = xd - z[p][d]; r2[p] = fmaf(e, e, r2[p]); }
+    }
+    const float gr = gs[r];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) acc[p] = fmaf(ex2f(fmaf(-HALF_LOG2E, r2[p], l2sf2)), gr, acc[p]);
+  }
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const int i = ib + p * blockDim.x;
+    if (i < M) atomicAdd(Kg + i, acc[p]);
+  }
 }
 
 // Symmetrised G_P = c/2 (Kg m^T + m Kg^T) + c/(2 noise) Psi + Kuu/2
@@ -445,7 +479,7 @@ void k_kuu(const float* Zs, int M, int Mp, int D, const float* sf2, float* Kf, O
            cudaStream_t st) {
   dim3 grid(Mp / 32, Mp / 32), blk(32, 8);
   svgp_note_launch();
-  kuu_kernel<OutP><<<grid, blk, 0, st>>>(Zs, M, Mp, D, sf2, Kf, Klo, has_lo);
+  SVGP_DP_DISPATCH(D, kuu_kernel<OutP, DP><<<grid, blk, 0, st>>>(Zs, M, Mp, D, sf2, Kf, Klo, has_lo));
 }
 template void k_kuu<float*>(const float*, int, int, int, const float*, float*, float*, bool, cudaStream_t);
 template void k_kuu<bf16*>(const float*, int, int, int, const float*, float*, bf16*, bool, cudaStream_t);
@@ -471,7 +505,7 @@ void k_gemv(const float* A, int Mp, int M, const float* x, float alpha, const fl
 void k_mu(const float* Zs, const float* Xs, int M, int B, int D, const float* sf2, const float* v,
           float* mu, cudaStream_t st) {
   cudaMemsetAsync(mu, 0, sizeof(float) * B, st);
-  dim3 grid((B + 127) / 128, (M + 255) / 256);
+  dim3 grid((B + 511) / 512, (M + 63) / 64);
   svgp_note_launch();
   SVGP_DP_DISPATCH(D, mu_kernel<DP><<<grid, 128, 0, st>>>(Zs, Xs, M, B, D, sf2, v, mu));
 }
@@ -487,7 +521,7 @@ void k_pointwise_gauss(const float* y, const float* mu, const float* noise, int 
 void k_kg(const float* Zs, const float* Xs, int M, int Mp, int B, int D, const float* sf2,
           const float* g, float* Kg, cudaStream_t st) {
   cudaMemsetAsync(Kg, 0, sizeof(float) * Mp, st);
-  dim3 grid(Mp / 128, (B + 255) / 256);
+  dim3 grid((M + 511) / 512, (B + 63) / 64);
   svgp_note_launch();
   SVGP_DP_DISPATCH(D, kg_kernel<DP><<<grid, 128, 0, st>>>(Zs, Xs, M, B, D, sf2, g, Kg));
 }

@@ -319,7 +319,6 @@ svgp_status svgp_create(const svgp_config* cfg, svgp_handle** out) {
     ok = dalloc(h, &h->kt.ZR, 2 * 64 * h->Mp) && dalloc(h, &h->kt.ZK, 2 * 64 * h->Mp) &&
          dalloc(h, &h->kt.XR, 2 * 64 * Bp) && dalloc(h, &h->kt.XK, 2 * 64 * Bp) &&
          dalloc(h, &h->kt.cz, 4 * h->Mp) && dalloc(h, &h->kt.cx, 4 * Bp);
-  h->kt.red = h->red;
   if (ok && h->mode == MODE_F32) { h->Kuu_lo = h->Kuu_f; h->P_lo = h->Pf; }
   if (ok) ok = build_ctx(h, h->gs, 128, 128) && build_ctx(h, h->gt, 128, 128);
   simt_init_attributes();
