@@ -98,6 +98,19 @@ __device__ __forceinline__ auto call_pre(E& e, int i0, int j0, float (&v)[32], i
 template <class E>
 __device__ __forceinline__ void call_pre(E&, int, int, float (&)[32], int, long) {}
 
+// block() with the warp's 32 x 32 shared-memory scratch (row stride lds, odd,
+// so row and column accesses are conflict-free) when the functor takes it.
+template <class E>
+__device__ __forceinline__ auto call_block(E& e, int i0, int j0, const float (&v)[32], const float (&vt)[32], int lane,
+                                           float* scr, int lds, int) -> decltype(e.block(i0, j0, v, vt, lane, scr, lds), void()) {
+  e.block(i0, j0, v, vt, lane, scr, lds);
+}
+template <class E>
+__device__ __forceinline__ void call_block(E& e, int i0, int j0, const float (&v)[32], const float (&vt)[32], int lane,
+                                           float*, int, long) {
+  e.block(i0, j0, v, vt, lane);
+}
+
 // Vt = L^T K~ = L^T Kuu + L^T diag(s): the diagonal of S~ is added in FP32 so
 // that it is not lost when Kuu is rounded (Section 2: S~ lower-bounds the
 // eigenvalues of K~).  Lt[i,j] = L[j,i].  s == nullptr: plain L^T S.
@@ -274,48 +287,41 @@ struct EpiP {
 };
 
 // G_K~ = -L (L^T G_P L + I/2) L^T on the lower region (acc = L S L^T part);
-// writes G_Kuu = G_K~ + P/2 - v v^T/2 (mirrored) and ds_i = G_K~_ii + 1/(2 s_i).
+// writes G_Kuu = G_K~ + P/2 - v v^T/2 (symmetric: each value is computed once
+// in the column layout, written directly, and written mirrored through the
+// warp's shared-memory scratch) and ds_i = G_K~_ii + 1/(2 s_i).
 struct EpiGK {
   float* GKuu; int ld; int M;
   const float* Pf; const float* v; const float* s; float* ds;
   __device__ bool skip() const { return false; }
   __device__ void begin_tile(int, int) {}
-  __device__ __forceinline__ void block(int i0, int j0, const float (&vr)[32], const float (&vt)[32], int lane) {
+  __device__ __forceinline__ void block(int i0, int j0, const float (&)[32], const float (&vt)[32], int lane,
+                                        float* scr, int lds) {
     if (j0 > i0 + 31) return;
-    // column layout loads (direct part): P[i0 + r][j], v[i0 + r]
     const int j = j0 + lane;
     const float vj = j < M ? __ldg(v + j) : 0.f;
-    float pc[32], vi_c[32];
+    const float vrow = (i0 + lane) < M ? __ldg(v + i0 + lane) : 0.f;     // v[i0 + lane], shuffled below
+    float pc[32];
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-      const int i = i0 + r;
-      pc[r] = (j <= i) ? __ldg(Pf + (size_t)i * ld + j) : 0.f;
-      vi_c[r] = i < M ? __ldg(v + i) : 0.f;
-    }
-    // row layout loads (mirror part): P[j0 + q][i], v[j0 + q]
-    const int i = i0 + lane;
-    const float vi = i < M ? __ldg(v + i) : 0.f;
-    float pr[32], vq[32];
-#pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      const int jj = j0 + q;
-      pr[q] = (jj < i) ? __ldg(Pf + (size_t)jj * ld + i) : 0.f;
-      vq[q] = jj < M ? __ldg(v + jj) : 0.f;
-    }
+    for (int r = 0; r < 32; ++r) pc[r] = (j <= i0 + r) ? __ldg(Pf + (size_t)(i0 + r) * ld + j) : 0.f;
+    __syncwarp();
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
       const int ii = i0 + r;
-      if (j > ii) continue;
-      const float gk = -vt[r];
-      GKuu[(size_t)ii * ld + j] = gk + 0.5f * pc[r] - 0.5f * vi_c[r] * vj;
-      if (ii == j && ii < M) ds[ii] = gk + 0.5f / s[ii];
+      const float vi = __shfl_sync(0xffffffffu, vrow, r);
+      const float g = -vt[r] + 0.5f * pc[r] - 0.5f * vi * vj;
+      scr[r * lds + lane] = g;
+      if (j <= ii) GKuu[(size_t)ii * ld + j] = g;
+      if (ii == j && ii < M) ds[ii] = -vt[r] + 0.5f / s[ii];
     }
+    __syncwarp();
+    // mirror: G[j0 + q][i0 + lane] = g(i0 + lane, j0 + q) for j0 + q < i0 + lane
+    const int i = i0 + lane;
 #pragma unroll
     for (int q = 0; q < 32; ++q) {
-      const int jj = j0 + q;
-      if (jj >= i) continue;
-      GKuu[(size_t)jj * ld + i] = -vr[q] + 0.5f * pr[q] - 0.5f * vi * vq[q];
+      if (j0 + q < i) GKuu[(size_t)(j0 + q) * ld + i] = scr[lane * lds + q];
     }
+    __syncwarp();
   }
   __device__ void reduce() {}
 };

@@ -6,14 +6,18 @@
 //
 // Generation of a 128 x 64 operand tile G[r, k] = sf2 exp(-1/2 |p_r - q_k|^2)
 // (scaled coordinates p, q) per k-block:
-//   1. the cross term S = p . q is a small tcgen05 MMA into TMEM, with each
-//      coordinate vector split into BF16 hi + lo parts: the row operand holds
-//      [hi, hi, lo] and the k operand [hi, lo, hi] along K, so one K <= 64
-//      MMA gives hi.hi + hi.lo + lo.hi (about 16 significant bits);
-//   2. four transform warps read S from TMEM (one row per thread), form
-//      exp2(log2(e) S + c_r + c_k) with the per-point offsets
-//      c = -1/2 log2(e) |p|^2 and log2(sf2), and store BF16 (or hi/lo BF16)
-//      values into the 128-byte-swizzled operand buffer of the main MMA;
+//   1. the whole exponent t = log2(G) is one small tcgen05 MMA into TMEM:
+//      with p' = sqrt(log2 e) p and the per-point constants
+//      c_r = -1/2 |p'_r|^2 and c_k = -1/2 |q'_k|^2 + log2(sf2),
+//        t = p'_r . q'_k + c_r + c_k,
+//      where each coordinate vector is split into BF16 hi + lo parts (row
+//      operand [hi, hi, lo], k operand [hi, lo, hi], giving hi.hi + hi.lo +
+//      lo.hi, about 16 significant bits) and each constant into three BF16
+//      parts (24 bits) paired with ones on the other side; padded points carry
+//      c = -1e30, so their values come out as exactly 0;
+//   2. the transform warps read t from TMEM (one row per thread), take exp2
+//      and store BF16 (or hi/lo BF16) values into the 128-byte-swizzled
+//      operand buffer of the main MMA;
 //   3. one thread issues the main tcgen05 MMA on the generated tile(s).
 // Warp roles (320 threads): 0 TMA producer, 1 TMEM allocator + MMA issuer,
 // 2..9 transform and then epilogue (warp w covers TMEM lanes 32 (w mod 4) ..
@@ -33,7 +37,7 @@ constexpr int NTW = 8;                        // transform / epilogue warps
 constexpr int KUF_THREADS = 64 + 32 * NTW;
 constexpr int STASH_LD = 129;                 // padded row stride (floats) of the W stash
 constexpr int STASH_BYTES = 128 * STASH_LD * 4;
-constexpr float LOG2E = 1.4426950408889634f;
+constexpr float SQRT_LOG2E = 1.2011224087864498f;   // sqrt(log2(e))
 
 enum { KIND_PSI = 0, KIND_W = 1 };
 
@@ -62,15 +66,10 @@ struct KGeo {
 };
 
 struct KufArgs {
-  // per-point constants c = -1/2 log2(e) |p|^2 of the row and k points
-  const float* crow_a;   // PSI: z rows (I);  W: unused
-  const float* crow_b;   // PSI: z rows (J);  W: x rows (batch)
-  const float* ck;       // PSI: x (batch);   W: z (inducing)
-  int nrow_a, nrow_b, nk;   // valid counts (rows beyond are zero)
   int nkb;                  // number of k-blocks
-  const float* sf2;
   int* errword;
 };
+
 
 __device__ __forceinline__ float ex2(float x) {
   float y;
@@ -109,25 +108,18 @@ __device__ __forceinline__ float ex2_poly(float t) {
 // the FMA pipe instead of the MUFU unit.
 constexpr int POLY_MASK = 0;
 
-// Transform 32 cross-term values s[q] = p_row . q_k (k = kbase + q) of one row
+// Transform 32 exponents t[q] (k = kcol0 + q within the k-block) of one row
 // into BF16 (hi, and lo = value - hi for NSPLIT = 3) operand values at
-// columns kcol0 + q of the 128-byte-swizzled tile(s).  ck[q] holds the k-point
-// constants.  When stash != null the FP32 values also go to
-// stash[(kcol0 + q) * STASH_LD + row].
+// columns kcol0 + q of the 128-byte-swizzled tile(s).  When stash != null the
+// FP32 values also go to stash[(kcol0 + q) * STASH_LD + row].
 template <int NSPLIT>
-__device__ __forceinline__ void gen32(const float (&s)[32], float crow, const float (&ck)[32], int kbase, int nk,
-                                      bool row_ok, unsigned char* hi, unsigned char* lo, int row, int kcol0,
+__device__ __forceinline__ void gen32(const float (&t)[32], unsigned char* hi, unsigned char* lo, int row, int kcol0,
                                       float* stash) {
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     float v[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int k = kbase + c * 8 + q;
-      const float t = fmaf(s[c * 8 + q], LOG2E, crow + ck[c * 8 + q]);
-      const float e = ((POLY_MASK >> q) & 1) ? ex2_poly<NSPLIT == 3 ? 6 : 5>(t) : ex2(t);
-      v[q] = (row_ok && k < nk) ? e : 0.f;
-    }
+    for (int q = 0; q < 8; ++q) v[q] = ((POLY_MASK >> q) & 1) ? ex2_poly<NSPLIT == 3 ? 6 : 5>(t[c * 8 + q]) : ex2(t[c * 8 + q]);
     if (stash) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) stash[(kcol0 + c * 8 + q) * STASH_LD + row] = v[q];
@@ -168,7 +160,7 @@ __device__ __forceinline__ void epi_block32(Epi& epi, int i0, int j0, const floa
 #pragma unroll
   for (int r = 0; r < 32; ++r) vt[r] = scr[r * 33 + lane];
   __syncwarp();
-  epi.block(i0, j0, v, vt, lane);
+  call_block(epi, i0, j0, v, vt, lane, scr, 33, 0);
 }
 
 // Fused epilogue of W = P Kuf for the 128 x 128 output block (rows i = m0 + r,
@@ -430,28 +422,9 @@ kuf_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // row-coordinate s
     const int quad = warp & 3, half = (warp - 2) >> 2;
     const int row = quad * 32 + lane, kcol0 = half * 32;
     const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
-    const float lsf2 = log2f(*ka.sf2);
-    float crA = 0.f, crB = 0.f;
-    bool okA = false, okB = false;
-    if (KIND == KIND_PSI) {
-      okA = (m0 + row) < ka.nrow_a;
-      okB = (n0 + row) < ka.nrow_b;
-      crA = lsf2 + (okA ? ka.crow_a[m0 + row] : 0.f);
-      crB = lsf2 + (okB ? ka.crow_b[n0 + row] : 0.f);
-    } else {
-      okB = (n0 + row) < ka.nrow_b;
-      crB = lsf2 + (okB ? ka.crow_b[n0 + row] : 0.f);
-    }
     for (int kb = 0; kb < nkb; ++kb) {
       if (*abort_flag) break;
       const int s = kb % S, b = kb & 1;
-      const int kbase = kb * KB + kcol0;
-      float ck[32];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float4 c4 = __ldg(reinterpret_cast<const float4*>(ka.ck + kbase + 4 * q));
-        ck[4 * q] = c4.x; ck[4 * q + 1] = c4.y; ck[4 * q + 2] = c4.z; ck[4 * q + 3] = c4.w;
-      }
       if (!mbar_wait(BAR(B_SFULL + b), (kb >> 1) & 1)) { *abort_flag = 1; break; }
       fence_after();
       float sa[32], sbv[32];
@@ -464,14 +437,13 @@ kuf_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // row-coordinate s
       if (!mbar_wait(BAR(B_EMPTY + s), ((kb / S) & 1) ^ 1)) { *abort_flag = 1; break; }
       unsigned char* st = stg + s * G::STAGE;
       if (KIND == KIND_PSI) {
-        gen32<NSPLIT>(sa, crA, ck, kbase, ka.nk, okA, st + G::OFF_GA, st + G::OFF_GA + GT, row, kcol0, nullptr);
-        if (!diag)
-          gen32<NSPLIT>(sbv, crB, ck, kbase, ka.nk, okB, st + G::OFF_GB, st + G::OFF_GB + GT, row, kcol0, nullptr);
+        gen32<NSPLIT>(sa, st + G::OFF_GA, st + G::OFF_GA + GT, row, kcol0, nullptr);
+        if (!diag) gen32<NSPLIT>(sbv, st + G::OFF_GB, st + G::OFF_GB + GT, row, kcol0, nullptr);
       } else {
         // the k-blocks covering the output rows [m0, m0 + 128) also fill the stash
         const int kb0 = kb * KB;
         float* sh = (kb0 >= m0 && kb0 < m0 + 128) ? stash + (size_t)(kb0 - m0) * STASH_LD : nullptr;
-        gen32<NSPLIT>(sbv, crB, ck, kbase, ka.nk, okB, st + G::OFF_GB, st + G::OFF_GB + GT, row, kcol0, sh);
+        gen32<NSPLIT>(sbv, st + G::OFF_GB, st + G::OFF_GB + GT, row, kcol0, sh);
       }
       fence_proxy_async();
       __syncwarp();
@@ -525,32 +497,52 @@ kuf_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // row-coordinate s
 
 namespace {
 
-// Split coordinates of the Kuf generator: row role [hi, hi, lo], k role
-// [hi, lo, hi] (64 BF16 per point, zero padded), and c = -1/2 log2(e) |p|^2.
-__global__ void kuf_prep_kernel(const float* __restrict__ P, int n, int npad, int D, bf16* __restrict__ R,
-                                bf16* __restrict__ K, float* __restrict__ c) {
+// Operand vectors of the exponent MMA (64 BF16 per point, zero padded) for
+// points p (scaled coordinates, n valid rows of npad):
+//   row role R = [p'hi (D), p'hi (D), p'lo (D), c_hi, c_mid, c_lo, 1, 1, 1]
+//   k role   K = [p'hi (D), p'lo (D), p'hi (D), 1, 1, 1, c'_hi, c'_mid, c'_lo]
+// with p' = sqrt(log2 e) p, c = -1/2 |p'|^2 and c' = c + log2(sf2); padded
+// rows get c = c' = -1e30.  R_a . K_b = t(a, b) = log2 of the SE-ARD value.
+__global__ void kuf_prep_kernel(const float* __restrict__ P, int n, int npad, int D, const float* __restrict__ sf2,
+                                bf16* __restrict__ R, bf16* __restrict__ K) {
   // one row per threadIdx.y (8 rows per block), 64 threads per row
   __shared__ float part_sum[8][2];
   const int Dp = (D + 3) & ~3;
   const int r = blockIdx.x * 8 + threadIdx.y;
   const int d = threadIdx.x;
-  const bool live = r < npad;
-  const int part = d / D;               // 0, 1, 2 or beyond (padding)
-  const bool val = live && r < n && part < 3;
-  const float x = val ? P[(size_t)r * Dp + d % D] : 0.f;
+  const bool live = r < npad, valid = r < n;
+  const int part = d / D;               // 0, 1, 2: coordinate slots; then constants
+  const float x = (valid && part < 3) ? SQRT_LOG2E * P[(size_t)r * Dp + d % D] : 0.f;
   const bf16 hi = __float2bfloat16_rn(x);
   const bf16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-  const bf16 z = __float2bfloat16_rn(0.f);
-  if (live) {
-    R[(size_t)r * 64 + d] = val ? (part == 2 ? lo : hi) : z;
-    K[(size_t)r * 64 + d] = val ? (part == 1 ? lo : hi) : z;
-  }
-  float sq = (val && part == 0) ? x * x : 0.f;
+  float sq = (part == 0) ? x * x : 0.f;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
   if ((d & 31) == 0) part_sum[threadIdx.y][d >> 5] = sq;
   __syncthreads();
-  if (d == 0 && live) c[r] = -0.5f * LOG2E * (part_sum[threadIdx.y][0] + part_sum[threadIdx.y][1]);
+  if (!live) return;
+  const float c_row = valid ? -0.5f * (part_sum[threadIdx.y][0] + part_sum[threadIdx.y][1]) : -1e30f;
+  const float c_k = valid ? c_row + log2f(*sf2) : -1e30f;
+  // three-way BF16 split of a constant: component q of (hi, mid, lo)
+  auto split3 = [](float c, int q) {
+    const float h = __bfloat162float(__float2bfloat16_rn(c));
+    const float m = __bfloat162float(__float2bfloat16_rn(c - h));
+    return q == 0 ? h : (q == 1 ? m : c - h - m);
+  };
+  const bf16 one = __float2bfloat16_rn(1.f), z = __float2bfloat16_rn(0.f);
+  bf16 rv = z, kv = z;
+  if (part < 3) {
+    rv = part == 2 ? lo : hi;
+    kv = part == 1 ? lo : hi;
+  } else if (d < 3 * D + 3) {
+    rv = __float2bfloat16_rn(split3(c_row, d - 3 * D));
+    kv = one;
+  } else if (d < 3 * D + 6) {
+    rv = one;
+    kv = __float2bfloat16_rn(split3(c_k, d - 3 * D - 3));
+  }
+  R[(size_t)r * 64 + d] = rv;
+  K[(size_t)r * 64 + d] = kv;
 }
 
 template <int KIND, int NSPLIT>
@@ -561,14 +553,14 @@ void set_kuf_attr() {
 
 }  // namespace
 
-void k_kuf_prep(const float* Zs, const float* Xs, int M, int Mp, int B, int Bp, int D, const KufTC& t,
-                cudaStream_t st) {
+void k_kuf_prep(const float* Zs, const float* Xs, int M, int Mp, int B, int Bp, int D, const float* sf2,
+                const KufTC& t, cudaStream_t st) {
   dim3 blk(64, 8);
   svgp_note_launch();
-  kuf_prep_kernel<<<(Mp + 7) / 8, blk, 0, st>>>(Zs, M, Mp, D, t.ZR, t.ZK, t.cz);
+  kuf_prep_kernel<<<(Mp + 7) / 8, blk, 0, st>>>(Zs, M, Mp, D, sf2, t.ZR, t.ZK);
   if (Xs && B > 0) {
     svgp_note_launch();
-    kuf_prep_kernel<<<(Bp + 7) / 8, blk, 0, st>>>(Xs, B, Bp, D, t.XR, t.XK, t.cx);
+    kuf_prep_kernel<<<(Bp + 7) / 8, blk, 0, st>>>(Xs, B, Bp, D, sf2, t.XR, t.XK);
   }
 }
 
@@ -579,14 +571,14 @@ void tc_kuf_init_attributes() {
   set_kuf_attr<KIND_W, 3>();
 }
 
-bool tc_kuf_supported(int D) { return D >= 1 && 3 * D <= 64 && tc_available(); }
+bool tc_kuf_supported(int D) { return D >= 1 && 3 * D + 6 <= 64 && tc_available(); }
 
 bool tc_psi(const GemmCtx& g, const KufGen& kg, const KufTC& t, int B, EpiPsi e) {
   if (!tc_kuf_supported(kg.D)) return false;
   const int Bp = (B + 127) / 128 * 128;
   CUtensorMap mr, mk;
   if (!tc_make_map(&mr, t.ZR, g.Mp, 64, 128) || !tc_make_map(&mk, t.XK, Bp, 64, 64)) return false;
-  KufArgs ka{t.cz, t.cz, t.cx, kg.M, kg.M, B, Bp / KB, kg.sf2, g.err};
+  KufArgs ka{Bp / KB, g.err};
   WEpi we{};
   svgp_note_launch();
   if (g.split)
@@ -609,7 +601,7 @@ bool tc_w(const GemmCtx& g, const bf16* P, const KufTC& t, const WEpi& we) {
   } else {
     mpl = mp;
   }
-  KufArgs ka{t.cz, t.cx, t.cz, we.gen.M, B, we.gen.M, g.Mp / KB, we.gen.sf2, g.err};
+  KufArgs ka{g.Mp / KB, g.err};
   EpiPsi ep{nullptr, 0};
   dim3 grid(Bp / 128, g.Mp / 128);
   svgp_note_launch();

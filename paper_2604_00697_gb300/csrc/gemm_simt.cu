@@ -158,7 +158,7 @@ __device__ __forceinline__ void simt_epilogue(Epi& epi, int m0, int n0, float (&
     __syncwarp();
 #pragma unroll
     for (int q = 0; q < 32; ++q) vt[q] = T[(bi * 32 + q) * ldT + bj * 32 + lane];
-    epi.block(m0 + bi * 32, n0 + bj * 32, v, vt, lane);
+    call_block(epi, m0 + bi * 32, n0 + bj * 32, v, vt, lane, T + (bi * 32) * ldT + bj * 32, ldT, 0);
   }
   epi.reduce();
 }

@@ -58,7 +58,7 @@ __device__ __forceinline__ void epi_block(Epi& epi, int i0, int j0, float (&v)[3
 #pragma unroll
   for (int r = 0; r < 32; ++r) vt[r] = scr[r * 33 + lane];
   __syncwarp();
-  epi.block(i0, j0, v, vt, lane);
+  call_block(epi, i0, j0, v, vt, lane, scr, 33, 0);
 }
 
 template <class Epi, int NSPLIT>

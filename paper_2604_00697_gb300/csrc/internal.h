@@ -47,12 +47,11 @@ bool tc_gemm(const GemmCtx& g, int tab, const bf16* A, const bf16* B, const Epi&
 // [hi, lo, hi]) and per-point offsets c = -1/2 log2(e) |p|^2.
 struct KufTC {
   bf16 *ZR, *ZK, *XR, *XK;
-  float *cz, *cx;
 };
 bool tc_kuf_supported(int D);
 void tc_kuf_init_attributes();
-void k_kuf_prep(const float* Zs, const float* Xs, int M, int Mp, int B, int Bp, int D, const KufTC& t,
-                cudaStream_t st);
+void k_kuf_prep(const float* Zs, const float* Xs, int M, int Mp, int B, int Bp, int D, const float* sf2,
+                const KufTC& t, cudaStream_t st);
 bool tc_psi(const GemmCtx& g, const KufGen& kg, const KufTC& t, int B, EpiPsi e);
 bool tc_w(const GemmCtx& g, const bf16* P, const KufTC& t, const WEpi& we);
 

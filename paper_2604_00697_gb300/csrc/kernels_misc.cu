@@ -33,35 +33,42 @@ __global__ void prep_coords_kernel(const float* __restrict__ Z, const float* __r
 }
 
 // Kuu = sf2 exp(-1/2 ||z~_i - z~_j||^2) (per-dimension differences), exact
-// sf2 on the diagonal, zero padding.  32x32 tiles, points staged in smem.
+// sf2 on the diagonal, zero padding.  64 x 64 tiles (16 elements per thread),
+// points staged in shared memory.
 template <class OutP, int DP>
-__global__ void kuu_kernel(const float* __restrict__ Zs, int M, int Mp, int D,
-                           const float* __restrict__ sf2p, float* __restrict__ Kf, OutP Klo, bool has_lo) {
-  __shared__ float zi[32][DP + 1], zj[32][DP + 1];
-  int Dp = (D + 3) & ~3;
-  int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
-  for (int e = threadIdx.y * 32 + threadIdx.x; e < 32 * DP; e += 32 * blockDim.y) {
-    int r = e / DP, d = e % DP;
+__global__ void __launch_bounds__(256) kuu_kernel(const float* __restrict__ Zs, int M, int Mp, int D,
+                                                  const float* __restrict__ sf2p, float* __restrict__ Kf,
+                                                  OutP Klo, bool has_lo) {
+  __shared__ float zi[64][DP + 1], zj[64][DP + 1];
+  const int Dp = (D + 3) & ~3;
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int e = ty * 32 + tx; e < 64 * DP; e += 256) {
+    const int r = e / DP, d = e % DP;
     zi[r][d] = d < Dp ? Zs[(size_t)(i0 + r) * Dp + d] : 0.f;
     zj[r][d] = d < Dp ? Zs[(size_t)(j0 + r) * Dp + d] : 0.f;
   }
   __syncthreads();
-  float sf2 = *sf2p;
-  for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
-    int i = i0 + rr, j = j0 + threadIdx.x;
-    float val = 0.f;
-    if (i < M && j < M) {
-      if (i == j) {
-        val = sf2;
-      } else {
-        float r2 = 0.f;
+  const float sf2 = *sf2p;
+#pragma unroll 2
+  for (int ri = 0; ri < 8; ++ri) {
+    const int rr = ty + 8 * ri, i = i0 + rr;
+    float val[2];
 #pragma unroll
-        for (int d = 0; d < DP; ++d) { float e = zi[rr][d] - zj[threadIdx.x][d]; r2 = fmaf(e, e, r2); }
-        val = sf2 * expf(-0.5f * r2);
-      }
+    for (int cj = 0; cj < 2; ++cj) {
+      const int cc = tx + 32 * cj, j = j0 + cc;
+      float r2 = 0.f;
+#pragma unroll
+      for (int d = 0; d < DP; ++d) { const float e = zi[rr][d] - zj[cc][d]; r2 = fmaf(e, e, r2); }
+      float v = (i == j) ? sf2 : sf2 * expf(-0.5f * r2);
+      val[cj] = (i < M && j < M) ? v : 0.f;
     }
-    Kf[(size_t)i * Mp + j] = val;
-    if (has_lo) put(Klo, (size_t)i * Mp + j, val);
+#pragma unroll
+    for (int cj = 0; cj < 2; ++cj) {
+      const size_t o = (size_t)i * Mp + j0 + tx + 32 * cj;
+      Kf[o] = val[cj];
+      if (has_lo) put(Klo, o, val[cj]);
+    }
   }
 }
 
@@ -94,29 +101,37 @@ __global__ void prep_L_kernel(const float* __restrict__ Lin, int M, int Mp, floa
 }
 
 // y = alpha * A (x + beta * x2)  (A: Mp x Mp FP32, rows < M); one warp per
-// row.  Optionally dot_out += sum_i y_i dotw_i.
-__global__ void gemv_kernel(const float* __restrict__ A, int Mp, int M, const float* __restrict__ x,
-                            float alpha, const float* __restrict__ x2, float beta, float* __restrict__ y,
-                            const float* __restrict__ dotw, double* dot_out) {
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+// row, the combined vector staged once per block in shared memory (Mp floats
+// of dynamic shared memory).  Optionally dot_out += sum_i y_i dotw_i.
+__global__ void __launch_bounds__(256) gemv_kernel(const float* __restrict__ A, int Mp, int M,
+                                                   const float* __restrict__ x, float alpha,
+                                                   const float* __restrict__ x2, float beta, float* __restrict__ y,
+                                                   const float* __restrict__ dotw, double* dot_out) {
+  extern __shared__ float xs[];
+  for (int j = threadIdx.x; j < Mp; j += blockDim.x) {
+    float xx = 0.f;
+    if (j < M) {
+      xx = x[j];
+      if (x2) xx = fmaf(beta, x2[j], xx);
+    }
+    xs[j] = xx;
+  }
+  __syncthreads();
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   double part = 0.0;
   if (warp < M) {
-    const float* row = A + (size_t)warp * Mp;
-    float acc = 0.f;
-    for (int j = lane * 4; j < M; j += 128) {
-      float4 a = *reinterpret_cast<const float4*>(row + j);
-      float xv[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        int jj = j + q;
-        float xx = jj < M ? x[jj] : 0.f;
-        if (x2 && jj < M) xx += beta * x2[jj];
-        xv[q] = xx;
-      }
-      acc = fmaf(a.x, xv[0], acc); acc = fmaf(a.y, xv[1], acc);
-      acc = fmaf(a.z, xv[2], acc); acc = fmaf(a.w, xv[3], acc);
+    const float4* row = reinterpret_cast<const float4*>(A + (size_t)warp * Mp);
+    const float4* xv = reinterpret_cast<const float4*>(xs);
+    float acc0 = 0.f, acc1 = 0.f;
+    const int n4 = Mp / 4;
+#pragma unroll 4
+    for (int k = lane; k < n4; k += 32) {
+      const float4 a = __ldg(row + k);
+      const float4 b = xv[k];
+      acc0 = fmaf(a.x, b.x, acc0); acc1 = fmaf(a.y, b.y, acc1);
+      acc0 = fmaf(a.z, b.z, acc0); acc1 = fmaf(a.w, b.w, acc1);
     }
-    acc = warp_sum(acc) * alpha;
+    const float acc = warp_sum(acc0 + acc1) * alpha;
     if (lane == 0) {
       y[warp] = acc;
       if (dotw) part = (double)acc * dotw[warp];
@@ -256,73 +271,82 @@ __global__ void gp_assemble_kernel(const float* __restrict__ Kuu, const float* _
                                    const float* __restrict__ Kg, const float* __restrict__ m,
                                    const float* __restrict__ w, const float* __restrict__ noise, float c,
                                    int M, int Mp, OutP out) {
-  float cn = c * 0.5f / *noise;
-  size_t tot = (size_t)Mp * Mp;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
-    int i = (int)(e / Mp), j = (int)(e % Mp);
+  // block: row i = blockIdx.y, 4 consecutive columns per thread
+  const float cn = c * 0.5f / *noise;
+  const int i = blockIdx.y;
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (j >= Mp) return;
+  const size_t e = (size_t)i * Mp + j;
+  const float4 ps = __ldg(reinterpret_cast<const float4*>(Psi + e));
+  const float4 ku = __ldg(reinterpret_cast<const float4*>(Kuu + e));
+  const float pv[4] = {ps.x, ps.y, ps.z, ps.w}, kv[4] = {ku.x, ku.y, ku.z, ku.w};
+  const bool row_ok = i < M;
+  const float kgi = row_ok ? Kg[i] : 0.f, mi = row_ok ? m[i] : 0.f, wi = row_ok ? w[i] : 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int jj = j + q;
     float val = 0.f;
-    if (i < M && j < M) {
-      val = 0.5f * c * (Kg[i] * m[j] + m[i] * Kg[j]) + cn * Psi[e] + 0.5f * Kuu[e]
-            - 0.5f * (m[i] * w[j] + w[i] * m[j]);
+    if (row_ok && jj < M) {
+      val = 0.5f * c * (kgi * m[jj] + mi * Kg[jj]) + cn * pv[q] + 0.5f * kv[q] - 0.5f * (mi * w[jj] + wi * m[jj]);
     }
-    put(out, e, val);
+    put(out, e + q, val);
   }
 }
 
-// Kuu side of the SE-ARD chain rule: a_ij = G_Kuu_ij Kuu_ij,
-//   rowacc_u[i][d] += sum_j a_ij (z~_jd - z~_id), rowacc_u[i][D+d] += a (.)^2,
-//   rowacc_u[i][2D] += sum_j a_ij.
-// One warp per row i (8 rows per block); lanes stride over j so the G_Kuu and
-// Kuu reads are coalesced; z~_j comes from 256-point chunks staged in shared
-// memory (padded rows, conflict-free); the row's sums are reduced by warp
-// shuffles and stored once.
+// Kuu-side chain rule: with A_ij = G_Kuu_ij Kuu_ij and e_d = z~_jd - z~_id,
+//   rowacc[i][d] += sum_j A_ij e_d,  rowacc[i][D + d] += sum_j A_ij e_d^2,
+//   rowacc[i][2D] += sum_j A_ij.
+// Block = 32 rows (lane = row i) x a range of JB columns j split over the 8
+// warps.  A is symmetric, so A_ij is read as A[j][i]: a warp reads 32
+// consecutive floats of row j.  z~_j is a uniform (broadcast) load.  Warp
+// partials meet in shared memory; one atomic per row and value per block.
 template <int DP>
 __global__ void __launch_bounds__(256) kuu_bwd_kernel(const float* __restrict__ GK, const float* __restrict__ Kuu,
                                                      const float* __restrict__ Zs, int M, int Mp, int D,
-                                                     float* __restrict__ rowacc) {
-  __shared__ float zc[256][DP + 1];
+                                                     float* __restrict__ rowacc, int JB) {
+  constexpr int W = 2 * DP + 1;
+  __shared__ float part[32][W + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * 8 + warp;
-  const bool live = i < M;
+  const int i = blockIdx.x * 32 + lane;
   const int Dp = (D + 3) & ~3;
-  float z[DP], aZ[DP], aL[DP];
+  for (int e = threadIdx.x; e < 32 * (W + 1); e += 256) (&part[0][0])[e] = 0.f;
+  float z[DP], aZ[DP], aL[DP], aS = 0.f;
 #pragma unroll
-  for (int d = 0; d < DP; ++d) { z[d] = (live && d < Dp) ? Zs[(size_t)i * Dp + d] : 0.f; aZ[d] = 0.f; aL[d] = 0.f; }
-  float aS = 0.f;
-  const float* gk = GK + (size_t)(live ? i : 0) * Mp;
-  const float* ku = Kuu + (size_t)(live ? i : 0) * Mp;
-  for (int j0 = 0; j0 < M; j0 += 256) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < 256 * DP; e += blockDim.x) {
-      const int r = e / DP, d = e % DP;
-      zc[r][d] = (j0 + r < M && d < Dp) ? Zs[(size_t)(j0 + r) * Dp + d] : 0.f;
-    }
-    __syncthreads();
-    if (!live) continue;
-    const int jn = min(256, M - j0);
-    for (int jj = lane; jj < jn; jj += 32) {
-      const float a = gk[j0 + jj] * ku[j0 + jj];
+  for (int d = 0; d < DP; ++d) { z[d] = (i < M && d < Dp) ? Zs[(size_t)i * Dp + d] : 0.f; aZ[d] = 0.f; aL[d] = 0.f; }
+  const int jb = blockIdx.y * JB, je = min(M, jb + JB);
+  if (i < M) {
+#pragma unroll 2
+    for (int j = jb + warp; j < je; j += 8) {
+      const float a = __ldg(GK + (size_t)j * Mp + i) * __ldg(Kuu + (size_t)j * Mp + i);
+      const float4* zj = reinterpret_cast<const float4*>(Zs + (size_t)j * Dp);
       aS += a;
 #pragma unroll
-      for (int d = 0; d < DP; ++d) { const float e = zc[jj][d] - z[d]; const float ae = a * e; aZ[d] += ae; aL[d] = fmaf(ae, e, aL[d]); }
+      for (int d4 = 0; d4 < DP / 4; ++d4) {
+        const float4 q = d4 * 4 < Dp ? __ldg(zj + d4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float qq[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int d = 4 * d4 + u;
+          const float e = qq[u] - z[d];
+          const float ae = a * e;
+          aZ[d] += ae;
+          aL[d] = fmaf(ae, e, aL[d]);
+        }
+      }
     }
   }
-  if (!live) return;
+  __syncthreads();
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    aS += __shfl_xor_sync(0xffffffffu, aS, o);
-#pragma unroll
-    for (int d = 0; d < DP; ++d) {
-      aZ[d] += __shfl_xor_sync(0xffffffffu, aZ[d], o);
-      aL[d] += __shfl_xor_sync(0xffffffffu, aL[d], o);
-    }
+  for (int d = 0; d < DP; ++d) {
+    if (d < D) { atomicAdd(&part[lane][d], aZ[d]); atomicAdd(&part[lane][D + d], aL[d]); }
   }
-  if (lane == 0) {
-    float* ra = rowacc + (size_t)i * (2 * D + 1);
-#pragma unroll
-    for (int d = 0; d < DP; ++d)
-      if (d < D) { ra[d] = aZ[d]; ra[D + d] = aL[d]; }
-    ra[2 * D] = aS;
+  atomicAdd(&part[lane][2 * D], aS);
+  __syncthreads();
+  const int Wd = 2 * D + 1;
+  for (int e = threadIdx.x; e < 32 * Wd; e += 256) {
+    const int r = e / Wd, k = e - r * Wd;
+    const int ii = blockIdx.x * 32 + r;
+    if (ii < M) atomicAdd(rowacc + (size_t)ii * Wd + k, part[r][k]);
   }
 }
 
@@ -333,41 +357,37 @@ __global__ void logs_kernel(const float* __restrict__ s, int M, double* red) {
   block_add_double(part, red + RED_LOGS);
 }
 
-// dZ_id = (rowacc_f[i][d] + 2 rowacc_u[i][d]) / ell_d ; FP64 sums of the
-// lengthscale and signal-variance parts (warp shuffles, then one shared
-// atomic per warp and one global atomic per block and value).
-__global__ void grad_finalize_kernel(const float* __restrict__ rf, const float* __restrict__ ru,
-                                     const float* __restrict__ ell, int M, int D, float* __restrict__ dZ,
-                                     double* acc_ell, double* red) {
-  __shared__ double sl[SVGP_MAXD + 2];
-  if (threadIdx.x < SVGP_MAXD + 2) sl[threadIdx.x] = 0.0;
-  __syncthreads();
+// dZ_id = (rowacc_f[i][d] + 2 rowacc_u[i][d]) / ell_d for a block of 64 rows
+// (coalesced over i*D + d); then the column sums of the lengthscale parts
+// rowacc_f[i][D + d] + rowacc_u[i][D + d] and of the signal-variance parts
+// rowacc_*[i][2D] over the block's rows (FP32), added in FP64 to acc_ell and
+// the reduction slots (one atomic per block and value).
+__global__ void __launch_bounds__(256) grad_finalize_kernel(const float* __restrict__ rf, const float* __restrict__ ru,
+                                                            const float* __restrict__ ell, int M, int D,
+                                                            float* __restrict__ dZ, double* acc_ell, double* red) {
   const int W = 2 * D + 1;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  const bool live = i < M;
-  const float* a = rf + (size_t)i * W;
-  const float* b = ru + (size_t)i * W;
-  for (int d = 0; d < D; ++d) {
-    double x = 0.0;
-    if (live) {
-      dZ[(size_t)i * D + d] = (a[d] + 2.0f * b[d]) / ell[d];
-      x = (double)a[D + d] + (double)b[D + d];
+  const int r0 = blockIdx.x * 64;
+  const int nr = min(64, M - r0);
+  for (int e = threadIdx.x; e < nr * D; e += blockDim.x) {
+    const int r = e / D, d = e - r * D;
+    const size_t o = (size_t)(r0 + r) * W + d;
+    dZ[(size_t)r0 * D + e] = (rf[o] + 2.0f * ru[o]) / ell[d];
+  }
+  // column sums: thread t < D -> lengthscale d = t; t == D -> rf[2D]; t == D + 1 -> ru[2D]
+  const int t = threadIdx.x;
+  if (t < D + 2) {
+    float acc = 0.f;
+#pragma unroll 8
+    for (int r = 0; r < nr; ++r) {
+      const size_t o = (size_t)(r0 + r) * W;
+      if (t < D) acc += rf[o + D + t] + ru[o + D + t];
+      else if (t == D) acc += rf[o + 2 * D];
+      else acc += ru[o + 2 * D];
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) atomicAdd(&sl[d], x);
+    if (t < D) atomicAdd(acc_ell + t, (double)acc);
+    else if (t == D) atomicAdd(red + RED_SUMA_F, (double)acc);
+    else atomicAdd(red + RED_SUMA_U, (double)acc);
   }
-  double xf = live ? (double)a[2 * D] : 0.0, xu = live ? (double)b[2 * D] : 0.0;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    xf += __shfl_xor_sync(0xffffffffu, xf, o);
-    xu += __shfl_xor_sync(0xffffffffu, xu, o);
-  }
-  if (lane == 0) { atomicAdd(&sl[SVGP_MAXD], xf); atomicAdd(&sl[SVGP_MAXD + 1], xu); }
-  __syncthreads();
-  if (threadIdx.x < D) atomicAdd(acc_ell + threadIdx.x, sl[threadIdx.x]);
-  if (threadIdx.x == 0) { atomicAdd(red + RED_SUMA_F, sl[SVGP_MAXD]); atomicAdd(red + RED_SUMA_U, sl[SVGP_MAXD + 1]); }
 }
 
 // Scalar assembly of Eq. (7) in FP64 (and the scalar gradients).
@@ -477,7 +497,7 @@ void k_prep_coords(const float* Z, const float* X, const float* ell, int M, int 
 template <class OutP>
 void k_kuu(const float* Zs, int M, int Mp, int D, const float* sf2, float* Kf, OutP Klo, bool has_lo,
            cudaStream_t st) {
-  dim3 grid(Mp / 32, Mp / 32), blk(32, 8);
+  dim3 grid(Mp / 64, Mp / 64), blk(32, 8);
   svgp_note_launch();
   SVGP_DP_DISPATCH(D, kuu_kernel<OutP, DP><<<grid, blk, 0, st>>>(Zs, M, Mp, D, sf2, Kf, Klo, has_lo));
 }
@@ -499,7 +519,7 @@ void k_gemv(const float* A, int Mp, int M, const float* x, float alpha, const fl
             float* y, const float* dotw, double* dot_out, cudaStream_t st) {
   int warps = M, blocks = (warps * 32 + 255) / 256;
   svgp_note_launch();
-  gemv_kernel<<<blocks, 256, 0, st>>>(A, Mp, M, x, alpha, x2, beta, y, dotw, dot_out);
+  gemv_kernel<<<blocks, 256, sizeof(float) * Mp, st>>>(A, Mp, M, x, alpha, x2, beta, y, dotw, dot_out);
 }
 
 void k_mu(const float* Zs, const float* Xs, int M, int B, int D, const float* sf2, const float* v,
@@ -529,11 +549,9 @@ void k_kg(const float* Zs, const float* Xs, int M, int Mp, int B, int D, const f
 template <class OutP>
 void k_gp_assemble(const float* Kuu, const float* Psi, const float* Kg, const float* m, const float* w,
                    const float* noise, float c, int M, int Mp, OutP out, cudaStream_t st) {
-  size_t tot = (size_t)Mp * Mp;
-  int grid = (int)((tot + 255) / 256);
-  if (grid > 152 * 16) grid = 152 * 16;
+  dim3 grid((Mp / 4 + 127) / 128, Mp);
   svgp_note_launch();
-  gp_assemble_kernel<OutP><<<grid, 256, 0, st>>>(Kuu, Psi, Kg, m, w, noise, c, M, Mp, out);
+  gp_assemble_kernel<OutP><<<grid, 128, 0, st>>>(Kuu, Psi, Kg, m, w, noise, c, M, Mp, out);
 }
 template void k_gp_assemble<float*>(const float*, const float*, const float*, const float*, const float*,
                                     const float*, float, int, int, float*, cudaStream_t);
@@ -545,9 +563,10 @@ template void k_gp_assemble<SplitPtr>(const float*, const float*, const float*, 
 void k_kuu_bwd(const float* GKuu, const float* Kuu, const float* Zs, int M, int Mp, int D,
                float* rowacc_u, double* red, cudaStream_t st) {
   (void)red;
-  const int grid = (M + 7) / 8;     // 8 warps per block, one warp per row
+  const int JB = 512;
+  dim3 grid((M + 31) / 32, (M + JB - 1) / JB);
   svgp_note_launch();
-  SVGP_DP_DISPATCH(D, kuu_bwd_kernel<DP><<<grid, 256, 0, st>>>(GKuu, Kuu, Zs, M, Mp, D, rowacc_u));
+  SVGP_DP_DISPATCH(D, kuu_bwd_kernel<DP><<<grid, 256, 0, st>>>(GKuu, Kuu, Zs, M, Mp, D, rowacc_u, JB));
 }
 
 void k_logs(const float* s, int M, double* red, cudaStream_t st) {
@@ -557,7 +576,7 @@ void k_logs(const float* s, int M, double* red, cudaStream_t st) {
 
 void k_grad_finalize(const float* rowacc_f, const float* rowacc_u, const float* ell, int M, int D,
                      float* dZ, double* acc_ell, double* red, cudaStream_t st) {
-  int grid = (M + 255) / 256;
+  int grid = (M + 63) / 64;
   svgp_note_launch();
   grad_finalize_kernel<<<grid, 256, 0, st>>>(rowacc_f, rowacc_u, ell, M, D, dZ, acc_ell, red);
 }

@@ -224,7 +224,7 @@ void prologue(svgp_handle* h, const svgp_params* p, const float* X, int B, const
   cudaMemsetAsync(h->red, 0, sizeof(double) * RED_COUNT, st);
   cudaMemsetAsync(h->acc_ell, 0, sizeof(double) * SVGP_MAXD, st);
   k_prep_coords(p->Z, X, p->ell, h->M, h->Mp, X ? B : 0, h->D, h->Zs, h->Xs, st);
-  if (h->tc_kuf) k_kuf_prep(h->Zs, X ? h->Xs : nullptr, h->M, h->Mp, X ? B : 0, (B + 127) / 128 * 128, h->D, h->kt, st);
+  if (h->tc_kuf) k_kuf_prep(h->Zs, X ? h->Xs : nullptr, h->M, h->Mp, X ? B : 0, (B + 127) / 128 * 128, h->D, p->sf2, h->kt, st);
   if (h->mode == MODE_F32) k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, (float*)nullptr, false, st);
   else if (h->mode == MODE_BF16) k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, H(h->Kuu_lo), true, st);
   else k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, SP(h, h->Kuu_lo), true, st);
@@ -317,8 +317,7 @@ svgp_status svgp_create(const svgp_config* cfg, svgp_handle** out) {
   h->tc_kuf = h->mode != MODE_F32 && tc_kuf_supported(h->D);
   if (ok && h->tc_kuf)
     ok = dalloc(h, &h->kt.ZR, 2 * 64 * h->Mp) && dalloc(h, &h->kt.ZK, 2 * 64 * h->Mp) &&
-         dalloc(h, &h->kt.XR, 2 * 64 * Bp) && dalloc(h, &h->kt.XK, 2 * 64 * Bp) &&
-         dalloc(h, &h->kt.cz, 4 * h->Mp) && dalloc(h, &h->kt.cx, 4 * Bp);
+         dalloc(h, &h->kt.XR, 2 * 64 * Bp) && dalloc(h, &h->kt.XK, 2 * 64 * Bp);
   if (ok && h->mode == MODE_F32) { h->Kuu_lo = h->Kuu_f; h->P_lo = h->Pf; }
   if (ok) ok = build_ctx(h, h->gs, 128, 128) && build_ctx(h, h->gt, 128, 128);
   simt_init_attributes();
