@@ -11,16 +11,20 @@
 //               tcgen05.mma.cta_group::1.kind::f16 (M=128, N=128, K=16) into
 //               one of two TMEM accumulators (256 columns), frees stages with
 //               tcgen05.commit and signals the finished accumulator;
-//   warps 2..5  epilogue: tcgen05.ld 32x32b.x32 of their 32 TMEM lanes,
-//               transpose 32x32 blocks through padded shared memory, run the
-//               shared epilogue functors (common.cuh), then release the
+//   warps 2..5  epilogue: tcgen05.ld 32x32b.x32 of their 32 TMEM lanes, then
+//               per 32 x 32 block the functor's epilogue (epi_tc.cuh): input
+//               blocks by TMA loads issued ahead, results staged in swizzled
+//               shared memory and written by TMA stores; then release the
 //               accumulator -- so the epilogue of tile t overlaps the
 //               mainloop of tile t+1.
 // Every mbarrier wait is bounded; on expiry the CTA raises ERRBIT_TIMEOUT,
 // stops issuing, drains its own copies and frees TMEM.
 #include <cuda.h>
 
+#include <cstring>
+
 #include "common.cuh"
+#include "epi_tc.cuh"
 #include "internal.h"
 #include "tc_common.cuh"
 
@@ -30,51 +34,38 @@ constexpr int BM = 128;
 constexpr int BN = 128;
 constexpr int BK = 64;                      // one 128-byte swizzle atom of BF16
 constexpr int TILE_BYTES = 128 * BK * 2;    // 16 KB per 128 x 64 operand tile
-constexpr int EPI_SCRATCH = 4 * 32 * 33 * 4;
+constexpr int EPI_BYTES = 4 * etc::WARP_BYTES;   // per epilogue warp: input slots + staging
 constexpr uint32_t TMEM_COLS = 2 * BN;      // two accumulators
 
 // Pipeline geometry per operand precision: NSPLIT = 1 (BF16) or 3 (hi/lo pairs).
 template <int NSPLIT> struct Geo {
   static constexpr int NT = NSPLIT == 1 ? 2 : 4;                 // operand tiles per stage
-  static constexpr int STAGES = NSPLIT == 1 ? 6 : 3;
+  static constexpr int STAGES = NSPLIT == 1 ? 4 : 2;
   static constexpr int STAGE_BYTES = NT * TILE_BYTES;
-  static constexpr int NBAR = 2 * STAGES + 4;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_SCRATCH + 1024 + 8 * NBAR + 64;
+  // [0,S) full, [S,2S) empty, acc_full[2], acc_empty[2], epilogue input[4 warps][2]
+  static constexpr int NBAR = 2 * STAGES + 4 + 8;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024 + 8 * NBAR + 64;
+  static_assert(SMEM <= 232448, "shared memory budget");
 };
 
 using namespace tc;
 constexpr uint32_t IDESC = idesc_bf16(BM, BN);
 
-// Epilogue hand-off: the warp's 32 TMEM lanes x 32 columns arrive in the row
-// layout (thread = row); a padded shared-memory transpose gives the column
-// layout; the functor then writes coalesced.
-template <class Epi>
-__device__ __forceinline__ void epi_block(Epi& epi, int i0, int j0, float (&v)[32], float* scr, int lane) {
-  call_pre(epi, i0, j0, v, lane, 0);
-  float vt[32];
-#pragma unroll
-  for (int q = 0; q < 32; ++q) scr[lane * 33 + q] = v[q];
-  __syncwarp();
-#pragma unroll
-  for (int r = 0; r < 32; ++r) vt[r] = scr[r * 33 + lane];
-  __syncwarp();
-  call_block(epi, i0, j0, v, vt, lane, scr, 33, 0);
-}
-
 template <class Epi, int NSPLIT>
 __global__ void __launch_bounds__(192, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmAl, const __grid_constant__ CUtensorMap tmBl,
-               const Tile* __restrict__ tiles, int ntiles, Epi epi, int* errword) {
+               const Tile* __restrict__ tiles, int ntiles, Epi epi, int* errword,
+               const __grid_constant__ etc::EpiMaps maps) {
   using G = Geo<NSPLIT>;
   constexpr int S = G::STAGES;
   if (epi.skip()) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   // stage s holds tiles [A_hi, B_hi, (A_lo, B_lo)]
-  float* scratch = reinterpret_cast<float*>(base + S * G::STAGE_BYTES);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + S * G::STAGE_BYTES + EPI_SCRATCH);
-  // bars: [0,S) full, [S,2S) empty, 2S+b acc_full[b], 2S+2+b acc_empty[b]
+  unsigned char* epi_base = base + S * G::STAGE_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(epi_base + EPI_BYTES);
+  // bars: [0,S) full, [S,2S) empty, 2S+b acc_full[b], 2S+2+b acc_empty[b], 2S+4+2w+k epilogue input
   volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars + G::NBAR);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   volatile int* consumed = abort_flag + 1;
@@ -91,6 +82,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       mbar_init(BAR(2 * S + b), 1);       // acc_full: one tcgen05.commit (or arrive)
       mbar_init(BAR(2 * S + 2 + b), 4);   // acc_empty: one arrive per epilogue warp
     }
+    for (int k = 0; k < 8; ++k) mbar_init(BAR(2 * S + 4 + k), 1);
     *abort_flag = 0;
     *consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -168,32 +160,69 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
-    const int quad = warp & 3;
-    float* scr = scratch + (warp - 2) * 32 * 33;
+    const int quad = warp & 3, ew = warp - 2;
+    unsigned char* ein = epi_base + ew * etc::WARP_BYTES;      // two input slots
+    unsigned char* eout = ein + etc::IN_BYTES;                 // staging slots
+    const uint32_t inbar0 = BAR(2 * S + 4 + 2 * ew);
+    int n_issued[2] = {0, 0}, n_used[2] = {0, 0};
+    // input block of (i0, j0) into slot k (lane 0 issues; the slot's previous
+    // contents were read by this warp before the preceding __syncwarp)
+    auto issue_in = [&](int k, int i0, int j0) {
+      int x, y;
+      if (!etc::tc_in(epi, i0, j0, x, y) || etc::tc_skip(epi, i0, j0)) return;
+      if (lane == 0) {
+        fence_proxy_async();
+        mbar_expect_tx(inbar0 + 8 * k, etc::SLOT);
+        tma_load_2d(smem_u32(ein + k * etc::SLOT), &maps.in, x, y, inbar0 + 8 * k);
+      }
+      ++n_issued[k];
+    };
     epi.begin_tile(0, 0);
     int lt = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
       const Tile tl = tiles[t];
       const int nk = (tl.k1 - tl.k0) / BK;
       const int b = lt & 1;
+      const int i0 = tl.m0 + quad * 32;
+      issue_in(0, i0, tl.n0);
+      issue_in(1, i0, tl.n0 + 32);
       if (!mbar_wait(BAR(2 * S + b), (lt >> 1) & 1)) { *abort_flag = 1; break; }
       fence_after();
       if (*abort_flag) break;
       const uint32_t acc = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * BN);
-      float v[32];
+      bool ok = true;
       for (int c = 0; c < BN / 32; ++c) {
-        if (nk > 0) {
-          tmem_ld32(acc + (uint32_t)(c * 32), v);
-        } else {
+        const int j0 = tl.n0 + c * 32, k = c & 1;
+        if (!etc::tc_skip(epi, i0, j0)) {
+          float v[32];
+          if (nk > 0) {
+            tmem_ld32(acc + (uint32_t)(c * 32), v);
+          } else {
 #pragma unroll
-          for (int q = 0; q < 32; ++q) v[q] = 0.f;
+            for (int q = 0; q < 32; ++q) v[q] = 0.f;
+          }
+          int x, y;
+          if (etc::tc_in(epi, i0, j0, x, y)) {
+            if (!mbar_wait(inbar0 + 8 * k, n_used[k] & 1)) { ok = false; }
+            ++n_used[k];
+          }
+          if (lane == 0) etc::bulk_wait_read();                 // staging slots free again
+          __syncwarp();
+          if (ok) etc::tc_epi(epi, i0, j0, v, lane, ein + k * etc::SLOT, eout, maps);
         }
-        epi_block(epi, tl.m0 + quad * 32, tl.n0 + c * 32, v, scr, lane);
+        __syncwarp();
+        if (c + 2 < BN / 32) issue_in(k, i0, tl.n0 + (c + 2) * 32);
       }
+      if (!ok) *abort_flag = 1;
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(BAR(2 * S + 2 + b));
+      if (!ok) break;
     }
+    // every input copy landed and every store completed before the CTA exits
+    for (int k = 0; k < 2; ++k)
+      for (; n_used[k] < n_issued[k]; ++n_used[k]) mbar_wait(inbar0 + 8 * k, n_used[k] & 1);
+    if (lane == 0) etc::bulk_wait_all();
   }
   __syncwarp();
   if (warp < 2) epi.begin_tile(0, 0);     // zero partials of the non-epilogue warps
@@ -239,7 +268,11 @@ void set_attr_both() {
   set_attr<Epi, 3>();
 }
 
-int num_sms() {
+int num_sms() { return tc_num_sms(); }
+
+}  // namespace
+
+int tc_num_sms() {
   static int n = 0;
   if (!n) {
     int dev = 0;
@@ -249,8 +282,6 @@ int num_sms() {
   }
   return n;
 }
-
-}  // namespace
 
 // 2-D BF16 row-major [rows][cols] (ld = cols), box 64 (k) x box_rows (rows).
 bool tc_make_map(CUtensorMap* m, const void* ptr, int rows, int cols, int box_rows) {
@@ -265,6 +296,57 @@ bool tc_make_map(CUtensorMap* m, const void* ptr, int rows, int cols, int box_ro
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
+
+namespace {
+
+// 32 x 32 blocks of an Mp x Mp matrix for the epilogue: FP32 with 128-byte
+// rows (128-byte swizzle) or BF16 with 64-byte rows (64-byte swizzle).
+bool block_map(CUtensorMap* m, const void* ptr, int Mp, bool f32) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || !ptr) return false;
+  const int es = f32 ? 4 : 2;
+  cuuint64_t dims[2] = {(cuuint64_t)Mp, (cuuint64_t)Mp};
+  cuuint64_t strides[1] = {(cuuint64_t)Mp * es};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t el[2] = {1, 1};
+  CUresult r = fn(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                  const_cast<void*>(ptr), dims, strides, box, el, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  f32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+bool out_maps(CUtensorMap* m, bf16* p, int Mp) { return block_map(m, p, Mp, false); }
+bool out_maps(CUtensorMap* m, const SplitPtr& p, int Mp) {
+  return block_map(m, p.hi, Mp, false) && block_map(m + 1, p.lo, Mp, false);
+}
+
+// Tensor maps of each epilogue: input block source and output planes in the
+// order epi_tc.cuh stores them.  All matrices are Mp x Mp (leading dimension Mp).
+template <class OutP>
+bool epi_maps(const EpiVt<OutP>& e, etc::EpiMaps& m, int Mp) {
+  return e.ld == Mp && (!e.s || block_map(&m.in, e.Lf, Mp, true)) && out_maps(m.out, e.out, Mp);
+}
+template <class OutP, int MODE>
+bool epi_maps(const EpiSym<OutP, MODE>& e, etc::EpiMaps& m, int Mp) {
+  return e.ld == Mp && out_maps(m.out, e.out, Mp);
+}
+bool epi_maps(const EpiLupd& e, etc::EpiMaps& m, int Mp) {
+  return e.ld == Mp && block_map(&m.in, e.Lf, Mp, true) && block_map(&m.out[0], e.Lf, Mp, true);
+}
+template <class OutP>
+bool epi_maps(const EpiStore<OutP>& e, etc::EpiMaps& m, int Mp) {
+  return e.ld == Mp && out_maps(m.out, e.out, Mp);
+}
+template <class OutP>
+bool epi_maps(const EpiP<OutP>& e, etc::EpiMaps& m, int Mp) {
+  return e.ld == Mp && (!e.Psi || block_map(&m.in, e.Psi, Mp, true)) && block_map(&m.out[0], e.Pf, Mp, true) &&
+         out_maps(m.out + 1, e.Plo, Mp);
+}
+bool epi_maps(const EpiGK& e, etc::EpiMaps& m, int Mp) {
+  return e.ld == Mp && block_map(&m.in, e.Pf, Mp, true) && block_map(&m.out[0], e.GKuu, Mp, true);
+}
+
+}  // namespace
 
 bool tc_available() {
   int dev = 0, major = 0, minor = 0;
@@ -281,13 +363,16 @@ bool tc_gemm(const GemmCtx& g, int tab, const bf16* A, const bf16* B, const Epi&
   const int grid = nt < num_sms() ? nt : num_sms();
   CUtensorMap ma, mb, mal, mbl;
   if (!tc_make_map(&ma, A, g.Mp, g.Mp, 128) || !tc_make_map(&mb, B, g.Mp, g.Mp, 128)) return false;
+  etc::EpiMaps em;
+  memset(&em, 0, sizeof(em));
+  if (!epi_maps(e, em, g.Mp)) return false;
   if (g.split) {
     if (!tc_make_map(&mal, A + MM, g.Mp, g.Mp, 128) || !tc_make_map(&mbl, B + MM, g.Mp, g.Mp, 128)) return false;
     svgp_note_launch();
-    tc_gemm_kernel<Epi, 3><<<grid, 192, Geo<3>::SMEM, g.st>>>(ma, mb, mal, mbl, g.tt[tab], nt, e, g.err);
+    tc_gemm_kernel<Epi, 3><<<grid, 192, Geo<3>::SMEM, g.st>>>(ma, mb, mal, mbl, g.tt[tab], nt, e, g.err, em);
   } else {
     svgp_note_launch();
-    tc_gemm_kernel<Epi, 1><<<grid, 192, Geo<1>::SMEM, g.st>>>(ma, mb, ma, mb, g.tt[tab], nt, e, g.err);
+    tc_gemm_kernel<Epi, 1><<<grid, 192, Geo<1>::SMEM, g.st>>>(ma, mb, ma, mb, g.tt[tab], nt, e, g.err, em);
   }
   return true;
 }

@@ -1,0 +1,421 @@
+// W = P Kuf with the SE-ARD operand generated on chip (kuf_common.cuh) and a
+// fused epilogue, for the data part of the backward pass (Section 3.1) and
+// for the predictive variance:
+//   gradient mode (rowpart != null): with A_in = c Kuf_in (v_i g_n + W_in /
+//     noise) (= G_Kuf o Kuf for the Gaussian likelihood), per row i the sums
+//       S0 = sum_n A_in,  S1_d = sum_n A_in x~_nd,  S2_d = sum_n A_in x~_nd^2
+//     (FP32, x~ and x~^2 staged in shared memory), reported in the
+//     difference form  sum_n A_in e_d = S1_d - z~_id S0  and
+//     sum_n A_in e_d^2 = S2_d - 2 z~_id S1_d + z~_id^2 S0  (e_d = x~_nd - z~_id);
+//   variance mode (colsum != null): colsum[n] += sum_i Kuf_in W_in.
+//
+// Grid: (groups of n-blocks) x (128-row blocks i of P).  A CTA keeps its rows
+// i and walks the n-blocks nb = blockIdx.x, blockIdx.x + gridDim.x, ...,
+// carrying the row sums in registers; at the end it writes one partial row
+// set rowpart[blockIdx.x][k][i] (no atomics; the gradient finalize adds the
+// gridDim.x partials).  Per n-block:
+//   * mainloop over the inducing k-blocks: exponent MMA for the 128 x 64 block
+//     Kuf^T[n, k], exp2 into the swizzled B operand, main MMA
+//     W[i, n] += P[i, k] Kuf[k, n];
+//   * one more exponent MMA T[i, n] = log2 Kuf_in for the epilogue (z rows of
+//     the block against the n-block), so Kuf_in is recomputed exactly as the
+//     generator computes it.
+// Warp roles (320 threads): 0 TMA producer, 1 TMEM allocator + MMA issuer,
+// 2..9 transform and then epilogue (warp w covers TMEM lanes 32 (w mod 4) ..
+// +31 and one half of the columns).  All waits are bounded; once a wait has
+// timed out the warps skip their work but still pass every named barrier.
+#include "common.cuh"
+#include "internal.h"
+#include "kuf_common.cuh"
+#include "tc_common.cuh"
+
+namespace {
+
+using namespace tc;
+using namespace kuf;
+
+constexpr int DPMAX = 24;                      // padded-dimension bound of the staged x~ rows
+
+template <int NSPLIT>
+struct WGeo {
+  static constexpr int NS = NSPLIT == 3 ? 2 : 1;                         // hi (+lo) planes
+  static constexpr int STAGES = NSPLIT == 3 ? 2 : 3;
+  // stage: [z k-role coordinate tile CT][P tiles NS*GT][generated Kuf^T tiles NS*GT]
+  static constexpr int OFF_P = CT;
+  static constexpr int OFF_G = CT + NS * GT;
+  static constexpr int STAGE = OFF_G + NS * GT;
+  // static tiles: z rows of the block (row role), x rows of the n-block in
+  // row role (generator) and in k role (epilogue exponent)
+  static constexpr int OFF_ZR = 0, OFF_XR = GT, OFF_XK = 2 * GT, STATIC = 3 * GT;
+  // epilogue floats: colbuf[128], gq[128], xq[128][2 DP]; reused for the final
+  // combination of the two column halves (128 x (2 DP + 1))
+  static constexpr int EPI_FLOATS = 256 + 128 * 2 * DPMAX;
+  static_assert(EPI_FLOATS >= 128 * (2 * DPMAX + 1), "combine buffer");
+  static constexpr int NBAR = 3 * STAGES + 8;
+  static constexpr int SMEM = 1024 + STATIC + STAGES * STAGE + 4 * EPI_FLOATS + 8 * NBAR + 64;
+  static_assert(SMEM <= 232448, "shared memory budget");
+  static constexpr uint32_t TMEM_COLS = 512;
+  // TMEM columns: W accumulator [0,128), generator exponents 2 x 64, epilogue exponents T
+  static constexpr uint32_t ACC = 0, T = 256;
+  __host__ __device__ static constexpr uint32_t SB(int b) { return 128 + 64 * b; }
+};
+
+struct WArgs {
+  int nkb;          // inducing k-blocks (Mp / 64)
+  int nblk;         // n-blocks (Bp / 128)
+  int Mp;
+  int* errword;
+  float* rowpart;   // gradient mode: [gridDim.x][2D + 1][Mp]
+};
+
+template <int NSPLIT, int DP>
+__global__ void __launch_bounds__(THREADS, 1)
+w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CUtensorMap tmZK,
+            const __grid_constant__ CUtensorMap tmXR, const __grid_constant__ CUtensorMap tmXK,
+            const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmPl, WArgs wa, WEpi we) {
+  using G = WGeo<NSPLIT>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sZR = base + G::OFF_ZR;
+  unsigned char* sXR = base + G::OFF_XR;
+  unsigned char* sXK = base + G::OFF_XK;
+  unsigned char* stg = base + G::STATIC;
+  float* ebuf = reinterpret_cast<float*>(stg + G::STAGES * G::STAGE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ebuf + G::EPI_FLOATS);
+  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars + G::NBAR);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* consumed = abort_flag + 1;
+  constexpr int S = G::STAGES;
+  auto BAR = [&](int idx) { return smem_u32(&bars[idx]); };
+  const int B_ZR = 0, B_TILE = 1, B_LD = 2, B_EMPTY = 2 + S, B_GEN = 2 + 2 * S, B_SFULL = 2 + 3 * S,
+            B_SEMPTY = 4 + 3 * S, B_ACC = 6 + 3 * S;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * 128;
+  const int nkb = wa.nkb;
+
+  if (threadIdx.x == 0) {
+    mbar_init(BAR(B_ZR), 1);
+    mbar_init(BAR(B_TILE), 1);
+    for (int s = 0; s < S; ++s) {
+      mbar_init(BAR(B_LD + s), 1);
+      mbar_init(BAR(B_EMPTY + s), 1);
+      mbar_init(BAR(B_GEN + s), NTW);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(BAR(B_SFULL + b), 1);
+      mbar_init(BAR(B_SEMPTY + b), NTW);
+    }
+    mbar_init(BAR(B_ACC), 1);
+    *abort_flag = 0;
+    *consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32((const void*)tmem_slot), G::TMEM_COLS);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  constexpr uint32_t ID_MAIN = idesc_bf16(128, 128);
+  constexpr uint32_t ID_DIST = idesc_bf16(128, 64);
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    mbar_expect_tx(BAR(B_ZR), GT);
+    tma_load_2d(smem_u32(sZR), &tmZR, 0, m0, BAR(B_ZR));
+    int g = 0, lt = 0;
+    bool ok = true;
+    for (int nb = blockIdx.x; nb < wa.nblk && ok; nb += gridDim.x, ++lt) {
+      // the previous n-block's MMAs (readers of sXR / sXK) have completed
+      if (lt > 0 && !mbar_wait(BAR(B_ACC), (lt - 1) & 1)) { ok = false; break; }
+      if (*abort_flag) { ok = false; break; }
+      mbar_expect_tx(BAR(B_TILE), 2 * GT);
+      tma_load_2d(smem_u32(sXR), &tmXR, 0, nb * 128, BAR(B_TILE));
+      tma_load_2d(smem_u32(sXK), &tmXK, 0, nb * 128, BAR(B_TILE));
+      for (int kb = 0; kb < nkb; ++kb, ++g) {
+        const int s = g % S;
+        if (!mbar_wait(BAR(B_EMPTY + s), ((g / S) & 1) ^ 1) || *abort_flag) { ok = false; break; }
+        unsigned char* st = stg + s * G::STAGE;
+        const uint32_t fb = BAR(B_LD + s);
+        mbar_expect_tx(fb, CT + G::NS * GT);
+        tma_load_2d(smem_u32(st), &tmZK, 0, kb * KB, fb);
+        tma_load_2d(smem_u32(st + G::OFF_P), &tmP, kb * KB, m0, fb);
+        if (NSPLIT == 3) tma_load_2d(smem_u32(st + G::OFF_P + GT), &tmPl, kb * KB, m0, fb);
+      }
+    }
+    if (!ok) *abort_flag = 1;
+    // every copy this thread issued lands before the CTA exits (bounded waits)
+    mbar_wait(BAR(B_ZR), 0);
+    if (lt > 0) mbar_wait(BAR(B_TILE), (lt - 1) & 1);
+    if (*abort_flag) {
+      for (int q = *consumed; q < g; ++q) mbar_wait(BAR(B_LD + q % S), (q / S) & 1);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    bool ok = mbar_wait(BAR(B_ZR), 0);
+    auto main_mma = [&](int gj, int kb) -> bool {
+      const int s = gj % S;
+      if (!mbar_wait(BAR(B_GEN + s), (gj / S) & 1)) return false;
+      fence_after();
+      unsigned char* st = stg + s * G::STAGE;
+      const uint64_t ad = sw128_desc(smem_u32(st + G::OFF_P));
+      const uint64_t adl = sw128_desc(smem_u32(st + G::OFF_P + GT));
+      const uint64_t bd = sw128_desc(smem_u32(st + G::OFF_G));
+      const uint64_t bdl = sw128_desc(smem_u32(st + G::OFF_G + GT));
+#pragma unroll
+      for (int kk = 0; kk < KB / 16; ++kk) {
+        const uint64_t o = (uint64_t)(kk * 2);
+        mma_bf16(tmem + G::ACC, ad + o, bd + o, ID_MAIN, (kb | kk) != 0);
+        if (NSPLIT == 3) {
+          mma_bf16(tmem + G::ACC, ad + o, bdl + o, ID_MAIN, 1);
+          mma_bf16(tmem + G::ACC, adl + o, bd + o, ID_MAIN, 1);
+        }
+      }
+      mma_commit(BAR(B_EMPTY + s));
+      return true;
+    };
+    int g = 0, lt = 0;
+    for (int nb = blockIdx.x; nb < wa.nblk && ok; nb += gridDim.x, ++lt) {
+      if (!mbar_wait(BAR(B_TILE), lt & 1)) { ok = false; break; }
+      fence_after();
+      const uint64_t ra = sw128_desc(smem_u32(sXR));
+      for (int kb = 0; kb < nkb; ++kb, ++g) {
+        const int s = g % S, b = g & 1;
+        if (!mbar_wait(BAR(B_LD + s), (g / S) & 1)) { ok = false; break; }
+        *consumed = g + 1;
+        if (!mbar_wait(BAR(B_SEMPTY + b), ((g >> 1) & 1) ^ 1)) { ok = false; break; }
+        fence_after();
+        const uint64_t kd = sw128_desc(smem_u32(stg + s * G::STAGE));
+#pragma unroll
+        for (int kk = 0; kk < KB / 16; ++kk) {
+          const uint64_t o = (uint64_t)(kk * 2);
+          mma_bf16(tmem + G::SB(b), ra + o, kd + o, ID_DIST, kk != 0);
+        }
+        mma_commit(BAR(B_SFULL + b));
+        // The first main MMA of an n-block overwrites the accumulator: it waits
+        // for that k-block's generated operand, which the transform warps
+        // produce only after their epilogue of the previous n-block has read
+        // the accumulator and the exponents T.
+        if (kb >= 1 && !main_mma(g - 1, kb - 1)) { ok = false; break; }
+      }
+      if (!ok) break;
+      if (!main_mma(g - 1, nkb - 1)) { ok = false; break; }
+      // epilogue exponents T[i, n] = log2 Kuf_in
+      const uint64_t zd = sw128_desc(smem_u32(sZR)), xd = sw128_desc(smem_u32(sXK));
+#pragma unroll
+      for (int kk = 0; kk < KB / 16; ++kk) {
+        const uint64_t o = (uint64_t)(kk * 2);
+        mma_bf16(tmem + G::T, zd + o, xd + o, ID_MAIN, kk != 0);
+      }
+      mma_commit(BAR(B_ACC));
+    }
+    if (!ok) {
+      *abort_flag = 1;
+      mma_commit(BAR(B_ACC));
+    }
+  } else if (warp >= 2) {
+    // ---------------- transform, then epilogue, per n-block ----------------
+    const int quad = warp & 3, half = (warp - 2) >> 2;
+    const int row = quad * 32 + lane, kcol0 = half * 32;
+    const int tid = threadIdx.x - 64;                     // 0 .. 255
+    const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+    const int D = we.gen.D, Dp = (D + 3) & ~3, B = we.gen.B;
+    const bool grad = wa.rowpart != nullptr;
+    constexpr int XW = 2 * DP;
+    float* colbuf = ebuf;
+    float* gq = ebuf + 128;
+    float* xq = ebuf + 256;
+    const int i = m0 + row;
+    float cv = 0.f, cn = 0.f;
+    if (grad) {
+      cv = i < we.gen.M ? we.c * __ldg(we.v + i) : 0.f;
+      cn = we.c / *we.noise;
+    }
+    float S0 = 0.f, S1[DP], S2[DP];
+#pragma unroll
+    for (int d = 0; d < DP; ++d) { S1[d] = 0.f; S2[d] = 0.f; }
+    int g = 0, lt = 0;
+    for (int nb = blockIdx.x; nb < wa.nblk; nb += gridDim.x, ++lt) {
+      const int n0 = nb * 128;
+      for (int kb = 0; kb < nkb; ++kb, ++g) {
+        if (*abort_flag) continue;
+        const int s = g % S, b = g & 1;
+        if (!mbar_wait(BAR(B_SFULL + b), (g >> 1) & 1)) { *abort_flag = 1; continue; }
+        fence_after();
+        float t[32];
+        tmem_ld32(tmem + lane_off + G::SB(b) + kcol0, t);
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(BAR(B_SEMPTY + b));
+        // the generated buffers of stage s are free once the main MMA of g - S finished
+        if (!mbar_wait(BAR(B_EMPTY + s), ((g / S) & 1) ^ 1)) { *abort_flag = 1; continue; }
+        unsigned char* st = stg + s * G::STAGE;
+        gen32<NSPLIT>(t, st + G::OFF_G, st + G::OFF_G + GT, row, kcol0);
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(BAR(B_GEN + s));
+      }
+      // epilogue of this n-block
+      bool ok = !*abort_flag;
+      if (ok && !mbar_wait(BAR(B_ACC), lt & 1)) { *abort_flag = 1; ok = false; }
+      fence_after();
+      if (ok) {
+        if (grad) {
+          constexpr int PER = 128 * DP / 256;
+          float xv[PER];
+#pragma unroll
+          for (int u = 0; u < PER; ++u) {
+            const int e = tid + 256 * u, n = e / DP, d = e - n * DP;
+            xv[u] = (n0 + n < B && d < D) ? __ldg(we.gen.Xs + (size_t)(n0 + n) * Dp + d) : 0.f;
+          }
+          const float gv = (tid < 128 && n0 + tid < B) ? __ldg(we.g + n0 + tid) : 0.f;
+#pragma unroll
+          for (int u = 0; u < PER; ++u) {
+            const int e = tid + 256 * u, n = e / DP, d = e - n * DP;
+            xq[n * XW + d] = xv[u];
+            xq[n * XW + DP + d] = xv[u] * xv[u];
+          }
+          if (tid < 128) gq[tid] = gv;
+        }
+        if (tid < 128) colbuf[tid] = 0.f;
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * NTW) : "memory");
+      if (ok) {
+        const uint32_t tacc = tmem + lane_off + G::ACC, texp = tmem + lane_off + G::T;
+        for (int ch = 2 * half; ch < 2 * half + 2; ++ch) {
+          float w[32], tt[32];
+          tmem_ld32(tacc + (uint32_t)(ch * 32), w);
+          tmem_ld32(texp + (uint32_t)(ch * 32), tt);
+          if (grad) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+              const int n = ch * 32 + q;
+              const float a = ex2(tt[q]) * fmaf(cv, gq[n], cn * w[q]);
+              S0 += a;
+              const float4* xr = reinterpret_cast<const float4*>(xq + n * XW);
+#pragma unroll
+              for (int d4 = 0; d4 < DP / 4; ++d4) {
+                const float4 x = xr[d4], x2 = xr[DP / 4 + d4];
+                S1[4 * d4 + 0] = fmaf(a, x.x, S1[4 * d4 + 0]);
+                S1[4 * d4 + 1] = fmaf(a, x.y, S1[4 * d4 + 1]);
+                S1[4 * d4 + 2] = fmaf(a, x.z, S1[4 * d4 + 2]);
+                S1[4 * d4 + 3] = fmaf(a, x.w, S1[4 * d4 + 3]);
+                S2[4 * d4 + 0] = fmaf(a, x2.x, S2[4 * d4 + 0]);
+                S2[4 * d4 + 1] = fmaf(a, x2.y, S2[4 * d4 + 1]);
+                S2[4 * d4 + 2] = fmaf(a, x2.z, S2[4 * d4 + 2]);
+                S2[4 * d4 + 3] = fmaf(a, x2.w, S2[4 * d4 + 3]);
+              }
+            }
+          } else if (we.colsum) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+              float sv = ex2(tt[q]) * w[q];
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+              if (lane == 0) atomicAdd(colbuf + ch * 32 + q, sv);
+            }
+          }
+        }
+      }
+      fence_before();
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * NTW) : "memory");
+      if (ok && we.colsum && tid < 128 && n0 + tid < B) atomicAdd(we.colsum + n0 + tid, colbuf[tid]);
+    }
+    // combine the two column halves and write this CTA's partial rows
+    if (grad) {
+      constexpr int CW = 2 * DP + 1;
+      float* comb = xq;
+      if (half == 1) {
+        comb[row * CW + 2 * DP] = S0;
+#pragma unroll
+        for (int d = 0; d < DP; ++d) { comb[row * CW + d] = S1[d]; comb[row * CW + DP + d] = S2[d]; }
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * NTW) : "memory");
+      if (half == 0 && !*abort_flag) {
+        S0 += comb[row * CW + 2 * DP];
+        const int W = 2 * D + 1;
+        float* out = wa.rowpart + (size_t)blockIdx.x * W * wa.Mp + i;
+#pragma unroll
+        for (int d = 0; d < DP; ++d) {
+          if (d < D) {
+            const float s1 = S1[d] + comb[row * CW + d], s2 = S2[d] + comb[row * CW + DP + d];
+            const float z = i < we.gen.M ? __ldg(we.gen.Zs + (size_t)i * Dp + d) : 0.f;
+            out[(size_t)d * wa.Mp] = fmaf(-z, S0, s1);
+            out[(size_t)(D + d) * wa.Mp] = fmaf(z, fmaf(z, S0, -2.0f * s1), s2);
+          }
+        }
+        out[(size_t)(2 * D) * wa.Mp] = S0;
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(wa.errword, ERRBIT_TIMEOUT);
+  if (warp == 1) {
+    fence_after();
+    tmem_dealloc(tmem, G::TMEM_COLS);
+  }
+}
+
+template <int NSPLIT, int DP>
+void set_w_attr() {
+  cudaFuncSetAttribute(w_tc_kernel<NSPLIT, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, WGeo<NSPLIT>::SMEM);
+}
+
+template <int NSPLIT>
+void launch_w(dim3 grid, cudaStream_t st, const CUtensorMap (&m)[6], const WArgs& wa, const WEpi& we) {
+  const int D = we.gen.D;
+  svgp_note_launch();
+  if (D <= 4)
+    w_tc_kernel<NSPLIT, 4><<<grid, THREADS, WGeo<NSPLIT>::SMEM, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
+  else if (D <= 8)
+    w_tc_kernel<NSPLIT, 8><<<grid, THREADS, WGeo<NSPLIT>::SMEM, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
+  else if (D <= 16)
+    w_tc_kernel<NSPLIT, 16><<<grid, THREADS, WGeo<NSPLIT>::SMEM, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
+  else
+    w_tc_kernel<NSPLIT, 24><<<grid, THREADS, WGeo<NSPLIT>::SMEM, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
+}
+
+}  // namespace
+
+void tc_w_init_attributes() {
+  set_w_attr<1, 4>();
+  set_w_attr<1, 8>();
+  set_w_attr<1, 16>();
+  set_w_attr<1, 24>();
+  set_w_attr<3, 4>();
+  set_w_attr<3, 8>();
+  set_w_attr<3, 16>();
+  set_w_attr<3, 24>();
+}
+
+int tc_w_groups(int Mp, int B) {
+  const int nblk = (B + 127) / 128, rb = Mp / 128;
+  int gn = tc_num_sms() / rb;
+  if (gn < 1) gn = 1;
+  if (gn > nblk) gn = nblk;
+  return gn;
+}
+
+int tc_w(const GemmCtx& g, const bf16* P, const KufTC& t, const WEpi& we, float* rowpart) {
+  if (!tc_kuf_supported(we.gen.D) || we.gen.D > DPMAX) return -1;
+  const int B = we.gen.B;
+  const int Bp = (B + 127) / 128 * 128;
+  CUtensorMap m[6];
+  if (!tc_make_map(&m[0], t.ZR, g.Mp, 64, 128) || !tc_make_map(&m[1], t.ZK, g.Mp, 64, 64) ||
+      !tc_make_map(&m[2], t.XR, Bp, 64, 128) || !tc_make_map(&m[3], t.XK, Bp, 64, 128) ||
+      !tc_make_map(&m[4], P, g.Mp, g.Mp, 128))
+    return -1;
+  if (g.split) {
+    if (!tc_make_map(&m[5], P + (size_t)g.Mp * g.Mp, g.Mp, g.Mp, 128)) return -1;
+  } else {
+    m[5] = m[4];
+  }
+  const int gn = tc_w_groups(g.Mp, B);
+  WArgs wa{g.Mp / KB, Bp / 128, g.Mp, g.err, we.rowacc ? rowpart : nullptr};
+  dim3 grid(gn, g.Mp / 128);
+  if (g.split) launch_w<3>(grid, g.st, m, wa, we);
+  else launch_w<1>(grid, g.st, m, wa, we);
+  return wa.rowpart ? gn : 0;
+}

@@ -38,6 +38,7 @@ void simt_init_attributes();
 // B point at the hi part (lo at +Mp*Mp when g.split).  Return false when the
 // tensor-core path is unavailable.
 bool tc_available();
+int tc_num_sms();
 void tc_init_attributes();
 template <class Epi>
 bool tc_gemm(const GemmCtx& g, int tab, const bf16* A, const bf16* B, const Epi& e);
@@ -53,7 +54,12 @@ void tc_kuf_init_attributes();
 void k_kuf_prep(const float* Zs, const float* Xs, int M, int Mp, int B, int Bp, int D, const float* sf2,
                 const KufTC& t, cudaStream_t st);
 bool tc_psi(const GemmCtx& g, const KufGen& kg, const KufTC& t, int B, EpiPsi e);
-bool tc_w(const GemmCtx& g, const bf16* P, const KufTC& t, const WEpi& we);
+// W = P Kuf with its fused epilogue.  Gradient mode (we.rowacc != null):
+// writes per-CTA partial rows rowpart[p][k][i] (p < returned count, k < 2D+1,
+// i < Mp) instead of rowacc; variance mode returns 0.  -1: not supported.
+int tc_w(const GemmCtx& g, const bf16* P, const KufTC& t, const WEpi& we, float* rowpart);
+int tc_w_groups(int Mp, int B);
+void tc_w_init_attributes();
 
 // Miscellaneous kernels (kernels_misc.cu).  OutP is float*, bf16* or SplitPtr.
 void k_prep_coords(const float* Z, const float* X, const float* ell, int M, int Mp, int B, int D,
@@ -79,8 +85,8 @@ void k_gp_assemble(const float* Kuu, const float* Psi, const float* Kg, const fl
 void k_kuu_bwd(const float* GKuu, const float* Kuu, const float* Zs, int M, int Mp, int D,
                float* rowacc_u, double* red, cudaStream_t st);
 void k_logs(const float* s, int M, double* red, cudaStream_t st);
-void k_grad_finalize(const float* rowacc_f, const float* rowacc_u, const float* ell, int M, int D,
-                     float* dZ, double* acc_ell, double* red, cudaStream_t st);
+void k_grad_finalize(const float* rowacc_f, const float* rowacc_u, const float* rowpart, int nparts, int Mp,
+                     const float* ell, int M, int D, float* dZ, double* acc_ell, double* red, cudaStream_t st);
 void k_terms_finalize(const double* red, const double* acc_ell, const float* sf2, const float* noise,
                       const float* ell, int M, int D, int B, double N, double* terms,
                       float* dsf2, float* dnoise, float* dell, int* errword, cudaStream_t st);

@@ -124,12 +124,21 @@ __global__ void __launch_bounds__(256) gemv_kernel(const float* __restrict__ A, 
     const float4* xv = reinterpret_cast<const float4*>(xs);
     float acc0 = 0.f, acc1 = 0.f;
     const int n4 = Mp / 4;
-#pragma unroll 4
-    for (int k = lane; k < n4; k += 32) {
-      const float4 a = __ldg(row + k);
-      const float4 b = xv[k];
-      acc0 = fmaf(a.x, b.x, acc0); acc1 = fmaf(a.y, b.y, acc1);
-      acc0 = fmaf(a.z, b.z, acc0); acc1 = fmaf(a.w, b.w, acc1);
+    // batches of 8 float4 per lane: all loads of a batch are in flight together
+    for (int k0 = lane; k0 < n4; k0 += 8 * 32) {
+      float4 a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = k0 + 32 * u;
+        a[u] = k < n4 ? __ldg(row + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = min(k0 + 32 * u, n4 - 1);
+        const float4 b = xv[k];
+        acc0 = fmaf(a[u].x, b.x, acc0); acc1 = fmaf(a[u].y, b.y, acc1);
+        acc0 = fmaf(a[u].z, b.z, acc0); acc1 = fmaf(a[u].w, b.w, acc1);
+      }
     }
     const float acc = warp_sum(acc0 + acc1) * alpha;
     if (lane == 0) {
@@ -296,46 +305,61 @@ __global__ void gp_assemble_kernel(const float* __restrict__ Kuu, const float* _
 // Kuu-side chain rule: with A_ij = G_Kuu_ij Kuu_ij and e_d = z~_jd - z~_id,
 //   rowacc[i][d] += sum_j A_ij e_d,  rowacc[i][D + d] += sum_j A_ij e_d^2,
 //   rowacc[i][2D] += sum_j A_ij.
-// Block = 32 rows (lane = row i) x a range of JB columns j split over the 8
-// warps.  A is symmetric, so A_ij is read as A[j][i]: a warp reads 32
-// consecutive floats of row j.  z~_j is a uniform (broadcast) load.  Warp
-// partials meet in shared memory; one atomic per row and value per block.
+// Block = 32 rows (lane = row i) x a range of at most 256 columns j, split
+// over the 8 warps.  A is symmetric, so A_ij is read as A[j][i]: a warp reads
+// 32 consecutive floats of row j (four rows in flight per warp).  z~_j of the
+// range is staged in shared memory and read as broadcasts.  Warp partials
+// meet in shared memory; one atomic per row and value per block.
 template <int DP>
 __global__ void __launch_bounds__(256) kuu_bwd_kernel(const float* __restrict__ GK, const float* __restrict__ Kuu,
                                                      const float* __restrict__ Zs, int M, int Mp, int D,
                                                      float* __restrict__ rowacc, int JB) {
   constexpr int W = 2 * DP + 1;
+  constexpr int U = 4;
+  __shared__ __align__(16) float zs[256][DP];
   __shared__ float part[32][W + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * 32 + lane;
   const int Dp = (D + 3) & ~3;
+  const int jb = blockIdx.y * JB, je = min(M, jb + JB);
   for (int e = threadIdx.x; e < 32 * (W + 1); e += 256) (&part[0][0])[e] = 0.f;
+  for (int e = threadIdx.x; e < JB * DP; e += 256) {
+    const int r = e / DP, d = e - r * DP;
+    zs[r][d] = (jb + r < je && d < Dp) ? __ldg(Zs + (size_t)(jb + r) * Dp + d) : 0.f;
+  }
   float z[DP], aZ[DP], aL[DP], aS = 0.f;
 #pragma unroll
   for (int d = 0; d < DP; ++d) { z[d] = (i < M && d < Dp) ? Zs[(size_t)i * Dp + d] : 0.f; aZ[d] = 0.f; aL[d] = 0.f; }
-  const int jb = blockIdx.y * JB, je = min(M, jb + JB);
+  __syncthreads();
   if (i < M) {
-#pragma unroll 2
-    for (int j = jb + warp; j < je; j += 8) {
-      const float a = __ldg(GK + (size_t)j * Mp + i) * __ldg(Kuu + (size_t)j * Mp + i);
-      const float4* zj = reinterpret_cast<const float4*>(Zs + (size_t)j * Dp);
-      aS += a;
+    for (int j = jb + warp; j < je; j += 8 * U) {
+      float a[U];
 #pragma unroll
-      for (int d4 = 0; d4 < DP / 4; ++d4) {
-        const float4 q = d4 * 4 < Dp ? __ldg(zj + d4) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float qq[4] = {q.x, q.y, q.z, q.w};
+      for (int u = 0; u < U; ++u) {
+        const int jj = j + 8 * u;
+        a[u] = jj < je ? __ldg(GK + (size_t)jj * Mp + i) * __ldg(Kuu + (size_t)jj * Mp + i) : 0.f;
+      }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int d = 4 * d4 + u;
-          const float e = qq[u] - z[d];
-          const float ae = a * e;
-          aZ[d] += ae;
-          aL[d] = fmaf(ae, e, aL[d]);
+      for (int u = 0; u < U; ++u) {
+        const int jj = min(j + 8 * u, je - 1) - jb;
+        const float4* zj = reinterpret_cast<const float4*>(&zs[jj][0]);
+        aS += a[u];
+#pragma unroll
+        for (int d4 = 0; d4 < DP / 4; ++d4) {
+          const float4 q = zj[d4];
+          const float qq[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int d = 4 * d4 + v;
+            const float e = qq[v] - z[d];
+            const float ae = a[u] * e;
+            aZ[d] += ae;
+            aL[d] = fmaf(ae, e, aL[d]);
+          }
         }
       }
     }
   }
-  __syncthreads();
 #pragma unroll
   for (int d = 0; d < DP; ++d) {
     if (d < D) { atomicAdd(&part[lane][d], aZ[d]); atomicAdd(&part[lane][D + d], aL[d]); }
@@ -357,31 +381,56 @@ __global__ void logs_kernel(const float* __restrict__ s, int M, double* red) {
   block_add_double(part, red + RED_LOGS);
 }
 
-// dZ_id = (rowacc_f[i][d] + 2 rowacc_u[i][d]) / ell_d for a block of 64 rows
-// (coalesced over i*D + d); then the column sums of the lengthscale parts
-// rowacc_f[i][D + d] + rowacc_u[i][D + d] and of the signal-variance parts
-// rowacc_*[i][2D] over the block's rows (FP32), added in FP64 to acc_ell and
-// the reduction slots (one atomic per block and value).
+// dZ_id = (rowacc_f[i][d] + 2 rowacc_u[i][d]) / ell_d for a block of RB rows;
+// then the column sums of the lengthscale parts rowacc_f[i][D + d] +
+// rowacc_u[i][D + d] and of the signal-variance parts rowacc_*[i][2D] over the
+// block's rows (FP32), added in FP64 to acc_ell and the reduction slots (one
+// atomic per block and value).  With nparts > 0 the data part rowacc_f is the
+// sum of nparts partial row sets rowpart[p][k][i] (k < 2D + 1, i < Mp), added
+// here in a fixed order.
 __global__ void __launch_bounds__(256) grad_finalize_kernel(const float* __restrict__ rf, const float* __restrict__ ru,
+                                                            const float* __restrict__ rowpart, int nparts, int Mp,
                                                             const float* __restrict__ ell, int M, int D,
                                                             float* __restrict__ dZ, double* acc_ell, double* red) {
+  constexpr int RB = 16;
+  __shared__ float tf[RB][2 * SVGP_MAXD + 2];
   const int W = 2 * D + 1;
-  const int r0 = blockIdx.x * 64;
-  const int nr = min(64, M - r0);
+  const int r0 = blockIdx.x * RB;
+  const int nr = min(RB, M - r0);
+  for (int e = threadIdx.x; e < RB * W; e += blockDim.x) {
+    const int k = e / RB, r = e - k * RB;
+    float v = 0.f;
+    if (r < nr) {
+      if (nparts > 0) {
+        const float* pp = rowpart + (size_t)k * Mp + r0 + r;
+        const size_t stride = (size_t)W * Mp;
+        int p = 0;
+        for (; p + 4 <= nparts; p += 4) {
+          const float a0 = __ldg(pp + p * stride), a1 = __ldg(pp + (p + 1) * stride);
+          const float a2 = __ldg(pp + (p + 2) * stride), a3 = __ldg(pp + (p + 3) * stride);
+          v += a0; v += a1; v += a2; v += a3;
+        }
+        for (; p < nparts; ++p) v += __ldg(pp + p * stride);
+      } else {
+        v = rf[(size_t)(r0 + r) * W + k];
+      }
+    }
+    tf[r][k] = v;
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < nr * D; e += blockDim.x) {
     const int r = e / D, d = e - r * D;
-    const size_t o = (size_t)(r0 + r) * W + d;
-    dZ[(size_t)r0 * D + e] = (rf[o] + 2.0f * ru[o]) / ell[d];
+    dZ[(size_t)r0 * D + e] = (tf[r][d] + 2.0f * ru[(size_t)(r0 + r) * W + d]) / ell[d];
   }
-  // column sums: thread t < D -> lengthscale d = t; t == D -> rf[2D]; t == D + 1 -> ru[2D]
+  // column sums: thread t < D -> lengthscale d = t; t == D -> data part of the
+  // signal variance; t == D + 1 -> Kuu part
   const int t = threadIdx.x;
   if (t < D + 2) {
     float acc = 0.f;
-#pragma unroll 8
     for (int r = 0; r < nr; ++r) {
       const size_t o = (size_t)(r0 + r) * W;
-      if (t < D) acc += rf[o + D + t] + ru[o + D + t];
-      else if (t == D) acc += rf[o + 2 * D];
+      if (t < D) acc += tf[r][D + t] + ru[o + D + t];
+      else if (t == D) acc += tf[r][2 * D];
       else acc += ru[o + 2 * D];
     }
     if (t < D) atomicAdd(acc_ell + t, (double)acc);
@@ -563,7 +612,7 @@ template void k_gp_assemble<SplitPtr>(const float*, const float*, const float*, 
 void k_kuu_bwd(const float* GKuu, const float* Kuu, const float* Zs, int M, int Mp, int D,
                float* rowacc_u, double* red, cudaStream_t st) {
   (void)red;
-  const int JB = 512;
+  const int JB = 256;
   dim3 grid((M + 31) / 32, (M + JB - 1) / JB);
   svgp_note_launch();
   SVGP_DP_DISPATCH(D, kuu_bwd_kernel<DP><<<grid, 256, 0, st>>>(GKuu, Kuu, Zs, M, Mp, D, rowacc_u, JB));
@@ -574,11 +623,11 @@ void k_logs(const float* s, int M, double* red, cudaStream_t st) {
   logs_kernel<<<(M + 255) / 256, 256, 0, st>>>(s, M, red);
 }
 
-void k_grad_finalize(const float* rowacc_f, const float* rowacc_u, const float* ell, int M, int D,
-                     float* dZ, double* acc_ell, double* red, cudaStream_t st) {
-  int grid = (M + 63) / 64;
+void k_grad_finalize(const float* rowacc_f, const float* rowacc_u, const float* rowpart, int nparts, int Mp,
+                     const float* ell, int M, int D, float* dZ, double* acc_ell, double* red, cudaStream_t st) {
+  int grid = (M + 15) / 16;
   svgp_note_launch();
-  grad_finalize_kernel<<<grid, 256, 0, st>>>(rowacc_f, rowacc_u, ell, M, D, dZ, acc_ell, red);
+  grad_finalize_kernel<<<grid, 256, 0, st>>>(rowacc_f, rowacc_u, rowpart, nparts, Mp, ell, M, D, dZ, acc_ell, red);
 }
 
 void k_terms_finalize(const double* red, const double* acc_ell, const float* sf2, const float* noise,

@@ -53,6 +53,7 @@ struct svgp_handle {
   void *Kuu_lo, *L_lo, *Lt_lo, *V, *S, *Y, *P_lo, *GP_lo;
   // vectors
   float *Zs, *Xs, *v, *w, *mu, *g, *Kg, *colsum, *rowacc_f, *rowacc_u, *dm_tmp;
+  float* rowpart;   // partial row sets of the tensor-core W epilogue
   double *red, *acc_ell, *resid_tmp;
   int *errword, *done, *iters_tmp;
   GemmCtx gs, gt;   // SIMT and tensor-core tile tables
@@ -207,9 +208,14 @@ void run_psi(svgp_handle* h, const svgp_params* p, int B) {
   if (!(h->tc_kuf && tc_psi(h->gt, kg, h->kt, B, e))) simt_psi(h->gs, kg, B, e);
 }
 
-void run_w(svgp_handle* h, const WEpi& we) {
+// Returns the number of partial row sets the tensor-core kernel wrote (0 when
+// the SIMT kernel accumulated into we.rowacc, or in variance mode).
+int run_w(svgp_handle* h, const WEpi& we) {
   ProfScope ps(h, SVGP_PROF_W);
-  if (!(h->tc_kuf && tc_w(h->gt, H(h->P_lo), h->kt, we))) simt_w(h->gs, h->Pf, we);
+  const int n = h->tc_kuf ? tc_w(h->gt, H(h->P_lo), h->kt, we, h->rowpart) : -1;
+  if (n >= 0) return n;
+  simt_w(h->gs, h->Pf, we);
+  return 0;
 }
 
 void prep_L(svgp_handle* h, const float* Lin, double* red) {
@@ -317,7 +323,8 @@ svgp_status svgp_create(const svgp_config* cfg, svgp_handle** out) {
   h->tc_kuf = h->mode != MODE_F32 && tc_kuf_supported(h->D);
   if (ok && h->tc_kuf)
     ok = dalloc(h, &h->kt.ZR, 2 * 64 * h->Mp) && dalloc(h, &h->kt.ZK, 2 * 64 * h->Mp) &&
-         dalloc(h, &h->kt.XR, 2 * 64 * Bp) && dalloc(h, &h->kt.XK, 2 * 64 * Bp);
+         dalloc(h, &h->kt.XR, 2 * 64 * Bp) && dalloc(h, &h->kt.XK, 2 * 64 * Bp) &&
+         dalloc(h, &h->rowpart, sizeof(float) * ((size_t)tc_num_sms() * 128 + h->Mp) * W);
   if (ok && h->mode == MODE_F32) { h->Kuu_lo = h->Kuu_f; h->P_lo = h->Pf; }
   if (ok) ok = build_ctx(h, h->gs, 128, 128) && build_ctx(h, h->gt, 128, 128);
   simt_init_attributes();
@@ -425,10 +432,11 @@ svgp_status svgp_backward(svgp_handle* h, const svgp_params* p, const svgp_batch
   cudaMemsetAsync(h->rowacc_u, 0, sizeof(float) * Mp * W, st);
   WEpi we{KufGen{h->Zs, h->Xs, h->D, M, b->B, p->sf2}, nullptr, nullptr, h->v, h->g, p->noise, c,
           h->rowacc_f, nullptr};
-  run_w(h, we);                                                                        // data part of dZ, dell, dsf2
+  const int nparts = run_w(h, we);                                                     // data part of dZ, dell, dsf2
   k_kuu_bwd(h->GKuu, h->Kuu_f, h->Zs, M, Mp, h->D, h->rowacc_u, h->red, st);          // Kuu part
   k_gemv(h->Pf, Mp, M, h->Kg, c, h->w, -1.0f / c, gr->dm, nullptr, nullptr, st);      // dm = P (c Kg - w)
-  k_grad_finalize(h->rowacc_f, h->rowacc_u, p->ell, M, h->D, gr->dZ, h->acc_ell, h->red, st);
+  k_grad_finalize(h->rowacc_f, h->rowacc_u, h->rowpart, nparts, Mp, p->ell, M, h->D, gr->dZ, h->acc_ell, h->red,
+                  st);
   k_terms_finalize(h->red, h->acc_ell, p->sf2, p->noise, p->ell, M, h->D, b->B, b->N, terms_dev, gr->dsf2,
                    gr->dnoise, gr->dell, h->errword, st);
   return check_launch(h, "svgp_backward");
