@@ -151,6 +151,18 @@ svgp_status svgp_ng_update_T(svgp_handle* h, const svgp_params* p, float* L_inou
                              const float* gamma_dev, int max_iters, double eps,
                              int* iters_dev, double* residual_dev);
 
+/* One training step's device work in a single call: svgp_ng_update_T on
+ * L_inout (same arguments and semantics), then svgp_backward with L = the
+ * updated L_inout (p->L is ignored).  The scaled coordinates, Kuu and the Kuf
+ * generator operands are prepared once for both parts; results equal those of
+ * the two separate calls.  Not in the paper as an operation of its own: it is
+ * the composition Section 3.3 runs every iteration (NG steps on T, then a
+ * gradient step on the other parameters). */
+svgp_status svgp_train_step(svgp_handle* h, const svgp_params* p, const svgp_batch* b,
+                            float* L_inout, const float* gamma_dev, int max_iters, double eps,
+                            int* iters_dev, double* residual_dev, double* terms_dev,
+                            const svgp_grads* g);
+
 /* Predictive moments at Ns test inputs Xs (Ns x D), same form as Eq. (7):
  * mean = K*u P m~, var = sf2 - diag(K*u P Ku*) (+ noise if include_noise).
  * 1 <= Ns <= B_max. mean, var: device float[Ns]. */

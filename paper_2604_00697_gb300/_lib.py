@@ -33,7 +33,7 @@ SVGP_NTERMS = len(TERMS)
 
 EXPORTED = [
     "svgp_create", "svgp_destroy", "svgp_set_stream", "svgp_bound", "svgp_backward",
-    "svgp_ng_update_T", "svgp_predict", "svgp_adam_step", "svgp_param_count",
+    "svgp_ng_update_T", "svgp_train_step", "svgp_predict", "svgp_adam_step", "svgp_param_count",
     "svgp_sync_status", "svgp_last_error", "svgp_status_string", "svgp_has_tensor_cores",
 ]
 
@@ -82,6 +82,8 @@ def load(path: str = LIB_PATH):
     lib.svgp_backward.argtypes = [H, POINTER(svgp_params), POINTER(svgp_batch), c_void_p, POINTER(svgp_grads)]
     lib.svgp_ng_update_T.argtypes = [H, POINTER(svgp_params), c_void_p, c_void_p, c_int, c_double, c_void_p,
                                      c_void_p]
+    lib.svgp_train_step.argtypes = [H, POINTER(svgp_params), POINTER(svgp_batch), c_void_p, c_void_p, c_int,
+                                    c_double, c_void_p, c_void_p, c_void_p, POINTER(svgp_grads)]
     lib.svgp_predict.argtypes = [H, POINTER(svgp_params), c_void_p, c_int, c_void_p, c_void_p, c_int]
     lib.svgp_adam_step.argtypes = [H, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                    c_void_p]
@@ -95,7 +97,7 @@ def load(path: str = LIB_PATH):
     lib.svgp_has_tensor_cores.argtypes = []
     lib.svgp_has_tensor_cores.restype = c_int
     for name in ("svgp_create", "svgp_set_stream", "svgp_bound", "svgp_backward", "svgp_ng_update_T",
-                 "svgp_predict", "svgp_adam_step", "svgp_sync_status"):
+                 "svgp_train_step", "svgp_predict", "svgp_adam_step", "svgp_sync_status"):
         getattr(lib, name).restype = c_int
     _lib = lib
     return lib
@@ -137,6 +139,12 @@ def svgp_backward(h, params, batch, terms_ptr, grads):
 def svgp_ng_update_T(h, params, L_ptr, gamma_ptr, max_iters, eps, iters_ptr=None, resid_ptr=None):
     _check(h, load().svgp_ng_update_T(h, byref(params), c_void_p(L_ptr), c_void_p(gamma_ptr), max_iters,
                                       c_double(eps), c_void_p(iters_ptr), c_void_p(resid_ptr)))
+
+
+def svgp_train_step(h, params, batch, L_ptr, gamma_ptr, max_iters, eps, iters_ptr, resid_ptr, terms_ptr, grads):
+    _check(h, load().svgp_train_step(h, byref(params), byref(batch), c_void_p(L_ptr), c_void_p(gamma_ptr),
+                                     max_iters, c_double(eps), c_void_p(iters_ptr), c_void_p(resid_ptr),
+                                     c_void_p(terms_ptr), byref(grads)))
 
 
 def svgp_predict(h, params, Xs_ptr, Ns, mean_ptr, var_ptr, include_noise=False):

@@ -123,47 +123,57 @@ psi_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // z, row role
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
+    // Event-driven issue: the exponent MMA of k-block d goes out as soon as its
+    // coordinates have landed and its TMEM buffer is free, ahead of the main
+    // MMA of earlier k-blocks, which waits for their generated tiles.  The
+    // exponent MMAs therefore run up to two k-blocks ahead of the transform.
     bool ok = mbar_wait(BAR(B_STATIC), 0);
-    auto main_mma = [&](int j) -> bool {
-      const int s = j % S;
-      if (!mbar_wait(BAR(B_GEN + s), (j / S) & 1)) return false;
-      fence_after();
-      unsigned char* st = stg + s * G::STAGE;
-      const uint64_t ad = sw128_desc(smem_u32(st + G::OFF_GA));
-      const uint64_t adl = sw128_desc(smem_u32(st + G::OFF_GA + GT));
-      const uint64_t bd = diag ? ad : sw128_desc(smem_u32(st + G::OFF_GB));
-      const uint64_t bdl = diag ? adl : sw128_desc(smem_u32(st + G::OFF_GB + GT));
+    fence_after();
+    const uint64_t ra = sw128_desc(smem_u32(sRowA));
+    const uint64_t rb = sw128_desc(smem_u32(sRowB));
+    int d = 0, mn = 0;
+    long long idle_since = clock64();
+    while (ok && mn < nkb) {
+      bool progressed = false;
+      if (d < nkb && mbar_try(BAR(B_LD + d % S), (d / S) & 1) &&
+          mbar_try(BAR(B_SEMPTY + (d & 1)), ((d >> 1) & 1) ^ 1)) {
+        fence_after();
+        *consumed = d + 1;
+        const int b = d & 1;
+        const uint64_t kd = sw128_desc(smem_u32(stg + (d % S) * G::STAGE));
 #pragma unroll
-      for (int kk = 0; kk < KB / 16; ++kk) {
-        const uint64_t o = (uint64_t)(kk * 2);
-        mma_bf16(tmem, ad + o, bd + o, ID_MAIN, (j | kk) != 0);
-        if (NSPLIT == 3) {
-          mma_bf16(tmem, ad + o, bdl + o, ID_MAIN, 1);
-          mma_bf16(tmem, adl + o, bd + o, ID_MAIN, 1);
+        for (int kk = 0; kk < KB / 16; ++kk) {
+          const uint64_t o = (uint64_t)(kk * 2);
+          mma_bf16(tmem + G::S_A(b), ra + o, kd + o, ID_DIST, kk != 0);
+          if (!diag) mma_bf16(tmem + G::S_B(b), rb + o, kd + o, ID_DIST, kk != 0);
         }
+        mma_commit(BAR(B_SFULL + b));
+        ++d;
+        progressed = true;
       }
-      mma_commit(BAR(B_EMPTY + s));
-      return true;
-    };
-    for (int kb = 0; kb < nkb && ok; ++kb) {
-      const int s = kb % S, b = kb & 1;
-      if (!mbar_wait(BAR(B_LD + s), (kb / S) & 1)) { ok = false; break; }
-      *consumed = kb + 1;
-      if (!mbar_wait(BAR(B_SEMPTY + b), ((kb >> 1) & 1) ^ 1)) { ok = false; break; }
-      fence_after();
-      const uint64_t kd = sw128_desc(smem_u32(stg + s * G::STAGE));
-      const uint64_t ra = sw128_desc(smem_u32(sRowA));
-      const uint64_t rb = sw128_desc(smem_u32(sRowB));
+      if (mn < d && mbar_try(BAR(B_GEN + mn % S), (mn / S) & 1)) {
+        fence_after();
+        unsigned char* st = stg + (mn % S) * G::STAGE;
+        const uint64_t ad = sw128_desc(smem_u32(st + G::OFF_GA));
+        const uint64_t adl = sw128_desc(smem_u32(st + G::OFF_GA + GT));
+        const uint64_t bd = diag ? ad : sw128_desc(smem_u32(st + G::OFF_GB));
+        const uint64_t bdl = diag ? adl : sw128_desc(smem_u32(st + G::OFF_GB + GT));
 #pragma unroll
-      for (int kk = 0; kk < KB / 16; ++kk) {
-        const uint64_t o = (uint64_t)(kk * 2);
-        mma_bf16(tmem + G::S_A(b), ra + o, kd + o, ID_DIST, kk != 0);
-        if (!diag) mma_bf16(tmem + G::S_B(b), rb + o, kd + o, ID_DIST, kk != 0);
+        for (int kk = 0; kk < KB / 16; ++kk) {
+          const uint64_t o = (uint64_t)(kk * 2);
+          mma_bf16(tmem, ad + o, bd + o, ID_MAIN, (mn | kk) != 0);
+          if (NSPLIT == 3) {
+            mma_bf16(tmem, ad + o, bdl + o, ID_MAIN, 1);
+            mma_bf16(tmem, adl + o, bd + o, ID_MAIN, 1);
+          }
+        }
+        mma_commit(BAR(B_EMPTY + mn % S));
+        ++mn;
+        progressed = true;
       }
-      mma_commit(BAR(B_SFULL + b));
-      if (kb >= 1 && !main_mma(kb - 1)) { ok = false; break; }
+      if (progressed) idle_since = clock64();
+      else if (clock64() - idle_since > WAIT_CYCLES || *abort_flag) ok = false;
     }
-    if (ok && nkb > 0) ok = main_mma(nkb - 1);
     if (!ok) *abort_flag = 1;
     mma_commit(BAR(B_ACC));
   } else if (warp >= 2) {
@@ -291,6 +301,7 @@ void tc_kuf_init_attributes() {
   set_psi_attr<1>();
   set_psi_attr<3>();
   tc_w_init_attributes();
+  tc_gemv_init_attributes();
 }
 
 bool tc_kuf_supported(int D) { return D >= 1 && 3 * D + 6 <= 64 && tc_available(); }

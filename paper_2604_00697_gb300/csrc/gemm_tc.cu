@@ -1,8 +1,8 @@
 // tcgen05 BF16 GEMMs for sm_103a: acc[i,j] = sum_k A[i,k] B[j,k], both
 // operands K-major BF16 (row-major, k contiguous), FP32 accumulation in TMEM.
 //
-// Persistent kernel: one CTA per SM walks the tile table (128 x 128 output
-// tiles, sorted by decreasing K length) with stride gridDim.x.  192 threads:
+// Persistent kernel: one CTA per SM walks its list of 128 x 128 output tiles
+// (a longest-processing-time-first schedule built on the host).  192 threads:
 //   warp 0      TMA producer: 128B-swizzled 128x64 tiles of A and B (and of
 //               their lo parts for split operands) into a STAGES-deep
 //               shared-memory ring (mbarrier full/empty pairs) that runs
@@ -55,7 +55,7 @@ template <class Epi, int NSPLIT>
 __global__ void __launch_bounds__(192, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmAl, const __grid_constant__ CUtensorMap tmBl,
-               const Tile* __restrict__ tiles, int ntiles, Epi epi, int* errword,
+               const Tile* __restrict__ tiles, const int* __restrict__ toff, Epi epi, int* errword,
                const __grid_constant__ etc::EpiMaps maps) {
   using G = Geo<NSPLIT>;
   constexpr int S = G::STAGES;
@@ -72,6 +72,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   auto BAR = [&](int i) { return smem_u32(&bars[i]); };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t_beg = toff[blockIdx.x], t_end = toff[blockIdx.x + 1];   // this CTA's tiles
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -98,7 +99,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
     int g = 0;          // running k-block counter over all tiles of this CTA
-    for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+    for (int t = t_beg; t < t_end && !*abort_flag; ++t) {
       const Tile tl = tiles[t];
       const int nk = (tl.k1 - tl.k0) / BK;
       for (int kb = 0; kb < nk; ++kb, ++g) {
@@ -124,7 +125,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
     int g = 0, lt = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+    for (int t = t_beg; t < t_end; ++t, ++lt) {
       const Tile tl = tiles[t];
       const int nk = (tl.k1 - tl.k0) / BK;
       const int b = lt & 1;
@@ -179,7 +180,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     };
     epi.begin_tile(0, 0);
     int lt = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+    for (int t = t_beg; t < t_end; ++t, ++lt) {
       const Tile tl = tiles[t];
       const int nk = (tl.k1 - tl.k0) / BK;
       const int b = lt & 1;
@@ -267,8 +268,6 @@ void set_attr_both() {
   set_attr<Epi, 1>();
   set_attr<Epi, 3>();
 }
-
-int num_sms() { return tc_num_sms(); }
 
 }  // namespace
 
@@ -359,8 +358,7 @@ bool tc_available() {
 template <class Epi>
 bool tc_gemm(const GemmCtx& g, int tab, const bf16* A, const bf16* B, const Epi& e) {
   const size_t MM = (size_t)g.Mp * g.Mp;
-  const int nt = g.nt[tab];
-  const int grid = nt < num_sms() ? nt : num_sms();
+  const int grid = g.ncta[tab];
   CUtensorMap ma, mb, mal, mbl;
   if (!tc_make_map(&ma, A, g.Mp, g.Mp, 128) || !tc_make_map(&mb, B, g.Mp, g.Mp, 128)) return false;
   etc::EpiMaps em;
@@ -369,10 +367,10 @@ bool tc_gemm(const GemmCtx& g, int tab, const bf16* A, const bf16* B, const Epi&
   if (g.split) {
     if (!tc_make_map(&mal, A + MM, g.Mp, g.Mp, 128) || !tc_make_map(&mbl, B + MM, g.Mp, g.Mp, 128)) return false;
     svgp_note_launch();
-    tc_gemm_kernel<Epi, 3><<<grid, 192, Geo<3>::SMEM, g.st>>>(ma, mb, mal, mbl, g.tt[tab], nt, e, g.err, em);
+    tc_gemm_kernel<Epi, 3><<<grid, 192, Geo<3>::SMEM, g.st>>>(ma, mb, mal, mbl, g.tt[tab], g.toff[tab], e, g.err, em);
   } else {
     svgp_note_launch();
-    tc_gemm_kernel<Epi, 1><<<grid, 192, Geo<1>::SMEM, g.st>>>(ma, mb, ma, mb, g.tt[tab], nt, e, g.err, em);
+    tc_gemm_kernel<Epi, 1><<<grid, 192, Geo<1>::SMEM, g.st>>>(ma, mb, ma, mb, g.tt[tab], g.toff[tab], e, g.err, em);
   }
   return true;
 }

@@ -153,54 +153,64 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
+    // Per n-block an event-driven loop: the exponent MMA of k-block d goes out
+    // as soon as its coordinates have landed and its TMEM buffer is free, ahead
+    // of the main MMA of earlier k-blocks (which waits for their generated
+    // tiles); then the epilogue exponents T.
     bool ok = mbar_wait(BAR(B_ZR), 0);
-    auto main_mma = [&](int gj, int kb) -> bool {
-      const int s = gj % S;
-      if (!mbar_wait(BAR(B_GEN + s), (gj / S) & 1)) return false;
-      fence_after();
-      unsigned char* st = stg + s * G::STAGE;
-      const uint64_t ad = sw128_desc(smem_u32(st + G::OFF_P));
-      const uint64_t adl = sw128_desc(smem_u32(st + G::OFF_P + GT));
-      const uint64_t bd = sw128_desc(smem_u32(st + G::OFF_G));
-      const uint64_t bdl = sw128_desc(smem_u32(st + G::OFF_G + GT));
-#pragma unroll
-      for (int kk = 0; kk < KB / 16; ++kk) {
-        const uint64_t o = (uint64_t)(kk * 2);
-        mma_bf16(tmem + G::ACC, ad + o, bd + o, ID_MAIN, (kb | kk) != 0);
-        if (NSPLIT == 3) {
-          mma_bf16(tmem + G::ACC, ad + o, bdl + o, ID_MAIN, 1);
-          mma_bf16(tmem + G::ACC, adl + o, bd + o, ID_MAIN, 1);
-        }
-      }
-      mma_commit(BAR(B_EMPTY + s));
-      return true;
-    };
     int g = 0, lt = 0;
     for (int nb = blockIdx.x; nb < wa.nblk && ok; nb += gridDim.x, ++lt) {
       if (!mbar_wait(BAR(B_TILE), lt & 1)) { ok = false; break; }
       fence_after();
       const uint64_t ra = sw128_desc(smem_u32(sXR));
-      for (int kb = 0; kb < nkb; ++kb, ++g) {
-        const int s = g % S, b = g & 1;
-        if (!mbar_wait(BAR(B_LD + s), (g / S) & 1)) { ok = false; break; }
-        *consumed = g + 1;
-        if (!mbar_wait(BAR(B_SEMPTY + b), ((g >> 1) & 1) ^ 1)) { ok = false; break; }
-        fence_after();
-        const uint64_t kd = sw128_desc(smem_u32(stg + s * G::STAGE));
+      int d = 0, mn = 0;
+      long long idle_since = clock64();
+      while (mn < nkb) {
+        bool progressed = false;
+        const int gd = g + d, gm = g + mn;
+        if (d < nkb && mbar_try(BAR(B_LD + gd % S), (gd / S) & 1) &&
+            mbar_try(BAR(B_SEMPTY + (gd & 1)), ((gd >> 1) & 1) ^ 1)) {
+          fence_after();
+          *consumed = gd + 1;
+          const uint64_t kd = sw128_desc(smem_u32(stg + (gd % S) * G::STAGE));
 #pragma unroll
-        for (int kk = 0; kk < KB / 16; ++kk) {
-          const uint64_t o = (uint64_t)(kk * 2);
-          mma_bf16(tmem + G::SB(b), ra + o, kd + o, ID_DIST, kk != 0);
+          for (int kk = 0; kk < KB / 16; ++kk) {
+            const uint64_t o = (uint64_t)(kk * 2);
+            mma_bf16(tmem + G::SB(gd & 1), ra + o, kd + o, ID_DIST, kk != 0);
+          }
+          mma_commit(BAR(B_SFULL + (gd & 1)));
+          ++d;
+          progressed = true;
         }
-        mma_commit(BAR(B_SFULL + b));
         // The first main MMA of an n-block overwrites the accumulator: it waits
         // for that k-block's generated operand, which the transform warps
         // produce only after their epilogue of the previous n-block has read
         // the accumulator and the exponents T.
-        if (kb >= 1 && !main_mma(g - 1, kb - 1)) { ok = false; break; }
+        if (mn < d && mbar_try(BAR(B_GEN + gm % S), (gm / S) & 1)) {
+          fence_after();
+          unsigned char* st = stg + (gm % S) * G::STAGE;
+          const uint64_t ad = sw128_desc(smem_u32(st + G::OFF_P));
+          const uint64_t adl = sw128_desc(smem_u32(st + G::OFF_P + GT));
+          const uint64_t bd = sw128_desc(smem_u32(st + G::OFF_G));
+          const uint64_t bdl = sw128_desc(smem_u32(st + G::OFF_G + GT));
+#pragma unroll
+          for (int kk = 0; kk < KB / 16; ++kk) {
+            const uint64_t o = (uint64_t)(kk * 2);
+            mma_bf16(tmem + G::ACC, ad + o, bd + o, ID_MAIN, (mn | kk) != 0);
+            if (NSPLIT == 3) {
+              mma_bf16(tmem + G::ACC, ad + o, bdl + o, ID_MAIN, 1);
+              mma_bf16(tmem + G::ACC, adl + o, bd + o, ID_MAIN, 1);
+            }
+          }
+          mma_commit(BAR(B_EMPTY + gm % S));
+          ++mn;
+          progressed = true;
+        }
+        if (progressed) idle_since = clock64();
+        else if (clock64() - idle_since > WAIT_CYCLES || *abort_flag) { ok = false; break; }
       }
+      g += nkb;
       if (!ok) break;
-      if (!main_mma(g - 1, nkb - 1)) { ok = false; break; }
       // epilogue exponents T[i, n] = log2 Kuf_in
       const uint64_t zd = sw128_desc(smem_u32(sZR)), xd = sw128_desc(smem_u32(sXK));
 #pragma unroll

@@ -22,6 +22,10 @@ struct GemmCtx {
   bool split;      // tensor-core operands are hi/lo BF16 pairs (lo at +Mp*Mp)
   Tile* tt[TT_COUNT];
   int nt[TT_COUNT];
+  // tensor-core schedule: CTA c of a launch of ncta[t] CTAs processes the
+  // tiles tt[t][toff[t][c] .. toff[t][c + 1])
+  int* toff[TT_COUNT];
+  int ncta[TT_COUNT];
 };
 
 // Process-wide count of kernel launches issued by the library (svgp_api.cu).
@@ -60,6 +64,11 @@ bool tc_psi(const GemmCtx& g, const KufGen& kg, const KufTC& t, int B, EpiPsi e)
 int tc_w(const GemmCtx& g, const bf16* P, const KufTC& t, const WEpi& we, float* rowpart);
 int tc_w_groups(int Mp, int B);
 void tc_w_init_attributes();
+// out[r] = sum_k Kuf(r, k) w_k for r < nrows, k < nk, from the row-role vectors
+// of the row points and the k-role vectors of the k points (kuf_prep).
+bool tc_kuf_gemv(const bf16* Rrole, int nrows, const bf16* Krole, int nk, const float* w, float* out, int* errword,
+                 cudaStream_t st);
+void tc_gemv_init_attributes();
 
 // Miscellaneous kernels (kernels_misc.cu).  OutP is float*, bf16* or SplitPtr.
 void k_prep_coords(const float* Z, const float* X, const float* ell, int M, int Mp, int B, int D,
@@ -68,7 +77,7 @@ template <class OutP>
 void k_kuu(const float* Zs, int M, int Mp, int D, const float* sf2, float* Kf, OutP Klo, bool has_lo,
            cudaStream_t st);
 template <class OutP>
-void k_prep_L(const float* Lin, int M, int Mp, float* Lf, OutP Llo, OutP Ltlo, double* red,
+void k_prep_L(const float* Lin, int M, int Mp, float* Lf, OutP Llo, OutP Ltlo, double* logdet,
               cudaStream_t st);
 void k_gemv(const float* A, int Mp, int M, const float* x, float alpha, const float* x2, float beta,
             float* y, const float* dotw, double* dot_out, cudaStream_t st);

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(256) kuu_kernel(const float* __restrict__ Zs, 
 // precision); strictly-upper entries forced to zero; sum log|L_ii|.
 template <class OutP>
 __global__ void prep_L_kernel(const float* __restrict__ Lin, int M, int Mp, float* __restrict__ Lf,
-                              OutP Llo, OutP Ltlo, double* red) {
+                              OutP Llo, OutP Ltlo, double* logdet) {
   __shared__ float tile[32][33];
   int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
   // Blocks strictly above the diagonal stay zero in L (and below it in L^T):
@@ -97,7 +97,7 @@ __global__ void prep_L_kernel(const float* __restrict__ Lin, int M, int Mp, floa
     // Lt[j0 + ty][i0 + tx] = L[i0 + tx][j0 + ty]
     put(Ltlo, (size_t)(j0 + ty) * Mp + i0 + tx, tile[tx][ty]);
   }
-  if (blockIdx.x == blockIdx.y) block_add_double(ld, red + RED_LOGDETL);
+  if (logdet && blockIdx.x == blockIdx.y) block_add_double(ld, logdet);
 }
 
 // y = alpha * A (x + beta * x2)  (A: Mp x Mp FP32, rows < M); one warp per
@@ -555,10 +555,10 @@ template void k_kuu<bf16*>(const float*, int, int, int, const float*, float*, bf
 template void k_kuu<SplitPtr>(const float*, int, int, int, const float*, float*, SplitPtr, bool, cudaStream_t);
 
 template <class OutP>
-void k_prep_L(const float* Lin, int M, int Mp, float* Lf, OutP Llo, OutP Ltlo, double* red, cudaStream_t st) {
+void k_prep_L(const float* Lin, int M, int Mp, float* Lf, OutP Llo, OutP Ltlo, double* logdet, cudaStream_t st) {
   dim3 grid(Mp / 32, Mp / 32), blk(32, 8);
   svgp_note_launch();
-  prep_L_kernel<OutP><<<grid, blk, 0, st>>>(Lin, M, Mp, Lf, Llo, Ltlo, red);
+  prep_L_kernel<OutP><<<grid, blk, 0, st>>>(Lin, M, Mp, Lf, Llo, Ltlo, logdet);
 }
 template void k_prep_L<float*>(const float*, int, int, float*, float*, float*, double*, cudaStream_t);
 template void k_prep_L<bf16*>(const float*, int, int, float*, bf16*, bf16*, double*, cudaStream_t);

@@ -99,18 +99,53 @@ bool upload_tiles(svgp_handle* h, const std::vector<Tile>& v, Tile** out, int* n
   return true;
 }
 
-bool build_ctx(svgp_handle* h, GemmCtx& g, int BM, int BN) {
+// Persistent-kernel schedule: longest-processing-time-first assignment of the
+// tiles to min(#tiles, #SMs) CTAs, cost = k-blocks x 750 + 5000 cycles (the
+// measured mainloop cost per 64-deep k-block and epilogue cost per tile).
+// Returns the tiles grouped by CTA; off[c] .. off[c + 1] are CTA c's.
+std::vector<Tile> lpt_schedule(const std::vector<Tile>& v, int nsm, std::vector<int>& off) {
+  const int G = std::max(1, std::min((int)v.size(), nsm));
+  std::vector<std::vector<Tile>> per(G);
+  std::vector<long long> load(G, 0);
+  for (const Tile& t : v) {            // v is sorted by decreasing k length
+    int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    per[c].push_back(t);
+    load[c] += (long long)(t.k1 - t.k0) / 64 * 750 + 5000;
+  }
+  std::vector<Tile> out;
+  off.assign(1, 0);
+  for (int c = 0; c < G; ++c) {
+    out.insert(out.end(), per[c].begin(), per[c].end());
+    off.push_back((int)out.size());
+  }
+  return out;
+}
+
+bool upload_sched(svgp_handle* h, const std::vector<Tile>& v, GemmCtx& g, int tab) {
+  std::vector<int> off;
+  std::vector<Tile> s = lpt_schedule(v, tc_num_sms(), off);
+  if (!upload_tiles(h, s, &g.tt[tab], &g.nt[tab])) return false;
+  if (!dalloc(h, &g.toff[tab], sizeof(int) * off.size())) return false;
+  cudaMemcpy(g.toff[tab], off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice);
+  g.ncta[tab] = (int)off.size() - 1;
+  return true;
+}
+
+bool build_ctx(svgp_handle* h, GemmCtx& g, int BM, int BN, bool sched) {
   int Mp = h->Mp;
   g.Mp = Mp;
   g.st = h->st;
   g.err = h->errword;
   g.split = h->mode == 2;
-  return upload_tiles(h, make_tiles(Mp, BM, BN, REG_FULL, K_M0_END), &g.tt[TT_VT], &g.nt[TT_VT]) &&
-         upload_tiles(h, make_tiles(Mp, BM, BN, REG_UPPER, K_N0_END), &g.tt[TT_SYM_IN], &g.nt[TT_SYM_IN]) &&
-         upload_tiles(h, make_tiles(Mp, BM, BN, REG_LOWER, K_N0_M1), &g.tt[TT_LUPD], &g.nt[TT_LUPD]) &&
-         upload_tiles(h, make_tiles(Mp, BM, BN, REG_FULL, K_0_M1), &g.tt[TT_LS], &g.nt[TT_LS]) &&
-         upload_tiles(h, make_tiles(Mp, BM, BN, REG_LOWER, K_0_N1), &g.tt[TT_OUT], &g.nt[TT_OUT]) &&
-         upload_tiles(h, make_tiles(Mp, BM, BN, REG_UPPER, K_ALL), &g.tt[TT_PSI], &g.nt[TT_PSI]);
+  const std::vector<Tile> tabs[TT_COUNT] = {
+      make_tiles(Mp, BM, BN, REG_FULL, K_M0_END),  make_tiles(Mp, BM, BN, REG_UPPER, K_N0_END),
+      make_tiles(Mp, BM, BN, REG_LOWER, K_N0_M1),  make_tiles(Mp, BM, BN, REG_FULL, K_0_M1),
+      make_tiles(Mp, BM, BN, REG_LOWER, K_0_N1),   make_tiles(Mp, BM, BN, REG_UPPER, K_ALL)};
+  for (int t = 0; t < TT_COUNT; ++t) {
+    const bool ok = (sched && t != TT_PSI) ? upload_sched(h, tabs[t], g, t) : upload_tiles(h, tabs[t], &g.tt[t], &g.nt[t]);
+    if (!ok) return false;
+  }
+  return true;
 }
 
 bool valid_params(const svgp_params* p) {
@@ -218,10 +253,12 @@ int run_w(svgp_handle* h, const WEpi& we) {
   return 0;
 }
 
-void prep_L(svgp_handle* h, const float* Lin, double* red) {
-  if (h->mode == MODE_F32) k_prep_L(Lin, h->M, h->Mp, h->Lf, F(h->L_lo), F(h->Lt_lo), red, h->st);
-  else if (h->mode == MODE_BF16) k_prep_L(Lin, h->M, h->Mp, h->Lf, H(h->L_lo), H(h->Lt_lo), red, h->st);
-  else k_prep_L(Lin, h->M, h->Mp, h->Lf, SP(h, h->L_lo), SP(h, h->Lt_lo), red, h->st);
+// FP32 and operand copies of L (and L^T); adds sum_i log|L_ii| to *logdet
+// when logdet != null.
+void prep_L(svgp_handle* h, const float* Lin, double* logdet) {
+  if (h->mode == MODE_F32) k_prep_L(Lin, h->M, h->Mp, h->Lf, F(h->L_lo), F(h->Lt_lo), logdet, h->st);
+  else if (h->mode == MODE_BF16) k_prep_L(Lin, h->M, h->Mp, h->Lf, H(h->L_lo), H(h->Lt_lo), logdet, h->st);
+  else k_prep_L(Lin, h->M, h->Mp, h->Lf, SP(h, h->L_lo), SP(h, h->Lt_lo), logdet, h->st);
 }
 
 // Common prologue: scaled coordinates, Kuu, L copies, log-dets; zero sums.
@@ -234,7 +271,7 @@ void prologue(svgp_handle* h, const svgp_params* p, const float* X, int B, const
   if (h->mode == MODE_F32) k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, (float*)nullptr, false, st);
   else if (h->mode == MODE_BF16) k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, H(h->Kuu_lo), true, st);
   else k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, SP(h, h->Kuu_lo), true, st);
-  prep_L(h, Lin, h->red);
+  prep_L(h, Lin, h->red + RED_LOGDETL);
 }
 
 // Forward pass of Eq. (7) up to the per-point Gaussian terms.
@@ -249,7 +286,8 @@ void forward(svgp_handle* h, const svgp_params* p, const svgp_batch* b, bool psi
   k_gemv(h->Pf, h->Mp, h->M, p->m, 1.f, nullptr, 0.f, h->v, nullptr, nullptr, st);          // v = P m
   k_gemv(h->Kuu_f, h->Mp, h->M, h->v, 1.f, nullptr, 0.f, h->w, h->v, h->red + RED_QUAD, st);  // w = Kuu v
   if (b) {
-    k_mu(h->Zs, h->Xs, h->M, b->B, h->D, p->sf2, h->v, h->mu, st);                          // mu = Kfu v
+    if (!(h->tc_kuf && tc_kuf_gemv(h->kt.XR, b->B, h->kt.ZK, h->M, h->v, h->mu, h->errword, st)))
+      k_mu(h->Zs, h->Xs, h->M, b->B, h->D, p->sf2, h->v, h->mu, st);                        // mu = Kfu v
     k_pointwise_gauss(b->y, h->mu, p->noise, b->B, h->g, h->red, st);
   }
 }
@@ -260,6 +298,60 @@ svgp_status validate_batch(svgp_handle* h, const svgp_batch* b) {
   if (!(b->N > 0)) return fail(h, SVGP_ERR_INVALID_ARG, "batch: N must be > 0");
   return SVGP_OK;
 }
+
+bool valid_grads(const svgp_grads* gr) {
+  return gr && gr->dZ && gr->dell && gr->dsf2 && gr->dnoise && gr->dm && gr->ds;
+}
+// Bound and gradient after the prologue: forward pass, then the backward
+// pass with T fixed (Section 3.1).
+void backward_tail(svgp_handle* h, const svgp_params* p, const svgp_batch* b, double* terms_dev, const svgp_grads* gr) {
+  cudaStream_t st = h->st;
+  const int M = h->M, Mp = h->Mp, W = 2 * h->D + 1;
+  const float c = (float)(b->N / b->B);
+  forward(h, p, b, true);
+  if (!(h->tc_kuf && tc_kuf_gemv(h->kt.ZR, M, h->kt.XK, b->B, h->g, h->Kg, h->errword, st)))
+    k_kg(h->Zs, h->Xs, M, Mp, b->B, h->D, p->sf2, h->g, h->Kg, st);                    // Kuf g
+  if (h->mode == MODE_F32) k_gp_assemble(h->Kuu_f, h->Psi, h->Kg, p->m, h->w, p->noise, c, M, Mp, F(h->GP_lo), st);
+  else if (h->mode == MODE_BF16) k_gp_assemble(h->Kuu_f, h->Psi, h->Kg, p->m, h->w, p->noise, c, M, Mp, H(h->GP_lo), st);
+  else k_gp_assemble(h->Kuu_f, h->Psi, h->Kg, p->m, h->w, p->noise, c, M, Mp, SP(h, h->GP_lo), st);
+  run_vt(h, h->GP_lo, nullptr, nullptr); // X1t = L^T G_P
+  run_sym<2>(h, nullptr);                // S = L^T G_P L + I/2
+  run_ls(h);                             // Y = L S
+  run_gk(h, p->s, gr->ds);               // G_K~ = -Y L^T -> G_Kuu, ds
+  cudaMemsetAsync(h->rowacc_f, 0, sizeof(float) * Mp * W, st);
+  cudaMemsetAsync(h->rowacc_u, 0, sizeof(float) * Mp * W, st);
+  WEpi we{KufGen{h->Zs, h->Xs, h->D, M, b->B, p->sf2}, nullptr, nullptr, h->v, h->g, p->noise, c,
+          h->rowacc_f, nullptr};
+  const int nparts = run_w(h, we);                                                     // data part of dZ, dell, dsf2
+  k_kuu_bwd(h->GKuu, h->Kuu_f, h->Zs, M, Mp, h->D, h->rowacc_u, h->red, st);          // Kuu part
+  k_gemv(h->Pf, Mp, M, h->Kg, c, h->w, -1.0f / c, gr->dm, nullptr, nullptr, st);      // dm = P (c Kg - w)
+  k_grad_finalize(h->rowacc_f, h->rowacc_u, h->rowpart, nparts, Mp, p->ell, M, h->D, gr->dZ, h->acc_ell, h->red,
+                  st);
+  k_terms_finalize(h->red, h->acc_ell, p->sf2, p->noise, p->ell, M, h->D, b->B, b->N, terms_dev, gr->dsf2,
+                   gr->dnoise, gr->dell, h->errword, st);
+}
+
+// NG iterations of Prop. 1 on L_inout after the prologue (K~ and the L copies
+// current); the L copies are refreshed between iterations, not after the last.
+void ng_loop(svgp_handle* h, const svgp_params* p, float* L_inout, const float* gamma_dev, int max_iters, double eps,
+             int* iters, double* resid) {
+  cudaStream_t st = h->st;
+  cudaMemsetAsync(h->done, 0, sizeof(int), st);
+  cudaMemsetAsync(iters, 0, sizeof(int), st);
+  for (int t = 0; t < max_iters; ++t) {
+    cudaMemsetAsync(h->red + RED_NG_RESID, 0, sizeof(double), st);
+    run_vt(h, h->Kuu_lo, p->s, h->done);         // Vt = L^T K~ (skipped once converged)
+    run_sym<0>(h, h->done);                      // A, Phi^T, ||A - I||^2
+    k_ng_check(h->red, h->M, eps, h->done, iters, resid, st);   // Eq. (8) stopping rule
+    run_lupd(h, L_inout, gamma_dev + t);         // L <- L - gamma L Phi  (Prop. 1)
+    if (t + 1 < max_iters) prep_L(h, L_inout, nullptr);
+  }
+}
+
+bool valid_ng_args(const svgp_params* p, const float* L_inout, const float* gamma_dev, int max_iters) {
+  return p && p->Z && p->ell && p->sf2 && p->s && L_inout && gamma_dev && max_iters >= 0 && max_iters <= 100000;
+}
+
 
 }  // namespace
 
@@ -326,7 +418,7 @@ svgp_status svgp_create(const svgp_config* cfg, svgp_handle** out) {
          dalloc(h, &h->kt.XR, 2 * 64 * Bp) && dalloc(h, &h->kt.XK, 2 * 64 * Bp) &&
          dalloc(h, &h->rowpart, sizeof(float) * ((size_t)tc_num_sms() * 128 + h->Mp) * W);
   if (ok && h->mode == MODE_F32) { h->Kuu_lo = h->Kuu_f; h->P_lo = h->Pf; }
-  if (ok) ok = build_ctx(h, h->gs, 128, 128) && build_ctx(h, h->gt, 128, 128);
+  if (ok) ok = build_ctx(h, h->gs, 128, 128, false) && build_ctx(h, h->gt, 128, 128, h->mode != MODE_F32);
   simt_init_attributes();
   if (h->mode != MODE_F32) tc_init_attributes();
   if (h->tc_kuf) tc_kuf_init_attributes();
@@ -410,59 +502,47 @@ svgp_status svgp_backward(svgp_handle* h, const svgp_params* p, const svgp_batch
                           const svgp_grads* gr) {
   if (!h) return SVGP_ERR_INVALID_ARG;
   if (!valid_params(p)) return fail(h, SVGP_ERR_INVALID_ARG, "params: null pointer");
-  if (!gr || !gr->dZ || !gr->dell || !gr->dsf2 || !gr->dnoise || !gr->dm || !gr->ds)
-    return fail(h, SVGP_ERR_INVALID_ARG, "grads: null pointer");
+  if (!valid_grads(gr)) return fail(h, SVGP_ERR_INVALID_ARG, "grads: null pointer");
   svgp_status s = validate_batch(h, b);
   if (s != SVGP_OK) return s;
-  cudaStream_t st = h->st;
-  const int M = h->M, Mp = h->Mp, W = 2 * h->D + 1;
-  const float c = (float)(b->N / b->B);
   prologue(h, p, b->X, b->B, p->L);
-  forward(h, p, b, true);
-  // backward, T fixed (Section 3.1)
-  k_kg(h->Zs, h->Xs, M, Mp, b->B, h->D, p->sf2, h->g, h->Kg, st);                      // Kuf g
-  if (h->mode == MODE_F32) k_gp_assemble(h->Kuu_f, h->Psi, h->Kg, p->m, h->w, p->noise, c, M, Mp, F(h->GP_lo), st);
-  else if (h->mode == MODE_BF16) k_gp_assemble(h->Kuu_f, h->Psi, h->Kg, p->m, h->w, p->noise, c, M, Mp, H(h->GP_lo), st);
-  else k_gp_assemble(h->Kuu_f, h->Psi, h->Kg, p->m, h->w, p->noise, c, M, Mp, SP(h, h->GP_lo), st);
-  run_vt(h, h->GP_lo, nullptr, nullptr); // X1t = L^T G_P
-  run_sym<2>(h, nullptr);                // S = L^T G_P L + I/2
-  run_ls(h);                             // Y = L S
-  run_gk(h, p->s, gr->ds);               // G_K~ = -Y L^T -> G_Kuu, ds
-  cudaMemsetAsync(h->rowacc_f, 0, sizeof(float) * Mp * W, st);
-  cudaMemsetAsync(h->rowacc_u, 0, sizeof(float) * Mp * W, st);
-  WEpi we{KufGen{h->Zs, h->Xs, h->D, M, b->B, p->sf2}, nullptr, nullptr, h->v, h->g, p->noise, c,
-          h->rowacc_f, nullptr};
-  const int nparts = run_w(h, we);                                                     // data part of dZ, dell, dsf2
-  k_kuu_bwd(h->GKuu, h->Kuu_f, h->Zs, M, Mp, h->D, h->rowacc_u, h->red, st);          // Kuu part
-  k_gemv(h->Pf, Mp, M, h->Kg, c, h->w, -1.0f / c, gr->dm, nullptr, nullptr, st);      // dm = P (c Kg - w)
-  k_grad_finalize(h->rowacc_f, h->rowacc_u, h->rowpart, nparts, Mp, p->ell, M, h->D, gr->dZ, h->acc_ell, h->red,
-                  st);
-  k_terms_finalize(h->red, h->acc_ell, p->sf2, p->noise, p->ell, M, h->D, b->B, b->N, terms_dev, gr->dsf2,
-                   gr->dnoise, gr->dell, h->errword, st);
+  backward_tail(h, p, b, terms_dev, gr);
   return check_launch(h, "svgp_backward");
 }
 
 svgp_status svgp_ng_update_T(svgp_handle* h, const svgp_params* p, float* L_inout, const float* gamma_dev,
                              int max_iters, double eps, int* iters_dev, double* residual_dev) {
   if (!h) return SVGP_ERR_INVALID_ARG;
-  if (!p || !p->Z || !p->ell || !p->sf2 || !p->s || !L_inout || !gamma_dev)
-    return fail(h, SVGP_ERR_INVALID_ARG, "ng_update_T: null pointer");
-  if (max_iters < 0 || max_iters > 100000) return fail(h, SVGP_ERR_INVALID_ARG, "ng_update_T: max_iters");
-  cudaStream_t st = h->st;
-  int* iters = iters_dev ? iters_dev : h->iters_tmp;
-  double* resid = residual_dev ? residual_dev : h->resid_tmp;
-  cudaMemsetAsync(h->done, 0, sizeof(int), st);
-  cudaMemsetAsync(iters, 0, sizeof(int), st);
+  if (!valid_ng_args(p, L_inout, gamma_dev, max_iters))
+    return fail(h, SVGP_ERR_INVALID_ARG, "ng_update_T: null pointer or max_iters out of [0, 100000]");
   prologue(h, p, nullptr, 0, L_inout);
-  for (int t = 0; t < max_iters; ++t) {
-    cudaMemsetAsync(h->red + RED_NG_RESID, 0, sizeof(double), st);
-    run_vt(h, h->Kuu_lo, p->s, h->done);         // Vt = L^T K~ (skipped once converged)
-    run_sym<0>(h, h->done);                      // A, Phi^T, ||A - I||^2
-    k_ng_check(h->red, h->M, eps, h->done, iters, resid, st);   // Eq. (8) stopping rule
-    run_lupd(h, L_inout, gamma_dev + t);         // L <- L - gamma L Phi  (Prop. 1)
-    if (t + 1 < max_iters) prep_L(h, L_inout, h->red + RED_COUNT - 1);
-  }
+  ng_loop(h, p, L_inout, gamma_dev, max_iters, eps, iters_dev ? iters_dev : h->iters_tmp,
+          residual_dev ? residual_dev : h->resid_tmp);
   return check_launch(h, "svgp_ng_update_T");
+}
+
+svgp_status svgp_train_step(svgp_handle* h, const svgp_params* p, const svgp_batch* b, float* L_inout,
+                            const float* gamma_dev, int max_iters, double eps, int* iters_dev, double* residual_dev,
+                            double* terms_dev, const svgp_grads* gr) {
+  if (!h) return SVGP_ERR_INVALID_ARG;
+  if (!valid_params(p) || !valid_ng_args(p, L_inout, gamma_dev, max_iters))
+    return fail(h, SVGP_ERR_INVALID_ARG, "train_step: null pointer or max_iters out of [0, 100000]");
+  if (!valid_grads(gr)) return fail(h, SVGP_ERR_INVALID_ARG, "grads: null pointer");
+  svgp_status s = validate_batch(h, b);
+  if (s != SVGP_OK) return s;
+  // one prologue (coordinates, Kuu, Kuf generator operands, L copies) serves both parts
+  prologue(h, p, b->X, b->B, L_inout);
+  ng_loop(h, p, L_inout, gamma_dev, max_iters, eps, iters_dev ? iters_dev : h->iters_tmp,
+          residual_dev ? residual_dev : h->resid_tmp);
+  if (max_iters > 0) {
+    // copies and log-determinant of the updated L
+    cudaMemsetAsync(h->red + RED_LOGDETL, 0, sizeof(double), h->st);
+    prep_L(h, L_inout, h->red + RED_LOGDETL);
+  }
+  svgp_params q = *p;
+  q.L = L_inout;
+  backward_tail(h, &q, b, terms_dev, gr);
+  return check_launch(h, "svgp_train_step");
 }
 
 svgp_status svgp_predict(svgp_handle* h, const svgp_params* p, const float* Xs, int Ns, float* mean, float* var,
@@ -473,7 +553,8 @@ svgp_status svgp_predict(svgp_handle* h, const svgp_params* p, const float* Xs, 
   cudaStream_t st = h->st;
   prologue(h, p, Xs, Ns, p->L);
   forward(h, p, nullptr, false);
-  k_mu(h->Zs, h->Xs, h->M, Ns, h->D, p->sf2, h->v, mean, st);
+  if (!(h->tc_kuf && tc_kuf_gemv(h->kt.XR, Ns, h->kt.ZK, h->M, h->v, mean, h->errword, st)))
+    k_mu(h->Zs, h->Xs, h->M, Ns, h->D, p->sf2, h->v, mean, st);
   cudaMemsetAsync(h->colsum, 0, sizeof(float) * Ns, st);
   WEpi we{KufGen{h->Zs, h->Xs, h->D, h->M, Ns, p->sf2}, nullptr, nullptr, nullptr, nullptr, nullptr, 0.f,
           nullptr, h->colsum};

@@ -119,7 +119,7 @@ extern "C" svgp_status svgp_predict_noalloc(const svgp_params* p, int M, int D, 
   // Same sequence as svgp_predict on an FP32 handle.
   k_prep_coords(p->Z, Xs, p->ell, M, Mp, Ns, D, Zs, Xsc, st);
   k_kuu(Zs, M, Mp, D, p->sf2, Kuu, (float*)nullptr, false, st);
-  k_prep_L(p->L, M, Mp, Lf, Llo, Lt, red, st);
+  k_prep_L(p->L, M, Mp, Lf, Llo, Lt, red + RED_LOGDETL, st);
   simt_gemm(g, TT_VT, Lt, Kuu, EpiVt<float*>{V, Mp, Lf, p->s, M, nullptr});
   simt_gemm(g, TT_SYM_IN, V, Lt, EpiSym<float*, 1>{S, Mp, M, red, nullptr});
   simt_gemm(g, TT_LS, Llo, S, EpiStore<float*>{Y, Mp, nullptr});

@@ -134,10 +134,20 @@ class RSVGP:
         C.svgp_adam_step(self.h, self.raw.data_ptr(), self.cons.data_ptr(), self.grad.data_ptr(),
                          self.m1.data_ptr(), self.m2.data_ptr(), self.step.data_ptr(), self.hyper.data_ptr())
 
+    def ng_backward(self, X, y, N, t_star=1, eps=0.0):
+        """NG update(s) of L given K~ (Prop. 1), then bound + gradient, in one
+        call (svgp_train_step: the preparation is shared by both parts)."""
+        self._sync_stream()
+        if t_star > self.gamma.numel():
+            raise ValueError("t_star larger than the gamma buffer")
+        C.svgp_train_step(self.h, self.params, self.batch(X, y, N), self.L.data_ptr(), self.gamma.data_ptr(),
+                          t_star, eps, self.iters.data_ptr(), self.resid.data_ptr(), self.terms.data_ptr(),
+                          self.grads)
+        return self.terms
+
     def train_step(self, X, y, N, t_star=1, eps=0.0):
         """NG update(s) of L given K~ (Prop. 1), then bound + gradient + Adam."""
-        self.ng_update(max_iters=t_star, eps=eps)
-        self.backward(X, y, N)
+        self.ng_backward(X, y, N, t_star=t_star, eps=eps)
         self.adam_step()
         return self.terms
 

@@ -241,3 +241,29 @@ def test_graph_captured_step_matches_eager():
     assert abs(float(a.terms[0]) - float(b.terms[0])) <= 1e-9 * abs(float(a.terms[0]))
     for m in ms:
         m.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_fused_train_step_matches_separate_calls(prec):
+    """svgp_train_step = svgp_ng_update_T followed by svgp_backward on the
+    updated L (two NG iterations, so the between-iteration copies and the
+    final log-determinant refresh are both exercised)."""
+    p, X, y, N = make_case("sinusoid_regression", "chol")
+    M, D = p["Z"].shape
+    B = X.shape[0]
+    a = _model(p, M, D, B, prec)
+    b = _model(p, M, D, B, prec)
+    Xd, yd = _dev(X), _dev(y)
+    for m in (a, b):
+        m.gamma[:2] = torch.tensor([0.7, 0.9], device=m.dev)
+    a.ng_update(max_iters=2)
+    ta = a.backward(Xd, yd, N).clone()
+    tb = b.ng_backward(Xd, yd, N, t_star=2).clone()
+    torch.cuda.synchronize()
+    assert int(a.iters.item()) == int(b.iters.item()) == 2
+    torch.testing.assert_close(a.L, b.L, rtol=0, atol=0)
+    np.testing.assert_allclose(tb.cpu().numpy(), ta.cpu().numpy(), rtol=2e-6, atol=1e-9)
+    np.testing.assert_allclose(b.grad.cpu().numpy(), a.grad.cpu().numpy(), rtol=1e-4,
+                               atol=1e-5 * float(a.grad.abs().max()))
+    a.close()
+    b.close()
