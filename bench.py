@@ -219,6 +219,17 @@ def reduce_timing(tot_ms, steps, ws):
     return tot_ms, ws * steps / (tot_ms / 1e3)
 
 
+# DRAM bytes (read + write) per launch of the kernels captured with
+# `ncu --set full` on the benchmark workload (cold caches); summaries with the
+# commands are in profiles/.  Keyed by (precision, contraction kind); a kernel
+# changed since its capture has no entry.
+NCU_DRAM_BYTES = {
+    ("bf16", "w"): 10455552,      # profiles/w_tc_kernel_M2048_B4096_bf16.md
+    ("bf16", "psi"): 817920,      # profiles/psi_tc_kernel_M2048_B4096_bf16.md
+    ("bf16", "vt"): 29666304,     # profiles/tc_gemm_EpiVt_M2048_bf16.md
+}
+
+
 def algorithmic_flops(M, B):
     """Algorithmic FLOPs of one launch of each contraction kind."""
     M3 = float(M) ** 3
@@ -333,7 +344,7 @@ def run_ours(args):
     e2e_wall = time.perf_counter() - t0
     e2e = {"value": ws * e2e_steps / e2e_wall, "unit": "steps/s",
            "h2d_bytes_per_step": int(B * D * 4 + B * 4), "d2h_bytes_per_step": 8,
-           "path": "eager svgp_ng_update_T + svgp_backward + svgp_adam_step via the ctypes binding"}
+           "path": "eager svgp_train_step (NG update + bound + backward) + svgp_adam_step via the ctypes binding"}
 
     ok_status = m.sync_status()
     line = {
@@ -371,7 +382,8 @@ def run_ours(args):
         step_share = {k: round(v / max(sum(tot.values()), 1e-9), 3) for k, v in tot.items()}
         line["roofline"] = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
                             "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": src,
-                            "traffic": None, "avg_launch_ms": avg_ms, "launches_per_step": n_l // reads,
+                            "traffic": NCU_DRAM_BYTES.get((prec, dom)), "traffic_unit": "bytes per launch (ncu)",
+                            "avg_launch_ms": avg_ms, "launches_per_step": n_l // reads,
                             "mma_passes_per_product": 3 if prec == "bf16x3" else 1,
                             "algorithmic_flops_per_launch": flops[dom], "contraction_share": step_share,
                             "contraction_ms_per_step": sum(tot.values()) / reads,
