@@ -30,12 +30,20 @@ sys.path.insert(0, ROOT)
 
 METRIC = "train steps/s at M=2048,B=4096: BF16-TC vs FP32 plain, bound rel err ≤1e-3"
 WORKLOAD = "gp_sample_regression"
+# other workloads (not the headline metric): the probit classification config
+WORKLOADS = {
+    "gp_sample_regression": dict(metric=METRIC, desc="gp_sample_regression M=2048 B=4096 D=16 N=1e6",
+                                 data="synthetic (GP sample via random Fourier features, D=16, seed 2)"),
+    "banana_like": dict(metric="probit train steps/s at M=256,B=2048,D=2 (config 4)",
+                        desc="banana_like M=256 B=2048 D=2 N=5e4, Bernoulli-probit, 20-point Gauss-Hermite",
+                        data="synthetic (two noisy crescents, labels {0,1}, seed 3)"),
+}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["bf16", "bf16x3", "fp32"])
@@ -45,6 +53,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--profile-step", action="store_true",
                     help="run two eager training steps (no timing) on an M x B case, for profilers")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS),
+                    help="banana_like: the probit classification configuration (not the headline metric)")
     ap.add_argument("--M", type=int, default=2048)
     ap.add_argument("--B", type=int, default=4096)
     return ap.parse_args()
@@ -94,12 +104,13 @@ def _blas_threads():
     return os.cpu_count() or 1
 
 
-def oracle_steps(max_seconds, max_steps):
+def oracle_steps(max_seconds, max_steps, workload=WORKLOAD):
     """Time full oracle training steps (NG + bound + gradient + Adam)."""
     import svgp_synth as S
     from oracle import rsvgp as O
 
-    prob = S.gp_sample_regression()
+    prob = S.WORKLOADS[workload]()
+    lik = prob.likelihood
     M, D = prob.M, prob.D
     p = dict(Z=prob.Z0.copy(), ell=np.ones(D), sf2=1.0, noise=1.0, m=np.zeros(M),
              s=np.full(M, 1e-4), L=1e-3 * np.eye(M))
@@ -116,8 +127,8 @@ def oracle_steps(max_seconds, max_steps):
         Kt = O.se_ard(c["Z"], c["Z"], c["ell"], c["sf2"]) + np.diag(c["s"])
         L, _ = O.ng_step(L, Kt, 1.0)
         c["L"] = L
-        g = O.grads(c, X, y, prob.N)
-        O.bound(c, X, y, prob.N)
+        g = O.grads(c, X, y, prob.N, likelihood=lik)
+        O.bound(c, X, y, prob.N, likelihood=lik)
         raw = O.adam_update(raw, g, state, 5e-3)
         times.append(time.perf_counter() - t0)
         if time.perf_counter() - t_start > max_seconds:
@@ -125,12 +136,12 @@ def oracle_steps(max_seconds, max_steps):
     return times
 
 
-def cpu_baseline(seconds):
-    times = oracle_steps(seconds, 1000)
+def cpu_baseline(seconds, workload=WORKLOAD):
+    times = oracle_steps(seconds, 1000, workload)
     per = statistics.mean(times)
     return {"value": 1.0 / per, "unit": "steps/s", "cores": _blas_threads(), "kind": "oracle",
             "sample": f"{len(times)} full FP64 NumPy oracle training steps (NG + bound + gradient + Adam) "
-                      f"at M=2048, B=4096, D=16 on the host cores ({per:.2f} s/step)"}
+                      f"of {WORKLOADS[workload]['desc']} on the host cores ({per:.2f} s/step)"}
 
 
 def run_reference(args):
@@ -138,17 +149,20 @@ def run_reference(args):
     if rank != 0:
         return
     budget = 150.0
-    times = oracle_steps(budget, args.warmup + args.steps)
+    times = oracle_steps(budget, args.warmup + args.steps, args.workload)
+    wl = WORKLOADS[args.workload]
+    import svgp_synth as S
+    prob = S.WORKLOADS[args.workload]()
     timed = times[min(args.warmup, max(len(times) - 1, 0)):]
     per = statistics.mean(timed)
     value = 1.0 / per
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
+        "impl": "reference", "metric": wl["metric"], "value": value, "unit": "steps/s", "n_gpus": args.gpus,
         "steps": len(timed), "warmup": min(args.warmup, len(times) - len(timed)), "ms_per_step": per * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (GP sample via random Fourier features, seed 2)",
-        "config": {"workload": "gp_sample_regression M=2048 B=4096 D=16 N=1e6", "M": 2048, "B": 4096, "D": 16,
-                   "N": 1e6, "l2": "oracle on host"},
+        "data": wl["data"],
+        "config": {"workload": wl["desc"], "M": prob.M, "B": prob.B, "D": prob.D, "N": prob.N,
+                   "l2": "oracle on host"},
         "cpu_baseline": {"value": value, "unit": "steps/s", "cores": _blas_threads(), "kind": "oracle",
                          "sample": f"{len(timed)} of the requested {args.steps} oracle steps (bounded to "
                                    f"{budget:.0f} s of CPU work)"},
@@ -221,12 +235,12 @@ def reduce_timing(tot_ms, steps, ws):
 
 # DRAM bytes (read + write) per launch of the kernels captured with
 # `ncu --set full` on the benchmark workload (cold caches); summaries with the
-# commands are in profiles/.  Keyed by (precision, contraction kind); a kernel
-# changed since its capture has no entry.
+# commands are in profiles/.  Keyed by (workload, precision, contraction
+# kind); a kernel changed since its capture has no entry.
 NCU_DRAM_BYTES = {
-    ("bf16", "w"): 10455552,      # profiles/w_tc_kernel_M2048_B4096_bf16.md
-    ("bf16", "psi"): 817920,      # profiles/psi_tc_kernel_M2048_B4096_bf16.md
-    ("bf16", "vt"): 29666304,     # profiles/tc_gemm_EpiVt_M2048_bf16.md
+    ("gp_sample_regression", "bf16", "w"): 10455552,      # profiles/w_tc_kernel_M2048_B4096_bf16.md
+    ("gp_sample_regression", "bf16", "psi"): 817920,      # profiles/psi_tc_kernel_M2048_B4096_bf16.md
+    ("gp_sample_regression", "bf16", "vt"): 29666304,     # profiles/tc_gemm_EpiVt_M2048_bf16.md
 }
 
 
@@ -250,14 +264,16 @@ def run_ours(args):
     from paper_2604_00697_gb300.model import RSVGP
     import svgp_synth as S
 
-    prob = S.gp_sample_regression()
+    prob = S.WORKLOADS[args.workload]()
     M, D, B, N = prob.M, prob.D, prob.B, prob.N
+    lik = prob.likelihood
+    wl = WORKLOADS[args.workload]
     prec = args.prec
     if prec == "bf16" and not _lib.svgp_has_tensor_cores():
         raise SystemExit("tensor-core path unavailable on this device")
 
     def new_model(pr):
-        m = RSVGP(M, D, B, prec=pr)
+        m = RSVGP(M, D, B, prec=pr, likelihood=lik)
         m.set_state(prob.Z0, np.ones(D), 1.0, 1.0, np.zeros(M), np.full(M, 1e-4), 1e-3 * np.eye(M))
         return m
 
@@ -348,11 +364,11 @@ def run_ours(args):
 
     ok_status = m.sync_status()
     line = {
-        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
+        "metric": wl["metric"], "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "bf16", "e2e": e2e,
-        "data": "synthetic (GP sample via random Fourier features, D=16, seed 2)",
-        "config": {"workload": "gp_sample_regression M=2048 B=4096 D=16 N=1e6", "M": M, "B": B, "D": D, "N": N,
+        "data": wl["data"],
+        "config": {"workload": wl["desc"], "M": M, "B": B, "D": D, "N": N,
                    "t_star": 1, "gamma": 1.0, "precision": prec, "graph": True,
                    "l2": "flushed between timed steps (256 MB write outside the step events)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
@@ -382,7 +398,7 @@ def run_ours(args):
         step_share = {k: round(v / max(sum(tot.values()), 1e-9), 3) for k, v in tot.items()}
         line["roofline"] = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
                             "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": src,
-                            "traffic": NCU_DRAM_BYTES.get((prec, dom)), "traffic_unit": "bytes per launch (ncu)",
+                            "traffic": NCU_DRAM_BYTES.get((args.workload, prec, dom)), "traffic_unit": "bytes per launch (ncu)",
                             "avg_launch_ms": avg_ms, "launches_per_step": n_l // reads,
                             "mma_passes_per_product": 3 if prec == "bf16x3" else 1,
                             "algorithmic_flops_per_launch": flops[dom], "contraction_share": step_share,
@@ -400,7 +416,7 @@ def run_ours(args):
     if not args.no_validate and rank == 0 and ws == 1:
         line["validity"] = validate(prec, prob)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, args.workload)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -421,7 +437,7 @@ def validate(prec, prob):
     out = {}
     p = dict(Z=f32(prob.Z0), ell=np.ones(D), sf2=1.0, noise=1.0, m=np.zeros(M), s=f32(np.full(M, 1e-4)),
              L=f32(1e-3 * np.eye(M)))
-    m = RSVGP(M, D, prob.B, prec=prec)
+    m = RSVGP(M, D, prob.B, prec=prec, likelihood=prob.likelihood)
     for name in ("init", "ng40"):
         m.set_state(p["Z"], p["ell"], p["sf2"], p["noise"], p["m"], p["s"], p["L"])
         if name == "ng40":
@@ -430,7 +446,7 @@ def validate(prec, prob):
             m.set_state(p["Z"], p["ell"], p["sf2"], p["noise"], p["m"], p["s"], p["L"])
         F = float(m.bound(torch.tensor(X, dtype=torch.float32, device="cuda"),
                           torch.tensor(y, dtype=torch.float32, device="cuda"), prob.N)[0])
-        ref = O.bound(p, X, y, prob.N)["F"]
+        ref = O.bound(p, X, y, prob.N, likelihood=prob.likelihood)["F"]
         out[name] = abs(F - ref) / abs(ref)
     m.close()
     out["tolerance"] = 1e-6 if prec == "fp32" else 1e-3

@@ -47,6 +47,11 @@ typedef enum {
   SVGP_ERR_UNSUPPORTED = 7    /* option not built for this device / precision   */
 } svgp_status;
 
+/* Likelihood of the data term.  SVGP_LIK_GAUSSIAN: p(y | f) = N(y; f, noise),
+ * its expectation in closed form (Appendix S3).  SVGP_LIK_BERNOULLI_PROBIT:
+ * binary labels y in {0, 1}, p(y | f) = Phi((2y - 1) f) (the classification
+ * experiments of Section 4.1), its expectation under N(mu_n, sigma_n^2) by a
+ * gh_points-node Gauss-Hermite rule (svgp_gauss_hermite). */
 typedef enum { SVGP_LIK_GAUSSIAN = 0, SVGP_LIK_BERNOULLI_PROBIT = 1 } svgp_lik;
 
 /* Arithmetic of the dense contractions.  SVGP_FP32: FP32 SIMT FMA kernels
@@ -63,13 +68,19 @@ typedef struct {
   int M;              /* number of inducing points, 1 <= M <= 8192              */
   int D;              /* input dimension, 1 <= D <= 32                          */
   int B_max;          /* largest minibatch / prediction block, >= 1             */
-  int lik;            /* svgp_lik; only SVGP_LIK_GAUSSIAN is built              */
+  int lik;            /* svgp_lik                                               */
   int prec;           /* svgp_prec                                              */
   void* cuda_stream;  /* cudaStream_t to run on; NULL = legacy default stream   */
+  int gh_points;      /* probit: nodes of the Gauss-Hermite rule, 1..32; 0 = 20 */
+  int unpreconditioned; /* 0: the preconditioned bound of Eq. (7), m = Kuu P m~
+                           (Section 3.2); 1: R-SVGP without the preconditioner,
+                           m = Kuu m~ (Section 2): mu_n = k_nu m~ and the KL
+                           term m~^T Kuu m~, everything else unchanged       */
 } svgp_config;
 
 /* Model state.  ell: D lengthscales; sf2: signal variance (1 float); noise:
- * Gaussian observation variance (1 float); m: preconditioned variational
+ * Gaussian observation variance (1 float; read only by the Gaussian
+ * likelihood, may be NULL for probit); m: preconditioned variational
  * mean m~ (M); s: diagonal of S~ (M, all > 0); L: factor of T (M x M). */
 typedef struct {
   const float* Z;
@@ -81,8 +92,9 @@ typedef struct {
   const float* L;
 } svgp_params;
 
-/* Minibatch: X (B x D), y (B).  N is the dataset size; the data term is
- * scaled by N / B (stochastic SVGP).  1 <= B <= B_max. */
+/* Minibatch: X (B x D), y (B; labels 0 or 1 for probit: y > 0.5 is class 1).
+ * N is the dataset size; the data term is scaled by N / B (stochastic SVGP).
+ * 1 <= B <= B_max. */
 typedef struct {
   const float* X;
   const float* y;
@@ -109,10 +121,12 @@ enum {
   SVGP_T_TRPKUU = 4,   /* tr(P Kuu)                                            */
   SVGP_T_QUAD = 5,     /* m~^T P Kuu P m~                                      */
   SVGP_T_LOGDETT = 6,  /* log|T| = 2 sum_i log|L_ii|                           */
-  SVGP_T_SQERR = 7,    /* sum_n (y_n - mu_n)^2                                 */
-  SVGP_T_SUMVAR = 8,   /* sum_n sigma_n^2                                      */
+  SVGP_T_SQERR = 7,    /* sum_n (y_n - mu_n)^2 (Gaussian; 0 for probit)        */
+  SVGP_T_SUMVAR = 8,   /* sum_n sigma_n^2 (probit: after clamping at 0)        */
   SVGP_T_LOGDETS = 9,  /* sum_i log s~_i                                       */
-  SVGP_NTERMS = 10
+  SVGP_T_NCLAMP = 10,  /* probit: points whose sigma_n^2 rounded below 0 and
+                          was clamped to 0 (0 for Gaussian)                    */
+  SVGP_NTERMS = 11
 };
 
 /* Create a handle and its workspace.  On success *out owns device memory of
@@ -123,16 +137,25 @@ void svgp_destroy(svgp_handle* h);
 /* Change the stream later calls are issued on (e.g. a graph-capture stream). */
 svgp_status svgp_set_stream(svgp_handle* h, void* cuda_stream);
 
-/* Bound, Eq. (7) (preconditioned R-SVGP), Gaussian likelihood.
+/* Bound, Eq. (7) (preconditioned R-SVGP), with the handle's likelihood.
  *   mu_n = k_nu P m~, sigma_n^2 = k_nn - k_nu P k_un, P = 2T - T K~ T,
- *   KL <= 1/2(-tr(P Kuu) + tr(K~T) - M + m~^T P Kuu P m~ - log|T| - log|S~|).
+ *   KL <= 1/2(-tr(P Kuu) + tr(K~T) - M + m~^T P Kuu P m~ - log|T| - log|S~|),
+ *   F = (N/B) sum_n E_n - KL.
+ * Gaussian: E_n in closed form, sum_n sigma_n^2 = B sf2 - <P, Kuf Kuf^T>.
+ * Probit: sigma_n^2 per point (clamped at 0), s_n = 2 y_n - 1 and
+ *   E_n = sum_k w_k / sqrt(pi) log Phi(s_n (mu_n + sqrt(2) sigma_n t_k))
+ * over the nodes t_k and weights w_k of the rule for exp(-t^2).
  * terms_dev: device float64[SVGP_NTERMS] (layout above). */
 svgp_status svgp_bound(svgp_handle* h, const svgp_params* p, const svgp_batch* b,
                        double* terms_dev);
 
 /* Bound (as svgp_bound) plus its gradient w.r.t. Z, ell, sf2, noise, m~, s~
  * with T held fixed (Section 3.1: T is optimised separately by NG; Prop. 2
- * concerns exactly this gradient).  terms_dev may be NULL. */
+ * concerns exactly this gradient).  terms_dev may be NULL.  Probit: the
+ * per-point derivatives g_n = dE_n/dmu_n and h_n = dE_n/dsigma_n^2 are those
+ * of the quadrature rule itself (h_n from the rule's derivative in sigma_n;
+ * below sigma_n = 1e-6 from 1/2 sum_k w_k / sqrt(pi) d^2/df^2 log Phi, its
+ * limit); dnoise is 0 (the bound does not depend on noise). */
 svgp_status svgp_backward(svgp_handle* h, const svgp_params* p, const svgp_batch* b,
                           double* terms_dev, const svgp_grads* g);
 
@@ -150,6 +173,28 @@ svgp_status svgp_backward(svgp_handle* h, const svgp_params* p, const svgp_batch
 svgp_status svgp_ng_update_T(svgp_handle* h, const svgp_params* p, float* L_inout,
                              const float* gamma_dev, int max_iters, double eps,
                              int* iters_dev, double* residual_dev);
+
+/* Gap of Prop. 3 (Section 3.3, Gaussian likelihood) for the batch b at
+ * T = p->L p->L^T: with K~ = K~_- + sigma2 I (K~_- = Kuu + S~', S~' diagonal
+ * and PD) the R-SVGP variance U_n and the lower bound L_n of the L-SVGP
+ * variance differ by G_n = ||(I - K~ T) k_un||^2 / sigma2; writes
+ * G = sum_n G_n to gap_dev (device double).  sigma2 <= 0 selects
+ * sigma2 = min_i s~_i.  Computed as <N N^T, Kuf Kuf^T> / sigma2 with
+ * N = I - T K~ by FP32 SIMT products (about 5 M^3 flops; Psi = Kuf Kuf^T in
+ * the handle's precision). */
+svgp_status svgp_variance_gap(svgp_handle* h, const svgp_params* p, const svgp_batch* b, double sigma2,
+                              double* gap_dev);
+
+/* svgp_ng_update_T with the gap stopping rule of Section 3.3 instead of the
+ * Frobenius residual: for t = 0 .. max_iters-1, G_t = G(L_t) as in
+ * svgp_variance_gap; if eps > 0 and G_t <= 2 noise eps: stop without
+ * updating; else L <- NG step with gamma_dev[t] (Prop. 1).  iters_dev
+ * (device int, may be NULL) receives the number of updates; gap_dev (device
+ * double, may be NULL) the gap of the returned L.  Gaussian likelihood only
+ * (SVGP_ERR_UNSUPPORTED otherwise). */
+svgp_status svgp_ng_update_T_gap(svgp_handle* h, const svgp_params* p, const svgp_batch* b, float* L_inout,
+                                 const float* gamma_dev, int max_iters, double eps, double sigma2,
+                                 int* iters_dev, double* gap_dev);
 
 /* One training step's device work in a single call: svgp_ng_update_T on
  * L_inout (same arguments and semantics), then svgp_backward with L = the
@@ -183,6 +228,14 @@ svgp_status svgp_predict(svgp_handle* h, const svgp_params* p, const float* Xs, 
 svgp_status svgp_adam_step(svgp_handle* h, float* raw, float* constrained, const float* grad,
                            float* m1, float* m2, int* step_dev, const float* hyper_dev,
                            const float* zbeta1_dev);
+
+/* Gauss-Hermite rule for the weight exp(-t^2) with n nodes, 1 <= n <= 64:
+ * integral of exp(-t^2) f(t) dt ~= sum_k weights[k] f(nodes[k]).  Host
+ * function (host arrays of n doubles; no GPU needed), ascending nodes.
+ * Computed by Newton's method on the orthonormal Hermite recurrence after
+ * bracketing every sign change; weights 1 / (n q_{n-1}(t_k)^2) with q_j the
+ * orthonormal polynomials.  Returns SVGP_OK or SVGP_ERR_INVALID_ARG. */
+svgp_status svgp_gauss_hermite(int n, double* nodes, double* weights);
 
 /* Number of floats in the flat parameter vector for this handle. */
 int svgp_param_count(const svgp_handle* h);

@@ -15,6 +15,10 @@ Everything here is plain NumPy in float64, written as the paper states it:
   KL upper bound, Eq. (7) (preconditioned R-SVGP bound).
 * Gaussian expected log-likelihood (Appendix S3, closed form), summed over a
   minibatch and scaled by N/B (stochastic SVGP, Section 1 / Eq. (1)).
+* Bernoulli likelihood with probit link (the classification experiments of
+  Section 4.1; GPflow's Bernoulli, Appendix S5.3): expected log-likelihood
+  by 20-point Gauss-Hermite quadrature, and its derivatives with respect to
+  the predictive mean and variance taken from the same quadrature rule.
 * Natural-gradient step on L, Prop. 1 / Eq. (6), with the Frobenius stopping
   residual of Eq. (8), taken in the order of Section 3.1 ("Alternating
   Optimisation") and Section 3.3.
@@ -41,9 +45,12 @@ __all__ = [
     "preconditioner",
     "bound",
     "grads",
+    "probit_terms",
     "ng_residual",
     "ng_step",
     "ng_solve",
+    "variance_gap",
+    "ng_solve_gap",
     "gamma_schedule",
     "predict",
     "softplus",
@@ -97,7 +104,7 @@ def _gauss_expected_loglik(y, mu, var, noise):
     return -0.5 * np.log(2 * math.pi * noise) - ((y - mu) ** 2 + var) / (2 * noise)
 
 
-def bound(p, X, y, N=None, likelihood="gaussian"):
+def bound(p, X, y, N=None, likelihood="gaussian", precond=True):
     """Preconditioned R-SVGP bound, Eq. (7), on one minibatch.
 
     F = (N/B) sum_n E_{N(mu_n, sigma_n^2)}[log p(y_n | f_n)] - KL_R with
@@ -109,6 +116,11 @@ def bound(p, X, y, N=None, likelihood="gaussian"):
 
     Returns a dict holding F and its terms.  ``N`` defaults to the batch size
     (full-batch ELBO, Eq. (1)).
+
+    ``precond=False`` gives the R-SVGP bound without the mean preconditioner
+    (Section 2, inverse-free parameterisation, with m = Kuu m~): mu_n =
+    k_nu m~ and the quadratic KL term m~^T Kuu m~ (the KL bound of Section 2);
+    sigma_n^2 and the trace terms are unchanged.
     """
     X = np.asarray(X, np.float64)
     y = np.asarray(y, np.float64)
@@ -119,8 +131,8 @@ def bound(p, X, y, N=None, likelihood="gaussian"):
     Kuu, Kuf, knn, Kt = kernel_blocks(p, X)
     T, P = preconditioner(L, Kt)
     # per-point moments (Eq. (7), first line)
-    mu = np.array([Kuf[:, n] @ P @ p["m"] for n in range(B)]) if B <= 64 else \
-        Kuf.T @ (P @ p["m"])
+    Pm = P @ p["m"] if precond else np.asarray(p["m"], np.float64)
+    mu = np.array([Kuf[:, n] @ Pm for n in range(B)]) if B <= 64 else Kuf.T @ Pm
     if B <= 64:
         var = np.array([knn[n] - Kuf[:, n] @ P @ Kuf[:, n] for n in range(B)])
     else:
@@ -135,7 +147,7 @@ def bound(p, X, y, N=None, likelihood="gaussian"):
     # KL upper bound (Eq. (7), second and third lines); each trace as a product
     tr_PKuu = np.trace(P @ Kuu)
     tr_KtT = np.trace(Kt @ T)
-    quad = p["m"] @ P @ Kuu @ P @ p["m"]
+    quad = Pm @ Kuu @ Pm
     sign, logdetT = np.linalg.slogdet(T)
     logdetS = np.sum(np.log(p["s"]))
     KL = 0.5 * (-tr_PKuu + tr_KtT - M + quad - logdetT - logdetS)
@@ -149,17 +161,43 @@ def probit_expected_loglik(y, mu, var, n_gh=20):
     Bernoulli likelihood with probit link (GPflow's Bernoulli, Appendix S5.3);
     20 nodes from numpy's hermgauss.  log Phi via scipy's log_ndtr.
     """
+    return probit_terms(y, mu, var, n_gh)[0]
+
+
+def probit_terms(y, mu, var, n_gh=20):
+    """Per-point probit terms (E_n, g_n, h_n) of the quadrature rule.
+
+    With nodes t_k and weights w_k of the rule for exp(-t^2) (numpy's
+    hermgauss), s_n = 2 y_n - 1, sd_n = sqrt(max(var_n, 0)) and
+    f_nk = mu_n + sqrt(2) sd_n t_k:
+
+      E_n = sum_k w_k / sqrt(pi) log Phi(s_n f_nk)
+      g_n = dE_n / dmu_n      = sum_k w_k / sqrt(pi) s_n r(s_n f_nk)
+      h_n = dE_n / dsigma_n^2 = sum_k w_k / sqrt(pi) s_n r(s_n f_nk) t_k / (sqrt(2) sd_n)
+
+    where r = phi / Phi is the inverse Mills ratio (the derivative of
+    log Phi).  h_n is the derivative of the rule itself, so it is what finite
+    differences of ``bound(..., likelihood="probit")`` give.
+    """
     from scipy.special import log_ndtr
 
     t, w = np.polynomial.hermite.hermgauss(n_gh)
-    s = 2.0 * np.asarray(y) - 1.0
-    sd = np.sqrt(np.maximum(var, 0.0))
+    s = 2.0 * np.asarray(y, np.float64) - 1.0
+    mu = np.asarray(mu, np.float64)
+    sd = np.sqrt(np.maximum(np.asarray(var, np.float64), 0.0))
     f = mu[:, None] + math.sqrt(2.0) * sd[:, None] * t[None, :]
-    return (w[None, :] / math.sqrt(math.pi) * log_ndtr(s[:, None] * f)).sum(axis=1)
+    a = s[:, None] * f
+    logPhi = log_ndtr(a)
+    r = np.exp(-0.5 * a * a - 0.5 * math.log(2.0 * math.pi) - logPhi)
+    wk = w[None, :] / math.sqrt(math.pi)
+    En = (wk * logPhi).sum(axis=1)
+    g = (wk * s[:, None] * r).sum(axis=1)
+    h = (wk * s[:, None] * r * t[None, :]).sum(axis=1) / (math.sqrt(2.0) * sd)
+    return En, g, h
 
 
-def grads(p, X, y, N=None):
-    """Gradient of the Gaussian-likelihood bound of Eq. (7) with T held fixed.
+def grads(p, X, y, N=None, likelihood="gaussian", precond=True):
+    """Gradient of the bound of Eq. (7) with T held fixed.
 
     T is a separate variational parameter optimised by natural gradients
     (Section 3.1, alternating optimisation), so the Adam step on
@@ -176,6 +214,13 @@ def grads(p, X, y, N=None):
       ds~   = diag(G_K~) + 1/(2 s~)
       dm~   = c P Kuf g - P w
       then the SE-ARD chain rule for Z, ell, sf2.
+
+    Without the preconditioner (``precond=False``: mu = Kuf^T m~, quadratic
+    term m~^T Kuu m~) v = m~, the m~ terms leave G_P and dm~ = c Kuf g - Kuu m~.
+
+    Gaussian likelihood: g_n = (y_n - mu_n) / noise, h_n = -1 / (2 noise).
+    Probit (``likelihood="probit"``): g_n, h_n from ``probit_terms``; the
+    bound does not depend on the noise variance, whose gradient is 0.
     """
     X = np.asarray(X, np.float64)
     y = np.asarray(y, np.float64)
@@ -186,21 +231,29 @@ def grads(p, X, y, N=None):
     m, s, L = p["m"], p["s"], p["L"]
     Kuu, Kuf, knn, Kt = kernel_blocks(p, X)
     T, P = preconditioner(L, Kt)
-    v = P @ m
+    v = P @ m if precond else np.asarray(m, np.float64)
     w = Kuu @ v
     mu = Kuf.T @ v
     var = knn - np.einsum("in,in->n", Kuf, P @ Kuf)
-    g = (y - mu) / noise
-    h = np.full(B, -0.5 / noise)
+    if likelihood == "gaussian":
+        g = (y - mu) / noise
+        h = np.full(B, -0.5 / noise)
+    elif likelihood == "probit":
+        _, g, h = probit_terms(y, mu, var)
+    else:
+        raise ValueError(likelihood)
     Kg = Kuf @ g
     G_Kuf = c * (np.outer(v, g) - 2.0 * (P @ Kuf) * h[None, :])
-    G_P = c * (np.outer(Kg, m) - (Kuf * h[None, :]) @ Kuf.T) \
-        - 0.5 * (-Kuu + np.outer(m, w) + np.outer(w, m))
+    if precond:
+        G_P = c * (np.outer(Kg, m) - (Kuf * h[None, :]) @ Kuf.T) \
+            - 0.5 * (-Kuu + np.outer(m, w) + np.outer(w, m))
+    else:
+        G_P = -c * (Kuf * h[None, :]) @ Kuf.T + 0.5 * Kuu
     G_Psym = 0.5 * (G_P + G_P.T)
     G_Kt = -T @ G_Psym @ T - 0.5 * T
     G_Kuu = G_Kt + 0.5 * P - 0.5 * np.outer(v, v)
     ds = np.diag(G_Kt) + 0.5 / s
-    dm = c * (P @ Kg) - P @ w
+    dm = c * (P @ Kg) - P @ w if precond else c * Kg - w
     # SE-ARD chain rule
     A_f = G_Kuf * Kuf                      # M x B
     A_u = G_Kuu * Kuu                      # M x M (symmetric)
@@ -212,8 +265,11 @@ def grads(p, X, y, N=None):
         dZ[:, d] = (A_f * df).sum(1) / ell[d] ** 2 + 2.0 * (A_u * du).sum(1) / ell[d] ** 2
         dell[d] = ((A_f * df * df).sum() + (A_u * du * du).sum()) / ell[d] ** 3
     dsf2 = c * h.sum() + (A_f.sum() + A_u.sum()) / sf2
-    Q = (y - mu) ** 2 + var
-    dnoise = c * np.sum(-0.5 / noise + Q / (2 * noise ** 2))
+    if likelihood == "gaussian":
+        Q = (y - mu) ** 2 + var
+        dnoise = c * np.sum(-0.5 / noise + Q / (2 * noise ** 2))
+    else:
+        dnoise = 0.0
     return dict(Z=dZ, ell=dell, sf2=dsf2, noise=dnoise, m=dm, s=ds)
 
 
@@ -256,6 +312,47 @@ def ng_solve(L, Kt, gammas, eps=0.0, max_iters=None):
             return L, it, r
         L, _ = ng_step(L, Kt, gammas[it])
     return L, max_iters, r
+
+
+def variance_gap(p, X, sigma2=None):
+    """Per-point gap G_n = U_n - L_n of Prop. 3 (Section 3.3).
+
+    With the split S~ = S~' + sigma^2 I (S~' diagonal, sigma2 defaults to
+    min_i s~_i), U_n is the R-SVGP predictive variance and L_n the lower
+    bound of Prop. 3 on the L-SVGP variance; their difference is
+      G_n = ||(I - K~ T) k_un||^2 / sigma^2.
+    The Gaussian stopping rule stops the NG iterations once
+    sum_n G_n <= 2 noise eps.
+    """
+    Kuu, Kuf, knn, Kt = kernel_blocks(p, np.asarray(X, np.float64))
+    L = np.asarray(p["L"], np.float64)
+    T = L @ L.T
+    if sigma2 is None:
+        sigma2 = float(np.min(p["s"]))
+    R = Kuf - Kt @ (T @ Kuf)
+    return (R * R).sum(axis=0) / sigma2
+
+
+def ng_solve_gap(p, X, gammas, eps, sigma2=None, max_iters=None):
+    """NG steps on p["L"] with the Prop. 3 gap stopping rule of Section 3.3.
+
+    For t = 0, 1, ...: G_t = sum_n G_n(L_t); stop (without updating) when
+    G_t <= 2 noise eps; otherwise L_{t+1} = NG step with gamma_t.  Returns
+    (L, number of updates applied, last gap computed).
+    """
+    q = dict(p)
+    Kt = kernel_blocks(q, np.asarray(X, np.float64))[3]
+    gammas = list(gammas)
+    max_iters = len(gammas) if max_iters is None else max_iters
+    L = np.asarray(q["L"], np.float64)
+    G = float("nan")
+    for it in range(max_iters):
+        q["L"] = L
+        G = float(variance_gap(q, X, sigma2).sum())
+        if G <= 2.0 * float(q["noise"]) * eps:
+            return L, it, G
+        L, _ = ng_step(L, Kt, gammas[it])
+    return L, max_iters, G
 
 
 def gamma_schedule(t, gamma0=1e-5, gammaT=1.0, ramp=10):

@@ -28,19 +28,20 @@ SVGP_FP32 = 0
 SVGP_BF16 = 1
 SVGP_BF16X3 = 2
 
-TERMS = ["F", "E", "KL", "trKT", "trPKuu", "quad", "logdetT", "sqerr", "sumvar", "logdetS"]
+TERMS = ["F", "E", "KL", "trKT", "trPKuu", "quad", "logdetT", "sqerr", "sumvar", "logdetS", "nclamp"]
 SVGP_NTERMS = len(TERMS)
 
 EXPORTED = [
     "svgp_create", "svgp_destroy", "svgp_set_stream", "svgp_bound", "svgp_backward",
     "svgp_ng_update_T", "svgp_train_step", "svgp_predict", "svgp_adam_step", "svgp_param_count",
     "svgp_sync_status", "svgp_last_error", "svgp_status_string", "svgp_has_tensor_cores",
+    "svgp_gauss_hermite", "svgp_variance_gap", "svgp_ng_update_T_gap",
 ]
 
 
 class svgp_config(ctypes.Structure):
     _fields_ = [("M", c_int), ("D", c_int), ("B_max", c_int), ("lik", c_int), ("prec", c_int),
-                ("cuda_stream", c_void_p)]
+                ("cuda_stream", c_void_p), ("gh_points", c_int), ("unpreconditioned", c_int)]
 
 
 class svgp_params(ctypes.Structure):
@@ -96,8 +97,14 @@ def load(path: str = LIB_PATH):
     lib.svgp_status_string.restype = c_char_p
     lib.svgp_has_tensor_cores.argtypes = []
     lib.svgp_has_tensor_cores.restype = c_int
+    lib.svgp_gauss_hermite.argtypes = [c_int, POINTER(c_double), POINTER(c_double)]
+    lib.svgp_variance_gap.argtypes = [H, POINTER(svgp_params), POINTER(svgp_batch), c_double, c_void_p]
+    lib.svgp_ng_update_T_gap.argtypes = [H, POINTER(svgp_params), POINTER(svgp_batch), c_void_p, c_void_p, c_int,
+                                         c_double, c_double, c_void_p, c_void_p]
+    lib.svgp_gauss_hermite.restype = c_int
     for name in ("svgp_create", "svgp_set_stream", "svgp_bound", "svgp_backward", "svgp_ng_update_T",
-                 "svgp_train_step", "svgp_predict", "svgp_adam_step", "svgp_sync_status"):
+                 "svgp_train_step", "svgp_predict", "svgp_adam_step", "svgp_sync_status", "svgp_variance_gap",
+                 "svgp_ng_update_T_gap"):
         getattr(lib, name).restype = c_int
     _lib = lib
     return lib
@@ -110,14 +117,24 @@ def _check(h, status):
         raise SvgpError(status, msg or lib.svgp_status_string(status).decode())
 
 
-def svgp_create(M, D, B_max, prec=SVGP_BF16, lik=SVGP_LIK_GAUSSIAN, cuda_stream=None):
+def svgp_create(M, D, B_max, prec=SVGP_BF16, lik=SVGP_LIK_GAUSSIAN, cuda_stream=None, gh_points=0,
+                unpreconditioned=False):
     lib = load()
-    cfg = svgp_config(M, D, B_max, lik, prec, cuda_stream)
+    cfg = svgp_config(M, D, B_max, lik, prec, cuda_stream, gh_points, int(bool(unpreconditioned)))
     h = c_void_p()
     st = lib.svgp_create(byref(cfg), byref(h))
     if st != SVGP_OK:
         raise SvgpError(st, lib.svgp_status_string(st).decode())
     return h
+
+
+def svgp_gauss_hermite(n):
+    """Nodes and weights (lists of n floats) of the Gauss-Hermite rule for exp(-t^2)."""
+    t, w = (c_double * max(n, 1))(), (c_double * max(n, 1))()
+    st = load().svgp_gauss_hermite(n, t, w)
+    if st != SVGP_OK:
+        raise SvgpError(st, "svgp_gauss_hermite: n out of [1, 64]")
+    return list(t), list(w)
 
 
 def svgp_destroy(h):
@@ -145,6 +162,16 @@ def svgp_train_step(h, params, batch, L_ptr, gamma_ptr, max_iters, eps, iters_pt
     _check(h, load().svgp_train_step(h, byref(params), byref(batch), c_void_p(L_ptr), c_void_p(gamma_ptr),
                                      max_iters, c_double(eps), c_void_p(iters_ptr), c_void_p(resid_ptr),
                                      c_void_p(terms_ptr), byref(grads)))
+
+
+def svgp_variance_gap(h, params, batch, sigma2, gap_ptr):
+    _check(h, load().svgp_variance_gap(h, byref(params), byref(batch), c_double(sigma2), c_void_p(gap_ptr)))
+
+
+def svgp_ng_update_T_gap(h, params, batch, L_ptr, gamma_ptr, max_iters, eps, sigma2, iters_ptr, gap_ptr):
+    _check(h, load().svgp_ng_update_T_gap(h, byref(params), byref(batch), c_void_p(L_ptr), c_void_p(gamma_ptr),
+                                          max_iters, c_double(eps), c_double(sigma2), c_void_p(iters_ptr),
+                                          c_void_p(gap_ptr)))
 
 
 def svgp_predict(h, params, Xs_ptr, Ns, mean_ptr, var_ptr, include_noise=False):

@@ -26,6 +26,11 @@ enum {
   RED_LOGS = 8,       // sum_i log s_i
   RED_SUMA_F = 9,     // sum (G_Kuf o Kuf)
   RED_SUMA_U = 10,    // sum (G_Kuu o Kuu)
+  RED_ELL = 11,       // probit: sum_n E_n
+  RED_SUMH = 12,      // probit: sum_n h_n
+  RED_SUMVAR = 13,    // probit: sum_n sigma_n^2 (clamped)
+  RED_NCLAMP = 14,    // probit: number of clamped sigma_n^2
+  RED_GAPDOT = 15,    // <N N^T, Psi> of the Prop. 3 gap
   RED_COUNT = 16
 };
 
@@ -197,6 +202,42 @@ struct EpiSym {
   }
 };
 
+// N = I - acc on the valid M x M block, zero in the padding (the matrix
+// I - T K~ of the Prop. 3 gap); FP32.
+struct EpiIminus {
+  float* out; int ld; int M;
+  const int* skip_flag;
+  __device__ bool skip() const { return skip_flag && *skip_flag; }
+  __device__ void begin_tile(int, int) {}
+  __device__ __forceinline__ void block(int i0, int j0, const float (&)[32], const float (&vt)[32], int lane) {
+    const int j = j0 + lane;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      const int i = i0 + r;
+      out[(size_t)i * ld + j] = (i < M && j < M) ? (i == j ? 1.0f : 0.0f) - vt[r] : 0.0f;
+    }
+  }
+  __device__ void reduce() {}
+};
+
+// <acc, Psi> over the valid M x M block, added to *dst (FP64).
+struct EpiDotPsi {
+  const float* Psi; int ld; int M; double* dst;
+  const int* skip_flag;
+  float p0;
+  __device__ bool skip() const { return skip_flag && *skip_flag; }
+  __device__ void begin_tile(int, int) { p0 = 0.f; }
+  __device__ __forceinline__ void block(int i0, int j0, const float (&)[32], const float (&vt)[32], int lane) {
+    const int j = j0 + lane;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      const int i = i0 + r;
+      if (i < M && j < M) p0 = fmaf(vt[r], __ldg(Psi + (size_t)i * ld + j), p0);
+    }
+  }
+  __device__ void reduce() { block_add_double(p0, dst); }
+};
+
 // NG update of L (Prop. 1): acc = (L Phi)_ij on the lower region;
 // L_ij <- L_ij - gamma * acc.  The whole launch is skipped when the Frobenius
 // stopping rule (Eq. (8), Section 3.3) fired.
@@ -357,8 +398,10 @@ struct KufGen {
 };
 
 // Epilogue data for W = P Kuf (the data part of the backward pass): for each
-// element A_in = c * Kuf_in * (v_i g_n + W_in / noise)  (= G_Kuf o Kuf for the
-// Gaussian likelihood) accumulates per row i, over scaled differences
+// element A_in = c * Kuf_in * (v_i g_n - 2 h_n W_in) (= G_Kuf o Kuf, with
+// g_n = dE_n/dmu_n and h_n = dE_n/dsigma_n^2; hn == null means the Gaussian
+// h_n = -1 / (2 noise), so -2 h_n = 1 / noise) accumulates per row i, over
+// scaled differences
 // e_d = x~_nd - z~_id,
 //   rowacc[i][d]     += A_in e_d          (d < D)
 //   rowacc[i][D + d] += A_in e_d^2
@@ -366,9 +409,9 @@ struct KufGen {
 // and, when colsum != null, colsum[n] += sum_i Kuf_in W_in (for sigma_n^2).
 struct WEpi {
   KufGen gen;
-  const float* Zraw;
-  const float* Xraw;
-  const float* v; const float* g; const float* noise;
+  const float* v; const float* g;
+  const float* hn;     // per-point h_n (B), or null (Gaussian: from noise)
+  const float* noise;
   float c;
   float* rowacc;       // M x (2D+1), may be null
   float* colsum;       // B, may be null

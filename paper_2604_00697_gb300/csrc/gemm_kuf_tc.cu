@@ -237,8 +237,11 @@ psi_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // z, row role
 //   k role   K = [p'hi (D), p'lo (D), p'hi (D), 1, 1, 1, c'_hi, c'_mid, c'_lo]
 // with p' = sqrt(log2 e) p, c = -1/2 |p'|^2 and c' = c + log2(sf2); padded
 // rows get c = c' = -1e30.  R_a . K_b = t(a, b) = log2 of the SE-ARD value.
+// With per-point weights hw (may be null) the k-role constant is
+// c' + 1/2 log2|hw_r| (c' = -1e30 where |hw_r| < 1e-30), so that the generated
+// value carries a factor sqrt|hw_r|.  R may be null (k role only).
 __global__ void kuf_prep_kernel(const float* __restrict__ P, int n, int npad, int D, const float* __restrict__ sf2,
-                                bf16* __restrict__ R, bf16* __restrict__ K) {
+                                const float* __restrict__ hw, bf16* __restrict__ R, bf16* __restrict__ K) {
   // one row per threadIdx.y (8 rows per block), 64 threads per row
   __shared__ float part_sum[8][2];
   const int Dp = (D + 3) & ~3;
@@ -256,7 +259,11 @@ __global__ void kuf_prep_kernel(const float* __restrict__ P, int n, int npad, in
   __syncthreads();
   if (!live) return;
   const float c_row = valid ? -0.5f * (part_sum[threadIdx.y][0] + part_sum[threadIdx.y][1]) : -1e30f;
-  const float c_k = valid ? c_row + log2f(*sf2) : -1e30f;
+  float c_k = valid ? c_row + log2f(*sf2) : -1e30f;
+  if (hw && valid) {
+    const float a = fabsf(hw[r]);
+    c_k = a < 1e-30f ? -1e30f : c_k + 0.5f * log2f(a);
+  }
   // three-way BF16 split of a constant: component q of (hi, mid, lo)
   auto split3 = [](float c, int q) {
     const float h = __bfloat162float(__float2bfloat16_rn(c));
@@ -275,7 +282,7 @@ __global__ void kuf_prep_kernel(const float* __restrict__ P, int n, int npad, in
     rv = one;
     kv = __float2bfloat16_rn(split3(c_k, d - 3 * D - 3));
   }
-  R[(size_t)r * 64 + d] = rv;
+  if (R) R[(size_t)r * 64 + d] = rv;
   K[(size_t)r * 64 + d] = kv;
 }
 
@@ -290,11 +297,18 @@ void k_kuf_prep(const float* Zs, const float* Xs, int M, int Mp, int B, int Bp, 
                 const KufTC& t, cudaStream_t st) {
   dim3 blk(64, 8);
   svgp_note_launch();
-  kuf_prep_kernel<<<(Mp + 7) / 8, blk, 0, st>>>(Zs, M, Mp, D, sf2, t.ZR, t.ZK);
+  kuf_prep_kernel<<<(Mp + 7) / 8, blk, 0, st>>>(Zs, M, Mp, D, sf2, nullptr, t.ZR, t.ZK);
   if (Xs && B > 0) {
     svgp_note_launch();
-    kuf_prep_kernel<<<(Bp + 7) / 8, blk, 0, st>>>(Xs, B, Bp, D, sf2, t.XR, t.XK);
+    kuf_prep_kernel<<<(Bp + 7) / 8, blk, 0, st>>>(Xs, B, Bp, D, sf2, nullptr, t.XR, t.XK);
   }
+}
+
+void k_kuf_prep_weighted(const float* Xs, int B, int Bp, int D, const float* sf2, const float* h, bf16* XKh,
+                         cudaStream_t st) {
+  dim3 blk(64, 8);
+  svgp_note_launch();
+  kuf_prep_kernel<<<(Bp + 7) / 8, blk, 0, st>>>(Xs, B, Bp, D, sf2, h, nullptr, XKh);
 }
 
 void tc_kuf_init_attributes() {
@@ -306,11 +320,11 @@ void tc_kuf_init_attributes() {
 
 bool tc_kuf_supported(int D) { return D >= 1 && 3 * D + 6 <= 64 && tc_available(); }
 
-bool tc_psi(const GemmCtx& g, const KufGen& kg, const KufTC& t, int B, EpiPsi e) {
+bool tc_psi(const GemmCtx& g, const KufGen& kg, const KufTC& t, const bf16* Kk, int B, EpiPsi e) {
   if (!tc_kuf_supported(kg.D)) return false;
   const int Bp = (B + 127) / 128 * 128;
   CUtensorMap mr, mk;
-  if (!tc_make_map(&mr, t.ZR, g.Mp, 64, 128) || !tc_make_map(&mk, t.XK, Bp, 64, 64)) return false;
+  if (!tc_make_map(&mr, t.ZR, g.Mp, 64, 128) || !tc_make_map(&mk, Kk, Bp, 64, 64)) return false;
   svgp_note_launch();
   if (g.split)
     psi_tc_kernel<3><<<g.nt[TT_PSI], THREADS, PsiGeo<3>::SMEM, g.st>>>(mr, mk, g.tt[TT_PSI], Bp / KB, g.err, e);

@@ -34,11 +34,13 @@ struct MemLoad {
 
 // Operand generated from the SE-ARD kernel: element (row, k) =
 // sf2 * exp(-1/2 ||rp_row - kp_k||^2) over scaled coordinates (stride Dp,
-// zero padded), zero when row >= nrow or k >= nk.
+// zero padded), zero when row >= nrow or k >= nk; times sqrt|kh_k| when the
+// per-k weights kh are given.
 struct GenLoad {
   const float* rp; int nrow;   // row points
   const float* kp; int nk;     // k points
   int Dp; const float* sf2;
+  const float* kh;             // per-k weights (may be null)
   float c[SVGP_MAXD];
   float lsf2;
   int myrow;
@@ -68,6 +70,7 @@ struct GenLoad {
           }
         }
         val = expf(lsf2 - 0.5f * r2);
+        if (kh) val *= sqrtf(fabsf(__ldg(kh + k)));
       }
       r[q] = val;
     }
@@ -239,7 +242,8 @@ __global__ void __launch_bounds__(256) simt_w_kernel(MemLoad la, GenLoad lb, int
       float kuf = expf(lsf2 - 0.5f * r2);
       prod = kuf * w;
       if (we.rowacc) {
-        float a = we.c * kuf * fmaf(vi, we.g[n], w * inv_noise);
+        const float hc = we.hn ? -2.0f * we.hn[n] : inv_noise;    // -2 h_n
+        float a = we.c * kuf * fmaf(vi, we.g[n], w * hc);
         accS += a;
 #pragma unroll
         for (int d = 0; d < SVGP_MAXD; ++d) {
@@ -310,10 +314,12 @@ template void simt_gemm<EpiLupd>(const GemmCtx&, int, const float*, const float*
 template void simt_gemm<EpiStore<float*>>(const GemmCtx&, int, const float*, const float*, const EpiStore<float*>&);
 template void simt_gemm<EpiP<float*>>(const GemmCtx&, int, const float*, const float*, const EpiP<float*>&);
 template void simt_gemm<EpiGK>(const GemmCtx&, int, const float*, const float*, const EpiGK&);
+template void simt_gemm<EpiIminus>(const GemmCtx&, int, const float*, const float*, const EpiIminus&);
+template void simt_gemm<EpiDotPsi>(const GemmCtx&, int, const float*, const float*, const EpiDotPsi&);
 
-void simt_psi(const GemmCtx& g, const KufGen& kg, int B, EpiPsi e) {
+void simt_psi(const GemmCtx& g, const KufGen& kg, int B, EpiPsi e, const float* hw) {
   int Dp = (kg.D + 3) & ~3;
-  GenLoad la{kg.Zs, kg.M, kg.Xs, B, Dp, kg.sf2}, lb{kg.Zs, kg.M, kg.Xs, B, Dp, kg.sf2};
+  GenLoad la{kg.Zs, kg.M, kg.Xs, B, Dp, kg.sf2, hw}, lb{kg.Zs, kg.M, kg.Xs, B, Dp, kg.sf2, hw};
   int Bp = (B + SK - 1) / SK * SK;
   svgp_note_launch();
   simt_gemm_tiles<EpiPsi, GenLoad, GenLoad><<<g.nt[TT_PSI], 256, SIMT_SMEM, g.st>>>(g.tt[TT_PSI], la, lb, e, 0, Bp);
@@ -340,6 +346,8 @@ void simt_init_attributes() {
   set_smem_attr<EpiStore<float*>>();
   set_smem_attr<EpiP<float*>>();
   set_smem_attr<EpiGK>();
+  set_smem_attr<EpiIminus>();
+  set_smem_attr<EpiDotPsi>();
   cudaFuncSetAttribute(simt_gemm_tiles<EpiPsi, GenLoad, GenLoad>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)SIMT_SMEM);
 }

@@ -1,8 +1,9 @@
 // W = P Kuf with the SE-ARD operand generated on chip (kuf_common.cuh) and a
 // fused epilogue, for the data part of the backward pass (Section 3.1) and
 // for the predictive variance:
-//   gradient mode (rowpart != null): with A_in = c Kuf_in (v_i g_n + W_in /
-//     noise) (= G_Kuf o Kuf for the Gaussian likelihood), per row i the sums
+//   gradient mode (rowpart != null): with A_in = c Kuf_in (v_i g_n - 2 h_n
+//     W_in) (= G_Kuf o Kuf; h_n = -1/(2 noise) for the Gaussian likelihood,
+//     per point for probit), per row i the sums
 //       S0 = sum_n A_in,  S1_d = sum_n A_in x~_nd,  S2_d = sum_n A_in x~_nd^2
 //     (FP32, x~ and x~^2 staged in shared memory), reported in the
 //     difference form  sum_n A_in e_d = S1_d - z~_id S0  and
@@ -240,7 +241,7 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
     float cv = 0.f, cn = 0.f;
     if (grad) {
       cv = i < we.gen.M ? we.c * __ldg(we.v + i) : 0.f;
-      cn = we.c / *we.noise;
+      if (!we.hn) cn = we.c / *we.noise;          // Gaussian: -2 c h_n = c / noise
     }
     float S0 = 0.f, S1[DP], S2[DP];
 #pragma unroll
@@ -288,7 +289,9 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
           }
           if (tid < 128) gq[tid] = gv;
         }
-        if (tid < 128) colbuf[tid] = 0.f;
+        // gradient mode: colbuf holds -2 c h_n of the n-block; variance mode: the column sums
+        if (tid < 128)
+          colbuf[tid] = (grad && n0 + tid < B) ? (we.hn ? -2.0f * we.c * __ldg(we.hn + n0 + tid) : cn) : 0.f;
       }
       asm volatile("bar.sync 1, %0;" ::"n"(32 * NTW) : "memory");
       if (ok) {
@@ -301,7 +304,7 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
               const int n = ch * 32 + q;
-              const float a = ex2(tt[q]) * fmaf(cv, gq[n], cn * w[q]);
+              const float a = ex2(tt[q]) * fmaf(cv, gq[n], colbuf[n] * w[q]);
               S0 += a;
               const float4* xr = reinterpret_cast<const float4*>(xq + n * XW);
 #pragma unroll

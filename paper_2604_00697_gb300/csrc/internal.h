@@ -12,7 +12,8 @@ enum TileTable {
   TT_LS = 3,      // full,  K [0, m0 + BM)    L S
   TT_OUT = 4,     // lower, K [0, n0 + BN)    Y L^T       = L S L^T
   TT_PSI = 5,     // upper, K given at launch Kuf Kuf^T
-  TT_COUNT = 6
+  TT_FULL = 6,    // full,  K [0, Mp)         general products (Prop. 3 gap)
+  TT_COUNT = 7
 };
 
 struct GemmCtx {
@@ -34,7 +35,9 @@ void svgp_note_launch();
 // FP32 SIMT contractions (gemm_simt.cu): acc = A B^T over table `tab`.
 template <class Epi>
 void simt_gemm(const GemmCtx& g, int tab, const float* A, const float* B, const Epi& e);
-void simt_psi(const GemmCtx& g, const KufGen& kg, int B, EpiPsi e);
+// hw (may be null): per-point weights h_n; the result is then
+// Kuf diag(|h|) Kuf^T (both generated operands scaled by sqrt|h_n|).
+void simt_psi(const GemmCtx& g, const KufGen& kg, int B, EpiPsi e, const float* hw);
 void simt_w(const GemmCtx& g, const float* P, const WEpi& we);
 void simt_init_attributes();
 
@@ -52,12 +55,19 @@ bool tc_gemm(const GemmCtx& g, int tab, const bf16* A, const bf16* B, const Epi&
 // [hi, lo, hi]) and per-point offsets c = -1/2 log2(e) |p|^2.
 struct KufTC {
   bf16 *ZR, *ZK, *XR, *XK;
+  bf16* XKh;   // k role of x with the constant raised by 1/2 log2|h_n| (probit Psi weights)
 };
 bool tc_kuf_supported(int D);
 void tc_kuf_init_attributes();
 void k_kuf_prep(const float* Zs, const float* Xs, int M, int Mp, int B, int Bp, int D, const float* sf2,
                 const KufTC& t, cudaStream_t st);
-bool tc_psi(const GemmCtx& g, const KufGen& kg, const KufTC& t, int B, EpiPsi e);
+// K-role vectors of the x points with the per-point weight sqrt|h_n| folded
+// into the constant (|h_n| < 1e-30 gives the value 0), for the weighted Psi.
+void k_kuf_prep_weighted(const float* Xs, int B, int Bp, int D, const float* sf2, const float* h, bf16* XKh,
+                         cudaStream_t st);
+// Psi = Kxf Kxf^T with the k-role vectors Kk of the x points (t.XK: Kuf Kuf^T;
+// t.XKh: Kuf diag(|h|) Kuf^T).
+bool tc_psi(const GemmCtx& g, const KufGen& kg, const KufTC& t, const bf16* Kk, int B, EpiPsi e);
 // W = P Kuf with its fused epilogue.  Gradient mode (we.rowacc != null):
 // writes per-CTA partial rows rowpart[p][k][i] (p < returned count, k < 2D+1,
 // i < Mp) instead of rowacc; variance mode returns 0.  -1: not supported.
@@ -83,10 +93,35 @@ void k_gemv(const float* A, int Mp, int M, const float* x, float alpha, const fl
             float* y, const float* dotw, double* dot_out, cudaStream_t st);
 void k_mu(const float* Zs, const float* Xs, int M, int B, int D, const float* sf2, const float* v,
           float* mu, cudaStream_t st);
+// K~ = Kuu + diag(s) in FP32 (Mp x Mp, zero padding).
+void k_kt_f32(const float* Kuu, const float* s, int M, int Mp, float* Kt, cudaStream_t st);
+// Prop. 3 gap from red[RED_GAPDOT] = <N N^T, Psi>: G = dot / sigma2 with
+// sigma2 = sigma2_host, or min_i s_i when sigma2_host <= 0.  Writes *gap (may
+// be null); with eps > 0 sets *done when G <= 2 noise eps.
+void k_gap_check(const double* red, const float* s, int M, double sigma2_host, const float* noise, double eps,
+                 int* done, double* gap, cudaStream_t st);
+// y = alpha (x + beta x2), n elements.
+void k_axpy(const float* x, float alpha, const float* x2, float beta, float* y, int n, cudaStream_t st);
 void k_pointwise_gauss(const float* y, const float* mu, const float* noise, int B, float* g,
                        double* red, cudaStream_t st);
+
+// Bernoulli-probit likelihood (probit.cu).  Gauss-Hermite rule for exp(-t^2).
+constexpr int GH_MAX = 32;
+struct GHRule {
+  int n;
+  double t[GH_MAX], w[GH_MAX];   // nodes, weights / sqrt(pi)
+};
+// Host: n nodes and weights of the rule (ascending); false if n is out of [1, 64].
+bool gauss_hermite_rule(int n, double* t, double* w);
+// Per point: sigma_n^2 = max(sf2 - colsum_n, 0), E_n, g_n, h_n; sums of E_n,
+// h_n, sigma_n^2 and the clamp count into red.
+void k_pointwise_probit(const float* y, const float* mu, const float* colsum, const float* sf2, int B,
+                        const GHRule& gh, float* g, float* h, double* red, cudaStream_t st);
 void k_kg(const float* Zs, const float* Xs, int M, int Mp, int B, int D, const float* sf2,
           const float* g, float* Kg, cudaStream_t st);
+// noise == null (probit): Psi holds Kuf diag(|h|) Kuf^T and enters with
+// coefficient c; otherwise Psi = Kuf Kuf^T with c / (2 noise).  m == null:
+// the bound without the preconditioner (no m~ terms in G_P).
 template <class OutP>
 void k_gp_assemble(const float* Kuu, const float* Psi, const float* Kg, const float* m,
                    const float* w, const float* noise, float c, int M, int Mp, OutP out,
@@ -96,8 +131,9 @@ void k_kuu_bwd(const float* GKuu, const float* Kuu, const float* Zs, int M, int 
 void k_logs(const float* s, int M, double* red, cudaStream_t st);
 void k_grad_finalize(const float* rowacc_f, const float* rowacc_u, const float* rowpart, int nparts, int Mp,
                      const float* ell, int M, int D, float* dZ, double* acc_ell, double* red, cudaStream_t st);
+// probit: E from red[RED_ELL], dsf2's data part from red[RED_SUMH], dnoise = 0.
 void k_terms_finalize(const double* red, const double* acc_ell, const float* sf2, const float* noise,
-                      const float* ell, int M, int D, int B, double N, double* terms,
+                      const float* ell, int M, int D, int B, double N, bool probit, double* terms,
                       float* dsf2, float* dnoise, float* dell, int* errword, cudaStream_t st);
 void k_predict_finalize(const float* colsum, const float* sf2, const float* noise, int Ns,
                         int include_noise, float* var, cudaStream_t st);

@@ -281,7 +281,7 @@ __global__ void gp_assemble_kernel(const float* __restrict__ Kuu, const float* _
                                    const float* __restrict__ w, const float* __restrict__ noise, float c,
                                    int M, int Mp, OutP out) {
   // block: row i = blockIdx.y, 4 consecutive columns per thread
-  const float cn = c * 0.5f / *noise;
+  const float cn = noise ? c * 0.5f / *noise : c;   // probit: Psi = Kuf diag(|h|) Kuf^T
   const int i = blockIdx.y;
   const int j = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
   if (j >= Mp) return;
@@ -290,13 +290,15 @@ __global__ void gp_assemble_kernel(const float* __restrict__ Kuu, const float* _
   const float4 ku = __ldg(reinterpret_cast<const float4*>(Kuu + e));
   const float pv[4] = {ps.x, ps.y, ps.z, ps.w}, kv[4] = {ku.x, ku.y, ku.z, ku.w};
   const bool row_ok = i < M;
-  const float kgi = row_ok ? Kg[i] : 0.f, mi = row_ok ? m[i] : 0.f, wi = row_ok ? w[i] : 0.f;
+  const bool mt = m != nullptr;   // the m~ terms of the preconditioned bound
+  const float kgi = row_ok ? Kg[i] : 0.f, mi = (row_ok && mt) ? m[i] : 0.f, wi = row_ok ? w[i] : 0.f;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int jj = j + q;
     float val = 0.f;
     if (row_ok && jj < M) {
-      val = 0.5f * c * (kgi * m[jj] + mi * Kg[jj]) + cn * pv[q] + 0.5f * kv[q] - 0.5f * (mi * w[jj] + wi * m[jj]);
+      val = cn * pv[q] + 0.5f * kv[q];
+      if (mt) val += 0.5f * c * (kgi * m[jj] + mi * Kg[jj]) - 0.5f * (mi * w[jj] + wi * m[jj]);
     }
     put(out, e + q, val);
   }
@@ -442,33 +444,36 @@ __global__ void __launch_bounds__(256) grad_finalize_kernel(const float* __restr
 // Scalar assembly of Eq. (7) in FP64 (and the scalar gradients).
 __global__ void terms_finalize_kernel(const double* __restrict__ red, const double* __restrict__ acc_ell,
                                       const float* __restrict__ sf2p, const float* __restrict__ noisep,
-                                      const float* __restrict__ ell, int M, int D, int B, double N,
+                                      const float* __restrict__ ell, int M, int D, int B, double N, bool probit,
                                       double* terms, float* dsf2, float* dnoise, float* dell,
                                       int* errword) {
   if (threadIdx.x != 0) return;
-  double sf2 = *sf2p, noise = *noisep, c = N / B;
+  double sf2 = *sf2p, noise = probit ? 1.0 : *noisep, c = N / B;
   double trA1 = red[RED_TRA1], froA1 = red[RED_FROA1];
   double trPKt = 2.0 * trA1 - froA1;                 // tr(P K~) = tr((2I - A1) A1)
   double trPKuu = trPKt - red[RED_SPDIAG];            // minus tr(P diag(s))
   double quad = red[RED_QUAD];
   double logdetT = 2.0 * red[RED_LOGDETL];
   double logdetS = red[RED_LOGS];
-  double sqerr = red[RED_SQERR];
-  double sumvar = (double)B * sf2 - red[RED_PPSI];    // sum_n sf2 - k_n^T P k_n
+  double sqerr = probit ? 0.0 : red[RED_SQERR];
+  // sum_n sigma_n^2: Gaussian from sum_n sf2 - k_n^T P k_n = B sf2 - <P, Psi>; probit per point
+  double sumvar = probit ? red[RED_SUMVAR] : (double)B * sf2 - red[RED_PPSI];
   const double LOG2PI = 1.8378770664093453;
-  double E = c * (-0.5 * B * (LOG2PI + log(noise)) - (sqerr + sumvar) / (2.0 * noise));
+  double E = probit ? c * red[RED_ELL]
+                    : c * (-0.5 * B * (LOG2PI + log(noise)) - (sqerr + sumvar) / (2.0 * noise));
   double KL = 0.5 * (-trPKuu + trA1 - M + quad - logdetT - logdetS);
   double F = E - KL;
   if (terms) {
     terms[SVGP_T_F] = F; terms[SVGP_T_E] = E; terms[SVGP_T_KL] = KL; terms[SVGP_T_TRKT] = trA1;
     terms[SVGP_T_TRPKUU] = trPKuu; terms[SVGP_T_QUAD] = quad; terms[SVGP_T_LOGDETT] = logdetT;
     terms[SVGP_T_SQERR] = sqerr; terms[SVGP_T_SUMVAR] = sumvar; terms[SVGP_T_LOGDETS] = logdetS;
+    terms[SVGP_T_NCLAMP] = probit ? red[RED_NCLAMP] : 0.0;
   }
   if (!isfinite(F)) atomicOr(errword, ERRBIT_NONFINITE);
   if (dsf2) {
-    double h = -0.5 / noise;
-    *dsf2 = (float)(c * B * h + (red[RED_SUMA_F] + red[RED_SUMA_U]) / sf2);
-    *dnoise = (float)(c * (-0.5 * B / noise + (sqerr + sumvar) / (2.0 * noise * noise)));
+    const double sumh = probit ? red[RED_SUMH] : -0.5 * B / noise;   // sum_n h_n
+    *dsf2 = (float)(c * sumh + (red[RED_SUMA_F] + red[RED_SUMA_U]) / sf2);
+    *dnoise = probit ? 0.f : (float)(c * (-0.5 * B / noise + (sqerr + sumvar) / (2.0 * noise * noise)));
     for (int d = 0; d < D; ++d) dell[d] = (float)(acc_ell[d] / ell[d]);
   }
 }
@@ -571,6 +576,58 @@ void k_gemv(const float* A, int Mp, int M, const float* x, float alpha, const fl
   gemv_kernel<<<blocks, 256, sizeof(float) * Mp, st>>>(A, Mp, M, x, alpha, x2, beta, y, dotw, dot_out);
 }
 
+namespace {
+__global__ void kt_f32_kernel(const float* __restrict__ Kuu, const float* __restrict__ s, int M, int Mp,
+                              float* __restrict__ Kt) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)Mp * Mp) return;
+  const int i = (int)(e / Mp), j = (int)(e % Mp);
+  Kt[e] = Kuu[e] + ((i == j && i < M) ? s[i] : 0.f);
+}
+
+__global__ void gap_check_kernel(const double* __restrict__ red, const float* __restrict__ s, int M,
+                                 double sigma2_host, const float* __restrict__ noise, double eps, int* done,
+                                 double* gap) {
+  __shared__ float mn[32];
+  float m = 3.4e38f;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) m = fminf(m, s[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) mn[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fminf(m, mn[w]);
+  if (done && *done) return;
+  const double sig2 = sigma2_host > 0.0 ? sigma2_host : (double)m;
+  const double G = red[RED_GAPDOT] / sig2;
+  if (gap) *gap = G;
+  if (done && eps > 0.0 && G <= 2.0 * (double)*noise * eps) *done = 1;
+}
+
+__global__ void axpy_kernel(const float* __restrict__ x, float alpha, const float* __restrict__ x2, float beta,
+                            float* __restrict__ y, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = alpha * (x[i] + beta * x2[i]);
+}
+}  // namespace
+
+void k_kt_f32(const float* Kuu, const float* s, int M, int Mp, float* Kt, cudaStream_t st) {
+  const size_t n = (size_t)Mp * Mp;
+  svgp_note_launch();
+  kt_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Kuu, s, M, Mp, Kt);
+}
+
+void k_gap_check(const double* red, const float* s, int M, double sigma2_host, const float* noise, double eps,
+                 int* done, double* gap, cudaStream_t st) {
+  svgp_note_launch();
+  gap_check_kernel<<<1, 256, 0, st>>>(red, s, M, sigma2_host, noise, eps, done, gap);
+}
+
+void k_axpy(const float* x, float alpha, const float* x2, float beta, float* y, int n, cudaStream_t st) {
+  svgp_note_launch();
+  axpy_kernel<<<(n + 255) / 256, 256, 0, st>>>(x, alpha, x2, beta, y, n);
+}
+
 void k_mu(const float* Zs, const float* Xs, int M, int B, int D, const float* sf2, const float* v,
           float* mu, cudaStream_t st) {
   cudaMemsetAsync(mu, 0, sizeof(float) * B, st);
@@ -631,10 +688,10 @@ void k_grad_finalize(const float* rowacc_f, const float* rowacc_u, const float* 
 }
 
 void k_terms_finalize(const double* red, const double* acc_ell, const float* sf2, const float* noise,
-                      const float* ell, int M, int D, int B, double N, double* terms, float* dsf2,
+                      const float* ell, int M, int D, int B, double N, bool probit, double* terms, float* dsf2,
                       float* dnoise, float* dell, int* errword, cudaStream_t st) {
   svgp_note_launch();
-  terms_finalize_kernel<<<1, 32, 0, st>>>(red, acc_ell, sf2, noise, ell, M, D, B, N, terms, dsf2, dnoise,
+  terms_finalize_kernel<<<1, 32, 0, st>>>(red, acc_ell, sf2, noise, ell, M, D, B, N, probit, terms, dsf2, dnoise,
                                           dell, errword);
 }
 

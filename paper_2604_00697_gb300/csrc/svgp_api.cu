@@ -54,6 +54,11 @@ struct svgp_handle {
   // vectors
   float *Zs, *Xs, *v, *w, *mu, *g, *Kg, *colsum, *rowacc_f, *rowacc_u, *dm_tmp;
   float* rowpart;   // partial row sets of the tensor-core W epilogue
+  bool probit;      // Bernoulli-probit likelihood (else Gaussian)
+  bool unprec;      // R-SVGP without the mean preconditioner (m = Kuu m~)
+  GHRule gh;        // probit: Gauss-Hermite rule (weights divided by sqrt(pi))
+  float* hn;        // probit: per-point h_n = dE_n/dsigma_n^2
+  float* gapN;      // Prop. 3 gap: N = I - T K~ (FP32, Mp x Mp)
   double *red, *acc_ell, *resid_tmp;
   int *errword, *done, *iters_tmp;
   GemmCtx gs, gt;   // SIMT and tensor-core tile tables
@@ -140,7 +145,8 @@ bool build_ctx(svgp_handle* h, GemmCtx& g, int BM, int BN, bool sched) {
   const std::vector<Tile> tabs[TT_COUNT] = {
       make_tiles(Mp, BM, BN, REG_FULL, K_M0_END),  make_tiles(Mp, BM, BN, REG_UPPER, K_N0_END),
       make_tiles(Mp, BM, BN, REG_LOWER, K_N0_M1),  make_tiles(Mp, BM, BN, REG_FULL, K_0_M1),
-      make_tiles(Mp, BM, BN, REG_LOWER, K_0_N1),   make_tiles(Mp, BM, BN, REG_UPPER, K_ALL)};
+      make_tiles(Mp, BM, BN, REG_LOWER, K_0_N1),   make_tiles(Mp, BM, BN, REG_UPPER, K_ALL),
+      make_tiles(Mp, BM, BN, REG_FULL, K_ALL)};
   for (int t = 0; t < TT_COUNT; ++t) {
     const bool ok = (sched && t != TT_PSI) ? upload_sched(h, tabs[t], g, t) : upload_tiles(h, tabs[t], &g.tt[t], &g.nt[t]);
     if (!ok) return false;
@@ -148,8 +154,8 @@ bool build_ctx(svgp_handle* h, GemmCtx& g, int BM, int BN, bool sched) {
   return true;
 }
 
-bool valid_params(const svgp_params* p) {
-  return p && p->Z && p->ell && p->sf2 && p->noise && p->m && p->s && p->L;
+bool valid_params(const svgp_handle* h, const svgp_params* p) {
+  return p && p->Z && p->ell && p->sf2 && (p->noise || h->probit) && p->m && p->s && p->L;
 }
 
 // Brackets one launch with timing events while profiling is enabled.
@@ -236,11 +242,13 @@ void run_lupd(svgp_handle* h, float* L_inout, const float* gamma) {  // L <- L -
   else tc_gemm(h->gt, TT_LUPD, H(h->L_lo), H(h->S), e);
 }
 
-void run_psi(svgp_handle* h, const svgp_params* p, int B) {
+// Psi = Kuf Kuf^T, or Kuf diag(|hw|) Kuf^T when hw != null (the tensor-core
+// path then reads the weighted k-role vectors kt.XKh, prepared from hw).
+void run_psi(svgp_handle* h, const svgp_params* p, int B, const float* hw) {
   ProfScope ps(h, SVGP_PROF_PSI);
   KufGen kg{h->Zs, h->Xs, h->D, h->M, B, p->sf2};
   EpiPsi e{h->Psi, h->Mp};
-  if (!(h->tc_kuf && tc_psi(h->gt, kg, h->kt, B, e))) simt_psi(h->gs, kg, B, e);
+  if (!(h->tc_kuf && tc_psi(h->gt, kg, h->kt, hw ? h->kt.XKh : h->kt.XK, B, e))) simt_psi(h->gs, kg, B, e, hw);
 }
 
 // Returns the number of partial row sets the tensor-core kernel wrote (0 when
@@ -274,21 +282,33 @@ void prologue(svgp_handle* h, const svgp_params* p, const float* X, int B, const
   prep_L(h, Lin, h->red + RED_LOGDETL);
 }
 
-// Forward pass of Eq. (7) up to the per-point Gaussian terms.
+// Forward pass of Eq. (7) up to the per-point likelihood terms.  Gaussian:
+// sum_n sigma_n^2 through <P, Psi> (psi = true builds Psi); probit: sigma_n^2
+// per point from the column sums of Kuf o (P Kuf), then the quadrature.
 void forward(svgp_handle* h, const svgp_params* p, const svgp_batch* b, bool psi) {
   cudaStream_t st = h->st;
+  psi = psi && !h->probit;
   k_logs(p->s, h->M, h->red, st);
   run_vt(h, h->Kuu_lo, p->s, nullptr);   // Vt = L^T K~
   run_sym<1>(h, nullptr);                // A1 = L^T K~ L ; S = 2I - A1 ; tr, Frobenius
-  if (psi) run_psi(h, p, b->B);          // Psi = Kuf Kuf^T (Kuf generated on chip)
+  if (psi) run_psi(h, p, b->B, nullptr); // Psi = Kuf Kuf^T (Kuf generated on chip)
   run_ls(h);                             // Y = L (2I - A1)
   run_p(h, p->s, psi ? h->Psi : nullptr);  // P = Y L^T ; sum s_i P_ii ; <P, Psi>
-  k_gemv(h->Pf, h->Mp, h->M, p->m, 1.f, nullptr, 0.f, h->v, nullptr, nullptr, st);          // v = P m
+  if (h->unprec) cudaMemcpyAsync(h->v, p->m, sizeof(float) * h->M, cudaMemcpyDeviceToDevice, st);  // v = m
+  else k_gemv(h->Pf, h->Mp, h->M, p->m, 1.f, nullptr, 0.f, h->v, nullptr, nullptr, st);     // v = P m
   k_gemv(h->Kuu_f, h->Mp, h->M, h->v, 1.f, nullptr, 0.f, h->w, h->v, h->red + RED_QUAD, st);  // w = Kuu v
   if (b) {
     if (!(h->tc_kuf && tc_kuf_gemv(h->kt.XR, b->B, h->kt.ZK, h->M, h->v, h->mu, h->errword, st)))
       k_mu(h->Zs, h->Xs, h->M, b->B, h->D, p->sf2, h->v, h->mu, st);                        // mu = Kfu v
-    k_pointwise_gauss(b->y, h->mu, p->noise, b->B, h->g, h->red, st);
+    if (h->probit) {
+      cudaMemsetAsync(h->colsum, 0, sizeof(float) * b->B, st);
+      WEpi wv{KufGen{h->Zs, h->Xs, h->D, h->M, b->B, p->sf2}, nullptr, nullptr, nullptr, nullptr, 0.f, nullptr,
+              h->colsum};
+      run_w(h, wv);                                                                       // k_n^T P k_n
+      k_pointwise_probit(b->y, h->mu, h->colsum, p->sf2, b->B, h->gh, h->g, h->hn, h->red, st);
+    } else {
+      k_pointwise_gauss(b->y, h->mu, p->noise, b->B, h->g, h->red, st);
+    }
   }
 }
 
@@ -309,26 +329,33 @@ void backward_tail(svgp_handle* h, const svgp_params* p, const svgp_batch* b, do
   const int M = h->M, Mp = h->Mp, W = 2 * h->D + 1;
   const float c = (float)(b->N / b->B);
   forward(h, p, b, true);
+  if (h->probit) {                                                                      // Kuf diag(|h|) Kuf^T
+    if (h->tc_kuf) k_kuf_prep_weighted(h->Xs, b->B, (b->B + 127) / 128 * 128, h->D, p->sf2, h->hn, h->kt.XKh, st);
+    run_psi(h, p, b->B, h->hn);
+  }
   if (!(h->tc_kuf && tc_kuf_gemv(h->kt.ZR, M, h->kt.XK, b->B, h->g, h->Kg, h->errword, st)))
     k_kg(h->Zs, h->Xs, M, Mp, b->B, h->D, p->sf2, h->g, h->Kg, st);                    // Kuf g
-  if (h->mode == MODE_F32) k_gp_assemble(h->Kuu_f, h->Psi, h->Kg, p->m, h->w, p->noise, c, M, Mp, F(h->GP_lo), st);
-  else if (h->mode == MODE_BF16) k_gp_assemble(h->Kuu_f, h->Psi, h->Kg, p->m, h->w, p->noise, c, M, Mp, H(h->GP_lo), st);
-  else k_gp_assemble(h->Kuu_f, h->Psi, h->Kg, p->m, h->w, p->noise, c, M, Mp, SP(h, h->GP_lo), st);
+  const float* nz = h->probit ? nullptr : p->noise;
+  const float* mt = h->unprec ? nullptr : p->m;
+  if (h->mode == MODE_F32) k_gp_assemble(h->Kuu_f, h->Psi, h->Kg, mt, h->w, nz, c, M, Mp, F(h->GP_lo), st);
+  else if (h->mode == MODE_BF16) k_gp_assemble(h->Kuu_f, h->Psi, h->Kg, mt, h->w, nz, c, M, Mp, H(h->GP_lo), st);
+  else k_gp_assemble(h->Kuu_f, h->Psi, h->Kg, mt, h->w, nz, c, M, Mp, SP(h, h->GP_lo), st);
   run_vt(h, h->GP_lo, nullptr, nullptr); // X1t = L^T G_P
   run_sym<2>(h, nullptr);                // S = L^T G_P L + I/2
   run_ls(h);                             // Y = L S
   run_gk(h, p->s, gr->ds);               // G_K~ = -Y L^T -> G_Kuu, ds
   cudaMemsetAsync(h->rowacc_f, 0, sizeof(float) * Mp * W, st);
   cudaMemsetAsync(h->rowacc_u, 0, sizeof(float) * Mp * W, st);
-  WEpi we{KufGen{h->Zs, h->Xs, h->D, M, b->B, p->sf2}, nullptr, nullptr, h->v, h->g, p->noise, c,
+  WEpi we{KufGen{h->Zs, h->Xs, h->D, M, b->B, p->sf2}, h->v, h->g, h->probit ? h->hn : nullptr, nz, c,
           h->rowacc_f, nullptr};
   const int nparts = run_w(h, we);                                                     // data part of dZ, dell, dsf2
   k_kuu_bwd(h->GKuu, h->Kuu_f, h->Zs, M, Mp, h->D, h->rowacc_u, h->red, st);          // Kuu part
-  k_gemv(h->Pf, Mp, M, h->Kg, c, h->w, -1.0f / c, gr->dm, nullptr, nullptr, st);      // dm = P (c Kg - w)
+  if (h->unprec) k_axpy(h->Kg, c, h->w, -1.0f / c, gr->dm, M, st);                   // dm = c Kg - w
+  else k_gemv(h->Pf, Mp, M, h->Kg, c, h->w, -1.0f / c, gr->dm, nullptr, nullptr, st); // dm = P (c Kg - w)
   k_grad_finalize(h->rowacc_f, h->rowacc_u, h->rowpart, nparts, Mp, p->ell, M, h->D, gr->dZ, h->acc_ell, h->red,
                   st);
-  k_terms_finalize(h->red, h->acc_ell, p->sf2, p->noise, p->ell, M, h->D, b->B, b->N, terms_dev, gr->dsf2,
-                   gr->dnoise, gr->dell, h->errword, st);
+  k_terms_finalize(h->red, h->acc_ell, p->sf2, p->noise, p->ell, M, h->D, b->B, b->N, h->probit, terms_dev,
+                   gr->dsf2, gr->dnoise, gr->dell, h->errword, st);
 }
 
 // NG iterations of Prop. 1 on L_inout after the prologue (K~ and the L copies
@@ -346,6 +373,17 @@ void ng_loop(svgp_handle* h, const svgp_params* p, float* L_inout, const float* 
     run_lupd(h, L_inout, gamma_dev + t);         // L <- L - gamma L Phi  (Prop. 1)
     if (t + 1 < max_iters) prep_L(h, L_inout, nullptr);
   }
+}
+
+// Prop. 3 gap for the current L (FP32 copy h->Lf) and the batch's Psi:
+// red[RED_GAPDOT] += <N N^T, Psi> with N = I - T K~, T = L L^T, K~ in FP32
+// (h->GKuu) -- three FP32 SIMT products: T = L L^T (into h->Pf), N, and
+// N N^T reduced against Psi.  Skipped while *skip != 0.
+void gap_compute(svgp_handle* h, const int* skip) {
+  const int M = h->M, Mp = h->Mp;
+  simt_gemm(h->gs, TT_LS, h->Lf, h->Lf, EpiStore<float*>{h->Pf, Mp, skip});
+  simt_gemm(h->gs, TT_FULL, h->Pf, h->GKuu, EpiIminus{h->gapN, Mp, M, skip});
+  simt_gemm(h->gs, TT_FULL, h->gapN, h->gapN, EpiDotPsi{h->Psi, Mp, M, h->red + RED_GAPDOT, skip});
 }
 
 bool valid_ng_args(const svgp_params* p, const float* L_inout, const float* gamma_dev, int max_iters) {
@@ -373,13 +411,19 @@ const char* svgp_status_string(int s) {
 
 int svgp_has_tensor_cores(void) { return tc_available() ? 1 : 0; }
 
+svgp_status svgp_gauss_hermite(int n, double* nodes, double* weights) {
+  return gauss_hermite_rule(n, nodes, weights) ? SVGP_OK : SVGP_ERR_INVALID_ARG;
+}
+
 svgp_status svgp_create(const svgp_config* cfg, svgp_handle** out) {
   if (!cfg || !out) return SVGP_ERR_INVALID_ARG;
   *out = nullptr;
   if (cfg->M < 1 || cfg->M > 8192 || cfg->D < 1 || cfg->D > SVGP_MAXD || cfg->B_max < 1 ||
       cfg->B_max > (1 << 22))
     return SVGP_ERR_INVALID_ARG;
-  if (cfg->lik != SVGP_LIK_GAUSSIAN) return SVGP_ERR_UNSUPPORTED;
+  if (cfg->lik != SVGP_LIK_GAUSSIAN && cfg->lik != SVGP_LIK_BERNOULLI_PROBIT) return SVGP_ERR_INVALID_ARG;
+  if (cfg->lik == SVGP_LIK_BERNOULLI_PROBIT && (cfg->gh_points < 0 || cfg->gh_points > GH_MAX))
+    return SVGP_ERR_INVALID_ARG;
   if (cfg->prec != SVGP_FP32 && cfg->prec != SVGP_BF16 && cfg->prec != SVGP_BF16X3) return SVGP_ERR_INVALID_ARG;
   if (cfg->prec != SVGP_FP32 && !tc_available()) return SVGP_ERR_UNSUPPORTED;
   svgp_handle* h = new svgp_handle();
@@ -393,6 +437,23 @@ svgp_status svgp_create(const svgp_config* cfg, svgp_handle** out) {
   h->st = (cudaStream_t)cfg->cuda_stream;
   h->err[0] = 0;
   h->prof = false;
+  h->probit = cfg->lik == SVGP_LIK_BERNOULLI_PROBIT;
+  h->unprec = cfg->unpreconditioned != 0;
+  h->gh.n = 0;
+  h->hn = nullptr;
+  h->kt.XKh = nullptr;
+  if (h->probit) {
+    h->gh.n = cfg->gh_points > 0 ? cfg->gh_points : 20;
+    double t[64], w[64];
+    if (!gauss_hermite_rule(h->gh.n, t, w)) {
+      delete h;
+      return SVGP_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < h->gh.n; ++k) {
+      h->gh.t[k] = t[k];
+      h->gh.w[k] = w[k] / 1.7724538509055160273;   // / sqrt(pi)
+    }
+  }
   size_t M2 = (size_t)h->Mp * h->Mp;
   size_t Bp = (size_t)(cfg->B_max + 127) / 128 * 128;
   // operand copies: FP32 (SIMT), BF16, or BF16 hi followed by BF16 lo
@@ -412,11 +473,16 @@ svgp_status svgp_create(const svgp_config* cfg, svgp_handle** out) {
             dalloc(h, &h->resid_tmp, sizeof(double)) && dalloc(h, &h->errword, sizeof(int)) &&
             dalloc(h, &h->done, sizeof(int)) && dalloc(h, &h->iters_tmp, sizeof(int));
   if (ok && h->mode != MODE_F32) ok = dalloc(h, &h->Kuu_lo, lob) && dalloc(h, &h->P_lo, lob);
+  if (ok) ok = dalloc(h, &h->gapN, M2 * 4);
   h->tc_kuf = h->mode != MODE_F32 && tc_kuf_supported(h->D);
   if (ok && h->tc_kuf)
     ok = dalloc(h, &h->kt.ZR, 2 * 64 * h->Mp) && dalloc(h, &h->kt.ZK, 2 * 64 * h->Mp) &&
          dalloc(h, &h->kt.XR, 2 * 64 * Bp) && dalloc(h, &h->kt.XK, 2 * 64 * Bp) &&
          dalloc(h, &h->rowpart, sizeof(float) * ((size_t)tc_num_sms() * 128 + h->Mp) * W);
+  if (ok && h->probit) {
+    ok = dalloc(h, &h->hn, sizeof(float) * Bp);
+    if (ok && h->tc_kuf) ok = dalloc(h, &h->kt.XKh, 2 * 64 * Bp);
+  }
   if (ok && h->mode == MODE_F32) { h->Kuu_lo = h->Kuu_f; h->P_lo = h->Pf; }
   if (ok) ok = build_ctx(h, h->gs, 128, 128, false) && build_ctx(h, h->gt, 128, 128, h->mode != MODE_F32);
   simt_init_attributes();
@@ -487,13 +553,13 @@ const char* svgp_last_error(const svgp_handle* h) { return h ? h->err : "null ha
 
 svgp_status svgp_bound(svgp_handle* h, const svgp_params* p, const svgp_batch* b, double* terms_dev) {
   if (!h) return SVGP_ERR_INVALID_ARG;
-  if (!valid_params(p)) return fail(h, SVGP_ERR_INVALID_ARG, "params: null pointer");
+  if (!valid_params(h, p)) return fail(h, SVGP_ERR_INVALID_ARG, "params: null pointer");
   if (!terms_dev) return fail(h, SVGP_ERR_INVALID_ARG, "terms_dev is null");
   svgp_status s = validate_batch(h, b);
   if (s != SVGP_OK) return s;
   prologue(h, p, b->X, b->B, p->L);
   forward(h, p, b, true);
-  k_terms_finalize(h->red, h->acc_ell, p->sf2, p->noise, p->ell, h->M, h->D, b->B, b->N, terms_dev,
+  k_terms_finalize(h->red, h->acc_ell, p->sf2, p->noise, p->ell, h->M, h->D, b->B, b->N, h->probit, terms_dev,
                    nullptr, nullptr, nullptr, h->errword, h->st);
   return check_launch(h, "svgp_bound");
 }
@@ -501,7 +567,7 @@ svgp_status svgp_bound(svgp_handle* h, const svgp_params* p, const svgp_batch* b
 svgp_status svgp_backward(svgp_handle* h, const svgp_params* p, const svgp_batch* b, double* terms_dev,
                           const svgp_grads* gr) {
   if (!h) return SVGP_ERR_INVALID_ARG;
-  if (!valid_params(p)) return fail(h, SVGP_ERR_INVALID_ARG, "params: null pointer");
+  if (!valid_params(h, p)) return fail(h, SVGP_ERR_INVALID_ARG, "params: null pointer");
   if (!valid_grads(gr)) return fail(h, SVGP_ERR_INVALID_ARG, "grads: null pointer");
   svgp_status s = validate_batch(h, b);
   if (s != SVGP_OK) return s;
@@ -521,11 +587,59 @@ svgp_status svgp_ng_update_T(svgp_handle* h, const svgp_params* p, float* L_inou
   return check_launch(h, "svgp_ng_update_T");
 }
 
+svgp_status svgp_variance_gap(svgp_handle* h, const svgp_params* p, const svgp_batch* b, double sigma2,
+                              double* gap_dev) {
+  if (!h) return SVGP_ERR_INVALID_ARG;
+  if (!valid_params(h, p) || !gap_dev) return fail(h, SVGP_ERR_INVALID_ARG, "variance_gap: null pointer");
+  svgp_status s = validate_batch(h, b);
+  if (s != SVGP_OK) return s;
+  cudaStream_t st = h->st;
+  prologue(h, p, b->X, b->B, p->L);
+  run_psi(h, p, b->B, nullptr);
+  k_kt_f32(h->Kuu_f, p->s, h->M, h->Mp, h->GKuu, st);
+  cudaMemsetAsync(h->red + RED_GAPDOT, 0, sizeof(double), st);
+  gap_compute(h, nullptr);
+  k_gap_check(h->red, p->s, h->M, sigma2, p->noise, 0.0, nullptr, gap_dev, st);
+  return check_launch(h, "svgp_variance_gap");
+}
+
+svgp_status svgp_ng_update_T_gap(svgp_handle* h, const svgp_params* p, const svgp_batch* b, float* L_inout,
+                                 const float* gamma_dev, int max_iters, double eps, double sigma2, int* iters_dev,
+                                 double* gap_dev) {
+  if (!h) return SVGP_ERR_INVALID_ARG;
+  if (!valid_ng_args(p, L_inout, gamma_dev, max_iters) || !p->noise)
+    return fail(h, SVGP_ERR_INVALID_ARG, "ng_update_T_gap: null pointer or max_iters out of [0, 100000]");
+  if (h->probit) return fail(h, SVGP_ERR_UNSUPPORTED, "ng_update_T_gap: the gap rule is for the Gaussian likelihood");
+  svgp_status s = validate_batch(h, b);
+  if (s != SVGP_OK) return s;
+  cudaStream_t st = h->st;
+  int* iters = iters_dev ? iters_dev : h->iters_tmp;
+  prologue(h, p, b->X, b->B, L_inout);
+  run_psi(h, p, b->B, nullptr);
+  k_kt_f32(h->Kuu_f, p->s, h->M, h->Mp, h->GKuu, st);
+  cudaMemsetAsync(h->done, 0, sizeof(int), st);
+  cudaMemsetAsync(iters, 0, sizeof(int), st);
+  for (int t = 0; t <= max_iters; ++t) {
+    // G(L_t); stop before updating once G <= 2 noise eps (the last pass only measures)
+    cudaMemsetAsync(h->red + RED_GAPDOT, 0, sizeof(double), st);
+    gap_compute(h, h->done);
+    k_gap_check(h->red, p->s, h->M, sigma2, p->noise, eps, h->done, gap_dev, st);
+    if (t == max_iters) break;
+    cudaMemsetAsync(h->red + RED_NG_RESID, 0, sizeof(double), st);
+    run_vt(h, h->Kuu_lo, p->s, h->done);
+    run_sym<0>(h, h->done);
+    k_ng_check(h->red, h->M, 0.0, h->done, iters, h->resid_tmp, st);
+    run_lupd(h, L_inout, gamma_dev + t);
+    prep_L(h, L_inout, nullptr);
+  }
+  return check_launch(h, "svgp_ng_update_T_gap");
+}
+
 svgp_status svgp_train_step(svgp_handle* h, const svgp_params* p, const svgp_batch* b, float* L_inout,
                             const float* gamma_dev, int max_iters, double eps, int* iters_dev, double* residual_dev,
                             double* terms_dev, const svgp_grads* gr) {
   if (!h) return SVGP_ERR_INVALID_ARG;
-  if (!valid_params(p) || !valid_ng_args(p, L_inout, gamma_dev, max_iters))
+  if (!valid_params(h, p) || !valid_ng_args(p, L_inout, gamma_dev, max_iters))
     return fail(h, SVGP_ERR_INVALID_ARG, "train_step: null pointer or max_iters out of [0, 100000]");
   if (!valid_grads(gr)) return fail(h, SVGP_ERR_INVALID_ARG, "grads: null pointer");
   svgp_status s = validate_batch(h, b);
@@ -548,7 +662,7 @@ svgp_status svgp_train_step(svgp_handle* h, const svgp_params* p, const svgp_bat
 svgp_status svgp_predict(svgp_handle* h, const svgp_params* p, const float* Xs, int Ns, float* mean, float* var,
                          int include_noise) {
   if (!h) return SVGP_ERR_INVALID_ARG;
-  if (!valid_params(p) || !Xs || !mean || !var) return fail(h, SVGP_ERR_INVALID_ARG, "predict: null pointer");
+  if (!valid_params(h, p) || !Xs || !mean || !var) return fail(h, SVGP_ERR_INVALID_ARG, "predict: null pointer");
   if (Ns < 1 || Ns > h->Bmax) return fail(h, SVGP_ERR_INVALID_ARG, "predict: Ns out of [1, B_max]");
   cudaStream_t st = h->st;
   prologue(h, p, Xs, Ns, p->L);
@@ -556,7 +670,7 @@ svgp_status svgp_predict(svgp_handle* h, const svgp_params* p, const float* Xs, 
   if (!(h->tc_kuf && tc_kuf_gemv(h->kt.XR, Ns, h->kt.ZK, h->M, h->v, mean, h->errword, st)))
     k_mu(h->Zs, h->Xs, h->M, Ns, h->D, p->sf2, h->v, mean, st);
   cudaMemsetAsync(h->colsum, 0, sizeof(float) * Ns, st);
-  WEpi we{KufGen{h->Zs, h->Xs, h->D, h->M, Ns, p->sf2}, nullptr, nullptr, nullptr, nullptr, nullptr, 0.f,
+  WEpi we{KufGen{h->Zs, h->Xs, h->D, h->M, Ns, p->sf2}, nullptr, nullptr, nullptr, nullptr, 0.f,
           nullptr, h->colsum};
   run_w(h, we);
   k_predict_finalize(h->colsum, p->sf2, p->noise, Ns, include_noise, var, st);

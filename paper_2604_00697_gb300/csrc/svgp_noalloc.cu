@@ -126,7 +126,7 @@ extern "C" svgp_status svgp_predict_noalloc(const svgp_params* p, int M, int D, 
   simt_gemm(g, TT_OUT, Y, Llo, EpiP<float*>{P, P, Mp, M, p->s, nullptr, red});
   k_gemv(P, Mp, M, p->m, 1.f, nullptr, 0.f, v, nullptr, nullptr, st);
   k_mu(Zs, Xsc, M, Ns, D, p->sf2, v, mean, st);
-  WEpi we{KufGen{Zs, Xsc, D, M, Ns, p->sf2}, nullptr, nullptr, nullptr, nullptr, nullptr, 0.f, nullptr, colsum};
+  WEpi we{KufGen{Zs, Xsc, D, M, Ns, p->sf2}, nullptr, nullptr, nullptr, nullptr, 0.f, nullptr, colsum};
   simt_w(g, P, we);
   k_predict_finalize(colsum, p->sf2, p->noise, Ns, include_noise, var, st);
   return cudaGetLastError() == cudaSuccess ? SVGP_OK : SVGP_ERR_CUDA;

@@ -28,13 +28,17 @@ class RSVGP:
     m~ (M) | s~ (M)].  ``params`` points into the constrained vector.
     """
 
-    def __init__(self, M: int, D: int, B_max: int, prec: str = "bf16", device: str = "cuda"):
+    def __init__(self, M: int, D: int, B_max: int, prec: str = "bf16", device: str = "cuda",
+                 likelihood: str = "gaussian", gh_points: int = 20, precond: bool = True):
         if not torch.cuda.is_available():
             raise RuntimeError("RSVGP needs a CUDA device (no CPU fallback)")
         self.M, self.D, self.B_max = M, D, B_max
         self.prec = prec
+        self.likelihood = likelihood
         self.dev = torch.device(device)
-        self.h = C.svgp_create(M, D, B_max, PREC[prec], cuda_stream=torch.cuda.current_stream().cuda_stream)
+        lik = {"gaussian": C.SVGP_LIK_GAUSSIAN, "probit": C.SVGP_LIK_BERNOULLI_PROBIT}[likelihood]
+        self.h = C.svgp_create(M, D, B_max, PREC[prec], lik=lik, cuda_stream=torch.cuda.current_stream().cuda_stream,
+                               gh_points=gh_points, unpreconditioned=not precond)
         self.n = C.svgp_param_count(self.h)
         f32 = dict(device=self.dev, dtype=torch.float32)
         self.cons = torch.zeros(self.n, **f32)
@@ -120,6 +124,26 @@ class RSVGP:
             raise ValueError("max_iters larger than the gamma buffer")
         C.svgp_ng_update_T(self.h, self.params, self.L.data_ptr(), self.gamma.data_ptr(), max_iters, eps,
                            self.iters.data_ptr(), self.resid.data_ptr())
+
+    def variance_gap(self, X, y, N, sigma2=0.0):
+        """Prop. 3 gap G = sum_n ||(I - K~ T) k_un||^2 / sigma2 (sigma2 <= 0: min s~)."""
+        self._sync_stream()
+        gap = torch.zeros(1, device=self.dev, dtype=torch.float64)
+        C.svgp_variance_gap(self.h, self.params, self.batch(X, y, N), sigma2, gap.data_ptr())
+        return gap
+
+    def ng_update_gap(self, X, y, N, max_iters=1, eps=0.0, gammas=None, sigma2=0.0):
+        """NG updates of L with the Prop. 3 gap stopping rule (Section 3.3)."""
+        self._sync_stream()
+        if gammas is not None:
+            g = torch.as_tensor(gammas, dtype=torch.float32)
+            self.gamma[: g.numel()] = g.to(self.dev)
+        if max_iters > self.gamma.numel():
+            raise ValueError("max_iters larger than the gamma buffer")
+        gap = torch.zeros(1, device=self.dev, dtype=torch.float64)
+        C.svgp_ng_update_T_gap(self.h, self.params, self.batch(X, y, N), self.L.data_ptr(), self.gamma.data_ptr(),
+                               max_iters, eps, sigma2, self.iters.data_ptr(), gap.data_ptr())
+        return gap
 
     def predict(self, Xs, include_noise=False):
         self._sync_stream()

@@ -15,6 +15,11 @@ TOL = {  # relative bound error, per-block relative gradient error
 }
 # unit roundoff of the contraction operands: FP32, BF16, BF16 hi+lo pair
 UNIT = {"fp32": 2.0 ** -24, "bf16": 2.0 ** -9, "bf16x3": 2.0 ** -17}
+# relative accuracy of the generated Kuf values: FP32 exp of an FP32 squared
+# distance (a few ulp); BF16 values; hi + lo BF16 values of 2^t whose exponent
+# t comes from a hi/lo BF16 split of the coordinates (about 16 bits of
+# p . q, so |t| 2^-16 absolute, 2^-12 relative for |t| up to 16)
+UNIT_KUF = {"fp32": 2.0 ** -21, "bf16": 2.0 ** -9, "bf16x3": 2.0 ** -12}
 
 
 def cond_Kt(p):
@@ -107,3 +112,47 @@ def rel(a, b):
     b = np.asarray(b, np.float64)
     nb = np.linalg.norm(b)
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def kernel_rounding_sensitivity(p, X, y, N, prec, likelihood="gaussian", draws=3):
+    """Largest per-block change over `draws` random roundings (one draw is
+    noisy: a block's change depends on how the random signs line up)."""
+    outs = [_one_rounding_sensitivity(p, X, y, N, prec, likelihood, seed) for seed in range(draws)]
+    return {k: max(o[k] for o in outs) if all(np.isfinite(o[k]) for o in outs) else float("nan") for k in outs[0]}
+
+
+def _one_rounding_sensitivity(p, X, y, N, prec, likelihood="gaussian", seed=0):
+    """Relative change of each oracle gradient block when the kernel blocks
+    and L are perturbed elementwise by relative noise of the size of the
+    mode's accuracy (Kuu, L: the operand unit roundoff; Kuf: that of the
+    generated values): the error that rounding only those inputs would cause.  NaN where the perturbed problem has no finite gradient
+    (a perturbed sigma_n^2 went below 0).  Used where cond(K~) alone
+    underestimates the sensitivity of the gradient (dZ sums contributions
+    that cancel)."""
+    u, uf = UNIT[prec], UNIT_KUF[prec]
+    rng = np.random.default_rng([seed, 23])
+    base = O.grads(p, X, y, N, likelihood=likelihood)
+    orig = O.kernel_blocks
+
+    def perturbed(pp, XX):
+        Kuu, Kuf, knn, _ = orig(pp, XX)
+        E = 1.0 + u * rng.standard_normal(Kuu.shape)
+        Kuu = Kuu * (0.5 * (E + E.T))
+        Kuf = Kuf * (1.0 + uf * rng.standard_normal(Kuf.shape))
+        return Kuu, Kuf, knn, Kuu + np.diag(pp["s"])
+
+    q = dict(p)
+    q["L"] = np.asarray(p["L"], np.float64) * (1.0 + u * rng.standard_normal(np.shape(p["L"])))
+    O.kernel_blocks = perturbed
+    try:
+        with np.errstate(all="ignore"):
+            g = O.grads(q, X, y, N, likelihood=likelihood)
+    finally:
+        O.kernel_blocks = orig
+    out = {}
+    for k in BLOCKS:
+        a, b = np.asarray(g[k], np.float64), np.asarray(base[k], np.float64)
+        nb = np.linalg.norm(b)
+        out[k] = float(np.linalg.norm(a - b) / nb) if nb > 0 and np.all(np.isfinite(a)) else \
+            (0.0 if nb == 0 and np.all(a == 0) else float("nan"))
+    return out

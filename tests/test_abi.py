@@ -64,3 +64,20 @@ def test_status_strings_without_gpu(lib):
     lib.svgp_status_string.restype = ctypes.c_char_p
     assert lib.svgp_status_string(0) == b"ok"
     assert lib.svgp_status_string(1) == b"invalid argument"
+
+
+def test_gauss_hermite_rule_matches_numpy(lib):
+    """The library's host-side Gauss-Hermite rule (probit likelihood) against
+    numpy's hermgauss, and its argument checks.  Host code only."""
+    import numpy as np
+
+    from paper_2604_00697_gb300 import _lib
+
+    for n in (1, 2, 3, 7, 20, 32, 64):
+        t, w = _lib.svgp_gauss_hermite(n)
+        tr, wr = np.polynomial.hermite.hermgauss(n)
+        np.testing.assert_allclose(t, tr, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(w, wr, rtol=1e-11, atol=1e-300)
+    for bad in (0, 65, -3):
+        with pytest.raises(_lib.SvgpError):
+            _lib.svgp_gauss_hermite(bad)

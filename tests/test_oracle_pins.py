@@ -289,6 +289,35 @@ def test_prop3_variance_sandwich(seed):
     assert np.all(Ln <= varL + 1e-10) and np.all(varL <= U + 1e-10)
     G = np.array([np.sum(((np.eye(8) - Kt @ T) @ k) ** 2) / sig2 for k in Kuf.T])
     np.testing.assert_allclose(U - Ln, G, rtol=1e-8, atol=1e-10)
+    np.testing.assert_allclose(O.variance_gap(p, X, sig2), U - Ln, rtol=1e-8, atol=1e-10)
+
+
+def test_gap_vanishes_at_T_inverse_and_stops_ng():
+    """G = 0 at T = K~^-1 (Prop. 3: U_n = L_n there); the gap-rule NG loop
+    stops before updating once G <= 2 noise eps, and otherwise applies the
+    same NG steps as the plain loop."""
+    p = _spaced_state(9, 2, 3)
+    X, _ = _batch(40, 2, 3)
+    Kt = O.se_ard(p["Z"], p["Z"], p["ell"], p["sf2"]) + np.diag(p["s"])
+    q = dict(p)
+    q["L"] = np.linalg.cholesky(np.linalg.inv(Kt))
+    assert np.max(np.abs(O.variance_gap(q, X))) < 1e-10
+    L, it, G = O.ng_solve_gap(q, X, [1.0] * 5, eps=1e-6)
+    assert it == 0 and np.array_equal(L, q["L"]) and G < 1e-10
+    gam = [0.5, 1.0, 1.0, 1.0]
+    L1, it1, G1 = O.ng_solve_gap(p, X, gam, eps=0.0)
+    L2, it2, _ = O.ng_solve(np.asarray(p["L"], np.float64), Kt, gam)
+    assert it1 == it2 == 4 and np.allclose(L1, L2, rtol=0, atol=0)
+    # a threshold between two iterates stops at the first one below it
+    Gs = []
+    for t in range(4):
+        r = dict(p)
+        r["L"] = O.ng_solve(np.asarray(p["L"], np.float64), Kt, gam, max_iters=t)[0]
+        Gs.append(O.variance_gap(r, X).sum())
+    assert Gs[3] < Gs[0]
+    eps = 0.5 * (Gs[2] + Gs[3]) / (2.0 * p["noise"]) if Gs[3] < Gs[2] else Gs[3] / (2.0 * p["noise"])
+    L3, it3, G3 = O.ng_solve_gap(p, X, gam, eps=eps)
+    assert it3 == next(t for t in range(4) if Gs[t] <= 2.0 * p["noise"] * eps)
 
 
 def test_probit_quadrature_matches_adaptive_integral():
@@ -304,6 +333,139 @@ def test_probit_quadrature_matches_adaptive_integral():
         ref, _ = integrate.quad(f, mu[n] - 12 * math.sqrt(var[n]), mu[n] + 12 * math.sqrt(var[n]),
                                 epsabs=1e-13, epsrel=1e-13)
         assert abs(got[n] - ref) < 1e-6 * max(1.0, abs(ref))
+
+
+def test_probit_mean_variance_derivatives_match_integrals():
+    """g_n and h_n of the quadrature rule against adaptive integrals of the
+    exact derivatives: dE/dmu = E[s r(s f)] and, by Price's theorem,
+    dE/dsigma^2 = 1/2 E[d^2/df^2 log Phi(s f)] = -1/2 E[r(a) (a + r(a))], a = s f."""
+    from scipy import integrate
+    from scipy.special import log_ndtr
+    mu = np.array([-1.3, 0.2, 2.1, 0.0])
+    var = np.array([0.4, 1.7, 0.05, 1e-3])
+    y = np.array([1.0, 0.0, 1.0, 0.0])
+    _, g, h = O.probit_terms(y, mu, var)
+    for n in range(4):
+        s = 2 * y[n] - 1
+        sd = math.sqrt(var[n])
+
+        def r(a):
+            return math.exp(stats.norm.logpdf(a) - log_ndtr(a))
+
+        def integ(fn):
+            val, _ = integrate.quad(lambda t: stats.norm.pdf(t, mu[n], sd) * fn(s * t),
+                                    mu[n] - 12 * sd, mu[n] + 12 * sd, epsabs=1e-13, epsrel=1e-13)
+            return val
+        g_ref = s * integ(r)
+        h_ref = -0.5 * integ(lambda a: r(a) * (a + r(a)))
+        assert abs(g[n] - g_ref) < 1e-6 * max(1.0, abs(g_ref)), (n, g[n], g_ref)
+        assert abs(h[n] - h_ref) < 1e-6 * max(1.0, abs(h_ref)), (n, h[n], h_ref)
+        assert h[n] < 0.0          # log Phi is concave
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_probit_gradients_match_central_differences(seed):
+    p = _spaced_state(9, 2, seed)
+    X, _ = _batch(25, 2, seed)
+    y = (np.random.default_rng([seed, 5]).uniform(size=25) < 0.5).astype(np.float64)
+    N = 211.0
+    g = O.grads(p, X, y, N, likelihood="probit")
+    assert g["noise"] == 0.0
+
+    def F(pp):
+        return O.bound(pp, X, y, N, likelihood="probit")["F"]
+
+    for k in ["Z", "ell", "sf2", "m", "s"]:
+        x = np.asarray(p[k], np.float64)
+        fd = np.zeros(x.shape)
+        for idx in np.ndindex(x.shape):
+            h = 1e-6 * max(1.0, abs(float(x[idx])))
+            xp, xm = x.copy(), x.copy()
+            xp[idx] += h
+            xm[idx] -= h
+            pp, pm = dict(p), dict(p)
+            pp[k] = xp if x.ndim else float(xp)
+            pm[k] = xm if x.ndim else float(xm)
+            fd[idx] = (F(pp) - F(pm)) / (2 * h)
+        err = np.linalg.norm(fd - g[k]) / np.linalg.norm(fd)
+        assert err < 1e-6, (k, err)
+
+
+def _lsvgp_bound(p, X, y, N):
+    """L-SVGP bound (Section 2) with m = Kuu m~ and an explicit inverse of K~."""
+    Kuu = O.se_ard(p["Z"], p["Z"], p["ell"], p["sf2"])
+    Kuf = O.se_ard(p["Z"], X, p["ell"], p["sf2"])
+    Kt = Kuu + np.diag(p["s"])
+    Ki = np.linalg.inv(Kt)
+    mu = Kuf.T @ p["m"]
+    var = p["sf2"] - np.einsum("in,in->n", Kuf, Ki @ Kuf)
+    noise = p["noise"]
+    En = -0.5 * np.log(2 * np.pi * noise) - ((y - mu) ** 2 + var) / (2 * noise)
+    KL = 0.5 * (-np.trace(Ki @ Kuu) + p["m"] @ Kuu @ p["m"] + np.linalg.slogdet(Kt)[1] - np.sum(np.log(p["s"])))
+    return (N / X.shape[0]) * En.sum() - KL
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_unpreconditioned_bound_equals_lsvgp_at_T_inverse(seed):
+    """Without the preconditioner the R-SVGP bound equals the L-SVGP bound at
+    T = K~^-1 and lies below it elsewhere (the KL bound of Section 2 is an
+    upper bound with equality at T = K~^-1)."""
+    p = _spaced_state(10, 2, seed)
+    X, y = _batch(30, 2, seed)
+    N = 90.0
+    Kt = O.se_ard(p["Z"], p["Z"], p["ell"], p["sf2"]) + np.diag(p["s"])
+    ref = _lsvgp_bound(p, X, y, N)
+    assert O.bound(p, X, y, N, precond=False)["F"] <= ref + 1e-9
+    p["L"] = np.linalg.cholesky(np.linalg.inv(Kt))
+    assert abs(O.bound(p, X, y, N, precond=False)["F"] - ref) < 1e-9 * max(1.0, abs(ref))
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_unpreconditioned_bound_below_exact_elbo_of_implied_q(seed):
+    """m = Kuu m~, S = Kuu - Kuu P Kuu: the bound is below the exact M-SVGP ELBO."""
+    p = _spaced_state(8, 2, seed)
+    X, y = _batch(20, 2, seed)
+    N = 60.0
+    Kuu = O.se_ard(p["Z"], p["Z"], p["ell"], p["sf2"])
+    Kt = Kuu + np.diag(p["s"])
+    q = dict(p)
+    # the exact ELBO helper implies m = Kuu P m~; choose m~' with P m~' = m~
+    T = p["L"] @ p["L"].T
+    P = 2 * T - T @ Kt @ T
+    q["m"] = np.linalg.solve(P, p["m"])
+    exact = _msvgp_elbo(q, X, y, N)[0]
+    assert O.bound(p, X, y, N, precond=False)["F"] <= exact + 1e-9
+
+
+@pytest.mark.parametrize("lik", ["gaussian", "probit"])
+def test_unpreconditioned_gradients_match_central_differences(lik):
+    p = _spaced_state(7, 2, 4)
+    X, y = _batch(18, 2, 4)
+    if lik == "probit":
+        y = (y > 0).astype(np.float64)
+    N = 70.0
+    g = O.grads(p, X, y, N, likelihood=lik, precond=False)
+
+    def F(pp):
+        return O.bound(pp, X, y, N, likelihood=lik, precond=False)["F"]
+
+    for k in ["Z", "ell", "sf2", "noise", "m", "s"]:
+        if lik == "probit" and k == "noise":
+            assert g[k] == 0.0
+            continue
+        x = np.asarray(p[k], np.float64)
+        fd = np.zeros(x.shape)
+        for idx in np.ndindex(x.shape):
+            h = 1e-6 * max(1.0, abs(float(x[idx])))
+            xp, xm = x.copy(), x.copy()
+            xp[idx] += h
+            xm[idx] -= h
+            pp, pm = dict(p), dict(p)
+            pp[k] = xp if x.ndim else float(xp)
+            pm[k] = xm if x.ndim else float(xm)
+            fd[idx] = (F(pp) - F(pm)) / (2 * h)
+        err = np.linalg.norm(fd - g[k]) / np.linalg.norm(fd)
+        assert err < 1e-6, (k, err)
 
 
 def test_predict_exact_gp_posterior():
