@@ -339,28 +339,41 @@ def run_ours(args):
     tot_ms, value = reduce_timing(sum(dev_ms), args.steps, ws)
     ms_per_step = tot_ms / args.steps
 
-    # end to end through the public API with host buffers: H2D of the batch
-    # from pinned memory, the step (eager calls), D2H of the bound.
+    # end to end through the public API with host buffers: every step copies
+    # its minibatch from pinned host memory into the model's input buffers,
+    # replays the training step captured once on those buffers
+    # (RSVGP.capture) and reads the bound back to the host.
     hX = [torch.tensor(b[0], dtype=torch.float32).pin_memory() for b in batches]
     hy = [torch.tensor(b[1], dtype=torch.float32).pin_memory() for b in batches]
     hout = torch.empty(1, dtype=torch.float64).pin_memory()
     Xin = torch.empty(B, D, device="cuda")
     yin = torch.empty(B, device="cuda")
-    for i in range(3):
+    Xin.copy_(Xd[0])
+    yin.copy_(yd[0])
+    s2 = torch.cuda.Stream()
+    s2.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s2):
         m.train_step(Xin, yin, N)
+        torch.cuda.synchronize()
+        ge = m.capture(Xin, yin, N)
+    torch.cuda.current_stream().wait_stream(s2)
+    torch.cuda.synchronize()
+    for i in range(3):
+        ge.replay()
     torch.cuda.synchronize()
     e2e_steps = max(5, args.steps // 2)
     t0 = time.perf_counter()
     for i in range(e2e_steps):
         Xin.copy_(hX[i % pool], non_blocking=True)
         yin.copy_(hy[i % pool], non_blocking=True)
-        terms = m.train_step(Xin, yin, N)
-        hout.copy_(terms[:1], non_blocking=True)
+        ge.replay()
+        hout.copy_(m.terms[:1], non_blocking=True)
     torch.cuda.synchronize()
     e2e_wall = time.perf_counter() - t0
     e2e = {"value": ws * e2e_steps / e2e_wall, "unit": "steps/s",
            "h2d_bytes_per_step": int(B * D * 4 + B * 4), "d2h_bytes_per_step": 8,
-           "path": "eager svgp_train_step (NG update + bound + backward) + svgp_adam_step via the ctypes binding"}
+           "path": "host->device copy of the minibatch, replay of the step captured with RSVGP.capture "
+                   "(svgp_train_step + svgp_adam_step), device->host copy of the bound"}
 
     ok_status = m.sync_status()
     line = {
@@ -435,7 +448,10 @@ def validate(prec, prob):
     f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
     X, y = f32(X), f32(y)
     out = {}
-    p = dict(Z=f32(prob.Z0), ell=np.ones(D), sf2=1.0, noise=1.0, m=np.zeros(M), s=f32(np.full(M, 1e-4)),
+    # probit configuration: s~ = 0.5 (with s~ = 1e-4 and 256 inducing points on
+    # the 2-D crescents cond(K~) is about 1e8 and BF16 NG iterations diverge)
+    s0 = 0.5 if prob.likelihood == "probit" else 1e-4
+    p = dict(Z=f32(prob.Z0), ell=np.ones(D), sf2=1.0, noise=1.0, m=np.zeros(M), s=f32(np.full(M, s0)),
              L=f32(1e-3 * np.eye(M)))
     m = RSVGP(M, D, prob.B, prec=prec, likelihood=prob.likelihood)
     for name in ("init", "ng40"):

@@ -59,6 +59,34 @@ __device__ __forceinline__ void put(const SplitPtr& p, size_t i, float x) {
 
 // Reduce a per-thread double over the block and add it to *dst (one atomic
 // per block).  Must be called by all threads of the block (any block shape).
+// Programmatic dependent launch.  Every kernel of the library starts with
+// pdl_enter(): it waits until the kernel launched before it on the stream has
+// completed and its memory is visible (a no-op without a programmatic
+// dependency), then allows the next kernel to be launched, so that kernel's
+// launch and CTA placement overlap this kernel's run.  No kernel touches
+// global memory (or allocates TMEM) before the wait.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Host side: launch `kern` with programmatic stream serialization allowed.
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<Args&&>(args)...);
+}
+
 __device__ __forceinline__ void block_add_double(double x, double* dst) {
   __shared__ double red_buf[32];
   const unsigned tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);

@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 psi_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // z, row role
               const __grid_constant__ CUtensorMap tmK,       // x, k role
               const Tile* __restrict__ tiles, int nkb, int* errword, EpiPsi epsi) {
+  pdl_enter();
   using G = PsiGeo<NSPLIT>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -242,6 +243,7 @@ psi_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // z, row role
 // value carries a factor sqrt|hw_r|.  R may be null (k role only).
 __global__ void kuf_prep_kernel(const float* __restrict__ P, int n, int npad, int D, const float* __restrict__ sf2,
                                 const float* __restrict__ hw, bf16* __restrict__ R, bf16* __restrict__ K) {
+  pdl_enter();
   // one row per threadIdx.y (8 rows per block), 64 threads per row
   __shared__ float part_sum[8][2];
   const int Dp = (D + 3) & ~3;
@@ -297,10 +299,10 @@ void k_kuf_prep(const float* Zs, const float* Xs, int M, int Mp, int B, int Bp, 
                 const KufTC& t, cudaStream_t st) {
   dim3 blk(64, 8);
   svgp_note_launch();
-  kuf_prep_kernel<<<(Mp + 7) / 8, blk, 0, st>>>(Zs, M, Mp, D, sf2, nullptr, t.ZR, t.ZK);
+  pdl_launch(kuf_prep_kernel, (Mp + 7) / 8, blk, 0, st, Zs, M, Mp, D, sf2, nullptr, t.ZR, t.ZK);
   if (Xs && B > 0) {
     svgp_note_launch();
-    kuf_prep_kernel<<<(Bp + 7) / 8, blk, 0, st>>>(Xs, B, Bp, D, sf2, nullptr, t.XR, t.XK);
+    pdl_launch(kuf_prep_kernel, (Bp + 7) / 8, blk, 0, st, Xs, B, Bp, D, sf2, nullptr, t.XR, t.XK);
   }
 }
 
@@ -308,7 +310,7 @@ void k_kuf_prep_weighted(const float* Xs, int B, int Bp, int D, const float* sf2
                          cudaStream_t st) {
   dim3 blk(64, 8);
   svgp_note_launch();
-  kuf_prep_kernel<<<(Bp + 7) / 8, blk, 0, st>>>(Xs, B, Bp, D, sf2, h, nullptr, XKh);
+  pdl_launch(kuf_prep_kernel, (Bp + 7) / 8, blk, 0, st, Xs, B, Bp, D, sf2, h, nullptr, XKh);
 }
 
 void tc_kuf_init_attributes() {
@@ -327,8 +329,8 @@ bool tc_psi(const GemmCtx& g, const KufGen& kg, const KufTC& t, const bf16* Kk, 
   if (!tc_make_map(&mr, t.ZR, g.Mp, 64, 128) || !tc_make_map(&mk, Kk, Bp, 64, 64)) return false;
   svgp_note_launch();
   if (g.split)
-    psi_tc_kernel<3><<<g.nt[TT_PSI], THREADS, PsiGeo<3>::SMEM, g.st>>>(mr, mk, g.tt[TT_PSI], Bp / KB, g.err, e);
+    pdl_launch(psi_tc_kernel<3>, g.nt[TT_PSI], THREADS, PsiGeo<3>::SMEM, g.st, mr, mk, g.tt[TT_PSI], Bp / KB, g.err, e);
   else
-    psi_tc_kernel<1><<<g.nt[TT_PSI], THREADS, PsiGeo<1>::SMEM, g.st>>>(mr, mk, g.tt[TT_PSI], Bp / KB, g.err, e);
+    pdl_launch(psi_tc_kernel<1>, g.nt[TT_PSI], THREADS, PsiGeo<1>::SMEM, g.st, mr, mk, g.tt[TT_PSI], Bp / KB, g.err, e);
   return true;
 }

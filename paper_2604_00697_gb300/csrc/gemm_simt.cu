@@ -171,6 +171,7 @@ constexpr size_t SIMT_SMEM = sizeof(float) * SB * (SB + 1) > sizeof(Smem) ? size
 template <class Epi, class LA, class LB>
 __global__ void __launch_bounds__(256) simt_gemm_tiles(const Tile* __restrict__ tiles, LA la, LB lb,
                                                        Epi epi, int kb_over, int ke_over) {
+  pdl_enter();
   if (epi.skip()) return;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   Smem& sm = *reinterpret_cast<Smem*>(dyn_smem);
@@ -188,6 +189,7 @@ __global__ void __launch_bounds__(256) simt_gemm_tiles(const Tile* __restrict__ 
 // W = P Kuf tile (rows i of P, columns n of the batch) with the fused
 // backward/predict epilogue (see WEpi in common.cuh).
 __global__ void __launch_bounds__(256) simt_w_kernel(MemLoad la, GenLoad lb, int Mp, WEpi we) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char dyn[];
   Smem& sm = *reinterpret_cast<Smem*>(dyn);
   float* T = reinterpret_cast<float*>(dyn);                  // reused after the mainloop
@@ -303,7 +305,7 @@ template <class Epi>
 void simt_gemm(const GemmCtx& g, int tab, const float* A, const float* B, const Epi& e) {
   MemLoad la{A, g.Mp}, lb{B, g.Mp};
   svgp_note_launch();
-  simt_gemm_tiles<Epi, MemLoad, MemLoad><<<g.nt[tab], 256, SIMT_SMEM, g.st>>>(g.tt[tab], la, lb, e, 0, 0);
+  pdl_launch(simt_gemm_tiles<Epi, MemLoad, MemLoad>, g.nt[tab], 256, SIMT_SMEM, g.st, g.tt[tab], la, lb, e, 0, 0);
 }
 
 template void simt_gemm<EpiVt<float*>>(const GemmCtx&, int, const float*, const float*, const EpiVt<float*>&);
@@ -322,7 +324,7 @@ void simt_psi(const GemmCtx& g, const KufGen& kg, int B, EpiPsi e, const float* 
   GenLoad la{kg.Zs, kg.M, kg.Xs, B, Dp, kg.sf2, hw}, lb{kg.Zs, kg.M, kg.Xs, B, Dp, kg.sf2, hw};
   int Bp = (B + SK - 1) / SK * SK;
   svgp_note_launch();
-  simt_gemm_tiles<EpiPsi, GenLoad, GenLoad><<<g.nt[TT_PSI], 256, SIMT_SMEM, g.st>>>(g.tt[TT_PSI], la, lb, e, 0, Bp);
+  pdl_launch(simt_gemm_tiles<EpiPsi, GenLoad, GenLoad>, g.nt[TT_PSI], 256, SIMT_SMEM, g.st, g.tt[TT_PSI], la, lb, e, 0, Bp);
 }
 
 void simt_w(const GemmCtx& g, const float* P, const WEpi& we) {
@@ -333,7 +335,7 @@ void simt_w(const GemmCtx& g, const float* P, const WEpi& we) {
   size_t smem = sizeof(float) * (SB * (SB + 1) + SB * Dp);
   if (smem < sizeof(Smem)) smem = sizeof(Smem);
   svgp_note_launch();
-  simt_w_kernel<<<grid, 256, smem, g.st>>>(la, lb, g.Mp, we);
+  pdl_launch(simt_w_kernel, grid, 256, smem, g.st, la, lb, g.Mp, we);
 }
 
 void simt_init_attributes() {

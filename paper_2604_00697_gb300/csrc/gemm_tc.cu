@@ -57,6 +57,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                const __grid_constant__ CUtensorMap tmAl, const __grid_constant__ CUtensorMap tmBl,
                const Tile* __restrict__ tiles, const int* __restrict__ toff, Epi epi, int* errword,
                const __grid_constant__ etc::EpiMaps maps) {
+  pdl_enter();
   using G = Geo<NSPLIT>;
   constexpr int S = G::STAGES;
   if (epi.skip()) return;
@@ -367,10 +368,10 @@ bool tc_gemm(const GemmCtx& g, int tab, const bf16* A, const bf16* B, const Epi&
   if (g.split) {
     if (!tc_make_map(&mal, A + MM, g.Mp, g.Mp, 128) || !tc_make_map(&mbl, B + MM, g.Mp, g.Mp, 128)) return false;
     svgp_note_launch();
-    tc_gemm_kernel<Epi, 3><<<grid, 192, Geo<3>::SMEM, g.st>>>(ma, mb, mal, mbl, g.tt[tab], g.toff[tab], e, g.err, em);
+    pdl_launch(tc_gemm_kernel<Epi, 3>, grid, 192, Geo<3>::SMEM, g.st, ma, mb, mal, mbl, g.tt[tab], g.toff[tab], e, g.err, em);
   } else {
     svgp_note_launch();
-    tc_gemm_kernel<Epi, 1><<<grid, 192, Geo<1>::SMEM, g.st>>>(ma, mb, ma, mb, g.tt[tab], g.toff[tab], e, g.err, em);
+    pdl_launch(tc_gemm_kernel<Epi, 1>, grid, 192, Geo<1>::SMEM, g.st, ma, mb, ma, mb, g.tt[tab], g.toff[tab], e, g.err, em);
   }
   return true;
 }

@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CUtensorMap tmZK,
             const __grid_constant__ CUtensorMap tmXR, const __grid_constant__ CUtensorMap tmXK,
             const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmPl, WArgs wa, WEpi we) {
+  pdl_enter();
   using G = WGeo<NSPLIT>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -381,13 +382,13 @@ void launch_w(dim3 grid, cudaStream_t st, const CUtensorMap (&m)[6], const WArgs
   const int D = we.gen.D;
   svgp_note_launch();
   if (D <= 4)
-    w_tc_kernel<NSPLIT, 4><<<grid, THREADS, WGeo<NSPLIT>::SMEM, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
+    pdl_launch(w_tc_kernel<NSPLIT, 4>, grid, THREADS, WGeo<NSPLIT>::SMEM, st, m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
   else if (D <= 8)
-    w_tc_kernel<NSPLIT, 8><<<grid, THREADS, WGeo<NSPLIT>::SMEM, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
+    pdl_launch(w_tc_kernel<NSPLIT, 8>, grid, THREADS, WGeo<NSPLIT>::SMEM, st, m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
   else if (D <= 16)
-    w_tc_kernel<NSPLIT, 16><<<grid, THREADS, WGeo<NSPLIT>::SMEM, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
+    pdl_launch(w_tc_kernel<NSPLIT, 16>, grid, THREADS, WGeo<NSPLIT>::SMEM, st, m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
   else
-    w_tc_kernel<NSPLIT, 24><<<grid, THREADS, WGeo<NSPLIT>::SMEM, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
+    pdl_launch(w_tc_kernel<NSPLIT, 24>, grid, THREADS, WGeo<NSPLIT>::SMEM, st, m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
 }
 
 }  // namespace

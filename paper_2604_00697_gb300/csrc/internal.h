@@ -100,6 +100,10 @@ void k_kt_f32(const float* Kuu, const float* s, int M, int Mp, float* Kt, cudaSt
 // be null); with eps > 0 sets *done when G <= 2 noise eps.
 void k_gap_check(const double* red, const float* s, int M, double sigma2_host, const float* noise, double eps,
                  int* done, double* gap, cudaStream_t st);
+// Zero up to three device ranges (byte counts, multiples of 4) in one launch
+// (a kernel rather than memset nodes keeps the step's launches programmatic).
+void k_zero(cudaStream_t st, void* p0, size_t b0, void* p1 = nullptr, size_t b1 = 0, void* p2 = nullptr,
+            size_t b2 = 0);
 // y = alpha (x + beta x2), n elements.
 void k_axpy(const float* x, float alpha, const float* x2, float beta, float* y, int n, cudaStream_t st);
 void k_pointwise_gauss(const float* y, const float* mu, const float* noise, int B, float* g,
@@ -139,5 +143,7 @@ void k_predict_finalize(const float* colsum, const float* sf2, const float* nois
                         int include_noise, float* var, cudaStream_t st);
 void k_adam(float* raw, float* cons, const float* grad, float* m1, float* m2, int* step,
             const float* hyper, const float* zbeta1, int M, int D, cudaStream_t st);
-void k_ng_check(const double* red, int M, double eps, int* done, int* iters, double* resid,
+// Eq. (8) stopping rule from red[RED_NG_RESID], which it resets to 0 for the
+// next iteration.
+void k_ng_check(double* red, int M, double eps, int* done, int* iters, double* resid,
                 cudaStream_t st);

@@ -19,6 +19,7 @@ __device__ __forceinline__ float warp_sum(float x) {
 __global__ void prep_coords_kernel(const float* __restrict__ Z, const float* __restrict__ X,
                                    const float* __restrict__ ell, int M, int Mp, int B, int D,
                                    float* __restrict__ Zs, float* __restrict__ Xs) {
+  pdl_enter();
   int Dp = (D + 3) & ~3;
   int tot = (Mp + B) * Dp;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
@@ -39,6 +40,7 @@ template <class OutP, int DP>
 __global__ void __launch_bounds__(256) kuu_kernel(const float* __restrict__ Zs, int M, int Mp, int D,
                                                   const float* __restrict__ sf2p, float* __restrict__ Kf,
                                                   OutP Klo, bool has_lo) {
+  pdl_enter();
   __shared__ float zi[64][DP + 1], zj[64][DP + 1];
   const int Dp = (D + 3) & ~3;
   const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
@@ -77,6 +79,7 @@ __global__ void __launch_bounds__(256) kuu_kernel(const float* __restrict__ Zs, 
 template <class OutP>
 __global__ void prep_L_kernel(const float* __restrict__ Lin, int M, int Mp, float* __restrict__ Lf,
                               OutP Llo, OutP Ltlo, double* logdet) {
+  pdl_enter();
   __shared__ float tile[32][33];
   int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
   // Blocks strictly above the diagonal stay zero in L (and below it in L^T):
@@ -101,13 +104,28 @@ __global__ void prep_L_kernel(const float* __restrict__ Lin, int M, int Mp, floa
 }
 
 // y = alpha * A (x + beta * x2)  (A: Mp x Mp FP32, rows < M); one warp per
-// row, the combined vector staged once per block in shared memory (Mp floats
-// of dynamic shared memory).  Optionally dot_out += sum_i y_i dotw_i.
+// row.  A lane issues the loads of its first 16 float4 of the row before the
+// combined vector is staged in shared memory (Mp floats of dynamic shared
+// memory), so the row's memory latency overlaps the staging; longer rows
+// continue in chunks of 16 float4 per lane.  Optionally
+// dot_out += sum_i y_i dotw_i.
 __global__ void __launch_bounds__(256) gemv_kernel(const float* __restrict__ A, int Mp, int M,
                                                    const float* __restrict__ x, float alpha,
                                                    const float* __restrict__ x2, float beta, float* __restrict__ y,
                                                    const float* __restrict__ dotw, double* dot_out) {
+  pdl_enter();
   extern __shared__ float xs[];
+  constexpr int CH = 16;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int n4 = Mp / 4;
+  const bool live = warp < M;
+  const float4* row = reinterpret_cast<const float4*>(A + (size_t)(live ? warp : 0) * Mp);
+  float4 a[CH];
+#pragma unroll
+  for (int u = 0; u < CH; ++u) {
+    const int k = lane + 32 * u;
+    a[u] = (live && k < n4) ? __ldg(row + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   for (int j = threadIdx.x; j < Mp; j += blockDim.x) {
     float xx = 0.f;
     if (j < M) {
@@ -117,27 +135,23 @@ __global__ void __launch_bounds__(256) gemv_kernel(const float* __restrict__ A, 
     xs[j] = xx;
   }
   __syncthreads();
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   double part = 0.0;
-  if (warp < M) {
-    const float4* row = reinterpret_cast<const float4*>(A + (size_t)warp * Mp);
+  if (live) {
     const float4* xv = reinterpret_cast<const float4*>(xs);
     float acc0 = 0.f, acc1 = 0.f;
-    const int n4 = Mp / 4;
-    // batches of 8 float4 per lane: all loads of a batch are in flight together
-    for (int k0 = lane; k0 < n4; k0 += 8 * 32) {
-      float4 a[8];
+    for (int k0 = 0;; k0 += 32 * CH) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int k = k0 + 32 * u;
-        a[u] = k < n4 ? __ldg(row + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int k = min(k0 + 32 * u, n4 - 1);
+      for (int u = 0; u < CH; ++u) {
+        const int k = min(k0 + lane + 32 * u, n4 - 1);
         const float4 b = xv[k];
         acc0 = fmaf(a[u].x, b.x, acc0); acc1 = fmaf(a[u].y, b.y, acc1);
         acc0 = fmaf(a[u].z, b.z, acc0); acc1 = fmaf(a[u].w, b.w, acc1);
+      }
+      if (k0 + 32 * CH >= n4) break;
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const int k = k0 + 32 * CH + lane + 32 * u;
+        a[u] = k < n4 ? __ldg(row + k) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
     const float acc = warp_sum(acc0 + acc1) * alpha;
@@ -171,6 +185,7 @@ template <int DP>
 __global__ void mu_kernel(const float* __restrict__ Zs, const float* __restrict__ Xs, int M, int B,
                           int D, const float* __restrict__ sf2p, const float* __restrict__ v,
                           float* __restrict__ mu) {
+  pdl_enter();
   __shared__ float zs[64][DP + 1];
   __shared__ float vs[64];
   const int Dp = (D + 3) & ~3;
@@ -216,6 +231,7 @@ __global__ void mu_kernel(const float* __restrict__ Zs, const float* __restrict_
 __global__ void pointwise_gauss_kernel(const float* __restrict__ y, const float* __restrict__ mu,
                                        const float* __restrict__ noise, int B, float* __restrict__ g,
                                        double* red) {
+  pdl_enter();
   double part = 0.0;
   float inv = 1.0f / *noise;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < B; n += gridDim.x * blockDim.x) {
@@ -231,6 +247,7 @@ template <int DP>
 __global__ void kg_kernel(const float* __restrict__ Zs, const float* __restrict__ Xs, int M, int B,
                           int D, const float* __restrict__ sf2p, const float* __restrict__ g,
                           float* __restrict__ Kg) {
+  pdl_enter();
   __shared__ float xs[64][DP + 1];
   __shared__ float gs[64];
   const int Dp = (D + 3) & ~3;
@@ -280,6 +297,7 @@ __global__ void gp_assemble_kernel(const float* __restrict__ Kuu, const float* _
                                    const float* __restrict__ Kg, const float* __restrict__ m,
                                    const float* __restrict__ w, const float* __restrict__ noise, float c,
                                    int M, int Mp, OutP out) {
+  pdl_enter();
   // block: row i = blockIdx.y, 4 consecutive columns per thread
   const float cn = noise ? c * 0.5f / *noise : c;   // probit: Psi = Kuf diag(|h|) Kuf^T
   const int i = blockIdx.y;
@@ -307,18 +325,22 @@ __global__ void gp_assemble_kernel(const float* __restrict__ Kuu, const float* _
 // Kuu-side chain rule: with A_ij = G_Kuu_ij Kuu_ij and e_d = z~_jd - z~_id,
 //   rowacc[i][d] += sum_j A_ij e_d,  rowacc[i][D + d] += sum_j A_ij e_d^2,
 //   rowacc[i][2D] += sum_j A_ij.
+// Accumulated in the expanded form S0 = sum_j A_ij, S1_d = sum_j A_ij z~_jd,
+// S2_d = sum_j A_ij z~_jd^2 (two FMAs per dimension and element) and reported
+// as S1_d - z~_id S0 and S2_d - 2 z~_id S1_d + z~_id^2 S0.
 // Block = 32 rows (lane = row i) x a range of at most 256 columns j, split
 // over the 8 warps.  A is symmetric, so A_ij is read as A[j][i]: a warp reads
-// 32 consecutive floats of row j (four rows in flight per warp).  z~_j of the
-// range is staged in shared memory and read as broadcasts.  Warp partials
-// meet in shared memory; one atomic per row and value per block.
+// 32 consecutive floats of row j (four rows in flight per warp).  z~_j and
+// z~_j^2 of the range are staged in shared memory and read as broadcasts.
+// Warp partials meet in shared memory; one atomic per row and value per block.
 template <int DP>
 __global__ void __launch_bounds__(256) kuu_bwd_kernel(const float* __restrict__ GK, const float* __restrict__ Kuu,
                                                      const float* __restrict__ Zs, int M, int Mp, int D,
                                                      float* __restrict__ rowacc, int JB) {
+  pdl_enter();
   constexpr int W = 2 * DP + 1;
   constexpr int U = 4;
-  __shared__ __align__(16) float zs[256][DP];
+  __shared__ __align__(16) float zs[256][2 * DP];
   __shared__ float part[32][W + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * 32 + lane;
@@ -327,11 +349,13 @@ __global__ void __launch_bounds__(256) kuu_bwd_kernel(const float* __restrict__ 
   for (int e = threadIdx.x; e < 32 * (W + 1); e += 256) (&part[0][0])[e] = 0.f;
   for (int e = threadIdx.x; e < JB * DP; e += 256) {
     const int r = e / DP, d = e - r * DP;
-    zs[r][d] = (jb + r < je && d < Dp) ? __ldg(Zs + (size_t)(jb + r) * Dp + d) : 0.f;
+    const float zv = (jb + r < je && d < Dp) ? __ldg(Zs + (size_t)(jb + r) * Dp + d) : 0.f;
+    zs[r][d] = zv;
+    zs[r][DP + d] = zv * zv;
   }
-  float z[DP], aZ[DP], aL[DP], aS = 0.f;
+  float S1[DP], S2[DP], S0 = 0.f;
 #pragma unroll
-  for (int d = 0; d < DP; ++d) { z[d] = (i < M && d < Dp) ? Zs[(size_t)i * Dp + d] : 0.f; aZ[d] = 0.f; aL[d] = 0.f; }
+  for (int d = 0; d < DP; ++d) { S1[d] = 0.f; S2[d] = 0.f; }
   __syncthreads();
   if (i < M) {
     for (int j = jb + warp; j < je; j += 8 * U) {
@@ -345,28 +369,32 @@ __global__ void __launch_bounds__(256) kuu_bwd_kernel(const float* __restrict__ 
       for (int u = 0; u < U; ++u) {
         const int jj = min(j + 8 * u, je - 1) - jb;
         const float4* zj = reinterpret_cast<const float4*>(&zs[jj][0]);
-        aS += a[u];
+        S0 += a[u];
 #pragma unroll
         for (int d4 = 0; d4 < DP / 4; ++d4) {
-          const float4 q = zj[d4];
-          const float qq[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const int d = 4 * d4 + v;
-            const float e = qq[v] - z[d];
-            const float ae = a[u] * e;
-            aZ[d] += ae;
-            aL[d] = fmaf(ae, e, aL[d]);
-          }
+          const float4 q = zj[d4], q2 = zj[DP / 4 + d4];
+          S1[4 * d4 + 0] = fmaf(a[u], q.x, S1[4 * d4 + 0]);
+          S1[4 * d4 + 1] = fmaf(a[u], q.y, S1[4 * d4 + 1]);
+          S1[4 * d4 + 2] = fmaf(a[u], q.z, S1[4 * d4 + 2]);
+          S1[4 * d4 + 3] = fmaf(a[u], q.w, S1[4 * d4 + 3]);
+          S2[4 * d4 + 0] = fmaf(a[u], q2.x, S2[4 * d4 + 0]);
+          S2[4 * d4 + 1] = fmaf(a[u], q2.y, S2[4 * d4 + 1]);
+          S2[4 * d4 + 2] = fmaf(a[u], q2.z, S2[4 * d4 + 2]);
+          S2[4 * d4 + 3] = fmaf(a[u], q2.w, S2[4 * d4 + 3]);
         }
       }
     }
   }
+  const float* zi = Zs + (size_t)(i < M ? i : 0) * Dp;
 #pragma unroll
   for (int d = 0; d < DP; ++d) {
-    if (d < D) { atomicAdd(&part[lane][d], aZ[d]); atomicAdd(&part[lane][D + d], aL[d]); }
+    if (d < D) {
+      const float z = i < M ? __ldg(zi + d) : 0.f;
+      atomicAdd(&part[lane][d], fmaf(-z, S0, S1[d]));
+      atomicAdd(&part[lane][D + d], fmaf(z, fmaf(z, S0, -2.0f * S1[d]), S2[d]));
+    }
   }
-  atomicAdd(&part[lane][2 * D], aS);
+  atomicAdd(&part[lane][2 * D], S0);
   __syncthreads();
   const int Wd = 2 * D + 1;
   for (int e = threadIdx.x; e < 32 * Wd; e += 256) {
@@ -377,6 +405,7 @@ __global__ void __launch_bounds__(256) kuu_bwd_kernel(const float* __restrict__ 
 }
 
 __global__ void logs_kernel(const float* __restrict__ s, int M, double* red) {
+  pdl_enter();
   double part = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x)
     part += log((double)s[i]);
@@ -394,6 +423,7 @@ __global__ void __launch_bounds__(256) grad_finalize_kernel(const float* __restr
                                                             const float* __restrict__ rowpart, int nparts, int Mp,
                                                             const float* __restrict__ ell, int M, int D,
                                                             float* __restrict__ dZ, double* acc_ell, double* red) {
+  pdl_enter();
   constexpr int RB = 16;
   __shared__ float tf[RB][2 * SVGP_MAXD + 2];
   const int W = 2 * D + 1;
@@ -447,6 +477,7 @@ __global__ void terms_finalize_kernel(const double* __restrict__ red, const doub
                                       const float* __restrict__ ell, int M, int D, int B, double N, bool probit,
                                       double* terms, float* dsf2, float* dnoise, float* dell,
                                       int* errword) {
+  pdl_enter();
   if (threadIdx.x != 0) return;
   double sf2 = *sf2p, noise = probit ? 1.0 : *noisep, c = N / B;
   double trA1 = red[RED_TRA1], froA1 = red[RED_FROA1];
@@ -481,6 +512,7 @@ __global__ void terms_finalize_kernel(const double* __restrict__ red, const doub
 __global__ void predict_finalize_kernel(const float* __restrict__ colsum, const float* __restrict__ sf2,
                                         const float* __restrict__ noise, int Ns, int inc,
                                         float* __restrict__ var) {
+  pdl_enter();
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= Ns) return;
   float v = *sf2 - colsum[n];
@@ -495,6 +527,7 @@ __device__ __forceinline__ float sigmoid_f(float x) { return 1.0f / (1.0f + expf
 __global__ void adam_kernel(float* __restrict__ raw, float* __restrict__ cons, const float* __restrict__ grad,
                             float* __restrict__ m1, float* __restrict__ m2, const int* __restrict__ step,
                             const float* __restrict__ hyper, const float* __restrict__ zbeta1, int M, int D) {
+  pdl_enter();
   int n = M * D + D + 2 + 2 * M;
   int t = *step + 1;
   float lr = hyper[0], b1 = hyper[1], b2 = hyper[2], eps = hyper[3];
@@ -524,13 +557,16 @@ __global__ void adam_kernel(float* __restrict__ raw, float* __restrict__ cons, c
   }
 }
 
-__global__ void step_inc_kernel(int* step) { if (threadIdx.x == 0 && blockIdx.x == 0) *step += 1; }
+__global__ void step_inc_kernel(int* step) {
+  pdl_enter(); if (threadIdx.x == 0 && blockIdx.x == 0) *step += 1; }
 
-__global__ void ng_check_kernel(const double* red, int M, double eps, int* done, int* iters,
+__global__ void ng_check_kernel(double* red, int M, double eps, int* done, int* iters,
                                 double* resid) {
+  pdl_enter();
   if (threadIdx.x != 0) return;
   if (*done) return;
   double r = sqrt(red[RED_NG_RESID] / M);
+  red[RED_NG_RESID] = 0.0;
   if (resid) *resid = r;
   if (eps > 0.0 && r < eps) { *done = 1; return; }
   if (iters) *iters += 1;
@@ -545,7 +581,7 @@ void k_prep_coords(const float* Z, const float* X, const float* ell, int M, int 
   int grid = (tot + 255) / 256;
   if (grid > 4096) grid = 4096;
   svgp_note_launch();
-  prep_coords_kernel<<<grid, 256, 0, st>>>(Z, X, ell, M, Mp, B, D, Zs, Xs);
+  pdl_launch(prep_coords_kernel, grid, 256, 0, st, Z, X, ell, M, Mp, B, D, Zs, Xs);
 }
 
 template <class OutP>
@@ -553,7 +589,7 @@ void k_kuu(const float* Zs, int M, int Mp, int D, const float* sf2, float* Kf, O
            cudaStream_t st) {
   dim3 grid(Mp / 64, Mp / 64), blk(32, 8);
   svgp_note_launch();
-  SVGP_DP_DISPATCH(D, kuu_kernel<OutP, DP><<<grid, blk, 0, st>>>(Zs, M, Mp, D, sf2, Kf, Klo, has_lo));
+  SVGP_DP_DISPATCH(D, pdl_launch(kuu_kernel<OutP, DP>, grid, blk, 0, st, Zs, M, Mp, D, sf2, Kf, Klo, has_lo));
 }
 template void k_kuu<float*>(const float*, int, int, int, const float*, float*, float*, bool, cudaStream_t);
 template void k_kuu<bf16*>(const float*, int, int, int, const float*, float*, bf16*, bool, cudaStream_t);
@@ -563,7 +599,7 @@ template <class OutP>
 void k_prep_L(const float* Lin, int M, int Mp, float* Lf, OutP Llo, OutP Ltlo, double* logdet, cudaStream_t st) {
   dim3 grid(Mp / 32, Mp / 32), blk(32, 8);
   svgp_note_launch();
-  prep_L_kernel<OutP><<<grid, blk, 0, st>>>(Lin, M, Mp, Lf, Llo, Ltlo, logdet);
+  pdl_launch(prep_L_kernel<OutP>, grid, blk, 0, st, Lin, M, Mp, Lf, Llo, Ltlo, logdet);
 }
 template void k_prep_L<float*>(const float*, int, int, float*, float*, float*, double*, cudaStream_t);
 template void k_prep_L<bf16*>(const float*, int, int, float*, bf16*, bf16*, double*, cudaStream_t);
@@ -573,12 +609,26 @@ void k_gemv(const float* A, int Mp, int M, const float* x, float alpha, const fl
             float* y, const float* dotw, double* dot_out, cudaStream_t st) {
   int warps = M, blocks = (warps * 32 + 255) / 256;
   svgp_note_launch();
-  gemv_kernel<<<blocks, 256, sizeof(float) * Mp, st>>>(A, Mp, M, x, alpha, x2, beta, y, dotw, dot_out);
+  pdl_launch(gemv_kernel, blocks, 256, sizeof(float) * Mp, st, A, Mp, M, x, alpha, x2, beta, y, dotw, dot_out);
 }
 
 namespace {
+struct ZeroList {
+  uint32_t* p[3];
+  size_t n[3];   // 32-bit words
+};
+
+__global__ void zero_kernel(ZeroList z) {
+  pdl_enter();
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < z.n[r]; e += stride) z.p[r][e] = 0u;
+}
+
 __global__ void kt_f32_kernel(const float* __restrict__ Kuu, const float* __restrict__ s, int M, int Mp,
                               float* __restrict__ Kt) {
+  pdl_enter();
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (size_t)Mp * Mp) return;
   const int i = (int)(e / Mp), j = (int)(e % Mp);
@@ -588,6 +638,7 @@ __global__ void kt_f32_kernel(const float* __restrict__ Kuu, const float* __rest
 __global__ void gap_check_kernel(const double* __restrict__ red, const float* __restrict__ s, int M,
                                  double sigma2_host, const float* __restrict__ noise, double eps, int* done,
                                  double* gap) {
+  pdl_enter();
   __shared__ float mn[32];
   float m = 3.4e38f;
   for (int i = threadIdx.x; i < M; i += blockDim.x) m = fminf(m, s[i]);
@@ -606,34 +657,46 @@ __global__ void gap_check_kernel(const double* __restrict__ red, const float* __
 
 __global__ void axpy_kernel(const float* __restrict__ x, float alpha, const float* __restrict__ x2, float beta,
                             float* __restrict__ y, int n) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = alpha * (x[i] + beta * x2[i]);
 }
 }  // namespace
 
+void k_zero(cudaStream_t st, void* p0, size_t b0, void* p1, size_t b1, void* p2, size_t b2) {
+  ZeroList z{{(uint32_t*)p0, (uint32_t*)p1, (uint32_t*)p2}, {p0 ? b0 / 4 : 0, p1 ? b1 / 4 : 0, p2 ? b2 / 4 : 0}};
+  size_t mx = z.n[0] > z.n[1] ? z.n[0] : z.n[1];
+  if (z.n[2] > mx) mx = z.n[2];
+  size_t grid = (mx + 255) / 256;
+  if (grid < 1) grid = 1;
+  if (grid > 1024) grid = 1024;
+  svgp_note_launch();
+  pdl_launch(zero_kernel, (unsigned)grid, 256, 0, st, z);
+}
+
 void k_kt_f32(const float* Kuu, const float* s, int M, int Mp, float* Kt, cudaStream_t st) {
   const size_t n = (size_t)Mp * Mp;
   svgp_note_launch();
-  kt_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Kuu, s, M, Mp, Kt);
+  pdl_launch(kt_f32_kernel, (unsigned)((n + 255) / 256), 256, 0, st, Kuu, s, M, Mp, Kt);
 }
 
 void k_gap_check(const double* red, const float* s, int M, double sigma2_host, const float* noise, double eps,
                  int* done, double* gap, cudaStream_t st) {
   svgp_note_launch();
-  gap_check_kernel<<<1, 256, 0, st>>>(red, s, M, sigma2_host, noise, eps, done, gap);
+  pdl_launch(gap_check_kernel, 1, 256, 0, st, red, s, M, sigma2_host, noise, eps, done, gap);
 }
 
 void k_axpy(const float* x, float alpha, const float* x2, float beta, float* y, int n, cudaStream_t st) {
   svgp_note_launch();
-  axpy_kernel<<<(n + 255) / 256, 256, 0, st>>>(x, alpha, x2, beta, y, n);
+  pdl_launch(axpy_kernel, (n + 255) / 256, 256, 0, st, x, alpha, x2, beta, y, n);
 }
 
 void k_mu(const float* Zs, const float* Xs, int M, int B, int D, const float* sf2, const float* v,
           float* mu, cudaStream_t st) {
-  cudaMemsetAsync(mu, 0, sizeof(float) * B, st);
+  k_zero(st, mu, sizeof(float) * B);
   dim3 grid((B + 511) / 512, (M + 63) / 64);
   svgp_note_launch();
-  SVGP_DP_DISPATCH(D, mu_kernel<DP><<<grid, 128, 0, st>>>(Zs, Xs, M, B, D, sf2, v, mu));
+  SVGP_DP_DISPATCH(D, pdl_launch(mu_kernel<DP>, grid, 128, 0, st, Zs, Xs, M, B, D, sf2, v, mu));
 }
 
 void k_pointwise_gauss(const float* y, const float* mu, const float* noise, int B, float* g,
@@ -641,15 +704,15 @@ void k_pointwise_gauss(const float* y, const float* mu, const float* noise, int 
   int grid = (B + 255) / 256;
   if (grid > 256) grid = 256;
   svgp_note_launch();
-  pointwise_gauss_kernel<<<grid, 256, 0, st>>>(y, mu, noise, B, g, red);
+  pdl_launch(pointwise_gauss_kernel, grid, 256, 0, st, y, mu, noise, B, g, red);
 }
 
 void k_kg(const float* Zs, const float* Xs, int M, int Mp, int B, int D, const float* sf2,
           const float* g, float* Kg, cudaStream_t st) {
-  cudaMemsetAsync(Kg, 0, sizeof(float) * Mp, st);
+  k_zero(st, Kg, sizeof(float) * Mp);
   dim3 grid((M + 511) / 512, (B + 63) / 64);
   svgp_note_launch();
-  SVGP_DP_DISPATCH(D, kg_kernel<DP><<<grid, 128, 0, st>>>(Zs, Xs, M, B, D, sf2, g, Kg));
+  SVGP_DP_DISPATCH(D, pdl_launch(kg_kernel<DP>, grid, 128, 0, st, Zs, Xs, M, B, D, sf2, g, Kg));
 }
 
 template <class OutP>
@@ -657,7 +720,7 @@ void k_gp_assemble(const float* Kuu, const float* Psi, const float* Kg, const fl
                    const float* noise, float c, int M, int Mp, OutP out, cudaStream_t st) {
   dim3 grid((Mp / 4 + 127) / 128, Mp);
   svgp_note_launch();
-  gp_assemble_kernel<OutP><<<grid, 128, 0, st>>>(Kuu, Psi, Kg, m, w, noise, c, M, Mp, out);
+  pdl_launch(gp_assemble_kernel<OutP>, grid, 128, 0, st, Kuu, Psi, Kg, m, w, noise, c, M, Mp, out);
 }
 template void k_gp_assemble<float*>(const float*, const float*, const float*, const float*, const float*,
                                     const float*, float, int, int, float*, cudaStream_t);
@@ -672,33 +735,33 @@ void k_kuu_bwd(const float* GKuu, const float* Kuu, const float* Zs, int M, int 
   const int JB = 256;
   dim3 grid((M + 31) / 32, (M + JB - 1) / JB);
   svgp_note_launch();
-  SVGP_DP_DISPATCH(D, kuu_bwd_kernel<DP><<<grid, 256, 0, st>>>(GKuu, Kuu, Zs, M, Mp, D, rowacc_u, JB));
+  SVGP_DP_DISPATCH(D, pdl_launch(kuu_bwd_kernel<DP>, grid, 256, 0, st, GKuu, Kuu, Zs, M, Mp, D, rowacc_u, JB));
 }
 
 void k_logs(const float* s, int M, double* red, cudaStream_t st) {
   svgp_note_launch();
-  logs_kernel<<<(M + 255) / 256, 256, 0, st>>>(s, M, red);
+  pdl_launch(logs_kernel, (M + 255) / 256, 256, 0, st, s, M, red);
 }
 
 void k_grad_finalize(const float* rowacc_f, const float* rowacc_u, const float* rowpart, int nparts, int Mp,
                      const float* ell, int M, int D, float* dZ, double* acc_ell, double* red, cudaStream_t st) {
   int grid = (M + 15) / 16;
   svgp_note_launch();
-  grad_finalize_kernel<<<grid, 256, 0, st>>>(rowacc_f, rowacc_u, rowpart, nparts, Mp, ell, M, D, dZ, acc_ell, red);
+  pdl_launch(grad_finalize_kernel, grid, 256, 0, st, rowacc_f, rowacc_u, rowpart, nparts, Mp, ell, M, D, dZ, acc_ell, red);
 }
 
 void k_terms_finalize(const double* red, const double* acc_ell, const float* sf2, const float* noise,
                       const float* ell, int M, int D, int B, double N, bool probit, double* terms, float* dsf2,
                       float* dnoise, float* dell, int* errword, cudaStream_t st) {
   svgp_note_launch();
-  terms_finalize_kernel<<<1, 32, 0, st>>>(red, acc_ell, sf2, noise, ell, M, D, B, N, probit, terms, dsf2, dnoise,
+  pdl_launch(terms_finalize_kernel, 1, 32, 0, st, red, acc_ell, sf2, noise, ell, M, D, B, N, probit, terms, dsf2, dnoise,
                                           dell, errword);
 }
 
 void k_predict_finalize(const float* colsum, const float* sf2, const float* noise, int Ns, int inc,
                         float* var, cudaStream_t st) {
   svgp_note_launch();
-  predict_finalize_kernel<<<(Ns + 255) / 256, 256, 0, st>>>(colsum, sf2, noise, Ns, inc, var);
+  pdl_launch(predict_finalize_kernel, (Ns + 255) / 256, 256, 0, st, colsum, sf2, noise, Ns, inc, var);
 }
 
 void k_adam(float* raw, float* cons, const float* grad, float* m1, float* m2, int* step, const float* hyper,
@@ -707,13 +770,13 @@ void k_adam(float* raw, float* cons, const float* grad, float* m1, float* m2, in
   int grid = (n + 255) / 256;
   if (grid > 1024) grid = 1024;
   svgp_note_launch();
-  adam_kernel<<<grid, 256, 0, st>>>(raw, cons, grad, m1, m2, step, hyper, zbeta1, M, D);
+  pdl_launch(adam_kernel, grid, 256, 0, st, raw, cons, grad, m1, m2, step, hyper, zbeta1, M, D);
   svgp_note_launch();
-  step_inc_kernel<<<1, 32, 0, st>>>(step);
+  pdl_launch(step_inc_kernel, 1, 32, 0, st, step);
 }
 
-void k_ng_check(const double* red, int M, double eps, int* done, int* iters, double* resid,
+void k_ng_check(double* red, int M, double eps, int* done, int* iters, double* resid,
                 cudaStream_t st) {
   svgp_note_launch();
-  ng_check_kernel<<<1, 32, 0, st>>>(red, M, eps, done, iters, resid);
+  pdl_launch(ng_check_kernel, 1, 32, 0, st, red, M, eps, done, iters, resid);
 }

@@ -29,6 +29,7 @@ __global__ void __launch_bounds__(THREADS, 2)
 kuf_gemv_kernel(const __grid_constant__ CUtensorMap tmRow, const __grid_constant__ CUtensorMap tmK,
                 const float* __restrict__ w, int nk, int nkb, int kb_per_group, float* __restrict__ out, int nrows,
                 int* errword) {
+  pdl_enter();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sRow = base;
@@ -161,7 +162,7 @@ bool tc_kuf_gemv(const bf16* Rrole, int nrows, const bf16* Krole, int nk, const 
   const int kp = (nk + 63) / 64 * 64;
   CUtensorMap mr, mk;
   if (!tc_make_map(&mr, Rrole, rows_p, 64, 128) || !tc_make_map(&mk, Krole, kp, 64, 64)) return false;
-  cudaMemsetAsync(out, 0, sizeof(float) * nrows, st);
+  k_zero(st, out, sizeof(float) * nrows);
   const int nkb = kp / 64, rb = rows_p / 128;
   // about two CTAs per SM, at least 8 k-blocks each
   int groups = (2 * tc_num_sms() + rb - 1) / rb;
@@ -171,6 +172,6 @@ bool tc_kuf_gemv(const bf16* Rrole, int nrows, const bf16* Krole, int nk, const 
   groups = (nkb + per - 1) / per;
   dim3 grid(rb, groups);
   svgp_note_launch();
-  kuf_gemv_kernel<<<grid, THREADS, GV_SMEM, st>>>(mr, mk, w, nk, nkb, per, out, nrows, errword);
+  pdl_launch(kuf_gemv_kernel, grid, THREADS, GV_SMEM, st, mr, mk, w, nk, nkb, per, out, nrows, errword);
   return true;
 }

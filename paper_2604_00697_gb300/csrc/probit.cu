@@ -105,6 +105,7 @@ __device__ __forceinline__ void log_phi_ratio(double a, double* lp, double* r) {
 __global__ void pointwise_probit_kernel(const float* __restrict__ y, const float* __restrict__ mu,
                                         const float* __restrict__ colsum, const float* __restrict__ sf2p, int B,
                                         GHRule gh, float* __restrict__ g, float* __restrict__ h, double* red) {
+  pdl_enter();
   const double SQRT2 = 1.41421356237309504880;
   const double sf2 = *sf2p;
   double sE = 0.0, sH = 0.0, sV = 0.0, sC = 0.0;
@@ -143,5 +144,5 @@ void k_pointwise_probit(const float* y, const float* mu, const float* colsum, co
   int grid = (B + 255) / 256;
   if (grid > 1024) grid = 1024;
   svgp_note_launch();
-  pointwise_probit_kernel<<<grid, 256, 0, st>>>(y, mu, colsum, sf2, B, gh, g, h, red);
+  pdl_launch(pointwise_probit_kernel, grid, 256, 0, st, y, mu, colsum, sf2, B, gh, g, h, red);
 }

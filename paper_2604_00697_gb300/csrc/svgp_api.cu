@@ -272,8 +272,7 @@ void prep_L(svgp_handle* h, const float* Lin, double* logdet) {
 // Common prologue: scaled coordinates, Kuu, L copies, log-dets; zero sums.
 void prologue(svgp_handle* h, const svgp_params* p, const float* X, int B, const float* Lin) {
   cudaStream_t st = h->st;
-  cudaMemsetAsync(h->red, 0, sizeof(double) * RED_COUNT, st);
-  cudaMemsetAsync(h->acc_ell, 0, sizeof(double) * SVGP_MAXD, st);
+  k_zero(st, h->red, sizeof(double) * RED_COUNT, h->acc_ell, sizeof(double) * SVGP_MAXD);
   k_prep_coords(p->Z, X, p->ell, h->M, h->Mp, X ? B : 0, h->D, h->Zs, h->Xs, st);
   if (h->tc_kuf) k_kuf_prep(h->Zs, X ? h->Xs : nullptr, h->M, h->Mp, X ? B : 0, (B + 127) / 128 * 128, h->D, p->sf2, h->kt, st);
   if (h->mode == MODE_F32) k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, (float*)nullptr, false, st);
@@ -301,7 +300,7 @@ void forward(svgp_handle* h, const svgp_params* p, const svgp_batch* b, bool psi
     if (!(h->tc_kuf && tc_kuf_gemv(h->kt.XR, b->B, h->kt.ZK, h->M, h->v, h->mu, h->errword, st)))
       k_mu(h->Zs, h->Xs, h->M, b->B, h->D, p->sf2, h->v, h->mu, st);                        // mu = Kfu v
     if (h->probit) {
-      cudaMemsetAsync(h->colsum, 0, sizeof(float) * b->B, st);
+      k_zero(st, h->colsum, sizeof(float) * b->B);
       WEpi wv{KufGen{h->Zs, h->Xs, h->D, h->M, b->B, p->sf2}, nullptr, nullptr, nullptr, nullptr, 0.f, nullptr,
               h->colsum};
       run_w(h, wv);                                                                       // k_n^T P k_n
@@ -344,8 +343,7 @@ void backward_tail(svgp_handle* h, const svgp_params* p, const svgp_batch* b, do
   run_sym<2>(h, nullptr);                // S = L^T G_P L + I/2
   run_ls(h);                             // Y = L S
   run_gk(h, p->s, gr->ds);               // G_K~ = -Y L^T -> G_Kuu, ds
-  cudaMemsetAsync(h->rowacc_f, 0, sizeof(float) * Mp * W, st);
-  cudaMemsetAsync(h->rowacc_u, 0, sizeof(float) * Mp * W, st);
+  k_zero(st, h->rowacc_f, sizeof(float) * Mp * W, h->rowacc_u, sizeof(float) * Mp * W);
   WEpi we{KufGen{h->Zs, h->Xs, h->D, M, b->B, p->sf2}, h->v, h->g, h->probit ? h->hn : nullptr, nz, c,
           h->rowacc_f, nullptr};
   const int nparts = run_w(h, we);                                                     // data part of dZ, dell, dsf2
@@ -363,10 +361,9 @@ void backward_tail(svgp_handle* h, const svgp_params* p, const svgp_batch* b, do
 void ng_loop(svgp_handle* h, const svgp_params* p, float* L_inout, const float* gamma_dev, int max_iters, double eps,
              int* iters, double* resid) {
   cudaStream_t st = h->st;
-  cudaMemsetAsync(h->done, 0, sizeof(int), st);
-  cudaMemsetAsync(iters, 0, sizeof(int), st);
+  // red[RED_NG_RESID] starts at 0 (prologue) and ng_check resets it after reading
+  k_zero(st, h->done, sizeof(int), iters, sizeof(int));
   for (int t = 0; t < max_iters; ++t) {
-    cudaMemsetAsync(h->red + RED_NG_RESID, 0, sizeof(double), st);
     run_vt(h, h->Kuu_lo, p->s, h->done);         // Vt = L^T K~ (skipped once converged)
     run_sym<0>(h, h->done);                      // A, Phi^T, ||A - I||^2
     k_ng_check(h->red, h->M, eps, h->done, iters, resid, st);   // Eq. (8) stopping rule
@@ -597,8 +594,7 @@ svgp_status svgp_variance_gap(svgp_handle* h, const svgp_params* p, const svgp_b
   prologue(h, p, b->X, b->B, p->L);
   run_psi(h, p, b->B, nullptr);
   k_kt_f32(h->Kuu_f, p->s, h->M, h->Mp, h->GKuu, st);
-  cudaMemsetAsync(h->red + RED_GAPDOT, 0, sizeof(double), st);
-  gap_compute(h, nullptr);
+  gap_compute(h, nullptr);   // red[RED_GAPDOT] is 0 after the prologue
   k_gap_check(h->red, p->s, h->M, sigma2, p->noise, 0.0, nullptr, gap_dev, st);
   return check_launch(h, "svgp_variance_gap");
 }
@@ -617,15 +613,13 @@ svgp_status svgp_ng_update_T_gap(svgp_handle* h, const svgp_params* p, const svg
   prologue(h, p, b->X, b->B, L_inout);
   run_psi(h, p, b->B, nullptr);
   k_kt_f32(h->Kuu_f, p->s, h->M, h->Mp, h->GKuu, st);
-  cudaMemsetAsync(h->done, 0, sizeof(int), st);
-  cudaMemsetAsync(iters, 0, sizeof(int), st);
+  k_zero(st, h->done, sizeof(int), iters, sizeof(int));
   for (int t = 0; t <= max_iters; ++t) {
     // G(L_t); stop before updating once G <= 2 noise eps (the last pass only measures)
-    cudaMemsetAsync(h->red + RED_GAPDOT, 0, sizeof(double), st);
+    if (t > 0) k_zero(st, h->red + RED_GAPDOT, sizeof(double));
     gap_compute(h, h->done);
     k_gap_check(h->red, p->s, h->M, sigma2, p->noise, eps, h->done, gap_dev, st);
     if (t == max_iters) break;
-    cudaMemsetAsync(h->red + RED_NG_RESID, 0, sizeof(double), st);
     run_vt(h, h->Kuu_lo, p->s, h->done);
     run_sym<0>(h, h->done);
     k_ng_check(h->red, h->M, 0.0, h->done, iters, h->resid_tmp, st);
@@ -650,7 +644,7 @@ svgp_status svgp_train_step(svgp_handle* h, const svgp_params* p, const svgp_bat
           residual_dev ? residual_dev : h->resid_tmp);
   if (max_iters > 0) {
     // copies and log-determinant of the updated L
-    cudaMemsetAsync(h->red + RED_LOGDETL, 0, sizeof(double), h->st);
+    k_zero(h->st, h->red + RED_LOGDETL, sizeof(double));
     prep_L(h, L_inout, h->red + RED_LOGDETL);
   }
   svgp_params q = *p;
@@ -669,7 +663,7 @@ svgp_status svgp_predict(svgp_handle* h, const svgp_params* p, const float* Xs, 
   forward(h, p, nullptr, false);
   if (!(h->tc_kuf && tc_kuf_gemv(h->kt.XR, Ns, h->kt.ZK, h->M, h->v, mean, h->errword, st)))
     k_mu(h->Zs, h->Xs, h->M, Ns, h->D, p->sf2, h->v, mean, st);
-  cudaMemsetAsync(h->colsum, 0, sizeof(float) * Ns, st);
+  k_zero(st, h->colsum, sizeof(float) * Ns);
   WEpi we{KufGen{h->Zs, h->Xs, h->D, h->M, Ns, p->sf2}, nullptr, nullptr, nullptr, nullptr, 0.f,
           nullptr, h->colsum};
   run_w(h, we);

@@ -41,6 +41,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 // make_tiles(): VT full / K [m0, Mp); SYM_IN upper / K [n0, Mp);
 // LS full / K [0, m0 + 128); OUT lower / K [0, n0 + 128).
 __global__ void na_tables_kernel(Tile* tab, int nb) {
+  pdl_enter();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int Mp = 128 * nb;
   int c[TT_COUNT] = {0};
@@ -86,7 +87,7 @@ extern "C" svgp_status svgp_predict_noalloc(const svgp_params* p, int M, int D, 
   Tile* tab = reinterpret_cast<Tile*>(b + OFF_TAB);
   if (nd.nb_built != nb) {
     svgp_note_launch();
-    na_tables_kernel<<<1, 32, 0, st>>>(tab, nb);
+    pdl_launch(na_tables_kernel, 1, 32, 0, st, tab, nb);
     nd.nb_built = nb;
   }
   GemmCtx g;
