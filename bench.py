@@ -34,6 +34,10 @@ WORKLOAD = "gp_sample_regression"
 WORKLOADS = {
     "gp_sample_regression": dict(metric=METRIC, desc="gp_sample_regression M=2048 B=4096 D=16 N=1e6",
                                  data="synthetic (GP sample via random Fourier features, D=16, seed 2)"),
+    "group64": dict(metric="group train steps/s: 64 SVGPs, M in {128..2048}, B=2048, D=8 (config 5)",
+                    desc="64 sinusoid_regression SVGPs, M ~ U{128,256,512,1024,2048} (seed 7), B=2048, D=8, "
+                         "N=1e5, data seeds 100..163; one CUDA graph with a branch per SVGP",
+                    data="synthetic (sums of 4 random sinusoids, D=8, seeds 100..163)"),
     "banana_like": dict(metric="probit train steps/s at M=256,B=2048,D=2 (config 4)",
                         desc="banana_like M=256 B=2048 D=2 N=5e4, Bernoulli-probit, 20-point Gauss-Hermite",
                         data="synthetic (two noisy crescents, labels {0,1}, seed 3)"),
@@ -148,6 +152,8 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
+    if args.workload == "group64":
+        raise SystemExit("--impl reference times the oracle on one SVGP workload, not on the group of 64")
     budget = 150.0
     times = oracle_steps(budget, args.warmup + args.steps, args.workload)
     wl = WORKLOADS[args.workload]
@@ -249,6 +255,69 @@ def algorithmic_flops(M, B):
     M3 = float(M) ** 3
     return {"vt": M3, "sym": M3 / 3, "lupd": M3 / 3, "ls": M3, "out": M3 / 3,
             "psi": float(M) * (M + 1) * B, "w": 2.0 * M * M * B}
+
+
+def run_group(args):
+    """Config 5: 64 independent SVGPs of uneven M stepped together; a step is
+    one training step of every member (one graph replay)."""
+    import torch
+
+    from paper_2604_00697_gb300.model import RSVGP, RSVGPGroup
+    import svgp_synth as S
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    rng = np.random.default_rng(7)
+    Ms = rng.choice([128, 256, 512, 1024, 2048], size=64)
+    B, D = 2048, 8
+    models, batches = [], []
+    for g, M in enumerate(Ms):
+        prob = S.sinusoid_regression(seed=100 + g, B=B, M=int(M), D=D)
+        m = RSVGP(int(M), D, B, prec=args.prec)
+        m.set_state(prob.Z0, np.ones(D), 1.0, 1.0, np.zeros(M), np.full(M, 1e-4), 1e-3 * np.eye(M))
+        X, y = prob.batch(0)
+        models.append(m)
+        batches.append((torch.tensor(X, dtype=torch.float32, device="cuda"),
+                        torch.tensor(y, dtype=torch.float32, device="cuda"), prob.N))
+    group = RSVGPGroup(models)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        group.train_step(batches)
+        torch.cuda.synchronize()
+        gr = group.capture(batches)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        gr.replay()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clk = Clocks(local)
+    clk.start()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(st)
+        gr.replay()
+        ev[i][1].record(st)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    tot = sum(a.elapsed_time(b) for a, b in ev)
+    tot_ms, value = reduce_timing(tot, args.steps, ws)
+    status = group.sync_status()
+    wl = WORKLOADS["group64"]
+    line = {"metric": wl["metric"], "value": value, "unit": "group steps/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.prec != "fp32" else "f32",
+            "data": wl["data"], "config": {"workload": wl["desc"], "members": 64, "B": B, "D": D,
+                                            "M_counts": {int(k): int((Ms == k).sum()) for k in sorted(set(Ms))},
+                                            "precision": args.prec, "graph": True,
+                                            "l2": "flushed between timed steps"},
+            "clocks": clocks, "device_status": status}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    group.close()
 
 
 def run_ours(args):
@@ -475,6 +544,8 @@ def main():
         run_profile_step(args)
     elif args.impl == "reference":
         run_reference(args)
+    elif args.workload == "group64":
+        run_group(args)
     else:
         run_ours(args)
 

@@ -149,6 +149,20 @@ svgp_status svgp_set_stream(svgp_handle* h, void* cuda_stream);
 svgp_status svgp_bound(svgp_handle* h, const svgp_params* p, const svgp_batch* b,
                        double* terms_dev);
 
+/* svgp_bound with the two cubic traces of the KL bound replaced by
+ * Hutchinson estimates over K probe vectors (Section 3.4):
+ *   tr(K~ T)  ~ (1/K) sum_k z_k^T L^T K~ L z_k,
+ *   tr(P Kuu) ~ (1/K) sum_k z_k^T P Kuu z_k;
+ * every other term exact.  probes: device float[M x K] row-major (column k
+ * is z_k; entries +-1 for Rademacher probes -- the caller draws them, so the
+ * estimate is reproducible), 1 <= K <= SVGP_HUTCH_KMAX.  The estimates take
+ * FP32 products of the M x M matrices with M x K blocks (about 14 M^2 K
+ * flops); the terms layout is that of svgp_bound (SVGP_T_TRKT and
+ * SVGP_T_TRPKUU hold the estimates). */
+#define SVGP_HUTCH_KMAX 256
+svgp_status svgp_bound_hutchinson(svgp_handle* h, const svgp_params* p, const svgp_batch* b,
+                                  const float* probes, int K, double* terms_dev);
+
 /* Bound (as svgp_bound) plus its gradient w.r.t. Z, ell, sf2, noise, m~, s~
  * with T held fixed (Section 3.1: T is optimised separately by NG; Prop. 2
  * concerns exactly this gradient).  terms_dev may be NULL.  Probit: the

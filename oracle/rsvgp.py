@@ -50,6 +50,7 @@ __all__ = [
     "ng_step",
     "ng_solve",
     "variance_gap",
+    "hutchinson_traces",
     "ng_solve_gap",
     "gamma_schedule",
     "predict",
@@ -104,7 +105,27 @@ def _gauss_expected_loglik(y, mu, var, noise):
     return -0.5 * np.log(2 * math.pi * noise) - ((y - mu) ** 2 + var) / (2 * noise)
 
 
-def bound(p, X, y, N=None, likelihood="gaussian", precond=True):
+def hutchinson_traces(p, probes):
+    """Hutchinson estimates (Section 3.4) of the two cubic KL traces.
+
+    With K probe vectors z_k (columns of ``probes``, M x K, entries +-1):
+      tr(K~ T)  ~ (1/K) sum_k z_k^T L^T K~ L z_k
+      tr(P Kuu) ~ (1/K) sum_k z_k^T P Kuu z_k
+    Each is unbiased for Rademacher probes; the average over all 2^M sign
+    patterns is exact.
+    """
+    Zp = np.asarray(probes, np.float64)
+    K = Zp.shape[1]
+    L = np.asarray(p["L"], np.float64)
+    Kuu = se_ard(p["Z"], p["Z"], p["ell"], p["sf2"])
+    Kt = Kuu + np.diag(p["s"])
+    T, P = preconditioner(L, Kt)
+    trKT = float(np.sum(Zp * (L.T @ (Kt @ (L @ Zp))))) / K
+    trPKuu = float(np.sum(Zp * (P @ (Kuu @ Zp)))) / K
+    return trKT, trPKuu
+
+
+def bound(p, X, y, N=None, likelihood="gaussian", precond=True, probes=None):
     """Preconditioned R-SVGP bound, Eq. (7), on one minibatch.
 
     F = (N/B) sum_n E_{N(mu_n, sigma_n^2)}[log p(y_n | f_n)] - KL_R with
@@ -121,6 +142,10 @@ def bound(p, X, y, N=None, likelihood="gaussian", precond=True):
     (Section 2, inverse-free parameterisation, with m = Kuu m~): mu_n =
     k_nu m~ and the quadratic KL term m~^T Kuu m~ (the KL bound of Section 2);
     sigma_n^2 and the trace terms are unchanged.
+
+    With ``probes`` (M x K, entries +-1) the two cubic traces tr(K~ T) and
+    tr(P Kuu) of the KL bound are the Hutchinson estimates of
+    ``hutchinson_traces`` (Section 3.4); every other term is exact.
     """
     X = np.asarray(X, np.float64)
     y = np.asarray(y, np.float64)
@@ -145,8 +170,11 @@ def bound(p, X, y, N=None, likelihood="gaussian", precond=True):
         raise ValueError(likelihood)
     E = (N / B) * En.sum()
     # KL upper bound (Eq. (7), second and third lines); each trace as a product
-    tr_PKuu = np.trace(P @ Kuu)
-    tr_KtT = np.trace(Kt @ T)
+    if probes is None:
+        tr_PKuu = np.trace(P @ Kuu)
+        tr_KtT = np.trace(Kt @ T)
+    else:
+        tr_KtT, tr_PKuu = hutchinson_traces(p, probes)
     quad = Pm @ Kuu @ Pm
     sign, logdetT = np.linalg.slogdet(T)
     logdetS = np.sum(np.log(p["s"]))

@@ -35,7 +35,7 @@ EXPORTED = [
     "svgp_create", "svgp_destroy", "svgp_set_stream", "svgp_bound", "svgp_backward",
     "svgp_ng_update_T", "svgp_train_step", "svgp_predict", "svgp_adam_step", "svgp_param_count",
     "svgp_sync_status", "svgp_last_error", "svgp_status_string", "svgp_has_tensor_cores",
-    "svgp_gauss_hermite", "svgp_variance_gap", "svgp_ng_update_T_gap",
+    "svgp_gauss_hermite", "svgp_variance_gap", "svgp_ng_update_T_gap", "svgp_bound_hutchinson",
 ]
 
 
@@ -99,12 +99,13 @@ def load(path: str = LIB_PATH):
     lib.svgp_has_tensor_cores.restype = c_int
     lib.svgp_gauss_hermite.argtypes = [c_int, POINTER(c_double), POINTER(c_double)]
     lib.svgp_variance_gap.argtypes = [H, POINTER(svgp_params), POINTER(svgp_batch), c_double, c_void_p]
+    lib.svgp_bound_hutchinson.argtypes = [H, POINTER(svgp_params), POINTER(svgp_batch), c_void_p, c_int, c_void_p]
     lib.svgp_ng_update_T_gap.argtypes = [H, POINTER(svgp_params), POINTER(svgp_batch), c_void_p, c_void_p, c_int,
                                          c_double, c_double, c_void_p, c_void_p]
     lib.svgp_gauss_hermite.restype = c_int
     for name in ("svgp_create", "svgp_set_stream", "svgp_bound", "svgp_backward", "svgp_ng_update_T",
                  "svgp_train_step", "svgp_predict", "svgp_adam_step", "svgp_sync_status", "svgp_variance_gap",
-                 "svgp_ng_update_T_gap"):
+                 "svgp_ng_update_T_gap", "svgp_bound_hutchinson"):
         getattr(lib, name).restype = c_int
     _lib = lib
     return lib
@@ -162,6 +163,14 @@ def svgp_train_step(h, params, batch, L_ptr, gamma_ptr, max_iters, eps, iters_pt
     _check(h, load().svgp_train_step(h, byref(params), byref(batch), c_void_p(L_ptr), c_void_p(gamma_ptr),
                                      max_iters, c_double(eps), c_void_p(iters_ptr), c_void_p(resid_ptr),
                                      c_void_p(terms_ptr), byref(grads)))
+
+
+SVGP_HUTCH_KMAX = 256
+
+
+def svgp_bound_hutchinson(h, params, batch, probes_ptr, K, terms_ptr):
+    _check(h, load().svgp_bound_hutchinson(h, byref(params), byref(batch), c_void_p(probes_ptr), K,
+                                           c_void_p(terms_ptr)))
 
 
 def svgp_variance_gap(h, params, batch, sigma2, gap_ptr):

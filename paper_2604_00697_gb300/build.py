@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsvgp.so")
 SOURCES = ["svgp_api.cu", "kernels_misc.cu", "gemm_simt.cu", "gemm_tc.cu", "gemm_kuf_tc.cu", "gemm_w_tc.cu",
-           "kuf_gemv_tc.cu", "svgp_noalloc.cu", "probit.cu"]
+           "kuf_gemv_tc.cu", "svgp_noalloc.cu", "probit.cu", "hutchinson.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

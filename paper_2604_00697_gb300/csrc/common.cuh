@@ -31,7 +31,10 @@ enum {
   RED_SUMVAR = 13,    // probit: sum_n sigma_n^2 (clamped)
   RED_NCLAMP = 14,    // probit: number of clamped sigma_n^2
   RED_GAPDOT = 15,    // <N N^T, Psi> of the Prop. 3 gap
-  RED_COUNT = 16
+  RED_HKT = 16,       // Hutchinson: sum_k z_k^T L^T K~ L z_k
+  RED_HW1 = 17,       // Hutchinson: sum_k z_k^T T Kuu z_k
+  RED_HX4 = 18,       // Hutchinson: sum_k z_k^T T K~ T Kuu z_k
+  RED_COUNT = 24
 };
 
 // One output tile of a GEMM: rows [m0, m0+BM), cols [n0, n0+BN), and the
@@ -68,6 +71,21 @@ __device__ __forceinline__ void put(const SplitPtr& p, size_t i, float x) {
 __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Packed FP32 pairs (Blackwell f32x2 FMA): two fused multiply-adds per
+// instruction, each rounded as fmaf.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pack2(float a, float b) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void unpack2(f32x2 v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ void fma2(f32x2& d, f32x2 a, f32x2 b) {   // d = a * b + d
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
 }
 
 // Host side: launch `kern` with programmatic stream serialization allowed.

@@ -10,17 +10,19 @@
 //     sum_n A_in e_d^2 = S2_d - 2 z~_id S1_d + z~_id^2 S0  (e_d = x~_nd - z~_id);
 //   variance mode (colsum != null): colsum[n] += sum_i Kuf_in W_in.
 //
-// Grid: (groups of n-blocks) x (128-row blocks i of P).  A CTA keeps its rows
-// i and walks the n-blocks nb = blockIdx.x, blockIdx.x + gridDim.x, ...,
-// carrying the row sums in registers; at the end it writes one partial row
-// set rowpart[blockIdx.x][k][i] (no atomics; the gradient finalize adds the
-// gridDim.x partials).  Per n-block:
+// Grid: (groups of n-blocks) x (row blocks of NI x 128 rows i of P).  A CTA
+// keeps its rows i and walks the n-blocks nb = blockIdx.x, blockIdx.x +
+// gridDim.x, ..., carrying the row sums in registers; at the end it writes one
+// partial row set rowpart[blockIdx.x][k][i] (no atomics; the gradient
+// finalize adds the gridDim.x partials).  Per n-block:
 //   * mainloop over the inducing k-blocks: exponent MMA for the 128 x 64 block
-//     Kuf^T[n, k], exp2 into the swizzled B operand, main MMA
-//     W[i, n] += P[i, k] Kuf[k, n];
-//   * one more exponent MMA T[i, n] = log2 Kuf_in for the epilogue (z rows of
-//     the block against the n-block), so Kuf_in is recomputed exactly as the
-//     generator computes it.
+//     Kuf^T[n, k], exp2 into the swizzled B operand, main MMAs
+//     W[i, n] += P[i, k] Kuf[k, n] for each of the NI 128-row blocks: with
+//     NI = 2 (BF16 operands) one generated tile feeds two accumulators, which
+//     halves the exps per output;
+//   * one more exponent MMA per row block, T[i, n] = log2 Kuf_in for the
+//     epilogue (z rows of the block against the n-block), so Kuf_in is
+//     recomputed exactly as the generator computes it.
 // Warp roles (320 threads): 0 TMA producer, 1 TMEM allocator + MMA issuer,
 // 2..9 transform and then epilogue (warp w covers TMEM lanes 32 (w mod 4) ..
 // +31 and one half of the columns).  All waits are bounded; once a wait has
@@ -37,17 +39,18 @@ using namespace kuf;
 
 constexpr int DPMAX = 24;                      // padded-dimension bound of the staged x~ rows
 
-template <int NSPLIT>
+template <int NSPLIT, int NI>
 struct WGeo {
+  static_assert(NI == 1 || (NI == 2 && NSPLIT == 1), "two row blocks only with BF16 operands");
   static constexpr int NS = NSPLIT == 3 ? 2 : 1;                         // hi (+lo) planes
-  static constexpr int STAGES = NSPLIT == 3 ? 2 : 3;
-  // stage: [z k-role coordinate tile CT][P tiles NS*GT][generated Kuf^T tiles NS*GT]
+  static constexpr int STAGES = (NSPLIT == 3 || NI == 2) ? 2 : 3;
+  // stage: [z k-role coordinate tile CT][P tiles NI*NS*GT][generated Kuf^T tiles NS*GT]
   static constexpr int OFF_P = CT;
-  static constexpr int OFF_G = CT + NS * GT;
+  static constexpr int OFF_G = CT + NI * NS * GT;
   static constexpr int STAGE = OFF_G + NS * GT;
-  // static tiles: z rows of the block (row role), x rows of the n-block in
-  // row role (generator) and in k role (epilogue exponent)
-  static constexpr int OFF_ZR = 0, OFF_XR = GT, OFF_XK = 2 * GT, STATIC = 3 * GT;
+  // static tiles: z rows of the row blocks (row role), x rows of the n-block
+  // in row role (generator) and in k role (epilogue exponent)
+  static constexpr int OFF_ZR = 0, OFF_XR = NI * GT, OFF_XK = (NI + 1) * GT, STATIC = (NI + 2) * GT;
   // epilogue floats: colbuf[128], gq[128], xq[128][2 DP]; reused for the final
   // combination of the two column halves (128 x (2 DP + 1))
   static constexpr int EPI_FLOATS = 256 + 128 * 2 * DPMAX;
@@ -56,9 +59,12 @@ struct WGeo {
   static constexpr int SMEM = 1024 + STATIC + STAGES * STAGE + 4 * EPI_FLOATS + 8 * NBAR + 64;
   static_assert(SMEM <= 232448, "shared memory budget");
   static constexpr uint32_t TMEM_COLS = 512;
-  // TMEM columns: W accumulator [0,128), generator exponents 2 x 64, epilogue exponents T
-  static constexpr uint32_t ACC = 0, T = 256;
-  __host__ __device__ static constexpr uint32_t SB(int b) { return 128 + 64 * b; }
+  // TMEM columns: W accumulators [0, 128 NI), generator exponents 2 x 64 after
+  // them, epilogue exponents T of row block 0 in [384, 512) and of row block 1
+  // in the generator buffers (free once the mainloop of the n-block is done)
+  __host__ __device__ static constexpr uint32_t ACC(int ib) { return 128 * ib; }
+  __host__ __device__ static constexpr uint32_t SB(int b) { return 128 * NI + 64 * b; }
+  __host__ __device__ static constexpr uint32_t T(int ib) { return ib == 0 ? 384 : 128 * NI; }
 };
 
 struct WArgs {
@@ -69,13 +75,13 @@ struct WArgs {
   float* rowpart;   // gradient mode: [gridDim.x][2D + 1][Mp]
 };
 
-template <int NSPLIT, int DP>
+template <int NSPLIT, int DP, int NI>
 __global__ void __launch_bounds__(THREADS, 1)
 w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CUtensorMap tmZK,
             const __grid_constant__ CUtensorMap tmXR, const __grid_constant__ CUtensorMap tmXK,
             const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmPl, WArgs wa, WEpi we) {
   pdl_enter();
-  using G = WGeo<NSPLIT>;
+  using G = WGeo<NSPLIT, NI>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sZR = base + G::OFF_ZR;
@@ -90,10 +96,10 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
   constexpr int S = G::STAGES;
   auto BAR = [&](int idx) { return smem_u32(&bars[idx]); };
   const int B_ZR = 0, B_TILE = 1, B_LD = 2, B_EMPTY = 2 + S, B_GEN = 2 + 2 * S, B_SFULL = 2 + 3 * S,
-            B_SEMPTY = 4 + 3 * S, B_ACC = 6 + 3 * S;
+            B_SEMPTY = 4 + 3 * S, B_ACC = 6 + 3 * S, B_EDONE = 7 + 3 * S;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * 128;
+  const int m0 = blockIdx.y * 128 * NI;
   const int nkb = wa.nkb;
 
   if (threadIdx.x == 0) {
@@ -109,6 +115,7 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
       mbar_init(BAR(B_SEMPTY + b), NTW);
     }
     mbar_init(BAR(B_ACC), 1);
+    mbar_init(BAR(B_EDONE), NTW);
     *abort_flag = 0;
     *consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -124,8 +131,8 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
-    mbar_expect_tx(BAR(B_ZR), GT);
-    tma_load_2d(smem_u32(sZR), &tmZR, 0, m0, BAR(B_ZR));
+    mbar_expect_tx(BAR(B_ZR), NI * GT);
+    for (int ib = 0; ib < NI; ++ib) tma_load_2d(smem_u32(sZR + ib * GT), &tmZR, 0, m0 + 128 * ib, BAR(B_ZR));
     int g = 0, lt = 0;
     bool ok = true;
     for (int nb = blockIdx.x; nb < wa.nblk && ok; nb += gridDim.x, ++lt) {
@@ -140,10 +147,13 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
         if (!mbar_wait(BAR(B_EMPTY + s), ((g / S) & 1) ^ 1) || *abort_flag) { ok = false; break; }
         unsigned char* st = stg + s * G::STAGE;
         const uint32_t fb = BAR(B_LD + s);
-        mbar_expect_tx(fb, CT + G::NS * GT);
+        mbar_expect_tx(fb, CT + NI * G::NS * GT);
         tma_load_2d(smem_u32(st), &tmZK, 0, kb * KB, fb);
-        tma_load_2d(smem_u32(st + G::OFF_P), &tmP, kb * KB, m0, fb);
-        if (NSPLIT == 3) tma_load_2d(smem_u32(st + G::OFF_P + GT), &tmPl, kb * KB, m0, fb);
+        for (int ib = 0; ib < NI; ++ib) {
+          unsigned char* pt = st + G::OFF_P + ib * G::NS * GT;
+          tma_load_2d(smem_u32(pt), &tmP, kb * KB, m0 + 128 * ib, fb);
+          if (NSPLIT == 3) tma_load_2d(smem_u32(pt + GT), &tmPl, kb * KB, m0 + 128 * ib, fb);
+        }
       }
     }
     if (!ok) *abort_flag = 1;
@@ -163,6 +173,8 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
     int g = 0, lt = 0;
     for (int nb = blockIdx.x; nb < wa.nblk && ok; nb += gridDim.x, ++lt) {
       if (!mbar_wait(BAR(B_TILE), lt & 1)) { ok = false; break; }
+      // the epilogue of the previous n-block has read the accumulators and T
+      if (lt > 0 && !mbar_wait(BAR(B_EDONE), (lt - 1) & 1)) { ok = false; break; }
       fence_after();
       const uint64_t ra = sw128_desc(smem_u32(sXR));
       int d = 0, mn = 0;
@@ -191,17 +203,20 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
         if (mn < d && mbar_try(BAR(B_GEN + gm % S), (gm / S) & 1)) {
           fence_after();
           unsigned char* st = stg + (gm % S) * G::STAGE;
-          const uint64_t ad = sw128_desc(smem_u32(st + G::OFF_P));
-          const uint64_t adl = sw128_desc(smem_u32(st + G::OFF_P + GT));
           const uint64_t bd = sw128_desc(smem_u32(st + G::OFF_G));
           const uint64_t bdl = sw128_desc(smem_u32(st + G::OFF_G + GT));
 #pragma unroll
-          for (int kk = 0; kk < KB / 16; ++kk) {
-            const uint64_t o = (uint64_t)(kk * 2);
-            mma_bf16(tmem + G::ACC, ad + o, bd + o, ID_MAIN, (mn | kk) != 0);
-            if (NSPLIT == 3) {
-              mma_bf16(tmem + G::ACC, ad + o, bdl + o, ID_MAIN, 1);
-              mma_bf16(tmem + G::ACC, adl + o, bd + o, ID_MAIN, 1);
+          for (int ib = 0; ib < NI; ++ib) {
+            const uint64_t ad = sw128_desc(smem_u32(st + G::OFF_P + ib * G::NS * GT));
+            const uint64_t adl = sw128_desc(smem_u32(st + G::OFF_P + ib * G::NS * GT + GT));
+#pragma unroll
+            for (int kk = 0; kk < KB / 16; ++kk) {
+              const uint64_t o = (uint64_t)(kk * 2);
+              mma_bf16(tmem + G::ACC(ib), ad + o, bd + o, ID_MAIN, (mn | kk) != 0);
+              if (NSPLIT == 3) {
+                mma_bf16(tmem + G::ACC(ib), ad + o, bdl + o, ID_MAIN, 1);
+                mma_bf16(tmem + G::ACC(ib), adl + o, bd + o, ID_MAIN, 1);
+              }
             }
           }
           mma_commit(BAR(B_EMPTY + gm % S));
@@ -213,12 +228,16 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
       }
       g += nkb;
       if (!ok) break;
-      // epilogue exponents T[i, n] = log2 Kuf_in
-      const uint64_t zd = sw128_desc(smem_u32(sZR)), xd = sw128_desc(smem_u32(sXK));
+      // epilogue exponents T[i, n] = log2 Kuf_in of each row block
+      const uint64_t xd = sw128_desc(smem_u32(sXK));
 #pragma unroll
-      for (int kk = 0; kk < KB / 16; ++kk) {
-        const uint64_t o = (uint64_t)(kk * 2);
-        mma_bf16(tmem + G::T, zd + o, xd + o, ID_MAIN, kk != 0);
+      for (int ib = 0; ib < NI; ++ib) {
+        const uint64_t zd = sw128_desc(smem_u32(sZR + ib * GT));
+#pragma unroll
+        for (int kk = 0; kk < KB / 16; ++kk) {
+          const uint64_t o = (uint64_t)(kk * 2);
+          mma_bf16(tmem + G::T(ib), zd + o, xd + o, ID_MAIN, kk != 0);
+        }
       }
       mma_commit(BAR(B_ACC));
     }
@@ -238,15 +257,22 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
     float* colbuf = ebuf;
     float* gq = ebuf + 128;
     float* xq = ebuf + 256;
-    const int i = m0 + row;
-    float cv = 0.f, cn = 0.f;
-    if (grad) {
-      cv = i < we.gen.M ? we.c * __ldg(we.v + i) : 0.f;
-      if (!we.hn) cn = we.c / *we.noise;          // Gaussian: -2 c h_n = c / noise
-    }
-    float S0 = 0.f, S1[DP], S2[DP];
+    float cv[NI], cn = 0.f;
 #pragma unroll
-    for (int d = 0; d < DP; ++d) { S1[d] = 0.f; S2[d] = 0.f; }
+    for (int ib = 0; ib < NI; ++ib) {
+      const int i = m0 + 128 * ib + row;
+      cv[ib] = (grad && i < we.gen.M) ? we.c * __ldg(we.v + i) : 0.f;
+    }
+    if (grad && !we.hn) cn = we.c / *we.noise;          // Gaussian: -2 c h_n = c / noise
+    // row sums as packed FP32 pairs: S1p[ib][j] = (S1_2j, S1_2j+1), likewise S2p
+    float S0[NI];
+    f32x2 S1p[NI][DP / 2], S2p[NI][DP / 2];
+#pragma unroll
+    for (int ib = 0; ib < NI; ++ib) {
+      S0[ib] = 0.f;
+#pragma unroll
+      for (int j = 0; j < DP / 2; ++j) { S1p[ib][j] = 0ull; S2p[ib][j] = 0ull; }
+    }
     int g = 0, lt = 0;
     for (int nb = blockIdx.x; nb < wa.nblk; nb += gridDim.x, ++lt) {
       const int n0 = nb * 128;
@@ -295,71 +321,85 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
           colbuf[tid] = (grad && n0 + tid < B) ? (we.hn ? -2.0f * we.c * __ldg(we.hn + n0 + tid) : cn) : 0.f;
       }
       asm volatile("bar.sync 1, %0;" ::"n"(32 * NTW) : "memory");
-      if (ok) {
-        const uint32_t tacc = tmem + lane_off + G::ACC, texp = tmem + lane_off + G::T;
-        for (int ch = 2 * half; ch < 2 * half + 2; ++ch) {
-          float w[32], tt[32];
-          tmem_ld32(tacc + (uint32_t)(ch * 32), w);
-          tmem_ld32(texp + (uint32_t)(ch * 32), tt);
+#pragma unroll
+      for (int ib = 0; ib < NI; ++ib) {
+       if (ok) {
+        const uint32_t tacc = tmem + lane_off + G::ACC(ib), texp = tmem + lane_off + G::T(ib);
+        // 16-column chunks: the row sums of both row blocks stay in registers
+        for (int ch = 4 * half; ch < 4 * half + 4; ++ch) {
+          float w[16], tt[16];
+          tmem_ld16(tacc + (uint32_t)(ch * 16), w);
+          tmem_ld16(texp + (uint32_t)(ch * 16), tt);
           if (grad) {
 #pragma unroll
-            for (int q = 0; q < 32; ++q) {
-              const int n = ch * 32 + q;
-              const float a = ex2(tt[q]) * fmaf(cv, gq[n], colbuf[n] * w[q]);
-              S0 += a;
-              const float4* xr = reinterpret_cast<const float4*>(xq + n * XW);
+            for (int q = 0; q < 16; ++q) {
+              const int n = ch * 16 + q;
+              const float a = ex2(tt[q]) * fmaf(cv[ib], gq[n], colbuf[n] * w[q]);
+              S0[ib] += a;
+              const f32x2 a2 = pack2(a, a);
+              const ulonglong2* xr = reinterpret_cast<const ulonglong2*>(xq + n * XW);
 #pragma unroll
               for (int d4 = 0; d4 < DP / 4; ++d4) {
-                const float4 x = xr[d4], x2 = xr[DP / 4 + d4];
-                S1[4 * d4 + 0] = fmaf(a, x.x, S1[4 * d4 + 0]);
-                S1[4 * d4 + 1] = fmaf(a, x.y, S1[4 * d4 + 1]);
-                S1[4 * d4 + 2] = fmaf(a, x.z, S1[4 * d4 + 2]);
-                S1[4 * d4 + 3] = fmaf(a, x.w, S1[4 * d4 + 3]);
-                S2[4 * d4 + 0] = fmaf(a, x2.x, S2[4 * d4 + 0]);
-                S2[4 * d4 + 1] = fmaf(a, x2.y, S2[4 * d4 + 1]);
-                S2[4 * d4 + 2] = fmaf(a, x2.z, S2[4 * d4 + 2]);
-                S2[4 * d4 + 3] = fmaf(a, x2.w, S2[4 * d4 + 3]);
+                const ulonglong2 x = xr[d4], x2 = xr[DP / 4 + d4];
+                fma2(S1p[ib][2 * d4], a2, x.x);
+                fma2(S1p[ib][2 * d4 + 1], a2, x.y);
+                fma2(S2p[ib][2 * d4], a2, x2.x);
+                fma2(S2p[ib][2 * d4 + 1], a2, x2.y);
               }
             }
           } else if (we.colsum) {
 #pragma unroll
-            for (int q = 0; q < 32; ++q) {
+            for (int q = 0; q < 16; ++q) {
               float sv = ex2(tt[q]) * w[q];
 #pragma unroll
               for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
-              if (lane == 0) atomicAdd(colbuf + ch * 32 + q, sv);
+              if (lane == 0) atomicAdd(colbuf + ch * 16 + q, sv);
             }
           }
         }
+       }
       }
       fence_before();
       asm volatile("bar.sync 1, %0;" ::"n"(32 * NTW) : "memory");
+      // accumulators and T of this n-block are read: the MMA warp may go on
+      if (lane == 0) mbar_arrive(BAR(B_EDONE));
       if (ok && we.colsum && tid < 128 && n0 + tid < B) atomicAdd(we.colsum + n0 + tid, colbuf[tid]);
     }
     // combine the two column halves and write this CTA's partial rows
     if (grad) {
       constexpr int CW = 2 * DP + 1;
       float* comb = xq;
-      if (half == 1) {
-        comb[row * CW + 2 * DP] = S0;
 #pragma unroll
-        for (int d = 0; d < DP; ++d) { comb[row * CW + d] = S1[d]; comb[row * CW + DP + d] = S2[d]; }
-      }
-      asm volatile("bar.sync 1, %0;" ::"n"(32 * NTW) : "memory");
-      if (half == 0 && !*abort_flag) {
-        S0 += comb[row * CW + 2 * DP];
-        const int W = 2 * D + 1;
-        float* out = wa.rowpart + (size_t)blockIdx.x * W * wa.Mp + i;
+      for (int ib = 0; ib < NI; ++ib) {
+        const int i = m0 + 128 * ib + row;
+        if (ib > 0) asm volatile("bar.sync 1, %0;" ::"n"(32 * NTW) : "memory");   // comb is free again
+        float S1[DP], S2[DP];
 #pragma unroll
-        for (int d = 0; d < DP; ++d) {
-          if (d < D) {
-            const float s1 = S1[d] + comb[row * CW + d], s2 = S2[d] + comb[row * CW + DP + d];
-            const float z = i < we.gen.M ? __ldg(we.gen.Zs + (size_t)i * Dp + d) : 0.f;
-            out[(size_t)d * wa.Mp] = fmaf(-z, S0, s1);
-            out[(size_t)(D + d) * wa.Mp] = fmaf(z, fmaf(z, S0, -2.0f * s1), s2);
-          }
+        for (int j = 0; j < DP / 2; ++j) {
+          unpack2(S1p[ib][j], S1[2 * j], S1[2 * j + 1]);
+          unpack2(S2p[ib][j], S2[2 * j], S2[2 * j + 1]);
         }
-        out[(size_t)(2 * D) * wa.Mp] = S0;
+        if (half == 1) {
+          comb[row * CW + 2 * DP] = S0[ib];
+#pragma unroll
+          for (int d = 0; d < DP; ++d) { comb[row * CW + d] = S1[d]; comb[row * CW + DP + d] = S2[d]; }
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * NTW) : "memory");
+        if (half == 0 && !*abort_flag) {
+          const float s0 = S0[ib] + comb[row * CW + 2 * DP];
+          const int W = 2 * D + 1;
+          float* out = wa.rowpart + (size_t)blockIdx.x * W * wa.Mp + i;
+#pragma unroll
+          for (int d = 0; d < DP; ++d) {
+            if (d < D) {
+              const float s1 = S1[d] + comb[row * CW + d], s2 = S2[d] + comb[row * CW + DP + d];
+              const float z = i < we.gen.M ? __ldg(we.gen.Zs + (size_t)i * Dp + d) : 0.f;
+              out[(size_t)d * wa.Mp] = fmaf(-z, s0, s1);
+              out[(size_t)(D + d) * wa.Mp] = fmaf(z, fmaf(z, s0, -2.0f * s1), s2);
+            }
+          }
+          out[(size_t)(2 * D) * wa.Mp] = s0;
+        }
       }
     }
   }
@@ -372,40 +412,53 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
   }
 }
 
-template <int NSPLIT, int DP>
+template <int NSPLIT, int DP, int NI>
 void set_w_attr() {
-  cudaFuncSetAttribute(w_tc_kernel<NSPLIT, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, WGeo<NSPLIT>::SMEM);
+  cudaFuncSetAttribute(w_tc_kernel<NSPLIT, DP, NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       WGeo<NSPLIT, NI>::SMEM);
 }
 
-template <int NSPLIT>
+template <int NSPLIT, int NI>
 void launch_w(dim3 grid, cudaStream_t st, const CUtensorMap (&m)[6], const WArgs& wa, const WEpi& we) {
   const int D = we.gen.D;
+  constexpr int SM = WGeo<NSPLIT, NI>::SMEM;
   svgp_note_launch();
   if (D <= 4)
-    pdl_launch(w_tc_kernel<NSPLIT, 4>, grid, THREADS, WGeo<NSPLIT>::SMEM, st, m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
+    pdl_launch(w_tc_kernel<NSPLIT, 4, NI>, grid, THREADS, SM, st, m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
   else if (D <= 8)
-    pdl_launch(w_tc_kernel<NSPLIT, 8>, grid, THREADS, WGeo<NSPLIT>::SMEM, st, m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
+    pdl_launch(w_tc_kernel<NSPLIT, 8, NI>, grid, THREADS, SM, st, m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
   else if (D <= 16)
-    pdl_launch(w_tc_kernel<NSPLIT, 16>, grid, THREADS, WGeo<NSPLIT>::SMEM, st, m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
+    pdl_launch(w_tc_kernel<NSPLIT, 16, NI>, grid, THREADS, SM, st, m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
   else
-    pdl_launch(w_tc_kernel<NSPLIT, 24>, grid, THREADS, WGeo<NSPLIT>::SMEM, st, m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
+    pdl_launch(w_tc_kernel<NSPLIT, 24, NI>, grid, THREADS, SM, st, m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
+}
+
+// Row blocks per CTA: two with BF16 operands when the 128-row blocks pair up
+// and the (row-pair, n-block) units still give every SM a CTA.
+int w_ni(bool split, int Mp, int B) {
+  const int nblk = (B + 127) / 128;
+  return (!split && (Mp / 128) % 2 == 0 && (Mp / 256) * nblk >= tc_num_sms()) ? 2 : 1;
 }
 
 }  // namespace
 
 void tc_w_init_attributes() {
-  set_w_attr<1, 4>();
-  set_w_attr<1, 8>();
-  set_w_attr<1, 16>();
-  set_w_attr<1, 24>();
-  set_w_attr<3, 4>();
-  set_w_attr<3, 8>();
-  set_w_attr<3, 16>();
-  set_w_attr<3, 24>();
+  set_w_attr<1, 4, 1>();
+  set_w_attr<1, 8, 1>();
+  set_w_attr<1, 16, 1>();
+  set_w_attr<1, 24, 1>();
+  set_w_attr<1, 4, 2>();
+  set_w_attr<1, 8, 2>();
+  set_w_attr<1, 16, 2>();
+  set_w_attr<1, 24, 2>();
+  set_w_attr<3, 4, 1>();
+  set_w_attr<3, 8, 1>();
+  set_w_attr<3, 16, 1>();
+  set_w_attr<3, 24, 1>();
 }
 
-int tc_w_groups(int Mp, int B) {
-  const int nblk = (B + 127) / 128, rb = Mp / 128;
+int tc_w_groups(int Mp, int B, bool split) {
+  const int nblk = (B + 127) / 128, rb = Mp / (128 * w_ni(split, Mp, B));
   int gn = tc_num_sms() / rb;
   if (gn < 1) gn = 1;
   if (gn > nblk) gn = nblk;
@@ -426,10 +479,12 @@ int tc_w(const GemmCtx& g, const bf16* P, const KufTC& t, const WEpi& we, float*
   } else {
     m[5] = m[4];
   }
-  const int gn = tc_w_groups(g.Mp, B);
+  const int ni = w_ni(g.split, g.Mp, B);
+  const int gn = tc_w_groups(g.Mp, B, g.split);
   WArgs wa{g.Mp / KB, Bp / 128, g.Mp, g.err, we.rowacc ? rowpart : nullptr};
-  dim3 grid(gn, g.Mp / 128);
-  if (g.split) launch_w<3>(grid, g.st, m, wa, we);
-  else launch_w<1>(grid, g.st, m, wa, we);
+  dim3 grid(gn, g.Mp / (128 * ni));
+  if (g.split) launch_w<3, 1>(grid, g.st, m, wa, we);
+  else if (ni == 2) launch_w<1, 2>(grid, g.st, m, wa, we);
+  else launch_w<1, 1>(grid, g.st, m, wa, we);
   return wa.rowpart ? gn : 0;
 }

@@ -72,7 +72,7 @@ bool tc_psi(const GemmCtx& g, const KufGen& kg, const KufTC& t, const bf16* Kk, 
 // writes per-CTA partial rows rowpart[p][k][i] (p < returned count, k < 2D+1,
 // i < Mp) instead of rowacc; variance mode returns 0.  -1: not supported.
 int tc_w(const GemmCtx& g, const bf16* P, const KufTC& t, const WEpi& we, float* rowpart);
-int tc_w_groups(int Mp, int B);
+int tc_w_groups(int Mp, int B, bool split);
 void tc_w_init_attributes();
 // out[r] = sum_k Kuf(r, k) w_k for r < nrows, k < nk, from the row-role vectors
 // of the row points and the k-role vectors of the k points (kuf_prep).
@@ -135,9 +135,14 @@ void k_kuu_bwd(const float* GKuu, const float* Kuu, const float* Zs, int M, int 
 void k_logs(const float* s, int M, double* red, cudaStream_t st);
 void k_grad_finalize(const float* rowacc_f, const float* rowacc_u, const float* rowpart, int nparts, int Mp,
                      const float* ell, int M, int D, float* dZ, double* acc_ell, double* red, cudaStream_t st);
+// Hutchinson sums of the KL traces into red[RED_HKT], red[RED_HW1],
+// red[RED_HX4] for K probes Z (M x K); buffers of M x K floats (hutchinson.cu).
+void k_hutchinson(const float* Lf, const float* Kuu, const float* s, int M, int Mp, const float* Z, int K,
+                  float* bufA, float* bufB, float* bufC, double* red, cudaStream_t st);
 // probit: E from red[RED_ELL], dsf2's data part from red[RED_SUMH], dnoise = 0.
+// hutch_K > 0: tr(K~T) and tr(P Kuu) from the Hutchinson sums over hutch_K probes.
 void k_terms_finalize(const double* red, const double* acc_ell, const float* sf2, const float* noise,
-                      const float* ell, int M, int D, int B, double N, bool probit, double* terms,
+                      const float* ell, int M, int D, int B, double N, bool probit, int hutch_K, double* terms,
                       float* dsf2, float* dnoise, float* dell, int* errword, cudaStream_t st);
 void k_predict_finalize(const float* colsum, const float* sf2, const float* noise, int Ns,
                         int include_noise, float* var, cudaStream_t st);

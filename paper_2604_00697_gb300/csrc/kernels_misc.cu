@@ -353,9 +353,11 @@ __global__ void __launch_bounds__(256) kuu_bwd_kernel(const float* __restrict__ 
     zs[r][d] = zv;
     zs[r][DP + d] = zv * zv;
   }
-  float S1[DP], S2[DP], S0 = 0.f;
+  // packed FP32 pairs: S1p[j] = (S1_2j, S1_2j+1), likewise S2p
+  f32x2 S1p[DP / 2], S2p[DP / 2];
+  float S0 = 0.f;
 #pragma unroll
-  for (int d = 0; d < DP; ++d) { S1[d] = 0.f; S2[d] = 0.f; }
+  for (int j = 0; j < DP / 2; ++j) { S1p[j] = 0ull; S2p[j] = 0ull; }
   __syncthreads();
   if (i < M) {
     for (int j = jb + warp; j < je; j += 8 * U) {
@@ -368,24 +370,27 @@ __global__ void __launch_bounds__(256) kuu_bwd_kernel(const float* __restrict__ 
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int jj = min(j + 8 * u, je - 1) - jb;
-        const float4* zj = reinterpret_cast<const float4*>(&zs[jj][0]);
+        const ulonglong2* zj = reinterpret_cast<const ulonglong2*>(&zs[jj][0]);
         S0 += a[u];
+        const f32x2 a2 = pack2(a[u], a[u]);
 #pragma unroll
         for (int d4 = 0; d4 < DP / 4; ++d4) {
-          const float4 q = zj[d4], q2 = zj[DP / 4 + d4];
-          S1[4 * d4 + 0] = fmaf(a[u], q.x, S1[4 * d4 + 0]);
-          S1[4 * d4 + 1] = fmaf(a[u], q.y, S1[4 * d4 + 1]);
-          S1[4 * d4 + 2] = fmaf(a[u], q.z, S1[4 * d4 + 2]);
-          S1[4 * d4 + 3] = fmaf(a[u], q.w, S1[4 * d4 + 3]);
-          S2[4 * d4 + 0] = fmaf(a[u], q2.x, S2[4 * d4 + 0]);
-          S2[4 * d4 + 1] = fmaf(a[u], q2.y, S2[4 * d4 + 1]);
-          S2[4 * d4 + 2] = fmaf(a[u], q2.z, S2[4 * d4 + 2]);
-          S2[4 * d4 + 3] = fmaf(a[u], q2.w, S2[4 * d4 + 3]);
+          const ulonglong2 q = zj[d4], q2 = zj[DP / 4 + d4];
+          fma2(S1p[2 * d4], a2, q.x);
+          fma2(S1p[2 * d4 + 1], a2, q.y);
+          fma2(S2p[2 * d4], a2, q2.x);
+          fma2(S2p[2 * d4 + 1], a2, q2.y);
         }
       }
     }
   }
   const float* zi = Zs + (size_t)(i < M ? i : 0) * Dp;
+  float S1[DP], S2[DP];
+#pragma unroll
+  for (int j = 0; j < DP / 2; ++j) {
+    unpack2(S1p[j], S1[2 * j], S1[2 * j + 1]);
+    unpack2(S2p[j], S2[2 * j], S2[2 * j + 1]);
+  }
 #pragma unroll
   for (int d = 0; d < DP; ++d) {
     if (d < D) {
@@ -475,7 +480,7 @@ __global__ void __launch_bounds__(256) grad_finalize_kernel(const float* __restr
 __global__ void terms_finalize_kernel(const double* __restrict__ red, const double* __restrict__ acc_ell,
                                       const float* __restrict__ sf2p, const float* __restrict__ noisep,
                                       const float* __restrict__ ell, int M, int D, int B, double N, bool probit,
-                                      double* terms, float* dsf2, float* dnoise, float* dell,
+                                      int hutch_K, double* terms, float* dsf2, float* dnoise, float* dell,
                                       int* errword) {
   pdl_enter();
   if (threadIdx.x != 0) return;
@@ -483,6 +488,10 @@ __global__ void terms_finalize_kernel(const double* __restrict__ red, const doub
   double trA1 = red[RED_TRA1], froA1 = red[RED_FROA1];
   double trPKt = 2.0 * trA1 - froA1;                 // tr(P K~) = tr((2I - A1) A1)
   double trPKuu = trPKt - red[RED_SPDIAG];            // minus tr(P diag(s))
+  if (hutch_K > 0) {                                  // Section 3.4 estimates
+    trA1 = red[RED_HKT] / hutch_K;
+    trPKuu = (2.0 * red[RED_HW1] - red[RED_HX4]) / hutch_K;
+  }
   double quad = red[RED_QUAD];
   double logdetT = 2.0 * red[RED_LOGDETL];
   double logdetS = red[RED_LOGS];
@@ -751,10 +760,10 @@ void k_grad_finalize(const float* rowacc_f, const float* rowacc_u, const float* 
 }
 
 void k_terms_finalize(const double* red, const double* acc_ell, const float* sf2, const float* noise,
-                      const float* ell, int M, int D, int B, double N, bool probit, double* terms, float* dsf2,
-                      float* dnoise, float* dell, int* errword, cudaStream_t st) {
+                      const float* ell, int M, int D, int B, double N, bool probit, int hutch_K, double* terms,
+                      float* dsf2, float* dnoise, float* dell, int* errword, cudaStream_t st) {
   svgp_note_launch();
-  pdl_launch(terms_finalize_kernel, 1, 32, 0, st, red, acc_ell, sf2, noise, ell, M, D, B, N, probit, terms, dsf2, dnoise,
+  pdl_launch(terms_finalize_kernel, 1, 32, 0, st, red, acc_ell, sf2, noise, ell, M, D, B, N, probit, hutch_K, terms, dsf2, dnoise,
                                           dell, errword);
 }
 

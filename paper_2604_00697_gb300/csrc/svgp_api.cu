@@ -59,6 +59,7 @@ struct svgp_handle {
   GHRule gh;        // probit: Gauss-Hermite rule (weights divided by sqrt(pi))
   float* hn;        // probit: per-point h_n = dE_n/dsigma_n^2
   float* gapN;      // Prop. 3 gap: N = I - T K~ (FP32, Mp x Mp)
+  float* hut;       // Hutchinson chains: three M x SVGP_HUTCH_KMAX buffers
   double *red, *acc_ell, *resid_tmp;
   int *errword, *done, *iters_tmp;
   GemmCtx gs, gt;   // SIMT and tensor-core tile tables
@@ -352,7 +353,7 @@ void backward_tail(svgp_handle* h, const svgp_params* p, const svgp_batch* b, do
   else k_gemv(h->Pf, Mp, M, h->Kg, c, h->w, -1.0f / c, gr->dm, nullptr, nullptr, st); // dm = P (c Kg - w)
   k_grad_finalize(h->rowacc_f, h->rowacc_u, h->rowpart, nparts, Mp, p->ell, M, h->D, gr->dZ, h->acc_ell, h->red,
                   st);
-  k_terms_finalize(h->red, h->acc_ell, p->sf2, p->noise, p->ell, M, h->D, b->B, b->N, h->probit, terms_dev,
+  k_terms_finalize(h->red, h->acc_ell, p->sf2, p->noise, p->ell, M, h->D, b->B, b->N, h->probit, 0, terms_dev,
                    gr->dsf2, gr->dnoise, gr->dell, h->errword, st);
 }
 
@@ -471,11 +472,12 @@ svgp_status svgp_create(const svgp_config* cfg, svgp_handle** out) {
             dalloc(h, &h->done, sizeof(int)) && dalloc(h, &h->iters_tmp, sizeof(int));
   if (ok && h->mode != MODE_F32) ok = dalloc(h, &h->Kuu_lo, lob) && dalloc(h, &h->P_lo, lob);
   if (ok) ok = dalloc(h, &h->gapN, M2 * 4);
+  if (ok) ok = dalloc(h, &h->hut, sizeof(float) * 3 * (size_t)h->M * SVGP_HUTCH_KMAX);
   h->tc_kuf = h->mode != MODE_F32 && tc_kuf_supported(h->D);
   if (ok && h->tc_kuf)
     ok = dalloc(h, &h->kt.ZR, 2 * 64 * h->Mp) && dalloc(h, &h->kt.ZK, 2 * 64 * h->Mp) &&
          dalloc(h, &h->kt.XR, 2 * 64 * Bp) && dalloc(h, &h->kt.XK, 2 * 64 * Bp) &&
-         dalloc(h, &h->rowpart, sizeof(float) * ((size_t)tc_num_sms() * 128 + h->Mp) * W);
+         dalloc(h, &h->rowpart, sizeof(float) * ((size_t)tc_num_sms() * 256 + h->Mp) * W);
   if (ok && h->probit) {
     ok = dalloc(h, &h->hn, sizeof(float) * Bp);
     if (ok && h->tc_kuf) ok = dalloc(h, &h->kt.XKh, 2 * 64 * Bp);
@@ -556,9 +558,26 @@ svgp_status svgp_bound(svgp_handle* h, const svgp_params* p, const svgp_batch* b
   if (s != SVGP_OK) return s;
   prologue(h, p, b->X, b->B, p->L);
   forward(h, p, b, true);
-  k_terms_finalize(h->red, h->acc_ell, p->sf2, p->noise, p->ell, h->M, h->D, b->B, b->N, h->probit, terms_dev,
+  k_terms_finalize(h->red, h->acc_ell, p->sf2, p->noise, p->ell, h->M, h->D, b->B, b->N, h->probit, 0, terms_dev,
                    nullptr, nullptr, nullptr, h->errword, h->st);
   return check_launch(h, "svgp_bound");
+}
+
+svgp_status svgp_bound_hutchinson(svgp_handle* h, const svgp_params* p, const svgp_batch* b, const float* probes,
+                                  int K, double* terms_dev) {
+  if (!h) return SVGP_ERR_INVALID_ARG;
+  if (!valid_params(h, p) || !probes || !terms_dev)
+    return fail(h, SVGP_ERR_INVALID_ARG, "bound_hutchinson: null pointer");
+  if (K < 1 || K > SVGP_HUTCH_KMAX) return fail(h, SVGP_ERR_INVALID_ARG, "bound_hutchinson: K out of [1, 256]");
+  svgp_status s = validate_batch(h, b);
+  if (s != SVGP_OK) return s;
+  prologue(h, p, b->X, b->B, p->L);
+  forward(h, p, b, true);
+  k_hutchinson(h->Lf, h->Kuu_f, p->s, h->M, h->Mp, probes, K, h->hut, h->hut + (size_t)h->M * SVGP_HUTCH_KMAX,
+               h->hut + 2 * (size_t)h->M * SVGP_HUTCH_KMAX, h->red, h->st);
+  k_terms_finalize(h->red, h->acc_ell, p->sf2, p->noise, p->ell, h->M, h->D, b->B, b->N, h->probit, K, terms_dev,
+                   nullptr, nullptr, nullptr, h->errword, h->st);
+  return check_launch(h, "svgp_bound_hutchinson");
 }
 
 svgp_status svgp_backward(svgp_handle* h, const svgp_params* p, const svgp_batch* b, double* terms_dev,

@@ -125,6 +125,14 @@ class RSVGP:
         C.svgp_ng_update_T(self.h, self.params, self.L.data_ptr(), self.gamma.data_ptr(), max_iters, eps,
                            self.iters.data_ptr(), self.resid.data_ptr())
 
+    def bound_hutchinson(self, X, y, N, probes):
+        """Bound with the KL traces estimated from the probe columns (M x K, +-1)."""
+        self._sync_stream()
+        pr = probes.to(self.dev, torch.float32).contiguous()
+        C.svgp_bound_hutchinson(self.h, self.params, self.batch(X, y, N), pr.data_ptr(), pr.shape[1],
+                                self.terms.data_ptr())
+        return self.terms
+
     def variance_gap(self, X, y, N, sigma2=0.0):
         """Prop. 3 gap G = sum_n ||(I - K~ T) k_un||^2 / sigma2 (sigma2 <= 0: min s~)."""
         self._sync_stream()
@@ -193,3 +201,45 @@ def paper_init(M, D, Z0, sf2=1.0, noise=1.0, ell=1.0, alpha=1e-4, beta=1e-3):
 
     return dict(Z=np.asarray(Z0, np.float64), ell=np.full(D, ell), sf2=sf2, noise=noise,
                 m=np.zeros(M), s=np.full(M, alpha), L=beta * np.eye(M))
+
+
+class RSVGPGroup:
+    """Many independent SVGPs (possibly of different M) trained together.
+
+    One training step of the group is one step of every member.  ``capture``
+    records all members' steps into ONE CUDA graph whose branches run on
+    separate streams forked from the capturing stream, so kernels of
+    different members overlap on the GPU (a small member's launches fill the
+    SMs a large member leaves idle) and the whole group step replays as a
+    single graph launch.
+    """
+
+    def __init__(self, models):
+        self.models = list(models)
+        self.streams = [torch.cuda.Stream() for _ in self.models]
+
+    def train_step(self, batches, t_star=1, eps=0.0):
+        """Eager group step: batches[i] = (X, y, N) for member i."""
+        cur = torch.cuda.current_stream()
+        for m, s, (X, y, N) in zip(self.models, self.streams, batches):
+            s.wait_stream(cur)
+            with torch.cuda.stream(s):
+                m.train_step(X, y, N, t_star=t_star, eps=eps)
+        for s in self.streams:
+            cur.wait_stream(s)
+
+    def capture(self, batches, t_star=1, eps=0.0):
+        """Capture one group step on fixed input buffers into a CUDA graph."""
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.train_step(batches, t_star=t_star, eps=eps)
+        for m in self.models:
+            m._sync_stream()
+        return g
+
+    def sync_status(self):
+        return [m.sync_status() for m in self.models]
+
+    def close(self):
+        for m in self.models:
+            m.close()

@@ -157,6 +157,64 @@ def test_ng_update_with_gap_rule_matches_oracle(prec):
     m.close()
 
 
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("K", [1, 16, 200])
+def test_bound_hutchinson_matches_oracle(prec, K):
+    """Bound with the KL traces estimated from K Rademacher probes (Section
+    3.4): same probes on both sides, so the estimate is compared exactly."""
+    M = 130
+    p, X, y, N = small_case(M, 3, 300, 6)
+    probes = np.where(np.random.default_rng([K, 8]).uniform(size=(M, K)) < 0.5, -1.0, 1.0)
+    ref = O.bound(p, X, y, N, probes=probes)
+    m = _model(p, M, 3, 300, prec)
+    t = m.bound_hutchinson(_dev(X), _dev(y), N, torch.tensor(probes, dtype=torch.float32)).cpu().numpy()
+    assert m.sync_status() == 0
+    tb, _, kappa = tolerances(prec, p)
+    assert abs(t[0] - ref["F"]) <= tb * abs(ref["F"]), (t[0], ref["F"])
+    # the estimates come from FP32 chains in every mode
+    tt = max(1e-5, 2.0 ** -24 * 8 * kappa)
+    assert abs(t[3] - ref["tr_KtT"]) <= tt * max(1.0, abs(ref["tr_KtT"])), (t[3], ref["tr_KtT"])
+    assert abs(t[4] - ref["tr_PKuu"]) <= tt * max(1.0, abs(ref["tr_PKuu"])), (t[4], ref["tr_PKuu"])
+    m.close()
+
+
+def test_group_step_matches_separate_models():
+    """Several SVGPs of different M stepped together (one CUDA graph with a
+    branch per member) give the results of stepping each alone."""
+    from paper_2604_00697_gb300.model import RSVGPGroup
+
+    sizes = [(40, 3, 100), (130, 3, 300), (256, 4, 512), (70, 2, 64)]
+    cases = [small_case(M, D, B, 20 + k) for k, (M, D, B) in enumerate(sizes)]
+
+    def make():
+        ms = []
+        for (M, D, B), (p, X, y, N) in zip(sizes, cases):
+            ms.append(_model(p, M, D, B, "bf16"))
+        return ms
+
+    solo = make()
+    for m, (p, X, y, N) in zip(solo, cases):
+        m.train_step(_dev(X), _dev(y), N)
+    torch.cuda.synchronize()
+    group = RSVGPGroup(make())
+    batches = [(_dev(X), _dev(y), N) for (p, X, y, N) in cases]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        g = group.capture(batches)
+    torch.cuda.current_stream().wait_stream(s)
+    g.replay()
+    torch.cuda.synchronize()
+    assert group.sync_status() == [0] * len(sizes)
+    for a, b in zip(solo, group.models):
+        np.testing.assert_allclose(b.terms.cpu().numpy()[:10], a.terms.cpu().numpy()[:10], rtol=1e-6, atol=1e-9)
+        np.testing.assert_allclose(b.cons.cpu().numpy(), a.cons.cpu().numpy(), rtol=1e-5, atol=1e-6)
+        np.testing.assert_allclose(b.L.cpu().numpy(), a.L.cpu().numpy(), rtol=1e-5, atol=1e-7)
+    for m in solo:
+        m.close()
+    group.close()
+
+
 def _probit_labels(X, seed):
     """Binary labels from a smooth random latent function of X."""
     rng = np.random.default_rng([seed, 41])

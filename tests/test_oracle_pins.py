@@ -320,6 +320,30 @@ def test_gap_vanishes_at_T_inverse_and_stops_ng():
     assert it3 == next(t for t in range(4) if Gs[t] <= 2.0 * p["noise"] * eps)
 
 
+def test_hutchinson_traces_exact_over_all_sign_patterns():
+    """Averaged over all 2^M Rademacher sign patterns the Hutchinson estimates
+    equal the exact traces (the off-diagonal terms cancel); the bound with
+    those probes equals the exact bound."""
+    import itertools
+    p = _spaced_state(6, 2, 7)
+    X, y = _batch(12, 2, 7)
+    Zp = np.array(list(itertools.product([-1.0, 1.0], repeat=6))).T       # 6 x 64
+    Kuu = O.se_ard(p["Z"], p["Z"], p["ell"], p["sf2"])
+    Kt = Kuu + np.diag(p["s"])
+    T = p["L"] @ p["L"].T
+    P = 2 * T - T @ Kt @ T
+    trKT, trPKuu = O.hutchinson_traces(p, Zp)
+    assert abs(trKT - np.trace(Kt @ T)) < 1e-10 * max(1.0, abs(trKT))
+    assert abs(trPKuu - np.trace(P @ Kuu)) < 1e-10 * max(1.0, abs(trPKuu))
+    F = O.bound(p, X, y, 40.0)["F"]
+    Fh = O.bound(p, X, y, 40.0, probes=Zp)["F"]
+    assert abs(F - Fh) < 1e-10 * abs(F)
+    # one probe: z^T A z with a single sign pattern differs from the trace
+    z = Zp[:, 5:6]
+    one = O.hutchinson_traces(p, z)[0]
+    assert abs(one - float(z[:, 0] @ p["L"].T @ Kt @ p["L"] @ z[:, 0])) < 1e-12 * max(1.0, abs(one))
+
+
 def test_probit_quadrature_matches_adaptive_integral():
     from scipy import integrate
     from scipy.special import log_ndtr
