@@ -87,6 +87,11 @@ __device__ __forceinline__ void unpack2(f32x2 v, float& a, float& b) {
 __device__ __forceinline__ void fma2(f32x2& d, f32x2 a, f32x2 b) {   // d = a * b + d
   asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
 }
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
 
 // Host side: launch `kern` with programmatic stream serialization allowed.
 template <typename... KArgs, typename... Args>

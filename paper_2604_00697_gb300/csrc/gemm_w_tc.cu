@@ -312,7 +312,6 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
           for (int u = 0; u < PER; ++u) {
             const int e = tid + 256 * u, n = e / DP, d = e - n * DP;
             xq[n * XW + d] = xv[u];
-            xq[n * XW + DP + d] = xv[u] * xv[u];
           }
           if (tid < 128) gq[tid] = gv;
         }
@@ -321,43 +320,57 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
           colbuf[tid] = (grad && n0 + tid < B) ? (we.hn ? -2.0f * we.c * __ldg(we.hn + n0 + tid) : cn) : 0.f;
       }
       asm volatile("bar.sync 1, %0;" ::"n"(32 * NTW) : "memory");
+      if (ok) {
+        // 8-column chunks of every row block at once: each x~ row read from
+        // shared memory (a broadcast to all 32 lanes, the cost that dominates
+        // this epilogue) serves the NI row blocks
+        for (int ch = 8 * half; ch < 8 * half + 8; ++ch) {
+          float w[NI][8], tt[NI][8];
 #pragma unroll
-      for (int ib = 0; ib < NI; ++ib) {
-       if (ok) {
-        const uint32_t tacc = tmem + lane_off + G::ACC(ib), texp = tmem + lane_off + G::T(ib);
-        // 16-column chunks: the row sums of both row blocks stay in registers
-        for (int ch = 4 * half; ch < 4 * half + 4; ++ch) {
-          float w[16], tt[16];
-          tmem_ld16(tacc + (uint32_t)(ch * 16), w);
-          tmem_ld16(texp + (uint32_t)(ch * 16), tt);
+          for (int ib = 0; ib < NI; ++ib) {
+            tmem_ld8(tmem + lane_off + G::ACC(ib) + (uint32_t)(ch * 8), w[ib]);
+            tmem_ld8(tmem + lane_off + G::T(ib) + (uint32_t)(ch * 8), tt[ib]);
+          }
           if (grad) {
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-              const int n = ch * 16 + q;
-              const float a = ex2(tt[q]) * fmaf(cv[ib], gq[n], colbuf[n] * w[q]);
-              S0[ib] += a;
-              const f32x2 a2 = pack2(a, a);
+            for (int q = 0; q < 8; ++q) {
+              const int n = ch * 8 + q;
+              const float gn = gq[n], hn = colbuf[n];
+              f32x2 a2[NI];
+#pragma unroll
+              for (int ib = 0; ib < NI; ++ib) {
+                const float a = ex2(tt[ib][q]) * fmaf(cv[ib], gn, hn * w[ib][q]);
+                S0[ib] += a;
+                a2[ib] = pack2(a, a);
+              }
+              // x~ from shared memory, x~^2 formed in registers (the broadcast
+              // reads, not the arithmetic, bound this loop)
               const ulonglong2* xr = reinterpret_cast<const ulonglong2*>(xq + n * XW);
 #pragma unroll
               for (int d4 = 0; d4 < DP / 4; ++d4) {
-                const ulonglong2 x = xr[d4], x2 = xr[DP / 4 + d4];
-                fma2(S1p[ib][2 * d4], a2, x.x);
-                fma2(S1p[ib][2 * d4 + 1], a2, x.y);
-                fma2(S2p[ib][2 * d4], a2, x2.x);
-                fma2(S2p[ib][2 * d4 + 1], a2, x2.y);
+                const ulonglong2 x = xr[d4];
+                const f32x2 xx0 = mul2(x.x, x.x), xx1 = mul2(x.y, x.y);
+#pragma unroll
+                for (int ib = 0; ib < NI; ++ib) {
+                  fma2(S1p[ib][2 * d4], a2[ib], x.x);
+                  fma2(S1p[ib][2 * d4 + 1], a2[ib], x.y);
+                  fma2(S2p[ib][2 * d4], a2[ib], xx0);
+                  fma2(S2p[ib][2 * d4 + 1], a2[ib], xx1);
+                }
               }
             }
           } else if (we.colsum) {
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-              float sv = ex2(tt[q]) * w[q];
+            for (int q = 0; q < 8; ++q) {
+              float sv = 0.f;
+#pragma unroll
+              for (int ib = 0; ib < NI; ++ib) sv = fmaf(ex2(tt[ib][q]), w[ib][q], sv);
 #pragma unroll
               for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
-              if (lane == 0) atomicAdd(colbuf + ch * 16 + q, sv);
+              if (lane == 0) atomicAdd(colbuf + ch * 8 + q, sv);
             }
           }
         }
-       }
       }
       fence_before();
       asm volatile("bar.sync 1, %0;" ::"n"(32 * NTW) : "memory");

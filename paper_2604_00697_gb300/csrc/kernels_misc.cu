@@ -330,8 +330,9 @@ __global__ void gp_assemble_kernel(const float* __restrict__ Kuu, const float* _
 // as S1_d - z~_id S0 and S2_d - 2 z~_id S1_d + z~_id^2 S0.
 // Block = 32 rows (lane = row i) x a range of at most 256 columns j, split
 // over the 8 warps.  A is symmetric, so A_ij is read as A[j][i]: a warp reads
-// 32 consecutive floats of row j (four rows in flight per warp).  z~_j and
-// z~_j^2 of the range are staged in shared memory and read as broadcasts.
+// 32 consecutive floats of row j (four rows in flight per warp).  z~_j of the
+// range is staged in shared memory and read as broadcasts (their cost bounds
+// the loop, so z~_j^2 is formed in registers).
 // Warp partials meet in shared memory; one atomic per row and value per block.
 template <int DP>
 __global__ void __launch_bounds__(256) kuu_bwd_kernel(const float* __restrict__ GK, const float* __restrict__ Kuu,
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(256) kuu_bwd_kernel(const float* __restrict__ 
   pdl_enter();
   constexpr int W = 2 * DP + 1;
   constexpr int U = 4;
-  __shared__ __align__(16) float zs[256][2 * DP];
+  __shared__ __align__(16) float zs[256][DP];
   __shared__ float part[32][W + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * 32 + lane;
@@ -351,7 +352,6 @@ __global__ void __launch_bounds__(256) kuu_bwd_kernel(const float* __restrict__ 
     const int r = e / DP, d = e - r * DP;
     const float zv = (jb + r < je && d < Dp) ? __ldg(Zs + (size_t)(jb + r) * Dp + d) : 0.f;
     zs[r][d] = zv;
-    zs[r][DP + d] = zv * zv;
   }
   // packed FP32 pairs: S1p[j] = (S1_2j, S1_2j+1), likewise S2p
   f32x2 S1p[DP / 2], S2p[DP / 2];
@@ -375,11 +375,11 @@ __global__ void __launch_bounds__(256) kuu_bwd_kernel(const float* __restrict__ 
         const f32x2 a2 = pack2(a[u], a[u]);
 #pragma unroll
         for (int d4 = 0; d4 < DP / 4; ++d4) {
-          const ulonglong2 q = zj[d4], q2 = zj[DP / 4 + d4];
+          const ulonglong2 q = zj[d4];
           fma2(S1p[2 * d4], a2, q.x);
           fma2(S1p[2 * d4 + 1], a2, q.y);
-          fma2(S2p[2 * d4], a2, q2.x);
-          fma2(S2p[2 * d4 + 1], a2, q2.y);
+          fma2(S2p[2 * d4], a2, mul2(q.x, q.x));
+          fma2(S2p[2 * d4 + 1], a2, mul2(q.y, q.y));
         }
       }
     }
