@@ -330,7 +330,7 @@ __global__ void gp_assemble_kernel(const float* __restrict__ Kuu, const float* _
 // as S1_d - z~_id S0 and S2_d - 2 z~_id S1_d + z~_id^2 S0.
 // Block = 32 rows (lane = row i) x a range of at most 256 columns j, split
 // over the 8 warps.  A is symmetric, so A_ij is read as A[j][i]: a warp reads
-// 32 consecutive floats of row j (four rows in flight per warp).  z~_j of the
+// 32 consecutive floats of row j (eight rows in flight per warp).  z~_j of the
 // range is staged in shared memory and read as broadcasts (their cost bounds
 // the loop, so z~_j^2 is formed in registers).
 // Warp partials meet in shared memory; one atomic per row and value per block.
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(256) kuu_bwd_kernel(const float* __restrict__ 
                                                      float* __restrict__ rowacc, int JB) {
   pdl_enter();
   constexpr int W = 2 * DP + 1;
-  constexpr int U = 4;
+  constexpr int U = 8;
   __shared__ __align__(16) float zs[256][DP];
   __shared__ float part[32][W + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -437,3 +437,47 @@ def test_fused_train_step_matches_separate_calls(prec):
                                atol=1e-5 * float(a.grad.abs().max()))
     a.close()
     b.close()
+
+
+def test_empty_batch_and_probit_options_are_rejected():
+    from paper_2604_00697_gb300 import _lib
+
+    p, X, y, N = small_case(20, 2, 30, 1)
+    m = _model(p, 20, 2, 30, "bf16")
+    with pytest.raises(_lib.SvgpError):
+        m.bound(_dev(X[:0]), _dev(y[:0]), N)        # B = 0
+    with pytest.raises(_lib.SvgpError):
+        m.bound_hutchinson(_dev(X), _dev(y), N, torch.ones(20, 257))   # K > 256
+    m.close()
+    with pytest.raises(_lib.SvgpError):           # gh_points > 32
+        _lib.svgp_create(20, 2, 30, _lib.SVGP_BF16, lik=_lib.SVGP_LIK_BERNOULLI_PROBIT, gh_points=33)
+    pm = _model(p, 20, 2, 30, "bf16", likelihood="probit")
+    with pytest.raises(_lib.SvgpError):           # the gap rule is for the Gaussian likelihood
+        pm.ng_update_gap(_dev(X), _dev(y), N, max_iters=1)
+    pm.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_ng_fixed_point_at_large_M(prec):
+    """M = 4096 (twice the benchmark's): at L = chol(K~^-1) the NG residual of
+    Eq. (8) is only rounding, about u cond(K~), and the update leaves L there
+    (a property that holds at any size, checked without an M^3 oracle run on
+    the GPU's side)."""
+    M, D = 4096, 4
+    rng = np.random.default_rng(31)
+    p = dict(Z=rng.uniform(-2, 2, size=(M, D)), ell=np.full(D, 0.8), sf2=1.0, noise=0.5,
+             m=np.zeros(M), s=np.full(M, 0.5), L=np.eye(M))
+    p = round_state(p)
+    Kt = O.se_ard(p["Z"], p["Z"], p["ell"], p["sf2"]) + np.diag(p["s"])
+    p["L"] = f32(np.linalg.cholesky(np.linalg.inv(Kt)))
+    ev = np.linalg.eigvalsh(Kt)
+    kappa = ev[-1] / ev[0]
+    m = _model(p, M, D, 8, prec)
+    m.ng_update(max_iters=1, eps=0.0, gammas=[1.0])
+    torch.cuda.synchronize()
+    assert m.sync_status() == 0
+    r = float(m.resid[0])
+    u = {"fp32": 2.0 ** -24, "bf16": 2.0 ** -9, "bf16x3": 2.0 ** -17}[prec]
+    assert r <= 8 * u * kappa, (r, kappa)
+    assert rel(m.L.double().cpu().numpy(), p["L"]) <= 8 * u * kappa
+    m.close()
