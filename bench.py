@@ -49,7 +49,7 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["bf16", "bf16x3", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -223,6 +223,15 @@ class Clocks:
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def window_median(dev_ms, windows=10):
+    """Median over `windows` equal windows of the timed steps of the mean
+    per-step device time (robust to a slow window)."""
+    n = len(dev_ms) // windows
+    if n < 1:
+        return None
+    return statistics.median(sum(dev_ms[w * n:(w + 1) * n]) / n for w in range(windows))
 
 
 def reduce_timing(tot_ms, steps, ws):
@@ -474,6 +483,7 @@ def run_ours(args):
                    "t_star": 1, "gamma": 1.0, "precision": prec, "graph": True,
                    "l2": "flushed between timed steps (256 MB write outside the step events)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "ms_per_step_window_median": window_median(dev_ms),
         "wall_s_timed": wall, "gpu_launches": launches * args.steps, "launches_per_step": launches,
         "clocks": clocks, "device_status": ok_status,
     }
