@@ -28,8 +28,18 @@ using namespace tc;
 
 constexpr int SLOT = 4096;                    // one 32 x 32 FP32 block (or two BF16 blocks)
 constexpr int IN_BYTES = 2 * SLOT;            // double-buffered input block
-constexpr int OUT_SLOTS = 4;
-constexpr int WARP_BYTES = IN_BYTES + OUT_SLOTS * SLOT;
+
+// Shared memory an epilogue needs per warp: whether it reads an input block
+// (double-buffered IN_BYTES) and how many 4 KB staging slots it writes.
+template <class Epi> struct EpiSmem;
+template <class OutP> struct EpiSmem<EpiVt<OutP>> { static constexpr bool input = true; static constexpr int out_slots = 1; };
+template <class OutP, int MODE> struct EpiSmem<EpiSym<OutP, MODE>> {
+  static constexpr bool input = false; static constexpr int out_slots = 2;
+};
+template <> struct EpiSmem<EpiLupd> { static constexpr bool input = true; static constexpr int out_slots = 1; };
+template <class OutP> struct EpiSmem<EpiStore<OutP>> { static constexpr bool input = false; static constexpr int out_slots = 1; };
+template <class OutP> struct EpiSmem<EpiP<OutP>> { static constexpr bool input = true; static constexpr int out_slots = 4; };
+template <> struct EpiSmem<EpiGK> { static constexpr bool input = true; static constexpr int out_slots = 2; };
 
 struct alignas(64) EpiMaps {
   CUtensorMap in;
@@ -124,6 +134,18 @@ __device__ __forceinline__ void store_out(const CUtensorMap* m, const unsigned c
   if (Out<OutP>::NMAP == 2) tma_store_2d(m + 1, b + 2048, x, y);
 }
 
+// The floats x[c0 .. min(c0 + 128, n)) into this SM's L1 (one 128-byte line
+// per lane of lanes 0..3; only addresses inside the n-element vector), so
+// that the per-block vector reads of the epilogue do not wait on DRAM.
+__device__ __forceinline__ void prefetch_l1(const float* x, int c0, int n, int lane) {
+  if (x && lane < 4 && c0 + 32 * lane < n) asm volatile("prefetch.global.L1 [%0];" ::"l"(x + c0 + 32 * lane));
+}
+
+// Tile hook, run by every epilogue warp before it waits for the accumulator:
+// vectors the block epilogues of tile (m0, n0) read (none by default).
+template <class Epi>
+__device__ __forceinline__ void tc_prefetch(const Epi&, int, int, int) {}
+
 // Staging complete: make it visible to the async proxy, then lane 0 issues
 // the stores the caller lists.
 __device__ __forceinline__ void staged() {
@@ -145,6 +167,8 @@ __device__ __forceinline__ bool tc_in(const EpiVt<OutP>& e, int i0, int j0, int&
   x = i0; y = j0;
   return e.s != nullptr;
 }
+template <class OutP>
+__device__ __forceinline__ void tc_prefetch(const EpiVt<OutP>& e, int, int n0, int lane) { prefetch_l1(e.s, n0, e.M, lane); }
 template <class OutP>
 __device__ __forceinline__ void tc_epi(EpiVt<OutP>& e, int i0, int j0, float (&v)[32], int lane,
                                        const unsigned char* in, unsigned char* out, const EpiMaps& maps) {
@@ -183,17 +207,31 @@ __device__ __forceinline__ void tc_epi(EpiSym<OutP, MODE>& e, int i0, int j0, fl
                                        const unsigned char*, unsigned char* out, const EpiMaps& maps) {
   const int i = i0 + lane;
   const bool diagblk = i0 == j0;
+  const bool rowin = i < e.M;
   float d[32];
+  // sums over the counted triangle (weight 1 on the diagonal, 2 off it) in
+  // four independent register partials, selected rather than branched
+  float s0[4] = {0.f, 0.f, 0.f, 0.f}, s1[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int q = 0; q < 32; ++q) {
     const int j = j0 + q;
     const bool dg = i == j;
     d[q] = sym_val<MODE>(v[q], dg);
-    if ((!diagblk || q >= lane) && i < e.M && j < e.M) {
-      const float a = v[q], w = dg ? 1.f : 2.f;
-      if (MODE == 0) { const float t = a - (dg ? 1.f : 0.f); e.p0 = fmaf(w * t, t, e.p0); }
-      if (MODE == 1) { if (dg) e.p0 += a; e.p1 = fmaf(w * a, a, e.p1); }
+    const bool cnt = (!diagblk || q >= lane) && rowin && j < e.M;
+    const float a = v[q], w = dg ? 1.f : 2.f;
+    if (MODE == 0) {
+      const float t = a - (dg ? 1.f : 0.f);
+      s0[q & 3] = cnt ? fmaf(w * t, t, s0[q & 3]) : s0[q & 3];
     }
+    if (MODE == 1) {
+      s0[q & 3] = (cnt && dg) ? s0[q & 3] + a : s0[q & 3];
+      s1[q & 3] = cnt ? fmaf(w * a, a, s1[q & 3]) : s1[q & 3];
+    }
+  }
+  if (MODE == 0) e.p0 += (s0[0] + s0[1]) + (s0[2] + s0[3]);
+  if (MODE == 1) {
+    e.p0 += (s0[0] + s0[1]) + (s0[2] + s0[3]);
+    e.p1 += (s1[0] + s1[1]) + (s1[2] + s1[3]);
   }
   Out<OutP>::row(out, lane, d);
   if (diagblk) {
@@ -235,12 +273,17 @@ __device__ __forceinline__ void tc_epi(EpiLupd& e, int i0, int j0, float (&v)[32
     tma_store_2d(&maps.out[0], out, j0, i0);
     bulk_commit();
   }
-  const int j = j0 + lane;
-#pragma unroll 4
+  // all 32 shared-memory reads before the first global store (the compiler
+  // cannot reorder them across stores that might alias)
+  const int j = j0 + lane, M = e.M;
+  float* Lout = e.Lout;
+  float col[32];
+#pragma unroll
+  for (int r = 0; r < 32; ++r) col[r] = *reinterpret_cast<const float*>(out + off32(r, lane));
+#pragma unroll
   for (int r = 0; r < 32; ++r) {
     const int ii = i0 + r;
-    if (j <= ii && ii < e.M && j < e.M)
-      e.Lout[(size_t)ii * e.M + j] = *reinterpret_cast<const float*>(out + off32(r, lane));
+    if (j <= ii && ii < M && j < M) Lout[(size_t)ii * M + j] = col[r];
   }
 }
 
@@ -270,20 +313,32 @@ __device__ __forceinline__ bool tc_in(const EpiP<OutP>& e, int i0, int j0, int& 
   return e.Psi != nullptr;
 }
 template <class OutP>
+__device__ __forceinline__ void tc_prefetch(const EpiP<OutP>& e, int m0, int n0, int lane) {
+  if (m0 == n0) prefetch_l1(e.s, m0, e.M, lane);
+}
+template <class OutP>
 __device__ __forceinline__ void tc_epi(EpiP<OutP>& e, int i0, int j0, float (&v)[32], int lane,
                                        const unsigned char* in, unsigned char* out, const EpiMaps& maps) {
   const int i = i0 + lane;
   const bool diagblk = i0 == j0;
   if (i < e.M) {
-    float ps[32];
-    if (e.Psi) ld_row_f32(in, lane, ps);
+    if (diagblk) {                                   // P_ii sits at q == lane
+      float pii = 0.f;
 #pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      const int j = j0 + q;
-      if (j <= i && j < e.M) {
-        if (j == i) e.p0 = fmaf(__ldg(e.s + i), v[q], e.p0);
-        if (e.Psi) e.p1 = fmaf((j == i ? 1.f : 2.f) * v[q], ps[q], e.p1);
+      for (int q = 0; q < 32; ++q) pii = q == lane ? v[q] : pii;
+      e.p0 = fmaf(__ldg(e.s + i), pii, e.p0);
+    }
+    if (e.Psi) {
+      float ps[32];
+      ld_row_f32(in, lane, ps);
+      float s1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int j = j0 + q;
+        const bool cnt = j <= i && j < e.M;
+        s1[q & 3] = cnt ? fmaf((j == i ? 1.f : 2.f) * v[q], ps[q], s1[q & 3]) : s1[q & 3];
       }
+      e.p1 += (s1[0] + s1[1]) + (s1[2] + s1[3]);
     }
   }
   row_f32(out, lane, v);
@@ -321,6 +376,11 @@ __device__ __forceinline__ bool tc_in(const EpiGK&, int i0, int j0, int& x, int&
   x = j0; y = i0;
   return true;
 }
+__device__ __forceinline__ void tc_prefetch(const EpiGK& e, int m0, int n0, int lane) {
+  prefetch_l1(e.v, m0, e.M, lane);
+  prefetch_l1(e.v, n0, e.M, lane);
+  if (m0 == n0) prefetch_l1(e.s, m0, e.M, lane);
+}
 __device__ __forceinline__ void tc_epi(EpiGK& e, int i0, int j0, float (&v)[32], int lane, const unsigned char* in,
                                        unsigned char* out, const EpiMaps& maps) {
   const int i = i0 + lane;
@@ -334,7 +394,12 @@ __device__ __forceinline__ void tc_epi(EpiGK& e, int i0, int j0, float (&v)[32],
   for (int q = 0; q < 32; ++q) {
     const float vj = __shfl_sync(0xffffffffu, vc, q);
     g[q] = -v[q] + 0.5f * p[q] - 0.5f * vi * vj;
-    if (diagblk && q == lane && i < e.M) e.ds[i] = -v[q] + 0.5f / e.s[i];
+  }
+  if (diagblk) {                                     // G_ii term at q == lane
+    float vii = 0.f;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) vii = q == lane ? v[q] : vii;
+    if (i < e.M) e.ds[i] = -vii + 0.5f / e.s[i];
   }
   row_f32(out, lane, g);
   if (diagblk) {

@@ -34,17 +34,25 @@ constexpr int BM = 128;
 constexpr int BN = 128;
 constexpr int BK = 64;                      // one 128-byte swizzle atom of BF16
 constexpr int TILE_BYTES = 128 * BK * 2;    // 16 KB per 128 x 64 operand tile
-constexpr int EPI_BYTES = 4 * etc::WARP_BYTES;   // per epilogue warp: input slots + staging
 constexpr uint32_t TMEM_COLS = 2 * BN;      // two accumulators
 
-// Pipeline geometry per operand precision: NSPLIT = 1 (BF16) or 3 (hi/lo pairs).
-template <int NSPLIT> struct Geo {
+// Pipeline geometry per epilogue and operand precision (NSPLIT = 1: BF16,
+// 3: hi/lo pairs).  The mainloop streams operand tiles from L2 and its rate
+// is set by the bytes in flight, so the ring takes every stage that fits
+// beside the epilogue's own buffers (input slots only where the epilogue
+// reads a matrix, and its staging slots).
+template <class Epi, int NSPLIT> struct Geo {
   static constexpr int NT = NSPLIT == 1 ? 2 : 4;                 // operand tiles per stage
-  static constexpr int STAGES = NSPLIT == 1 ? 4 : 2;
   static constexpr int STAGE_BYTES = NT * TILE_BYTES;
+  static constexpr int IN = etc::EpiSmem<Epi>::input ? etc::IN_BYTES : 0;
+  static constexpr int WARP = IN + etc::EpiSmem<Epi>::out_slots * etc::SLOT;
+  static constexpr int EPI_BYTES = 4 * WARP;                     // four epilogue warps
+  static constexpr int fixed(int st) { return EPI_BYTES + 1024 + 8 * (2 * st + 12) + 64; }
+  static constexpr int fit(int st) { return st * STAGE_BYTES + fixed(st) <= 232448; }
+  static constexpr int STAGES = fit(6) ? 6 : fit(5) ? 5 : fit(4) ? 4 : fit(3) ? 3 : 2;
   // [0,S) full, [S,2S) empty, acc_full[2], acc_empty[2], epilogue input[4 warps][2]
   static constexpr int NBAR = 2 * STAGES + 4 + 8;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024 + 8 * NBAR + 64;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + fixed(STAGES);
   static_assert(SMEM <= 232448, "shared memory budget");
 };
 
@@ -58,14 +66,14 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                const Tile* __restrict__ tiles, const int* __restrict__ toff, Epi epi, int* errword,
                const __grid_constant__ etc::EpiMaps maps) {
   pdl_enter();
-  using G = Geo<NSPLIT>;
+  using G = Geo<Epi, NSPLIT>;
   constexpr int S = G::STAGES;
   if (epi.skip()) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   // stage s holds tiles [A_hi, B_hi, (A_lo, B_lo)]
   unsigned char* epi_base = base + S * G::STAGE_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(epi_base + EPI_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(epi_base + G::EPI_BYTES);
   // bars: [0,S) full, [S,2S) empty, 2S+b acc_full[b], 2S+2+b acc_empty[b], 2S+4+2w+k epilogue input
   volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars + G::NBAR);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -163,8 +171,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
     const int quad = warp & 3, ew = warp - 2;
-    unsigned char* ein = epi_base + ew * etc::WARP_BYTES;      // two input slots
-    unsigned char* eout = ein + etc::IN_BYTES;                 // staging slots
+    unsigned char* ein = epi_base + ew * G::WARP;              // two input slots (if any)
+    unsigned char* eout = ein + G::IN;                         // staging slots
     const uint32_t inbar0 = BAR(2 * S + 4 + 2 * ew);
     int n_issued[2] = {0, 0}, n_used[2] = {0, 0};
     // input block of (i0, j0) into slot k (lane 0 issues; the slot's previous
@@ -188,11 +196,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       const int i0 = tl.m0 + quad * 32;
       issue_in(0, i0, tl.n0);
       issue_in(1, i0, tl.n0 + 32);
+      etc::tc_prefetch(epi, tl.m0, tl.n0, lane);
       if (!mbar_wait(BAR(2 * S + b), (lt >> 1) & 1)) { *abort_flag = 1; break; }
       fence_after();
       if (*abort_flag) break;
       const uint32_t acc = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * BN);
       bool ok = true;
+#pragma unroll
       for (int c = 0; c < BN / 32; ++c) {
         const int j0 = tl.n0 + c * 32, k = c & 1;
         if (!etc::tc_skip(epi, i0, j0)) {
@@ -261,7 +271,7 @@ EncodeTiledFn encode_fn() {
 
 template <class Epi, int NSPLIT>
 void set_attr() {
-  cudaFuncSetAttribute(tc_gemm_kernel<Epi, NSPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Geo<NSPLIT>::SMEM);
+  cudaFuncSetAttribute(tc_gemm_kernel<Epi, NSPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Geo<Epi, NSPLIT>::SMEM);
 }
 
 template <class Epi>
@@ -368,10 +378,10 @@ bool tc_gemm(const GemmCtx& g, int tab, const bf16* A, const bf16* B, const Epi&
   if (g.split) {
     if (!tc_make_map(&mal, A + MM, g.Mp, g.Mp, 128) || !tc_make_map(&mbl, B + MM, g.Mp, g.Mp, 128)) return false;
     svgp_note_launch();
-    pdl_launch(tc_gemm_kernel<Epi, 3>, grid, 192, Geo<3>::SMEM, g.st, ma, mb, mal, mbl, g.tt[tab], g.toff[tab], e, g.err, em);
+    pdl_launch(tc_gemm_kernel<Epi, 3>, grid, 192, Geo<Epi, 3>::SMEM, g.st, ma, mb, mal, mbl, g.tt[tab], g.toff[tab], e, g.err, em);
   } else {
     svgp_note_launch();
-    pdl_launch(tc_gemm_kernel<Epi, 1>, grid, 192, Geo<1>::SMEM, g.st, ma, mb, ma, mb, g.tt[tab], g.toff[tab], e, g.err, em);
+    pdl_launch(tc_gemm_kernel<Epi, 1>, grid, 192, Geo<Epi, 1>::SMEM, g.st, ma, mb, ma, mb, g.tt[tab], g.toff[tab], e, g.err, em);
   }
   return true;
 }
