@@ -476,15 +476,36 @@ __global__ void __launch_bounds__(256) grad_finalize_kernel(const float* __restr
   }
 }
 
-// Scalar assembly of Eq. (7) in FP64 (and the scalar gradients).
+// Scalar assembly of Eq. (7) in FP64 (and the scalar gradients).  FP64
+// divisions and logarithms are long dependent chains on this part, so the
+// independent results go to different warps: warp 0 lane d the lengthscale
+// gradient d, warp 1 the bound's terms, warp 2 the sf2 and noise gradients.
 __global__ void terms_finalize_kernel(const double* __restrict__ red, const double* __restrict__ acc_ell,
                                       const float* __restrict__ sf2p, const float* __restrict__ noisep,
                                       const float* __restrict__ ell, int M, int D, int B, double N, bool probit,
                                       int hutch_K, double* terms, float* dsf2, float* dnoise, float* dell,
                                       int* errword) {
   pdl_enter();
-  if (threadIdx.x != 0) return;
-  double sf2 = *sf2p, noise = probit ? 1.0 : *noisep, c = N / B;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    if (dsf2 && lane < D) dell[lane] = (float)(acc_ell[lane] / ell[lane]);
+    return;
+  }
+  if (lane != 0) return;
+  const double noise = probit ? 1.0 : *noisep, c = N / B;
+  const double sqerr = probit ? 0.0 : red[RED_SQERR];
+  if (warp == 2) {
+    if (dsf2) {
+      const double sf2 = *sf2p;
+      // sum_n sigma_n^2 as below
+      const double sumvar = probit ? red[RED_SUMVAR] : (double)B * sf2 - red[RED_PPSI];
+      const double sumh = probit ? red[RED_SUMH] : -0.5 * B / noise;   // sum_n h_n
+      *dsf2 = (float)(c * sumh + (red[RED_SUMA_F] + red[RED_SUMA_U]) / sf2);
+      *dnoise = probit ? 0.f : (float)(c * (-0.5 * B / noise + (sqerr + sumvar) / (2.0 * noise * noise)));
+    }
+    return;
+  }
+  const double sf2 = *sf2p;
   double trA1 = red[RED_TRA1], froA1 = red[RED_FROA1];
   double trPKt = 2.0 * trA1 - froA1;                 // tr(P K~) = tr((2I - A1) A1)
   double trPKuu = trPKt - red[RED_SPDIAG];            // minus tr(P diag(s))
@@ -495,7 +516,6 @@ __global__ void terms_finalize_kernel(const double* __restrict__ red, const doub
   double quad = red[RED_QUAD];
   double logdetT = 2.0 * red[RED_LOGDETL];
   double logdetS = red[RED_LOGS];
-  double sqerr = probit ? 0.0 : red[RED_SQERR];
   // sum_n sigma_n^2: Gaussian from sum_n sf2 - k_n^T P k_n = B sf2 - <P, Psi>; probit per point
   double sumvar = probit ? red[RED_SUMVAR] : (double)B * sf2 - red[RED_PPSI];
   const double LOG2PI = 1.8378770664093453;
@@ -510,12 +530,6 @@ __global__ void terms_finalize_kernel(const double* __restrict__ red, const doub
     terms[SVGP_T_NCLAMP] = probit ? red[RED_NCLAMP] : 0.0;
   }
   if (!isfinite(F)) atomicOr(errword, ERRBIT_NONFINITE);
-  if (dsf2) {
-    const double sumh = probit ? red[RED_SUMH] : -0.5 * B / noise;   // sum_n h_n
-    *dsf2 = (float)(c * sumh + (red[RED_SUMA_F] + red[RED_SUMA_U]) / sf2);
-    *dnoise = probit ? 0.f : (float)(c * (-0.5 * B / noise + (sqerr + sumvar) / (2.0 * noise * noise)));
-    for (int d = 0; d < D; ++d) dell[d] = (float)(acc_ell[d] / ell[d]);
-  }
 }
 
 __global__ void predict_finalize_kernel(const float* __restrict__ colsum, const float* __restrict__ sf2,
@@ -763,7 +777,7 @@ void k_terms_finalize(const double* red, const double* acc_ell, const float* sf2
                       const float* ell, int M, int D, int B, double N, bool probit, int hutch_K, double* terms,
                       float* dsf2, float* dnoise, float* dell, int* errword, cudaStream_t st) {
   svgp_note_launch();
-  pdl_launch(terms_finalize_kernel, 1, 32, 0, st, red, acc_ell, sf2, noise, ell, M, D, B, N, probit, hutch_K, terms, dsf2, dnoise,
+  pdl_launch(terms_finalize_kernel, 1, 96, 0, st, red, acc_ell, sf2, noise, ell, M, D, B, N, probit, hutch_K, terms, dsf2, dnoise,
                                           dell, errword);
 }
 
