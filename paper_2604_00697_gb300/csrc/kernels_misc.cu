@@ -3,6 +3,8 @@
 // assembly, FP64 scalar finalisation and the fused Adam update.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -328,8 +330,8 @@ __global__ void gp_assemble_kernel(const float* __restrict__ Kuu, const float* _
 // Accumulated in the expanded form S0 = sum_j A_ij, S1_d = sum_j A_ij z~_jd,
 // S2_d = sum_j A_ij z~_jd^2 (two FMAs per dimension and element) and reported
 // as S1_d - z~_id S0 and S2_d - 2 z~_id S1_d + z~_id^2 S0.
-// Block = 32 rows (lane = row i) x a range of at most 256 columns j, split
-// over the 8 warps.  A is symmetric, so A_ij is read as A[j][i]: a warp reads
+// Block = 32 rows (lane = row i) x a range of JB columns j, split over the 8
+// warps; the host sizes JB so that the grid fills the SMs in one wave.  A is symmetric, so A_ij is read as A[j][i]: a warp reads
 // 32 consecutive floats of row j (eight rows in flight per warp).  z~_j of the
 // range is staged in shared memory and read as broadcasts (their cost bounds
 // the loop, so z~_j^2 is formed in registers).
@@ -341,7 +343,7 @@ __global__ void __launch_bounds__(256) kuu_bwd_kernel(const float* __restrict__ 
   pdl_enter();
   constexpr int W = 2 * DP + 1;
   constexpr int U = 8;
-  __shared__ __align__(16) float zs[256][DP];
+  extern __shared__ __align__(16) float zs[];      // [JB][DP]
   __shared__ float part[32][W + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * 32 + lane;
@@ -351,7 +353,7 @@ __global__ void __launch_bounds__(256) kuu_bwd_kernel(const float* __restrict__ 
   for (int e = threadIdx.x; e < JB * DP; e += 256) {
     const int r = e / DP, d = e - r * DP;
     const float zv = (jb + r < je && d < Dp) ? __ldg(Zs + (size_t)(jb + r) * Dp + d) : 0.f;
-    zs[r][d] = zv;
+    zs[r * DP + d] = zv;
   }
   // packed FP32 pairs: S1p[j] = (S1_2j, S1_2j+1), likewise S2p
   f32x2 S1p[DP / 2], S2p[DP / 2];
@@ -370,7 +372,7 @@ __global__ void __launch_bounds__(256) kuu_bwd_kernel(const float* __restrict__ 
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int jj = min(j + 8 * u, je - 1) - jb;
-        const ulonglong2* zj = reinterpret_cast<const ulonglong2*>(&zs[jj][0]);
+        const ulonglong2* zj = reinterpret_cast<const ulonglong2*>(&zs[jj * DP]);
         S0 += a[u];
         const f32x2 a2 = pack2(a[u], a[u]);
 #pragma unroll
@@ -430,7 +432,7 @@ __global__ void __launch_bounds__(256) grad_finalize_kernel(const float* __restr
                                                             float* __restrict__ dZ, double* acc_ell, double* red) {
   pdl_enter();
   constexpr int RB = 16;
-  __shared__ float tf[RB][2 * SVGP_MAXD + 2];
+  __shared__ float tf[RB][2 * SVGP_MAXD + 2], tu[RB][2 * SVGP_MAXD + 2];
   const int W = 2 * D + 1;
   const int r0 = blockIdx.x * RB;
   const int nr = min(RB, M - r0);
@@ -453,11 +455,12 @@ __global__ void __launch_bounds__(256) grad_finalize_kernel(const float* __restr
       }
     }
     tf[r][k] = v;
+    tu[r][k] = r < nr ? ru[(size_t)(r0 + r) * W + k] : 0.f;     // staged: the sums below read it per row
   }
   __syncthreads();
   for (int e = threadIdx.x; e < nr * D; e += blockDim.x) {
     const int r = e / D, d = e - r * D;
-    dZ[(size_t)r0 * D + e] = (tf[r][d] + 2.0f * ru[(size_t)(r0 + r) * W + d]) / ell[d];
+    dZ[(size_t)r0 * D + e] = (tf[r][d] + 2.0f * tu[r][d]) / ell[d];
   }
   // column sums: thread t < D -> lengthscale d = t; t == D -> data part of the
   // signal variance; t == D + 1 -> Kuu part
@@ -465,10 +468,9 @@ __global__ void __launch_bounds__(256) grad_finalize_kernel(const float* __restr
   if (t < D + 2) {
     float acc = 0.f;
     for (int r = 0; r < nr; ++r) {
-      const size_t o = (size_t)(r0 + r) * W;
-      if (t < D) acc += tf[r][D + t] + ru[o + D + t];
+      if (t < D) acc += tf[r][D + t] + tu[r][D + t];
       else if (t == D) acc += tf[r][2 * D];
-      else acc += ru[o + 2 * D];
+      else acc += tu[r][2 * D];
     }
     if (t < D) atomicAdd(acc_ell + t, (double)acc);
     else if (t == D) atomicAdd(red + RED_SUMA_F, (double)acc);
@@ -755,10 +757,23 @@ template void k_gp_assemble<SplitPtr>(const float*, const float*, const float*, 
 void k_kuu_bwd(const float* GKuu, const float* Kuu, const float* Zs, int M, int Mp, int D,
                float* rowacc_u, double* red, cudaStream_t st) {
   (void)red;
-  const int JB = 256;
-  dim3 grid((M + 31) / 32, (M + JB - 1) / JB);
-  svgp_note_launch();
-  SVGP_DP_DISPATCH(D, pdl_launch(kuu_bwd_kernel<DP>, grid, 256, 0, st, GKuu, Kuu, Zs, M, Mp, D, rowacc_u, JB));
+  // One wave: blocks per SM x SMs slots, shared out over the row blocks; JB
+  // a multiple of 8, the staged z~ with the static partials within 48 KB.
+  SVGP_DP_DISPATCH(D, {
+    const int jbmax = std::min(512, 9216 / DP);
+    static int occ = 0;
+    if (!occ) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kuu_bwd_kernel<DP>, 256, (size_t)jbmax * DP * 4);
+      if (occ < 1) occ = 1;
+    }
+    const int gx = (M + 31) / 32;
+    const int gy0 = std::max(1, occ * tc_num_sms() / gx);
+    int JB = ((M + gy0 - 1) / gy0 + 7) / 8 * 8;
+    JB = std::max(8, std::min(JB, jbmax));
+    dim3 grid(gx, (M + JB - 1) / JB);
+    svgp_note_launch();
+    pdl_launch(kuu_bwd_kernel<DP>, grid, 256, (size_t)JB * DP * 4, st, GKuu, Kuu, Zs, M, Mp, D, rowacc_u, JB);
+  });
 }
 
 void k_logs(const float* s, int M, double* red, cudaStream_t st) {
