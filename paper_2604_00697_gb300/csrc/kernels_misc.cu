@@ -419,7 +419,7 @@ __global__ void logs_kernel(const float* __restrict__ s, int M, double* red) {
   block_add_double(part, red + RED_LOGS);
 }
 
-// dZ_id = (rowacc_f[i][d] + 2 rowacc_u[i][d]) / ell_d for a block of RB rows;
+// dZ_id = (rowacc_f[i][d] + 2 rowacc_u[i][d]) / ell_d for a block of RB = 8 rows;
 // then the column sums of the lengthscale parts rowacc_f[i][D + d] +
 // rowacc_u[i][D + d] and of the signal-variance parts rowacc_*[i][2D] over the
 // block's rows (FP32), added in FP64 to acc_ell and the reduction slots (one
@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(256) grad_finalize_kernel(const float* __restr
                                                             const float* __restrict__ ell, int M, int D,
                                                             float* __restrict__ dZ, double* acc_ell, double* red) {
   pdl_enter();
-  constexpr int RB = 16;
+  constexpr int RB = 8;
   __shared__ float tf[RB][2 * SVGP_MAXD + 2], tu[RB][2 * SVGP_MAXD + 2];
   const int W = 2 * D + 1;
   const int r0 = blockIdx.x * RB;
@@ -443,13 +443,21 @@ __global__ void __launch_bounds__(256) grad_finalize_kernel(const float* __restr
       if (nparts > 0) {
         const float* pp = rowpart + (size_t)k * Mp + r0 + r;
         const size_t stride = (size_t)W * Mp;
+        // eight loads in flight, added in part order
         int p = 0;
-        for (; p + 4 <= nparts; p += 4) {
-          const float a0 = __ldg(pp + p * stride), a1 = __ldg(pp + (p + 1) * stride);
-          const float a2 = __ldg(pp + (p + 2) * stride), a3 = __ldg(pp + (p + 3) * stride);
-          v += a0; v += a1; v += a2; v += a3;
+        for (; p + 8 <= nparts; p += 8) {
+          float a[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) a[u] = __ldg(pp + (p + u) * stride);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v += a[u];
         }
-        for (; p < nparts; ++p) v += __ldg(pp + p * stride);
+        float a[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = p + u < nparts ? __ldg(pp + (p + u) * stride) : 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (p + u < nparts) v += a[u];
       } else {
         v = rf[(size_t)(r0 + r) * W + k];
       }
@@ -783,7 +791,7 @@ void k_logs(const float* s, int M, double* red, cudaStream_t st) {
 
 void k_grad_finalize(const float* rowacc_f, const float* rowacc_u, const float* rowpart, int nparts, int Mp,
                      const float* ell, int M, int D, float* dZ, double* acc_ell, double* red, cudaStream_t st) {
-  int grid = (M + 15) / 16;
+  int grid = (M + 7) / 8;
   svgp_note_launch();
   pdl_launch(grad_finalize_kernel, grid, 256, 0, st, rowacc_f, rowacc_u, rowpart, nparts, Mp, ell, M, D, dZ, acc_ell, red);
 }
