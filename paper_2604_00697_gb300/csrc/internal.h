@@ -75,8 +75,9 @@ int tc_w(const GemmCtx& g, const bf16* P, const KufTC& t, const WEpi& we, float*
 int tc_w_groups(int Mp, int B, bool split);
 void tc_w_init_attributes();
 // out[r] = sum_k Kuf(r, k) w_k for r < nrows, k < nk, from the row-role vectors
-// of the row points and the k-role vectors of the k points (kuf_prep).
-bool tc_kuf_gemv(const bf16* Rrole, int nrows, const bf16* Krole, int nk, const float* w, float* out, int* errword,
+// of the row points and the k-role vectors of the k points (kuf_prep); the
+// kernel accumulates, so out is zeroed first unless out_zeroed.
+bool tc_kuf_gemv(const bf16* Rrole, int nrows, const bf16* Krole, int nk, const float* w, float* out, bool out_zeroed, int* errword,
                  cudaStream_t st);
 void tc_gemv_init_attributes();
 
@@ -100,8 +101,12 @@ void k_kt_f32(const float* Kuu, const float* s, int M, int Mp, float* Kt, cudaSt
 // be null); with eps > 0 sets *done when G <= 2 noise eps.
 void k_gap_check(const double* red, const float* s, int M, double sigma2_host, const float* noise, double eps,
                  int* done, double* gap, cudaStream_t st);
-// Zero up to three device ranges (byte counts, multiples of 4) in one launch
-// (a kernel rather than memset nodes keeps the step's launches programmatic).
+// Zero up to ZERO_MAX device ranges (byte counts, multiples of 4; null
+// pointers skipped) in one launch (a kernel rather than memset nodes keeps
+// the step's launches programmatic).
+constexpr int ZERO_MAX = 8;
+struct ZeroRange { void* p; size_t bytes; };
+void k_zero_n(cudaStream_t st, const ZeroRange* r, int n);
 void k_zero(cudaStream_t st, void* p0, size_t b0, void* p1 = nullptr, size_t b1 = 0, void* p2 = nullptr,
             size_t b2 = 0);
 // y = alpha (x + beta x2), n elements.

@@ -82,27 +82,31 @@ template <class OutP>
 __global__ void prep_L_kernel(const float* __restrict__ Lin, int M, int Mp, float* __restrict__ Lf,
                               OutP Llo, OutP Ltlo, double* logdet) {
   pdl_enter();
-  __shared__ float tile[32][33];
-  int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
-  // Blocks strictly above the diagonal stay zero in L (and below it in L^T):
+  // block: a strip of 128 rows x 32 columns (sixteen rows per thread)
+  __shared__ float tile[128][33];
+  const int i0 = blockIdx.y * 128, j0 = blockIdx.x * 32;
+  // Strips strictly above the diagonal stay zero in L (and below it in L^T):
   // nothing else ever writes there, and the buffers start zeroed.
-  if (j0 > i0 + 31) return;
-  int tx = threadIdx.x;
+  if (j0 > i0 + 127) return;
+  const int tx = threadIdx.x;
   double ld = 0.0;
-  for (int ty = threadIdx.y; ty < 32; ty += blockDim.y) {
-    int i = i0 + ty, j = j0 + tx;
-    float val = (i < M && j < M && j <= i) ? Lin[(size_t)i * M + j] : 0.f;
+#pragma unroll 4
+  for (int ty = threadIdx.y; ty < 128; ty += blockDim.y) {
+    const int i = i0 + ty, j = j0 + tx;
+    const float val = (i < M && j < M && j <= i) ? Lin[(size_t)i * M + j] : 0.f;
     Lf[(size_t)i * Mp + j] = val;
     put(Llo, (size_t)i * Mp + j, val);
     tile[ty][tx] = val;
     if (i == j && i < M) ld += (double)logf(fabsf(val));
   }
   __syncthreads();
-  for (int ty = threadIdx.y; ty < 32; ty += blockDim.y) {
-    // Lt[j0 + ty][i0 + tx] = L[i0 + tx][j0 + ty]
-    put(Ltlo, (size_t)(j0 + ty) * Mp + i0 + tx, tile[tx][ty]);
+#pragma unroll 4
+  for (int e = threadIdx.y; e < 4 * 32; e += blockDim.y) {
+    // Lt[j0 + r][i0 + 32 c + tx] = L[i0 + 32 c + tx][j0 + r]
+    const int r = e & 31, c = e >> 5;
+    put(Ltlo, (size_t)(j0 + r) * Mp + i0 + 32 * c + tx, tile[32 * c + tx][r]);
   }
-  if (logdet && blockIdx.x == blockIdx.y) block_add_double(ld, logdet);
+  if (logdet && j0 >= i0) block_add_double(ld, logdet);
 }
 
 // y = alpha * A (x + beta * x2)  (A: Mp x Mp FP32, rows < M); one warp per
@@ -630,7 +634,7 @@ template void k_kuu<SplitPtr>(const float*, int, int, int, const float*, float*,
 
 template <class OutP>
 void k_prep_L(const float* Lin, int M, int Mp, float* Lf, OutP Llo, OutP Ltlo, double* logdet, cudaStream_t st) {
-  dim3 grid(Mp / 32, Mp / 32), blk(32, 8);
+  dim3 grid(Mp / 32, Mp / 128), blk(32, 8);
   svgp_note_launch();
   pdl_launch(prep_L_kernel<OutP>, grid, blk, 0, st, Lin, M, Mp, Lf, Llo, Ltlo, logdet);
 }
@@ -647,15 +651,15 @@ void k_gemv(const float* A, int Mp, int M, const float* x, float alpha, const fl
 
 namespace {
 struct ZeroList {
-  uint32_t* p[3];
-  size_t n[3];   // 32-bit words
+  uint32_t* p[ZERO_MAX];
+  size_t n[ZERO_MAX];   // 32-bit words
 };
 
 __global__ void zero_kernel(ZeroList z) {
   pdl_enter();
   const size_t stride = (size_t)gridDim.x * blockDim.x;
 #pragma unroll
-  for (int r = 0; r < 3; ++r)
+  for (int r = 0; r < ZERO_MAX; ++r)
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < z.n[r]; e += stride) z.p[r][e] = 0u;
 }
 
@@ -696,15 +700,25 @@ __global__ void axpy_kernel(const float* __restrict__ x, float alpha, const floa
 }
 }  // namespace
 
-void k_zero(cudaStream_t st, void* p0, size_t b0, void* p1, size_t b1, void* p2, size_t b2) {
-  ZeroList z{{(uint32_t*)p0, (uint32_t*)p1, (uint32_t*)p2}, {p0 ? b0 / 4 : 0, p1 ? b1 / 4 : 0, p2 ? b2 / 4 : 0}};
-  size_t mx = z.n[0] > z.n[1] ? z.n[0] : z.n[1];
-  if (z.n[2] > mx) mx = z.n[2];
+void k_zero_n(cudaStream_t st, const ZeroRange* r, int n) {
+  ZeroList z;
+  size_t mx = 0;
+  for (int k = 0; k < ZERO_MAX; ++k) {
+    const bool on = k < n && r[k].p;
+    z.p[k] = on ? (uint32_t*)r[k].p : nullptr;
+    z.n[k] = on ? r[k].bytes / 4 : 0;
+    if (z.n[k] > mx) mx = z.n[k];
+  }
   size_t grid = (mx + 255) / 256;
   if (grid < 1) grid = 1;
   if (grid > 1024) grid = 1024;
   svgp_note_launch();
   pdl_launch(zero_kernel, (unsigned)grid, 256, 0, st, z);
+}
+
+void k_zero(cudaStream_t st, void* p0, size_t b0, void* p1, size_t b1, void* p2, size_t b2) {
+  const ZeroRange r[3] = {{p0, b0}, {p1, b1}, {p2, b2}};
+  k_zero_n(st, r, 3);
 }
 
 void k_kt_f32(const float* Kuu, const float* s, int M, int Mp, float* Kt, cudaStream_t st) {

@@ -156,13 +156,13 @@ void tc_gemv_init_attributes() {
   cudaFuncSetAttribute(kuf_gemv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, GV_SMEM);
 }
 
-bool tc_kuf_gemv(const bf16* Rrole, int nrows, const bf16* Krole, int nk, const float* w, float* out, int* errword,
+bool tc_kuf_gemv(const bf16* Rrole, int nrows, const bf16* Krole, int nk, const float* w, float* out, bool out_zeroed, int* errword,
                  cudaStream_t st) {
   const int rows_p = (nrows + 127) / 128 * 128;
   const int kp = (nk + 63) / 64 * 64;
   CUtensorMap mr, mk;
   if (!tc_make_map(&mr, Rrole, rows_p, 64, 128) || !tc_make_map(&mk, Krole, kp, 64, 64)) return false;
-  k_zero(st, out, sizeof(float) * nrows);
+  if (!out_zeroed) k_zero(st, out, sizeof(float) * nrows);
   const int nkb = kp / 64, rb = rows_p / 128;
   // about two CTAs per SM, at least 8 k-blocks each
   int groups = (2 * tc_num_sms() + rb - 1) / rb;

@@ -270,16 +270,26 @@ void prep_L(svgp_handle* h, const float* Lin, double* logdet) {
   else k_prep_L(Lin, h->M, h->Mp, h->Lf, SP(h, h->L_lo), SP(h, h->Lt_lo), logdet, h->st);
 }
 
-// Common prologue: scaled coordinates, Kuu, L copies, log-dets; zero sums.
-void prologue(svgp_handle* h, const svgp_params* p, const float* X, int B, const float* Lin) {
+// Common prologue: scaled coordinates, Kuu, L copies, log-det of L (unless
+// logdet_L is false); zero sums.  One launch zeroes every accumulator the
+// forward and backward passes that follow add into (mu and Kuf g of the
+// tensor-core gemvs, the row sums of the chain rules), and the NG loop's
+// flag and counter when given.
+void prologue(svgp_handle* h, const svgp_params* p, const float* X, int B, const float* Lin, bool logdet_L = true,
+              int* ng_done = nullptr, int* ng_iters = nullptr) {
   cudaStream_t st = h->st;
-  k_zero(st, h->red, sizeof(double) * RED_COUNT, h->acc_ell, sizeof(double) * SVGP_MAXD);
+  const size_t rows = sizeof(float) * (size_t)h->Mp * (2 * h->D + 1);
+  const ZeroRange zr[8] = {{h->red, sizeof(double) * RED_COUNT}, {h->acc_ell, sizeof(double) * SVGP_MAXD},
+                           {X ? h->mu : nullptr, sizeof(float) * (size_t)B}, {h->Kg, sizeof(float) * (size_t)h->Mp},
+                           {h->rowacc_f, rows}, {h->rowacc_u, rows},
+                           {ng_done, sizeof(int)}, {ng_iters, sizeof(int)}};
+  k_zero_n(st, zr, 8);
   k_prep_coords(p->Z, X, p->ell, h->M, h->Mp, X ? B : 0, h->D, h->Zs, h->Xs, st);
   if (h->tc_kuf) k_kuf_prep(h->Zs, X ? h->Xs : nullptr, h->M, h->Mp, X ? B : 0, (B + 127) / 128 * 128, h->D, p->sf2, h->kt, st);
   if (h->mode == MODE_F32) k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, (float*)nullptr, false, st);
   else if (h->mode == MODE_BF16) k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, H(h->Kuu_lo), true, st);
   else k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, SP(h, h->Kuu_lo), true, st);
-  prep_L(h, Lin, h->red + RED_LOGDETL);
+  prep_L(h, Lin, logdet_L ? h->red + RED_LOGDETL : nullptr);
 }
 
 // Forward pass of Eq. (7) up to the per-point likelihood terms.  Gaussian:
@@ -298,7 +308,7 @@ void forward(svgp_handle* h, const svgp_params* p, const svgp_batch* b, bool psi
   else k_gemv(h->Pf, h->Mp, h->M, p->m, 1.f, nullptr, 0.f, h->v, nullptr, nullptr, st);     // v = P m
   k_gemv(h->Kuu_f, h->Mp, h->M, h->v, 1.f, nullptr, 0.f, h->w, h->v, h->red + RED_QUAD, st);  // w = Kuu v
   if (b) {
-    if (!(h->tc_kuf && tc_kuf_gemv(h->kt.XR, b->B, h->kt.ZK, h->M, h->v, h->mu, h->errword, st)))
+    if (!(h->tc_kuf && tc_kuf_gemv(h->kt.XR, b->B, h->kt.ZK, h->M, h->v, h->mu, true, h->errword, st)))
       k_mu(h->Zs, h->Xs, h->M, b->B, h->D, p->sf2, h->v, h->mu, st);                        // mu = Kfu v
     if (h->probit) {
       k_zero(st, h->colsum, sizeof(float) * b->B);
@@ -326,14 +336,14 @@ bool valid_grads(const svgp_grads* gr) {
 // pass with T fixed (Section 3.1).
 void backward_tail(svgp_handle* h, const svgp_params* p, const svgp_batch* b, double* terms_dev, const svgp_grads* gr) {
   cudaStream_t st = h->st;
-  const int M = h->M, Mp = h->Mp, W = 2 * h->D + 1;
+  const int M = h->M, Mp = h->Mp;
   const float c = (float)(b->N / b->B);
   forward(h, p, b, true);
   if (h->probit) {                                                                      // Kuf diag(|h|) Kuf^T
     if (h->tc_kuf) k_kuf_prep_weighted(h->Xs, b->B, (b->B + 127) / 128 * 128, h->D, p->sf2, h->hn, h->kt.XKh, st);
     run_psi(h, p, b->B, h->hn);
   }
-  if (!(h->tc_kuf && tc_kuf_gemv(h->kt.ZR, M, h->kt.XK, b->B, h->g, h->Kg, h->errword, st)))
+  if (!(h->tc_kuf && tc_kuf_gemv(h->kt.ZR, M, h->kt.XK, b->B, h->g, h->Kg, true, h->errword, st)))
     k_kg(h->Zs, h->Xs, M, Mp, b->B, h->D, p->sf2, h->g, h->Kg, st);                    // Kuf g
   const float* nz = h->probit ? nullptr : p->noise;
   const float* mt = h->unprec ? nullptr : p->m;
@@ -344,7 +354,6 @@ void backward_tail(svgp_handle* h, const svgp_params* p, const svgp_batch* b, do
   run_sym<2>(h, nullptr);                // S = L^T G_P L + I/2
   run_ls(h);                             // Y = L S
   run_gk(h, p->s, gr->ds);               // G_K~ = -Y L^T -> G_Kuu, ds
-  k_zero(st, h->rowacc_f, sizeof(float) * Mp * W, h->rowacc_u, sizeof(float) * Mp * W);
   WEpi we{KufGen{h->Zs, h->Xs, h->D, M, b->B, p->sf2}, h->v, h->g, h->probit ? h->hn : nullptr, nz, c,
           h->rowacc_f, nullptr};
   const int nparts = run_w(h, we);                                                     // data part of dZ, dell, dsf2
@@ -360,10 +369,11 @@ void backward_tail(svgp_handle* h, const svgp_params* p, const svgp_batch* b, do
 // NG iterations of Prop. 1 on L_inout after the prologue (K~ and the L copies
 // current); the L copies are refreshed between iterations, not after the last.
 void ng_loop(svgp_handle* h, const svgp_params* p, float* L_inout, const float* gamma_dev, int max_iters, double eps,
-             int* iters, double* resid) {
+             int* iters, double* resid, bool zeroed = false) {
   cudaStream_t st = h->st;
-  // red[RED_NG_RESID] starts at 0 (prologue) and ng_check resets it after reading
-  k_zero(st, h->done, sizeof(int), iters, sizeof(int));
+  // red[RED_NG_RESID] starts at 0 (prologue) and ng_check resets it after reading;
+  // done and iters start at 0 (here, or in the prologue when zeroed)
+  if (!zeroed) k_zero(st, h->done, sizeof(int), iters, sizeof(int));
   for (int t = 0; t < max_iters; ++t) {
     run_vt(h, h->Kuu_lo, p->s, h->done);         // Vt = L^T K~ (skipped once converged)
     run_sym<0>(h, h->done);                      // A, Phi^T, ||A - I||^2
@@ -658,14 +668,11 @@ svgp_status svgp_train_step(svgp_handle* h, const svgp_params* p, const svgp_bat
   svgp_status s = validate_batch(h, b);
   if (s != SVGP_OK) return s;
   // one prologue (coordinates, Kuu, Kuf generator operands, L copies) serves both parts
-  prologue(h, p, b->X, b->B, L_inout);
-  ng_loop(h, p, L_inout, gamma_dev, max_iters, eps, iters_dev ? iters_dev : h->iters_tmp,
-          residual_dev ? residual_dev : h->resid_tmp);
-  if (max_iters > 0) {
-    // copies and log-determinant of the updated L
-    k_zero(h->st, h->red + RED_LOGDETL, sizeof(double));
-    prep_L(h, L_inout, h->red + RED_LOGDETL);
-  }
+  // the log-det of L is taken after the NG update (the prologue's is of the old L)
+  int* iters = iters_dev ? iters_dev : h->iters_tmp;
+  prologue(h, p, b->X, b->B, L_inout, max_iters == 0, h->done, iters);
+  ng_loop(h, p, L_inout, gamma_dev, max_iters, eps, iters, residual_dev ? residual_dev : h->resid_tmp, true);
+  if (max_iters > 0) prep_L(h, L_inout, h->red + RED_LOGDETL);   // copies and log-det of the updated L
   svgp_params q = *p;
   q.L = L_inout;
   backward_tail(h, &q, b, terms_dev, gr);
@@ -680,7 +687,7 @@ svgp_status svgp_predict(svgp_handle* h, const svgp_params* p, const float* Xs, 
   cudaStream_t st = h->st;
   prologue(h, p, Xs, Ns, p->L);
   forward(h, p, nullptr, false);
-  if (!(h->tc_kuf && tc_kuf_gemv(h->kt.XR, Ns, h->kt.ZK, h->M, h->v, mean, h->errword, st)))
+  if (!(h->tc_kuf && tc_kuf_gemv(h->kt.XR, Ns, h->kt.ZK, h->M, h->v, mean, false, h->errword, st)))
     k_mu(h->Zs, h->Xs, h->M, Ns, h->D, p->sf2, h->v, mean, st);
   k_zero(st, h->colsum, sizeof(float) * Ns);
   WEpi we{KufGen{h->Zs, h->Xs, h->D, h->M, Ns, p->sf2}, nullptr, nullptr, nullptr, nullptr, 0.f,
