@@ -82,8 +82,9 @@ bool tc_kuf_gemv(const bf16* Rrole, int nrows, const bf16* Krole, int nk, const 
 void tc_gemv_init_attributes();
 
 // Miscellaneous kernels (kernels_misc.cu).  OutP is float*, bf16* or SplitPtr.
+// With logs != null also *logs += sum_i log s[i] (i < M).
 void k_prep_coords(const float* Z, const float* X, const float* ell, int M, int Mp, int B, int D,
-                   float* Zs, float* Xs, cudaStream_t st);
+                   float* Zs, float* Xs, cudaStream_t st, const float* s = nullptr, double* logs = nullptr);
 template <class OutP>
 void k_kuu(const float* Zs, int M, int Mp, int D, const float* sf2, float* Kf, OutP Klo, bool has_lo,
            cudaStream_t st);

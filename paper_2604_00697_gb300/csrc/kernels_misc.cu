@@ -20,7 +20,8 @@ __device__ __forceinline__ float warp_sum(float x) {
 // Z) Mp rows, padding zero.
 __global__ void prep_coords_kernel(const float* __restrict__ Z, const float* __restrict__ X,
                                    const float* __restrict__ ell, int M, int Mp, int B, int D,
-                                   float* __restrict__ Zs, float* __restrict__ Xs) {
+                                   float* __restrict__ Zs, float* __restrict__ Xs, const float* __restrict__ s,
+                                   double* logs) {
   pdl_enter();
   int Dp = (D + 3) & ~3;
   int tot = (Mp + B) * Dp;
@@ -32,6 +33,13 @@ __global__ void prep_coords_kernel(const float* __restrict__ Z, const float* __r
       int n = r - Mp;
       Xs[(size_t)n * Dp + d] = (d < D) ? X[(size_t)n * D + d] / ell[d] : 0.f;
     }
+  }
+  // *logs += sum_i log s~_i (the log-det of diag(s~) in the KL term), by the
+  // blocks whose first index is below M
+  if (logs && blockIdx.x * blockDim.x < M) {
+    double part = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) part += log((double)s[i]);
+    block_add_double(part, logs);
   }
 }
 
@@ -54,17 +62,27 @@ __global__ void __launch_bounds__(256) kuu_kernel(const float* __restrict__ Zs, 
   }
   __syncthreads();
   const float sf2 = *sf2p;
+  // this thread's two columns z~_j in registers; z~_i read as warp broadcasts
+  float zc[2][DP];
+#pragma unroll
+  for (int cj = 0; cj < 2; ++cj)
+#pragma unroll
+    for (int d = 0; d < DP; ++d) zc[cj][d] = zj[tx + 32 * cj][d];
 #pragma unroll 2
   for (int ri = 0; ri < 8; ++ri) {
     const int rr = ty + 8 * ri, i = i0 + rr;
+    float r2[2] = {0.f, 0.f};
+#pragma unroll
+    for (int d = 0; d < DP; ++d) {
+      const float a = zi[rr][d];
+#pragma unroll
+      for (int cj = 0; cj < 2; ++cj) { const float e = a - zc[cj][d]; r2[cj] = fmaf(e, e, r2[cj]); }
+    }
     float val[2];
 #pragma unroll
     for (int cj = 0; cj < 2; ++cj) {
-      const int cc = tx + 32 * cj, j = j0 + cc;
-      float r2 = 0.f;
-#pragma unroll
-      for (int d = 0; d < DP; ++d) { const float e = zi[rr][d] - zj[cc][d]; r2 = fmaf(e, e, r2); }
-      float v = (i == j) ? sf2 : sf2 * expf(-0.5f * r2);
+      const int j = j0 + tx + 32 * cj;
+      float v = (i == j) ? sf2 : sf2 * expf(-0.5f * r2[cj]);
       val[cj] = (i < M && j < M) ? v : 0.f;
     }
 #pragma unroll
@@ -612,13 +630,13 @@ __global__ void ng_check_kernel(double* red, int M, double eps, int* done, int* 
 }  // namespace
 
 void k_prep_coords(const float* Z, const float* X, const float* ell, int M, int Mp, int B, int D,
-                   float* Zs, float* Xs, cudaStream_t st) {
+                   float* Zs, float* Xs, cudaStream_t st, const float* s, double* logs) {
   int Dp = (D + 3) & ~3;
   int tot = (Mp + B) * Dp;
   int grid = (tot + 255) / 256;
   if (grid > 4096) grid = 4096;
   svgp_note_launch();
-  pdl_launch(prep_coords_kernel, grid, 256, 0, st, Z, X, ell, M, Mp, B, D, Zs, Xs);
+  pdl_launch(prep_coords_kernel, grid, 256, 0, st, Z, X, ell, M, Mp, B, D, Zs, Xs, s, logs);
 }
 
 template <class OutP>

@@ -284,7 +284,7 @@ void prologue(svgp_handle* h, const svgp_params* p, const float* X, int B, const
                            {h->rowacc_f, rows}, {h->rowacc_u, rows},
                            {ng_done, sizeof(int)}, {ng_iters, sizeof(int)}};
   k_zero_n(st, zr, 8);
-  k_prep_coords(p->Z, X, p->ell, h->M, h->Mp, X ? B : 0, h->D, h->Zs, h->Xs, st);
+  k_prep_coords(p->Z, X, p->ell, h->M, h->Mp, X ? B : 0, h->D, h->Zs, h->Xs, st, p->s, h->red + RED_LOGS);
   if (h->tc_kuf) k_kuf_prep(h->Zs, X ? h->Xs : nullptr, h->M, h->Mp, X ? B : 0, (B + 127) / 128 * 128, h->D, p->sf2, h->kt, st);
   if (h->mode == MODE_F32) k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, (float*)nullptr, false, st);
   else if (h->mode == MODE_BF16) k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, H(h->Kuu_lo), true, st);
@@ -298,7 +298,6 @@ void prologue(svgp_handle* h, const svgp_params* p, const float* X, int B, const
 void forward(svgp_handle* h, const svgp_params* p, const svgp_batch* b, bool psi) {
   cudaStream_t st = h->st;
   psi = psi && !h->probit;
-  k_logs(p->s, h->M, h->red, st);
   run_vt(h, h->Kuu_lo, p->s, nullptr);   // Vt = L^T K~
   run_sym<1>(h, nullptr);                // A1 = L^T K~ L ; S = 2I - A1 ; tr, Frobenius
   if (psi) run_psi(h, p, b->B, nullptr); // Psi = Kuf Kuf^T (Kuf generated on chip)
