@@ -256,7 +256,7 @@ def reduce_timing(tot_ms, steps, ws):
 NCU_DRAM_BYTES = {
     ("gp_sample_regression", "bf16", "w"): 10435328,      # profiles/w_tc_kernel_M2048_B4096_bf16.md
     ("gp_sample_regression", "bf16", "psi"): 832768,      # profiles/psi_tc_kernel_M2048_B4096_bf16.md
-    ("gp_sample_regression", "bf16", "vt"): 29664512,     # profiles/tc_gemm_EpiVt_M2048_bf16.md
+    ("gp_sample_regression", "bf16", "vt"): 29684224,     # profiles/tc_gemm_EpiVt_M2048_bf16.md
 }
 
 
