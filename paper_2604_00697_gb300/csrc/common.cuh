@@ -59,6 +59,24 @@ __device__ __forceinline__ void put(const SplitPtr& p, size_t i, float x) {
   p.hi[i] = h;
   p.lo[i] = __float2bfloat16_rn(x - __bfloat162float(h));
 }
+// Four consecutive elements from i (a multiple of 4): one vector store per plane.
+__device__ __forceinline__ void put4(float* p, size_t i, const float (&x)[4]) {
+  *reinterpret_cast<float4*>(p + i) = make_float4(x[0], x[1], x[2], x[3]);
+}
+__device__ __forceinline__ uint2 bf16x4(float a, float b, float c, float d) {
+  __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+  return make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
+}
+__device__ __forceinline__ void put4(bf16* p, size_t i, const float (&x)[4]) {
+  *reinterpret_cast<uint2*>(p + i) = bf16x4(x[0], x[1], x[2], x[3]);
+}
+__device__ __forceinline__ void put4(const SplitPtr& p, size_t i, const float (&x)[4]) {
+  float r[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) r[q] = x[q] - __bfloat162float(__float2bfloat16_rn(x[q]));
+  *reinterpret_cast<uint2*>(p.hi + i) = bf16x4(x[0], x[1], x[2], x[3]);
+  *reinterpret_cast<uint2*>(p.lo + i) = bf16x4(r[0], r[1], r[2], r[3]);
+}
 
 // Reduce a per-thread double over the block and add it to *dst (one atomic
 // per block).  Must be called by all threads of the block (any block shape).

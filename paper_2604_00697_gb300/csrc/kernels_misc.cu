@@ -45,15 +45,25 @@ __global__ void prep_coords_kernel(const float* __restrict__ Z, const float* __r
 
 // Kuu = sf2 exp(-1/2 ||z~_i - z~_j||^2) (per-dimension differences), exact
 // sf2 on the diagonal, zero padding.  64 x 64 tiles (16 elements per thread),
-// points staged in shared memory.
+// points staged in shared memory.  Only the tiles on and below the diagonal
+// are computed (blockIdx.x enumerates them row by row); an off-diagonal tile
+// is also written transposed, through shared memory -- (a - b)^2 = (b - a)^2
+// exactly, so the mirror is the value the upper tile would compute.
 template <class OutP, int DP>
 __global__ void __launch_bounds__(256) kuu_kernel(const float* __restrict__ Zs, int M, int Mp, int D,
                                                   const float* __restrict__ sf2p, float* __restrict__ Kf,
                                                   OutP Klo, bool has_lo) {
   pdl_enter();
   __shared__ float zi[64][DP + 1], zj[64][DP + 1];
+  __shared__ float tile[64][65];
   const int Dp = (D + 3) & ~3;
-  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  // lower-triangle tile t -> (bi, bj), bj <= bi
+  const int t = blockIdx.x;
+  int bi = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+  while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+  while (bi * (bi + 1) / 2 > t) --bi;
+  const int bj = t - bi * (bi + 1) / 2;
+  const int i0 = bi * 64, j0 = bj * 64;
   const int tx = threadIdx.x, ty = threadIdx.y;
   for (int e = ty * 32 + tx; e < 64 * DP; e += 256) {
     const int r = e / DP, d = e % DP;
@@ -90,6 +100,21 @@ __global__ void __launch_bounds__(256) kuu_kernel(const float* __restrict__ Zs, 
       const size_t o = (size_t)i * Mp + j0 + tx + 32 * cj;
       Kf[o] = val[cj];
       if (has_lo) put(Klo, o, val[cj]);
+      tile[rr][tx + 32 * cj] = val[cj];
+    }
+  }
+  if (bi == bj) return;
+  __syncthreads();
+  // mirror: Kuu[j0 + r][i0 + c] = tile[c][r]
+#pragma unroll 2
+  for (int r = ty; r < 64; r += 8) {
+#pragma unroll
+    for (int cj = 0; cj < 2; ++cj) {
+      const int c = tx + 32 * cj;
+      const size_t o = (size_t)(j0 + r) * Mp + i0 + c;
+      const float v = tile[c][r];
+      Kf[o] = v;
+      if (has_lo) put(Klo, o, v);
     }
   }
 }
@@ -150,13 +175,20 @@ __global__ void __launch_bounds__(256) gemv_kernel(const float* __restrict__ A, 
     const int k = lane + 32 * u;
     a[u] = (live && k < n4) ? __ldg(row + k) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  for (int j = threadIdx.x; j < Mp; j += blockDim.x) {
-    float xx = 0.f;
-    if (j < M) {
-      xx = x[j];
-      if (x2) xx = fmaf(beta, x2[j], xx);
+  // staging: eight loads in flight per thread before the shared-memory stores
+  for (int j0 = threadIdx.x; j0 < Mp; j0 += 8 * blockDim.x) {
+    float xv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int j = j0 + u * blockDim.x;
+      xv[u] = j < M ? __ldg(x + j) : 0.f;
+      if (x2 && j < M) xv[u] = fmaf(beta, __ldg(x2 + j), xv[u]);
     }
-    xs[j] = xx;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int j = j0 + u * blockDim.x;
+      if (j < Mp) xs[j] = xv[u];
+    }
   }
   __syncthreads();
   double part = 0.0;
@@ -334,16 +366,17 @@ __global__ void gp_assemble_kernel(const float* __restrict__ Kuu, const float* _
   const bool row_ok = i < M;
   const bool mt = m != nullptr;   // the m~ terms of the preconditioned bound
   const float kgi = row_ok ? Kg[i] : 0.f, mi = (row_ok && mt) ? m[i] : 0.f, wi = row_ok ? w[i] : 0.f;
+  float val[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int jj = j + q;
-    float val = 0.f;
+    val[q] = 0.f;
     if (row_ok && jj < M) {
-      val = cn * pv[q] + 0.5f * kv[q];
-      if (mt) val += 0.5f * c * (kgi * m[jj] + mi * Kg[jj]) - 0.5f * (mi * w[jj] + wi * m[jj]);
+      val[q] = cn * pv[q] + 0.5f * kv[q];
+      if (mt) val[q] += 0.5f * c * (kgi * m[jj] + mi * Kg[jj]) - 0.5f * (mi * w[jj] + wi * m[jj]);
     }
-    put(out, e + q, val);
   }
+  put4(out, e, val);
 }
 
 // Kuu-side chain rule: with A_ij = G_Kuu_ij Kuu_ij and e_d = z~_jd - z~_id,
@@ -372,6 +405,7 @@ __global__ void __launch_bounds__(256) kuu_bwd_kernel(const float* __restrict__ 
   const int Dp = (D + 3) & ~3;
   const int jb = blockIdx.y * JB, je = min(M, jb + JB);
   for (int e = threadIdx.x; e < 32 * (W + 1); e += 256) (&part[0][0])[e] = 0.f;
+#pragma unroll 8
   for (int e = threadIdx.x; e < JB * DP; e += 256) {
     const int r = e / DP, d = e - r * DP;
     const float zv = (jb + r < je && d < Dp) ? __ldg(Zs + (size_t)(jb + r) * Dp + d) : 0.f;
@@ -642,7 +676,8 @@ void k_prep_coords(const float* Z, const float* X, const float* ell, int M, int 
 template <class OutP>
 void k_kuu(const float* Zs, int M, int Mp, int D, const float* sf2, float* Kf, OutP Klo, bool has_lo,
            cudaStream_t st) {
-  dim3 grid(Mp / 64, Mp / 64), blk(32, 8);
+  const int nb = Mp / 64;
+  dim3 grid(nb * (nb + 1) / 2), blk(32, 8);
   svgp_note_launch();
   SVGP_DP_DISPATCH(D, pdl_launch(kuu_kernel<OutP, DP>, grid, blk, 0, st, Zs, M, Mp, D, sf2, Kf, Klo, has_lo));
 }
