@@ -285,6 +285,12 @@ def run_group(args):
         prob = S.sinusoid_regression(seed=100 + g, B=B, M=int(M), D=D)
         m = RSVGP(int(M), D, B, prec=args.prec)
         m.set_state(prob.Z0, np.ones(D), 1.0, 1.0, np.zeros(M), np.full(M, 1e-4), 1e-3 * np.eye(M))
+        # same preparation and learning rates as the single-model workloads:
+        # L brought near chol(K~^-1) by 40 NG updates (untimed), Adam 1e-3
+        # (2e-4 for Z) so that one NG step per training step keeps tracking
+        m.ng_update(max_iters=40, gammas=[1.0] * 40)
+        m.hyper[0] = 1e-3
+        m.hyper[4] = 0.2
         X, y = prob.batch(0)
         models.append(m)
         batches.append((torch.tensor(X, dtype=torch.float32, device="cuda"),
