@@ -366,6 +366,17 @@ __global__ void gp_assemble_kernel(const float* __restrict__ Kuu, const float* _
   const bool row_ok = i < M;
   const bool mt = m != nullptr;   // the m~ terms of the preconditioned bound
   const float kgi = row_ok ? Kg[i] : 0.f, mi = (row_ok && mt) ? m[i] : 0.f, wi = row_ok ? w[i] : 0.f;
+  // Kg and w are Mp-long workspace vectors (16-byte aligned): one vector load
+  // each; m~ is the caller's (any alignment, M long): scalar loads
+  float kgv[4] = {0.f, 0.f, 0.f, 0.f}, wv[4] = {0.f, 0.f, 0.f, 0.f}, mv[4] = {0.f, 0.f, 0.f, 0.f};
+  if (mt && row_ok) {
+    const float4 k4 = __ldg(reinterpret_cast<const float4*>(Kg + j));
+    const float4 w4 = __ldg(reinterpret_cast<const float4*>(w + j));
+    kgv[0] = k4.x; kgv[1] = k4.y; kgv[2] = k4.z; kgv[3] = k4.w;
+    wv[0] = w4.x; wv[1] = w4.y; wv[2] = w4.z; wv[3] = w4.w;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) mv[q] = j + q < M ? __ldg(m + j + q) : 0.f;
+  }
   float val[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -373,7 +384,7 @@ __global__ void gp_assemble_kernel(const float* __restrict__ Kuu, const float* _
     val[q] = 0.f;
     if (row_ok && jj < M) {
       val[q] = cn * pv[q] + 0.5f * kv[q];
-      if (mt) val[q] += 0.5f * c * (kgi * m[jj] + mi * Kg[jj]) - 0.5f * (mi * w[jj] + wi * m[jj]);
+      if (mt) val[q] += 0.5f * c * (kgi * mv[q] + mi * kgv[q]) - 0.5f * (mi * wv[q] + wi * mv[q]);
     }
   }
   put4(out, e, val);
