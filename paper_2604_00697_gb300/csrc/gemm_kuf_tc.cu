@@ -241,13 +241,25 @@ psi_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // z, row role
 // With per-point weights hw (may be null) the k-role constant is
 // c' + 1/2 log2|hw_r| (c' = -1e30 where |hw_r| < 1e-30), so that the generated
 // value carries a factor sqrt|hw_r|.  R may be null (k role only).
-__global__ void kuf_prep_kernel(const float* __restrict__ P, int n, int npad, int D, const float* __restrict__ sf2,
-                                const float* __restrict__ hw, bf16* __restrict__ R, bf16* __restrict__ K) {
+// One point set of the preparation: rows P (n valid of npad), optional
+// weights, and the row-role / k-role outputs (either may be null).
+struct PrepJob {
+  const float* P; int n, npad; const float* hw; bf16* R; bf16* K;
+};
+
+__global__ void kuf_prep_kernel(PrepJob j0, PrepJob j1, int nb0, int D, const float* __restrict__ sf2) {
   pdl_enter();
+  // blocks [0, nb0) prepare j0, the rest j1 (one launch for both point sets);
   // one row per threadIdx.y (8 rows per block), 64 threads per row
+  const bool second = (int)blockIdx.x >= nb0;
+  const float* __restrict__ P = second ? j1.P : j0.P;
+  const int n = second ? j1.n : j0.n, npad = second ? j1.npad : j0.npad;
+  const float* __restrict__ hw = second ? j1.hw : j0.hw;
+  bf16* __restrict__ R = second ? j1.R : j0.R;
+  bf16* __restrict__ K = second ? j1.K : j0.K;
   __shared__ float part_sum[8][2];
   const int Dp = (D + 3) & ~3;
-  const int r = blockIdx.x * 8 + threadIdx.y;
+  const int r = ((int)blockIdx.x - (second ? nb0 : 0)) * 8 + threadIdx.y;
   const int d = threadIdx.x;
   const bool live = r < npad, valid = r < n;
   const int part = d / D;               // 0, 1, 2: coordinate slots; then constants
@@ -298,19 +310,18 @@ void set_psi_attr() {
 void k_kuf_prep(const float* Zs, const float* Xs, int M, int Mp, int B, int Bp, int D, const float* sf2,
                 const KufTC& t, cudaStream_t st) {
   dim3 blk(64, 8);
+  const PrepJob z{Zs, M, Mp, nullptr, t.ZR, t.ZK}, x{Xs, B, Bp, nullptr, t.XR, t.XK};
+  const int nbz = (Mp + 7) / 8, nbx = (Xs && B > 0) ? (Bp + 7) / 8 : 0;
   svgp_note_launch();
-  pdl_launch(kuf_prep_kernel, (Mp + 7) / 8, blk, 0, st, Zs, M, Mp, D, sf2, nullptr, t.ZR, t.ZK);
-  if (Xs && B > 0) {
-    svgp_note_launch();
-    pdl_launch(kuf_prep_kernel, (Bp + 7) / 8, blk, 0, st, Xs, B, Bp, D, sf2, nullptr, t.XR, t.XK);
-  }
+  pdl_launch(kuf_prep_kernel, nbz + nbx, blk, 0, st, z, x, nbz, D, sf2);
 }
 
 void k_kuf_prep_weighted(const float* Xs, int B, int Bp, int D, const float* sf2, const float* h, bf16* XKh,
                          cudaStream_t st) {
   dim3 blk(64, 8);
+  const PrepJob x{Xs, B, Bp, h, nullptr, XKh};
   svgp_note_launch();
-  pdl_launch(kuf_prep_kernel, (Bp + 7) / 8, blk, 0, st, Xs, B, Bp, D, sf2, h, nullptr, XKh);
+  pdl_launch(kuf_prep_kernel, (Bp + 7) / 8, blk, 0, st, x, x, (Bp + 7) / 8, D, sf2);
 }
 
 void tc_kuf_init_attributes() {
