@@ -164,9 +164,9 @@ bool tc_kuf_gemv(const bf16* Rrole, int nrows, const bf16* Krole, int nk, const 
   if (!tc_make_map(&mr, Rrole, rows_p, 64, 128) || !tc_make_map(&mk, Krole, kp, 64, 64)) return false;
   if (!out_zeroed) k_zero(st, out, sizeof(float) * nrows);
   const int nkb = kp / 64, rb = rows_p / 128;
-  // about two CTAs per SM, at least 8 k-blocks each
+  // about two CTAs per SM (both resident), at least 4 k-blocks each
   int groups = (2 * tc_num_sms() + rb - 1) / rb;
-  if (groups > (nkb + 7) / 8) groups = (nkb + 7) / 8;
+  if (groups > (nkb + 3) / 4) groups = (nkb + 3) / 4;
   if (groups < 1) groups = 1;
   const int per = (nkb + groups - 1) / groups;
   groups = (nkb + per - 1) / per;
