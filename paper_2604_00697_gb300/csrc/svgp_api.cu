@@ -47,6 +47,11 @@ struct svgp_handle {
   int M, Mp, D, Dp, Bmax;
   int mode;       // MODE_F32 / MODE_BF16 / MODE_SPLIT (svgp_prec)
   cudaStream_t st;
+  // second stream for Psi = Kuf Kuf^T, which depends only on the prologue:
+  // forked from st after the prologue, joined before the first reader
+  cudaStream_t st_aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool psi_pending = false;
   char err[512];
   // matrices
   float *Kuu_f, *Lf, *Pf, *Psi, *GKuu;
@@ -252,6 +257,27 @@ void run_psi(svgp_handle* h, const svgp_params* p, int B, const float* hw) {
   if (!(h->tc_kuf && tc_psi(h->gt, kg, h->kt, hw ? h->kt.XKh : h->kt.XK, B, e))) simt_psi(h->gs, kg, B, e, hw);
 }
 
+// Psi of the Gaussian bound on the second stream (it needs only the
+// prologue's coordinates and Kuf operands): the products that follow on st
+// do not wait for it until join_psi, so Psi fills the SMs their tails leave.
+void fork_psi(svgp_handle* h, const svgp_params* p, int B) {
+  if (h->psi_pending || h->probit) return;
+  cudaEventRecord(h->ev_fork, h->st);
+  cudaStreamWaitEvent(h->st_aux, h->ev_fork, 0);
+  cudaStream_t main = h->st;
+  h->st = h->gs.st = h->gt.st = h->st_aux;
+  run_psi(h, p, B, nullptr);
+  h->st = h->gs.st = h->gt.st = main;
+  cudaEventRecord(h->ev_join, h->st_aux);
+  h->psi_pending = true;
+}
+
+void join_psi(svgp_handle* h) {
+  if (!h->psi_pending) return;
+  cudaStreamWaitEvent(h->st, h->ev_join, 0);
+  h->psi_pending = false;
+}
+
 // Returns the number of partial row sets the tensor-core kernel wrote (0 when
 // the SIMT kernel accumulated into we.rowacc, or in variance mode).
 int run_w(svgp_handle* h, const WEpi& we) {
@@ -298,10 +324,11 @@ void prologue(svgp_handle* h, const svgp_params* p, const float* X, int B, const
 void forward(svgp_handle* h, const svgp_params* p, const svgp_batch* b, bool psi) {
   cudaStream_t st = h->st;
   psi = psi && !h->probit;
+  if (psi) fork_psi(h, p, b->B);         // Psi = Kuf Kuf^T (Kuf generated on chip), second stream
   run_vt(h, h->Kuu_lo, p->s, nullptr);   // Vt = L^T K~
   run_sym<1>(h, nullptr);                // A1 = L^T K~ L ; S = 2I - A1 ; tr, Frobenius
-  if (psi) run_psi(h, p, b->B, nullptr); // Psi = Kuf Kuf^T (Kuf generated on chip)
   run_ls(h);                             // Y = L (2I - A1)
+  if (psi) join_psi(h);
   run_p(h, p->s, psi ? h->Psi : nullptr);  // P = Y L^T ; sum s_i P_ii ; <P, Psi>
   if (h->unprec) cudaMemcpyAsync(h->v, p->m, sizeof(float) * h->M, cudaMemcpyDeviceToDevice, st);  // v = m
   else k_gemv(h->Pf, h->Mp, h->M, p->m, 1.f, nullptr, 0.f, h->v, nullptr, nullptr, st);     // v = P m
@@ -442,6 +469,12 @@ svgp_status svgp_create(const svgp_config* cfg, svgp_handle** out) {
   h->Bmax = cfg->B_max;
   h->mode = cfg->prec;   // svgp_prec values coincide with MODE_*
   h->st = (cudaStream_t)cfg->cuda_stream;
+  if (cudaStreamCreateWithFlags(&h->st_aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    svgp_destroy(h);
+    return SVGP_ERR_CUDA;
+  }
   h->err[0] = 0;
   h->prof = false;
   h->probit = cfg->lik == SVGP_LIK_BERNOULLI_PROBIT;
@@ -510,6 +543,9 @@ svgp_status svgp_create(const svgp_config* cfg, svgp_handle** out) {
 
 void svgp_destroy(svgp_handle* h) {
   if (!h) return;
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->st_aux) cudaStreamDestroy(h->st_aux);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
   delete h;
@@ -670,6 +706,7 @@ svgp_status svgp_train_step(svgp_handle* h, const svgp_params* p, const svgp_bat
   // the log-det of L is taken after the NG update (the prologue's is of the old L)
   int* iters = iters_dev ? iters_dev : h->iters_tmp;
   prologue(h, p, b->X, b->B, L_inout, max_iters == 0, h->done, iters);
+  fork_psi(h, p, b->B);   // overlaps the NG update; joined before P in the forward pass
   ng_loop(h, p, L_inout, gamma_dev, max_iters, eps, iters, residual_dev ? residual_dev : h->resid_tmp, true);
   if (max_iters > 0) prep_L(h, L_inout, h->red + RED_LOGDETL);   // copies and log-det of the updated L
   svgp_params q = *p;
