@@ -260,21 +260,30 @@ void run_psi(svgp_handle* h, const svgp_params* p, int B, const float* hw) {
 // Psi of the Gaussian bound on the second stream (it needs only the
 // prologue's coordinates and Kuf operands): the products that follow on st
 // do not wait for it until join_psi, so Psi fills the SMs their tails leave.
-void fork_psi(svgp_handle* h, const svgp_params* p, int B) {
-  if (h->psi_pending || h->probit) return;
+// Runs f's launches on the second stream after everything issued so far on
+// st; join_aux makes st wait for them.
+template <class F>
+void on_aux(svgp_handle* h, F&& f) {
   cudaEventRecord(h->ev_fork, h->st);
   cudaStreamWaitEvent(h->st_aux, h->ev_fork, 0);
   cudaStream_t main = h->st;
   h->st = h->gs.st = h->gt.st = h->st_aux;
-  run_psi(h, p, B, nullptr);
+  f();
   h->st = h->gs.st = h->gt.st = main;
   cudaEventRecord(h->ev_join, h->st_aux);
+}
+
+void join_aux(svgp_handle* h) { cudaStreamWaitEvent(h->st, h->ev_join, 0); }
+
+void fork_psi(svgp_handle* h, const svgp_params* p, int B) {
+  if (h->psi_pending || h->probit) return;
+  on_aux(h, [&] { run_psi(h, p, B, nullptr); });
   h->psi_pending = true;
 }
 
 void join_psi(svgp_handle* h) {
   if (!h->psi_pending) return;
-  cudaStreamWaitEvent(h->st, h->ev_join, 0);
+  join_aux(h);
   h->psi_pending = false;
 }
 
@@ -371,6 +380,14 @@ void backward_tail(svgp_handle* h, const svgp_params* p, const svgp_batch* b, do
   }
   if (!(h->tc_kuf && tc_kuf_gemv(h->kt.ZR, M, h->kt.XK, b->B, h->g, h->Kg, true, h->errword, st)))
     k_kg(h->Zs, h->Xs, M, Mp, b->B, h->D, p->sf2, h->g, h->Kg, st);                    // Kuf g
+  // W = P Kuf with the data part of the chain rule needs only the forward
+  // pass: on the second stream, beside the G_Kuu chain; joined before the
+  // gradient finalize
+  const float* nz0 = h->probit ? nullptr : p->noise;
+  WEpi we{KufGen{h->Zs, h->Xs, h->D, M, b->B, p->sf2}, h->v, h->g, h->probit ? h->hn : nullptr, nz0, c,
+          h->rowacc_f, nullptr};
+  int nparts = 0;
+  on_aux(h, [&] { nparts = run_w(h, we); });                                          // data part of dZ, dell, dsf2
   const float* nz = h->probit ? nullptr : p->noise;
   const float* mt = h->unprec ? nullptr : p->m;
   if (h->mode == MODE_F32) k_gp_assemble(h->Kuu_f, h->Psi, h->Kg, mt, h->w, nz, c, M, Mp, F(h->GP_lo), st);
@@ -380,12 +397,10 @@ void backward_tail(svgp_handle* h, const svgp_params* p, const svgp_batch* b, do
   run_sym<2>(h, nullptr);                // S = L^T G_P L + I/2
   run_ls(h);                             // Y = L S
   run_gk(h, p->s, gr->ds);               // G_K~ = -Y L^T -> G_Kuu, ds
-  WEpi we{KufGen{h->Zs, h->Xs, h->D, M, b->B, p->sf2}, h->v, h->g, h->probit ? h->hn : nullptr, nz, c,
-          h->rowacc_f, nullptr};
-  const int nparts = run_w(h, we);                                                     // data part of dZ, dell, dsf2
   k_kuu_bwd(h->GKuu, h->Kuu_f, h->Zs, M, Mp, h->D, h->rowacc_u, h->red, st);          // Kuu part
   if (h->unprec) k_axpy(h->Kg, c, h->w, -1.0f / c, gr->dm, M, st);                   // dm = c Kg - w
   else k_gemv(h->Pf, Mp, M, h->Kg, c, h->w, -1.0f / c, gr->dm, nullptr, nullptr, st); // dm = P (c Kg - w)
+  join_aux(h);                                                                         // W done
   k_grad_finalize(h->rowacc_f, h->rowacc_u, h->rowpart, nparts, Mp, p->ell, M, h->D, gr->dZ, h->acc_ell, h->red,
                   st);
   k_terms_finalize(h->red, h->acc_ell, p->sf2, p->noise, p->ell, M, h->D, b->B, b->N, h->probit, 0, terms_dev,
