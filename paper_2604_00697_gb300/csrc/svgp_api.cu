@@ -380,14 +380,18 @@ void backward_tail(svgp_handle* h, const svgp_params* p, const svgp_batch* b, do
   }
   if (!(h->tc_kuf && tc_kuf_gemv(h->kt.ZR, M, h->kt.XK, b->B, h->g, h->Kg, true, h->errword, st)))
     k_kg(h->Zs, h->Xs, M, Mp, b->B, h->D, p->sf2, h->g, h->Kg, st);                    // Kuf g
-  // W = P Kuf with the data part of the chain rule needs only the forward
-  // pass: on the second stream, beside the G_Kuu chain; joined before the
-  // gradient finalize
+  // W = P Kuf with the data part of the chain rule, and dm~, need only the
+  // forward pass and Kuf g: on the second stream, beside the G_Kuu chain;
+  // joined before the gradient finalize
   const float* nz0 = h->probit ? nullptr : p->noise;
   WEpi we{KufGen{h->Zs, h->Xs, h->D, M, b->B, p->sf2}, h->v, h->g, h->probit ? h->hn : nullptr, nz0, c,
           h->rowacc_f, nullptr};
   int nparts = 0;
-  on_aux(h, [&] { nparts = run_w(h, we); });                                          // data part of dZ, dell, dsf2
+  on_aux(h, [&] {
+    nparts = run_w(h, we);                                                                // data part of dZ, dell, dsf2
+    if (h->unprec) k_axpy(h->Kg, c, h->w, -1.0f / c, gr->dm, M, h->st);                // dm = c Kg - w
+    else k_gemv(h->Pf, Mp, M, h->Kg, c, h->w, -1.0f / c, gr->dm, nullptr, nullptr, h->st); // dm = P (c Kg - w)
+  });
   const float* nz = h->probit ? nullptr : p->noise;
   const float* mt = h->unprec ? nullptr : p->m;
   if (h->mode == MODE_F32) k_gp_assemble(h->Kuu_f, h->Psi, h->Kg, mt, h->w, nz, c, M, Mp, F(h->GP_lo), st);
@@ -398,9 +402,7 @@ void backward_tail(svgp_handle* h, const svgp_params* p, const svgp_batch* b, do
   run_ls(h);                             // Y = L S
   run_gk(h, p->s, gr->ds);               // G_K~ = -Y L^T -> G_Kuu, ds
   k_kuu_bwd(h->GKuu, h->Kuu_f, h->Zs, M, Mp, h->D, h->rowacc_u, h->red, st);          // Kuu part
-  if (h->unprec) k_axpy(h->Kg, c, h->w, -1.0f / c, gr->dm, M, st);                   // dm = c Kg - w
-  else k_gemv(h->Pf, Mp, M, h->Kg, c, h->w, -1.0f / c, gr->dm, nullptr, nullptr, st); // dm = P (c Kg - w)
-  join_aux(h);                                                                         // W done
+  join_aux(h);                                                                         // W and dm done
   k_grad_finalize(h->rowacc_f, h->rowacc_u, h->rowpart, nparts, Mp, p->ell, M, h->D, gr->dZ, h->acc_ell, h->red,
                   st);
   k_terms_finalize(h->red, h->acc_ell, p->sf2, p->noise, p->ell, M, h->D, b->B, b->N, h->probit, 0, terms_dev,
