@@ -7,7 +7,7 @@ step on all of {Z, ell, sf2, noise, m~, s~} -- the alternating optimisation of
 Section 3.1 -- on a fresh minibatch resident in HBM, captured as a CUDA graph.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
-oracle on the same workload instead (the reference arm of this build).
+oracle on the same workload instead (the reference arm).
 Multi-GPU runs (torchrun) are independent replicas, one per GPU (the step is
 not sharded), so the scaling is weak.
 """

@@ -262,7 +262,7 @@ svgp_status svgp_sync_status(svgp_handle* h);
 const char* svgp_last_error(const svgp_handle* h);
 const char* svgp_status_string(int status);
 
-/* 1 if this build has tensor-core (tcgen05) kernels for the current device. */
+/* 1 if the library's tensor-core (tcgen05) kernels can run on the current device. */
 int svgp_has_tensor_cores(void);
 
 /* Instrumentation.  Kinds of dense-contraction launches that can be timed. */

@@ -1,7 +1,6 @@
 """Multi-process host logic of the benchmark on CPU ranks (gloo, world size 2).
 
-The step is not sharded on this build's one-GPU runs: N GPUs run N
-independent replicas.  What needs checking without a GPU is the timing
+The step is not sharded: N GPUs run N independent replicas.  What needs checking without a GPU is the timing
 aggregation (max over ranks, whole-job throughput) and that the reference arm
 prints from rank 0 only.
 """
