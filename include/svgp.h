@@ -26,6 +26,11 @@
  *    a device error word, read and cleared by svgp_sync_status().
  *  * The handle owns its workspace (allocated once in svgp_create for M and
  *    B_max) and is not thread-safe; use one handle per host thread/stream.
+ *  * The handle also owns a second CUDA stream: within a call, products that
+ *    depend only on earlier results of the same call (Psi, and the W product
+ *    of the gradient) are forked onto it from the handle's stream and joined
+ *    back before the call's last launch, so every call is complete in the
+ *    handle's stream order and a graph captured on that stream holds both.
  */
 #ifndef SVGP_H_
 #define SVGP_H_
@@ -130,7 +135,9 @@ enum {
 };
 
 /* Create a handle and its workspace.  On success *out owns device memory of
- * about 10 M^2 floats + O(B_max M / 64); destroy with svgp_destroy. */
+ * about 10 M^2 floats + O(B_max M / 64) and a second CUDA stream with two
+ * events; destroy with svgp_destroy.  SVGP_ERR_CUDA if the stream or events
+ * cannot be created. */
 svgp_status svgp_create(const svgp_config* cfg, svgp_handle** out);
 void svgp_destroy(svgp_handle* h);
 
