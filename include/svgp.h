@@ -190,7 +190,9 @@ svgp_status svgp_backward(svgp_handle* h, const svgp_params* p, const svgp_batch
  * receives the number of updates applied; residual_dev (device double, may be
  * NULL) the last residual computed (that of L before the last update when no
  * early stop happened).  Non-convergence is not an error: it shows as
- * iters == max_iters with residual >= eps. */
+ * iters == max_iters with residual >= eps.  A residual that is not finite (a
+ * diverging step size, or non-finite L, Z or s~) stops the loop before the
+ * update and records SVGP_ERR_NONFINITE in the device error word. */
 svgp_status svgp_ng_update_T(svgp_handle* h, const svgp_params* p, float* L_inout,
                              const float* gamma_dev, int max_iters, double eps,
                              int* iters_dev, double* residual_dev);
@@ -265,6 +267,19 @@ int svgp_param_count(const svgp_handle* h);
  * Returns SVGP_OK, SVGP_ERR_NONFINITE, SVGP_ERR_TIMEOUT or SVGP_ERR_CUDA. */
 svgp_status svgp_sync_status(svgp_handle* h);
 
+/* Check of the failure path of the bounded device waits (not an operation
+ * of the paper).  Every pipeline wait of the tensor-core kernels is bounded:
+ * when it gives up, the kernel stops issuing work, waits (bounded) for its
+ * own copies in flight, frees its TMEM, records SVGP_ERR_TIMEOUT in the
+ * device error word and returns.  This call launches, on the handle's stream,
+ * a one-block kernel whose bounded wait -- the same helper -- waits on an
+ * mbarrier that nothing ever arrives on, with a limit of 2^26 SM cycles
+ * (about 32 ms), so the wait runs out and the error word records the
+ * timeout; the next svgp_sync_status returns SVGP_ERR_TIMEOUT and clears it.
+ * No copy, MMA or memory access other than the error word is involved.
+ * SVGP_ERR_UNSUPPORTED without a tensor-core (sm_103a) device. */
+svgp_status svgp_check_wait_timeout(svgp_handle* h);
+
 /* Human-readable text of the last host-side error on this handle. */
 const char* svgp_last_error(const svgp_handle* h);
 const char* svgp_status_string(int status);
@@ -317,8 +332,9 @@ long long svgp_launch_count(const svgp_handle* h);
  * SVGP_ERR_INVALID_ARG.  Arguments are as for svgp_predict (device pointers;
  * p->L is the M x M factor of T); cuda_stream is the stream to run on (NULL:
  * legacy default stream).  The first call on a device performs a one-time
- * set-up on the host (it looks up the array's device address), so make that
- * first call before any stream capture.  Every call uses the same array and
+ * set-up on the host (it looks up the array's device address and copies the
+ * tile tables into the array), so make that first call before any stream
+ * capture.  Every call uses the same array and
  * clears what must start at zero; calls that overlap on the GPU (on different
  * streams, or from different host threads) race and must be serialised by
  * the caller.  Returns SVGP_ERR_CUDA when a launch fails. */

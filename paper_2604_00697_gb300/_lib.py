@@ -247,6 +247,17 @@ def svgp_launch_count(h=None):
     return int(lib.svgp_launch_count(h))
 
 
+EXPORTED += ["svgp_check_wait_timeout"]
+
+
+def svgp_check_wait_timeout(h):
+    """Launch the probe whose bounded device wait runs out (see svgp.h)."""
+    lib = load()
+    lib.svgp_check_wait_timeout.argtypes = [c_void_p]
+    lib.svgp_check_wait_timeout.restype = c_int
+    _check(h, lib.svgp_check_wait_timeout(h))
+
+
 EXPORTED += ["svgp_predict_noalloc"]
 
 

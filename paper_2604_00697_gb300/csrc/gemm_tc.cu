@@ -63,12 +63,10 @@ template <class Epi, int NSPLIT>
 __global__ void __launch_bounds__(192, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmAl, const __grid_constant__ CUtensorMap tmBl,
-               const Tile* __restrict__ tiles, const int* __restrict__ toff, Epi epi, int* errword,
-               const __grid_constant__ etc::EpiMaps maps) {
-  pdl_enter();
+               const TcTile* __restrict__ tiles, const int* __restrict__ toff, Epi epi, int* errword,
+               const __grid_constant__ etc::EpiMaps maps, float* __restrict__ kpart, int* kflag) {
   using G = Geo<Epi, NSPLIT>;
   constexpr int S = G::STAGES;
-  if (epi.skip()) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   // stage s holds tiles [A_hi, B_hi, (A_lo, B_lo)]
@@ -81,8 +79,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   auto BAR = [&](int i) { return smem_u32(&bars[i]); };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t_beg = toff[blockIdx.x], t_end = toff[blockIdx.x + 1];   // this CTA's tiles
 
+  // Set-up that touches no global memory (barriers, TMEM, the tensor maps in
+  // the parameter space) runs before the wait for the previous kernel, so it
+  // overlaps that kernel's tail.  The TMEM allocation can only wait for a
+  // co-resident CTA of an earlier kernel to free its columns, and such a CTA
+  // never waits on this kernel.
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(BAR(s), 1);
@@ -104,12 +106,18 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
+  pdl_enter();
+  if (epi.skip()) {
+    if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
+    return;
+  }
+  const int t_beg = toff[blockIdx.x], t_end = toff[blockIdx.x + 1];   // this CTA's tiles
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
     int g = 0;          // running k-block counter over all tiles of this CTA
     for (int t = t_beg; t < t_end && !*abort_flag; ++t) {
-      const Tile tl = tiles[t];
+      const TcTile tl = tiles[t];
       const int nk = (tl.k1 - tl.k0) / BK;
       for (int kb = 0; kb < nk; ++kb, ++g) {
         const int s = g % S;
@@ -135,7 +143,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     // ---------------- MMA issuer ----------------
     int g = 0, lt = 0;
     for (int t = t_beg; t < t_end; ++t, ++lt) {
-      const Tile tl = tiles[t];
+      const TcTile tl = tiles[t];
       const int nk = (tl.k1 - tl.k0) / BK;
       const int b = lt & 1;
       if (!mbar_wait(BAR(2 * S + 2 + b), ((lt >> 1) & 1) ^ 1)) { *abort_flag = 1; break; }
@@ -190,18 +198,57 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     epi.begin_tile(0, 0);
     int lt = 0;
     for (int t = t_beg; t < t_end; ++t, ++lt) {
-      const Tile tl = tiles[t];
+      const TcTile tl = tiles[t];
       const int nk = (tl.k1 - tl.k0) / BK;
       const int b = lt & 1;
       const int i0 = tl.m0 + quad * 32;
+      const uint32_t acc = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * BN);
+      if (tl.role == TC_PRODUCER) {
+        // producer chunk of a split tile: raw FP32 partial sums of its K range
+        // into the workspace slot (rows i0 .. i0 + 31), then count this warp done
+        if (!mbar_wait(BAR(2 * S + b), (lt >> 1) & 1)) { *abort_flag = 1; break; }
+        fence_after();
+        float* dst = kpart + (size_t)tl.slot * (BM * BN) + (size_t)(quad * 32 + lane) * BN;
+#pragma unroll
+        for (int c = 0; c < BN / 32; ++c) {
+          float v[32];
+          tmem_ld32(acc + (uint32_t)(c * 32), v);
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            __stcg(reinterpret_cast<float4*>(dst + c * 32) + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+        }
+        fence_before();
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(BAR(2 * S + 2 + b));
+          atomicAdd(kflag + 2 * tl.slot, 1);
+        }
+        continue;
+      }
+      const float* part = nullptr;     // owner chunk: the producer's partial rows
+      if (tl.role == TC_OWNER) part = kpart + (size_t)tl.slot * (BM * BN) + (size_t)(quad * 32 + lane) * BN;
       issue_in(0, i0, tl.n0);
       issue_in(1, i0, tl.n0 + 32);
       etc::tc_prefetch(epi, tl.m0, tl.n0, lane);
       if (!mbar_wait(BAR(2 * S + b), (lt >> 1) & 1)) { *abort_flag = 1; break; }
       fence_after();
       if (*abort_flag) break;
-      const uint32_t acc = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * BN);
       bool ok = true;
+      if (part) {
+        // the four producer warps of this tile have stored their partials
+        // (bounded wait; the producer chunk never waits on anything)
+        if (lane == 0) {
+          const long long t0 = clock64();
+          while (ld_acquire(kflag + 2 * tl.slot) < 4) {
+            if (clock64() - t0 > WAIT_CYCLES || *abort_flag) { ok = false; break; }
+            __nanosleep(64);
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        if (ok) (void)ld_acquire(kflag + 2 * tl.slot);
+        __syncwarp();
+      }
 #pragma unroll
       for (int c = 0; c < BN / 32; ++c) {
         const int j0 = tl.n0 + c * 32, k = c & 1;
@@ -212,6 +259,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           } else {
 #pragma unroll
             for (int q = 0; q < 32; ++q) v[q] = 0.f;
+          }
+          if (part && ok) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const float4 p = __ldcg(reinterpret_cast<const float4*>(part + c * 32) + q);
+              v[4 * q] += p.x; v[4 * q + 1] += p.y; v[4 * q + 2] += p.z; v[4 * q + 3] += p.w;
+            }
           }
           int x, y;
           if (etc::tc_in(epi, i0, j0, x, y)) {
@@ -229,6 +283,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(BAR(2 * S + 2 + b));
+      // the last of the four owner warps to finish reading resets the slot's
+      // counts for the next launch
+      if (part && ok && lane == 0 && atomicAdd(kflag + 2 * tl.slot + 1, 1) == 3) {
+        kflag[2 * tl.slot] = 0;
+        kflag[2 * tl.slot + 1] = 0;
+      }
       if (!ok) break;
     }
     // every input copy landed and every store completed before the CTA exits
@@ -246,6 +306,19 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
   }
+}
+
+// Failure-path probe: one thread waits, with the bounded wait every pipeline
+// uses, on an mbarrier that nothing ever arrives on, so the wait gives up
+// after `limit` cycles and raises ERRBIT_TIMEOUT as an expired pipeline
+// wait does.  No copy, MMA or TMEM allocation is involved.
+__global__ void wait_probe_kernel(int* errword, long long limit) {
+  pdl_enter();
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(smem_u32(&bar), 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (!mbar_wait_for(smem_u32(&bar), 0, limit)) atomicOr(errword, ERRBIT_TIMEOUT);
 }
 
 // ---------------------------------------------------------------------------
@@ -358,6 +431,11 @@ bool epi_maps(const EpiGK& e, etc::EpiMaps& m, int Mp) {
 
 }  // namespace
 
+void tc_wait_probe(int* errword, cudaStream_t st) {
+  svgp_note_launch();
+  pdl_launch(wait_probe_kernel, 1, 32, 0, st, errword, 1ll << 26);   // about 32 ms at 2 GHz
+}
+
 bool tc_available() {
   int dev = 0, major = 0, minor = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
@@ -378,10 +456,12 @@ bool tc_gemm(const GemmCtx& g, int tab, const bf16* A, const bf16* B, const Epi&
   if (g.split) {
     if (!tc_make_map(&mal, A + MM, g.Mp, g.Mp, 128) || !tc_make_map(&mbl, B + MM, g.Mp, g.Mp, 128)) return false;
     svgp_note_launch();
-    pdl_launch(tc_gemm_kernel<Epi, 3>, grid, 192, Geo<Epi, 3>::SMEM, g.st, ma, mb, mal, mbl, g.tt[tab], g.toff[tab], e, g.err, em);
+    pdl_launch(tc_gemm_kernel<Epi, 3>, grid, 192, Geo<Epi, 3>::SMEM, g.st, ma, mb, mal, mbl, g.tct[tab], g.toff[tab], e, g.err, em,
+               g.kpart, g.kflag);
   } else {
     svgp_note_launch();
-    pdl_launch(tc_gemm_kernel<Epi, 1>, grid, 192, Geo<Epi, 1>::SMEM, g.st, ma, mb, ma, mb, g.tt[tab], g.toff[tab], e, g.err, em);
+    pdl_launch(tc_gemm_kernel<Epi, 1>, grid, 192, Geo<Epi, 1>::SMEM, g.st, ma, mb, ma, mb, g.tct[tab], g.toff[tab], e, g.err, em,
+               g.kpart, g.kflag);
   }
   return true;
 }

@@ -16,6 +16,16 @@ enum TileTable {
   TT_COUNT = 7
 };
 
+// One work item of the persistent tensor-core GEMM: an output tile and its K
+// range, whole (role TC_WHOLE) or one of two K chunks of a split tile.  The
+// producer chunk (TC_PRODUCER) writes its FP32 partial sums to workspace slot
+// `slot` and counts itself done; the owner chunk (TC_OWNER) waits for that
+// count, adds the partial and runs the epilogue.
+enum { TC_WHOLE = 0, TC_PRODUCER = 1, TC_OWNER = 2 };
+struct TcTile {
+  int m0, n0, k0, k1, role, slot;
+};
+
 struct GemmCtx {
   int Mp;
   cudaStream_t st;
@@ -24,9 +34,15 @@ struct GemmCtx {
   Tile* tt[TT_COUNT];
   int nt[TT_COUNT];
   // tensor-core schedule: CTA c of a launch of ncta[t] CTAs processes the
-  // tiles tt[t][toff[t][c] .. toff[t][c + 1])
+  // items tct[t][toff[t][c] .. toff[t][c + 1])
+  TcTile* tct[TT_COUNT];
   int* toff[TT_COUNT];
   int ncta[TT_COUNT];
+  // split-K workspace: 128 x 128 FP32 partial per slot, and per slot the
+  // producer's done count and the owner warps' read count (zero between launches)
+  float* kpart;
+  int* kflag;
+  int nslot;
 };
 
 // Process-wide count of kernel launches issued by the library (svgp_api.cu).
@@ -45,6 +61,8 @@ void simt_init_attributes();
 // B point at the hi part (lo at +Mp*Mp when g.split).  Return false when the
 // tensor-core path is unavailable.
 bool tc_available();
+// One-block probe whose bounded mbarrier wait runs out (raises ERRBIT_TIMEOUT).
+void tc_wait_probe(int* errword, cudaStream_t st);
 int tc_num_sms();
 void tc_init_attributes();
 template <class Epi>
@@ -156,5 +174,5 @@ void k_adam(float* raw, float* cons, const float* grad, float* m1, float* m2, in
             const float* hyper, const float* zbeta1, int M, int D, cudaStream_t st);
 // Eq. (8) stopping rule from red[RED_NG_RESID], which it resets to 0 for the
 // next iteration.
-void k_ng_check(double* red, int M, double eps, int* done, int* iters, double* resid,
+void k_ng_check(double* red, int M, double eps, int* done, int* iters, double* resid, int* errword,
                 cudaStream_t st);

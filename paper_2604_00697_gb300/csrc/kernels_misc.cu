@@ -660,14 +660,18 @@ __global__ void adam_kernel(float* __restrict__ raw, float* __restrict__ cons, c
 __global__ void step_inc_kernel(int* step) {
   pdl_enter(); if (threadIdx.x == 0 && blockIdx.x == 0) *step += 1; }
 
+// Eq. (8) residual of the current iterate; stops the loop (done = 1) when it
+// is below eps, or when it is not finite (a diverging step size or a
+// non-finite L or K~), which also sets the device error word.
 __global__ void ng_check_kernel(double* red, int M, double eps, int* done, int* iters,
-                                double* resid) {
+                                double* resid, int* errword) {
   pdl_enter();
   if (threadIdx.x != 0) return;
   if (*done) return;
   double r = sqrt(red[RED_NG_RESID] / M);
   red[RED_NG_RESID] = 0.0;
   if (resid) *resid = r;
+  if (!isfinite(r)) { *done = 1; atomicOr(errword, ERRBIT_NONFINITE); return; }
   if (eps > 0.0 && r < eps) { *done = 1; return; }
   if (iters) *iters += 1;
 }
@@ -899,8 +903,8 @@ void k_adam(float* raw, float* cons, const float* grad, float* m1, float* m2, in
   pdl_launch(step_inc_kernel, 1, 32, 0, st, step);
 }
 
-void k_ng_check(double* red, int M, double eps, int* done, int* iters, double* resid,
+void k_ng_check(double* red, int M, double eps, int* done, int* iters, double* resid, int* errword,
                 cudaStream_t st) {
   svgp_note_launch();
-  pdl_launch(ng_check_kernel, 1, 32, 0, st, red, M, eps, done, iters, resid);
+  pdl_launch(ng_check_kernel, 1, 32, 0, st, red, M, eps, done, iters, resid, errword);
 }

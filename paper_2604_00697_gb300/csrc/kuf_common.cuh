@@ -62,8 +62,11 @@ __device__ __forceinline__ float ex2_poly(float t) {
 }
 
 // Elements q (of each group of 8 generated values) whose exponential runs on
-// the FMA pipe instead of the MUFU unit.
-constexpr int POLY_MASK = 0;
+// the FMA pipe instead of the MUFU unit (a build-time choice).
+#ifndef SVGP_POLY_MASK
+#define SVGP_POLY_MASK 0
+#endif
+constexpr int POLY_MASK = SVGP_POLY_MASK;
 
 // Transform 32 exponents t[q] (k = kcol0 + q within the k-block) of one row
 // into BF16 (hi, and lo = value - hi for NSPLIT = 3) operand values at

@@ -110,32 +110,87 @@ bool upload_tiles(svgp_handle* h, const std::vector<Tile>& v, Tile** out, int* n
   return true;
 }
 
-// Persistent-kernel schedule: longest-processing-time-first assignment of the
-// tiles to min(#tiles, #SMs) CTAs, cost = k-blocks x 750 + 5000 cycles (the
-// measured mainloop cost per 64-deep k-block and epilogue cost per tile).
-// Returns the tiles grouped by CTA; off[c] .. off[c + 1] are CTA c's.
-std::vector<Tile> lpt_schedule(const std::vector<Tile>& v, int nsm, std::vector<int>& off) {
+// Persistent-kernel schedule.  Cost model of a work item in cycles: k-blocks x
+// 750 (the measured mainloop cost per 64-deep k-block) plus its epilogue (5000
+// for a whole or owner item, 2000 more for the owner's read of the partial,
+// 1500 for a producer's partial store).
+long long item_cost(const TcTile& t) {
+  const long long k = (long long)(t.k1 - t.k0) / 64 * 750;
+  return k + (t.role == TC_PRODUCER ? 1500 : t.role == TC_OWNER ? 7000 : 5000);
+}
+
+// Longest-processing-time-first assignment of the items to min(#items, nsm)
+// CTAs; within a CTA producer chunks come first (they never wait, so every
+// owner's producer finishes whatever the owners do), then the rest by
+// decreasing cost.  Returns the items grouped by CTA (off[c] .. off[c + 1]
+// are CTA c's) and the modelled makespan.
+std::vector<TcTile> lpt_schedule(std::vector<TcTile> v, int nsm, std::vector<int>& off, long long* makespan) {
+  std::stable_sort(v.begin(), v.end(), [](const TcTile& a, const TcTile& b) { return item_cost(a) > item_cost(b); });
   const int G = std::max(1, std::min((int)v.size(), nsm));
-  std::vector<std::vector<Tile>> per(G);
+  std::vector<std::vector<TcTile>> per(G);
   std::vector<long long> load(G, 0);
-  for (const Tile& t : v) {            // v is sorted by decreasing k length
+  for (const TcTile& t : v) {
     int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
     per[c].push_back(t);
-    load[c] += (long long)(t.k1 - t.k0) / 64 * 750 + 5000;
+    load[c] += item_cost(t);
   }
-  std::vector<Tile> out;
+  std::vector<TcTile> out;
   off.assign(1, 0);
   for (int c = 0; c < G; ++c) {
+    std::stable_partition(per[c].begin(), per[c].end(), [](const TcTile& t) { return t.role == TC_PRODUCER; });
     out.insert(out.end(), per[c].begin(), per[c].end());
     off.push_back((int)out.size());
+  }
+  if (makespan) *makespan = *std::max_element(load.begin(), load.end());
+  return out;
+}
+
+// Split-K plan of a tile table: tiles of at least kmin k-blocks become a
+// producer and an owner chunk (K boundary at a 64 multiple, slots from
+// *slot); kmin = 0 splits nothing.
+std::vector<TcTile> split_items(const std::vector<Tile>& v, int kmin, int* slot) {
+  std::vector<TcTile> out;
+  for (const Tile& t : v) {
+    const int nk = (t.k1 - t.k0) / 64;
+    if (kmin > 0 && nk >= kmin) {
+      const int kmid = t.k0 + (nk / 2) * 64;
+      out.push_back(TcTile{t.m0, t.n0, t.k0, kmid, TC_PRODUCER, *slot});
+      out.push_back(TcTile{t.m0, t.n0, kmid, t.k1, TC_OWNER, *slot});
+      ++*slot;
+    } else {
+      out.push_back(TcTile{t.m0, t.n0, t.k0, t.k1, TC_WHOLE, 0});
+    }
   }
   return out;
 }
 
-bool upload_sched(svgp_handle* h, const std::vector<Tile>& v, GemmCtx& g, int tab) {
+// Items of a table for the tensor-core GEMM.  Tables whose tiles have uneven
+// K ranges and few long tiles (the triangular products) get the split
+// threshold with the smallest modelled makespan among a few candidates
+// (ties: fewer splits); the full products keep whole tiles.
+std::vector<TcTile> plan_items(const std::vector<Tile>& v, bool may_split, int nsm, int* slot,
+                               std::vector<int>& off) {
+  int best = 0;
+  long long best_ms = 0;
+  if (may_split) {
+    const int cand[] = {0, 32, 28, 24, 20, 16, 12};
+    for (int kmin : cand) {
+      int tmp = 0;
+      std::vector<int> o;
+      long long ms = 0;
+      lpt_schedule(split_items(v, kmin, &tmp), nsm, o, &ms);
+      if (kmin == 0 || ms < best_ms * 97 / 100) { best = kmin; best_ms = ms; }
+    }
+  }
+  return lpt_schedule(split_items(v, best, slot), nsm, off, nullptr);
+}
+
+bool upload_sched(svgp_handle* h, const std::vector<Tile>& v, GemmCtx& g, int tab, bool may_split, int* slot) {
   std::vector<int> off;
-  std::vector<Tile> s = lpt_schedule(v, tc_num_sms(), off);
-  if (!upload_tiles(h, s, &g.tt[tab], &g.nt[tab])) return false;
+  std::vector<TcTile> s = plan_items(v, may_split, tc_num_sms(), slot, off);
+  if (!dalloc(h, &g.tct[tab], sizeof(TcTile) * std::max<size_t>(s.size(), 1))) return false;
+  cudaMemcpy(g.tct[tab], s.data(), sizeof(TcTile) * s.size(), cudaMemcpyHostToDevice);
+  g.nt[tab] = (int)s.size();
   if (!dalloc(h, &g.toff[tab], sizeof(int) * off.size())) return false;
   cudaMemcpy(g.toff[tab], off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice);
   g.ncta[tab] = (int)off.size() - 1;
@@ -153,10 +208,18 @@ bool build_ctx(svgp_handle* h, GemmCtx& g, int BM, int BN, bool sched) {
       make_tiles(Mp, BM, BN, REG_LOWER, K_N0_M1),  make_tiles(Mp, BM, BN, REG_FULL, K_0_M1),
       make_tiles(Mp, BM, BN, REG_LOWER, K_0_N1),   make_tiles(Mp, BM, BN, REG_UPPER, K_ALL),
       make_tiles(Mp, BM, BN, REG_FULL, K_ALL)};
+  // the triangular tables (symmetric and lower outputs) may split long tiles
+  const bool tri[TT_COUNT] = {false, true, true, false, true, false, false};
+  int slot = 0;
   for (int t = 0; t < TT_COUNT; ++t) {
-    const bool ok = (sched && t != TT_PSI) ? upload_sched(h, tabs[t], g, t) : upload_tiles(h, tabs[t], &g.tt[t], &g.nt[t]);
+    const bool ok = (sched && t != TT_PSI) ? upload_sched(h, tabs[t], g, t, tri[t], &slot)
+                                           : upload_tiles(h, tabs[t], &g.tt[t], &g.nt[t]);
     if (!ok) return false;
   }
+  g.nslot = slot;
+  if (sched && slot > 0)
+    return dalloc(h, &g.kpart, sizeof(float) * 128 * 128 * (size_t)slot) &&
+           dalloc(h, &g.kflag, sizeof(int) * 2 * (size_t)slot);
   return true;
 }
 
@@ -420,7 +483,7 @@ void ng_loop(svgp_handle* h, const svgp_params* p, float* L_inout, const float* 
   for (int t = 0; t < max_iters; ++t) {
     run_vt(h, h->Kuu_lo, p->s, h->done);         // Vt = L^T K~ (skipped once converged)
     run_sym<0>(h, h->done);                      // A, Phi^T, ||A - I||^2
-    k_ng_check(h->red, h->M, eps, h->done, iters, resid, st);   // Eq. (8) stopping rule
+    k_ng_check(h->red, h->M, eps, h->done, iters, resid, h->errword, st);   // Eq. (8) stopping rule
     run_lupd(h, L_inout, gamma_dev + t);         // L <- L - gamma L Phi  (Prop. 1)
     if (t + 1 < max_iters) prep_L(h, L_inout, nullptr);
   }
@@ -703,7 +766,7 @@ svgp_status svgp_ng_update_T_gap(svgp_handle* h, const svgp_params* p, const svg
     if (t == max_iters) break;
     run_vt(h, h->Kuu_lo, p->s, h->done);
     run_sym<0>(h, h->done);
-    k_ng_check(h->red, h->M, 0.0, h->done, iters, h->resid_tmp, st);
+    k_ng_check(h->red, h->M, 0.0, h->done, iters, h->resid_tmp, h->errword, st);
     run_lupd(h, L_inout, gamma_dev + t);
     prep_L(h, L_inout, nullptr);
   }
@@ -759,13 +822,24 @@ svgp_status svgp_adam_step(svgp_handle* h, float* raw, float* constrained, const
   return check_launch(h, "svgp_adam_step");
 }
 
+svgp_status svgp_check_wait_timeout(svgp_handle* h) {
+  if (!h) return SVGP_ERR_INVALID_ARG;
+  if (!tc_available()) return fail(h, SVGP_ERR_UNSUPPORTED, "check_wait_timeout: no tensor-core device");
+  tc_wait_probe(h->errword, h->st);
+  return check_launch(h, "svgp_check_wait_timeout");
+}
+
 svgp_status svgp_sync_status(svgp_handle* h) {
   if (!h) return SVGP_ERR_INVALID_ARG;
   if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(h, SVGP_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
   int e = 0;
   if (cudaMemcpy(&e, h->errword, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SVGP_ERR_CUDA;
   cudaMemset(h->errword, 0, sizeof(int));
-  if (e & ERRBIT_TIMEOUT) return fail(h, SVGP_ERR_TIMEOUT, "a device pipeline wait timed out");
+  if (e & ERRBIT_TIMEOUT) {
+    // a launch that gave up may have left split-K counts behind: clear them
+    if (h->gt.kflag) cudaMemset(h->gt.kflag, 0, sizeof(int) * 2 * (size_t)h->gt.nslot);
+    return fail(h, SVGP_ERR_TIMEOUT, "a device pipeline wait timed out");
+  }
   if (e & ERRBIT_NONFINITE) return fail(h, SVGP_ERR_NONFINITE, "non-finite bound");
   return SVGP_OK;
 }

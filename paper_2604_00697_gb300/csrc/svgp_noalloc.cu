@@ -30,8 +30,9 @@ constexpr size_t OFF_VEC = OFF_P + MAT;                          // v (MAXM floa
 constexpr size_t OFF_COL = al(OFF_VEC + sizeof(float) * NA_MAXM);
 constexpr size_t OFF_RED = al(OFF_COL + sizeof(float) * NA_MAXN);
 constexpr size_t OFF_ERR = al(OFF_RED + sizeof(double) * RED_COUNT);
-constexpr size_t OFF_TAB = al(OFF_ERR + sizeof(int));
-constexpr size_t NA_BYTES = al(OFF_TAB + sizeof(Tile) * TT_COUNT * NA_TAB);
+constexpr size_t OFF_TAB = al(OFF_ERR + sizeof(int));        // tables for Mp = 128, then Mp = 256
+constexpr size_t TAB_SET = sizeof(Tile) * TT_COUNT * NA_TAB;
+constexpr size_t NA_BYTES = al(OFF_TAB + 2 * TAB_SET);
 
 // The scratch itself (about 2.7 MB; every GPU that loads the library holds
 // it until the process exits).
@@ -39,10 +40,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
 // Tile tables for Mp = 128 * nb (nb = 1 or 2), in the layout of
 // make_tiles(): VT full / K [m0, Mp); SYM_IN upper / K [n0, Mp);
-// LS full / K [0, m0 + 128); OUT lower / K [0, n0 + 128).
-__global__ void na_tables_kernel(Tile* tab, int nb) {
-  pdl_enter();
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// LS full / K [0, m0 + 128); OUT lower / K [0, n0 + 128).  Built on the host.
+void na_tables(Tile* tab, int nb) {
   const int Mp = 128 * nb;
   int c[TT_COUNT] = {0};
   for (int a = 0; a < nb; ++a)
@@ -57,7 +56,6 @@ __global__ void na_tables_kernel(Tile* tab, int nb) {
 
 struct NaDevice {
   unsigned char* base;   // device address of g_noalloc_scratch on this device
-  int nb_built;          // tile tables currently written for this Mp / 128 (0: none)
 };
 NaDevice g_na[64];
 
@@ -75,21 +73,25 @@ extern "C" svgp_status svgp_predict_noalloc(const svgp_params* p, int M, int D, 
   if (!nd.base) {
     // One-time set-up on this device (must not run inside a stream capture):
     // the host-side symbol is only a stand-in, the kernels need its device
-    // address; the FP32 kernels need their shared-memory limits raised.
+    // address; the tile tables of both padded sizes are copied in once, so no
+    // call depends on the work an earlier call enqueued; the FP32 kernels need
+    // their shared-memory limits raised.
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return SVGP_ERR_CUDA;
+    Tile tabs[2 * TT_COUNT * NA_TAB];
+    memset(tabs, 0, sizeof(tabs));
+    na_tables(tabs, 1);
+    na_tables(tabs + TT_COUNT * NA_TAB, 2);
+    if (cudaMemcpyToSymbol(g_noalloc_scratch, tabs, sizeof(tabs), OFF_TAB, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess)
+      return SVGP_ERR_CUDA;
     simt_init_attributes();
     nd.base = reinterpret_cast<unsigned char*>(ptr);
   }
   unsigned char* b = nd.base;
   const int Mp = (M + 127) / 128 * 128;
   const int nb = Mp / 128;
-  Tile* tab = reinterpret_cast<Tile*>(b + OFF_TAB);
-  if (nd.nb_built != nb) {
-    svgp_note_launch();
-    pdl_launch(na_tables_kernel, 1, 32, 0, st, tab, nb);
-    nd.nb_built = nb;
-  }
+  Tile* tab = reinterpret_cast<Tile*>(b + OFF_TAB + (nb - 1) * TAB_SET);
   GemmCtx g;
   memset(&g, 0, sizeof(g));
   g.Mp = Mp;

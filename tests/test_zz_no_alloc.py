@@ -25,17 +25,22 @@ def _noalloc(lib, params, M, D, Xd, Ns, mean, var, stream):
     return fn(ctypes.addressof(params), M, D, Xd.data_ptr(), Ns, mean.data_ptr(), var.data_ptr(), 1, stream)
 
 
-def test_predict_noalloc_matches_predict_twice():
+def test_predict_noalloc_matches_predict_call_after_call():
+    """Calls in a row on one device, alternating inducing-point counts whose
+    padded sizes differ (M <= 128 and 129..256), each checked against
+    svgp_predict on an FP32 handle and against the oracle's predictive
+    moments."""
+    from oracle import rsvgp as O
     from paper_2604_00697_gb300 import _lib
     from paper_2604_00697_gb300.model import RSVGP
 
     lib = _lib.load()
-    M, D, Ns = 150, 3, 300
-    p, _, _, _ = small_case(M, D, 4, 9, state="chol")
+    D, Ns = 3, 300
     stream = torch.cuda.current_stream().cuda_stream
-    m = RSVGP(M, D, Ns, prec="fp32")
-    m.set_state(p["Z"], p["ell"], p["sf2"], p["noise"], p["m"], p["s"], p["L"])
-    for call in range(2):
+    for call, M in enumerate((150, 100, 200, 100, 256)):
+        p, _, _, _ = small_case(M, D, 4, 9 + call, state="chol")
+        m = RSVGP(M, D, Ns, prec="fp32")
+        m.set_state(p["Z"], p["ell"], p["sf2"], p["noise"], p["m"], p["s"], p["L"])
         Xs = f32(np.random.default_rng(40 + call).normal(size=(Ns, D)))
         Xd = torch.tensor(Xs, dtype=torch.float32, device="cuda")
         ref_mean, ref_var = m.predict(Xd, include_noise=True)
@@ -44,9 +49,12 @@ def test_predict_noalloc_matches_predict_twice():
         st = _noalloc(lib, m.params, M, D, Xd, Ns, mean, var, stream)
         torch.cuda.synchronize()
         assert st == _lib.SVGP_OK
-        assert rel(mean.double().cpu().numpy(), ref_mean.double().cpu().numpy()) <= 1e-4
-        assert rel(var.double().cpu().numpy(), ref_var.double().cpu().numpy()) <= 1e-4
-    m.close()
+        gm, gv = mean.double().cpu().numpy(), var.double().cpu().numpy()
+        assert rel(gm, ref_mean.double().cpu().numpy()) <= 1e-4, (M, call)
+        assert rel(gv, ref_var.double().cpu().numpy()) <= 1e-4, (M, call)
+        om, ov = O.predict(p, Xs, include_noise=True)
+        assert rel(gm, om) <= 1e-4 and rel(gv, ov) <= 1e-4, (M, call, rel(gm, om), rel(gv, ov))
+        m.close()
 
 
 def test_predict_noalloc_rejects_sizes_beyond_its_limit():
