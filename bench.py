@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32-plain and single-BF16 comparison lines")
     ap.add_argument("--no-autograd", action="store_true", help="skip the steps/s through the autograd Function")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the cost model's split-K thresholds")
     ap.add_argument("--no-validate", action="store_true", help="skip the oracle bound and gradient check")
     ap.add_argument("--validate-single", action="store_true", help="also check the single-BF16 form")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
@@ -487,6 +488,8 @@ def run_ours(args):
     yd = [torch.tensor(b[1], dtype=torch.float32, device="cuda") for b in batches]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
 
+    tuned = {}
+
     def time_model(pr, steps, warmup, profile=False):
         m = new_model(pr)
         # bring L near chol(K~^-1) first (untimed): NG updates with gamma = 1
@@ -498,6 +501,10 @@ def run_ours(args):
         m.hyper[0] = 1e-3
         m.hyper[4] = 0.2
         torch.cuda.synchronize()
+        if pr != "fp32" and not args.no_autotune:
+            # measured split-K thresholds of the triangular products (eager,
+            # before any graph is captured; the state is restored)
+            tuned[pr] = m.autotune_split(Xd[0], yd[0], N)
         n0 = _lib.svgp_launch_count(m.h)
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
@@ -618,6 +625,10 @@ def run_ours(args):
         "wall_s_timed": wall, "gpu_launches": launches * args.steps, "launches_per_step": launches,
         "clocks": clocks, "device_status": ok_status,
     }
+    if prec in tuned:
+        line["autotune"] = {"split_kmin": {k: v["kmin"] for k, v in tuned[prec].items()},
+                            "measured_ms_per_step": {k: v["ms_per_step"] for k, v in tuned[prec].items()},
+                            "method": "each candidate timed over 4 eager training steps from one state"}
     # roofline of the dominant contraction kind (events inside the graph)
     if prof:
         line["roofline"] = roofline(prof, prec, M, B, args.workload)

@@ -311,6 +311,28 @@ svgp_status svgp_profile_enable(svgp_handle* h, int enable);
  * SVGP_PROF_NKINDS entries. */
 svgp_status svgp_profile_read(svgp_handle* h, float* ms, int* counts);
 
+/* Split-K schedule of the persistent tensor-core GEMM (tuning; not an
+ * operation of the paper).  The triangular products (kinds SVGP_PROF_SYM,
+ * SVGP_PROF_LUPD and SVGP_PROF_OUT) have output tiles whose K ranges differ
+ * by up to the whole matrix; a tile of at least kmin 64-deep k-blocks is
+ * computed as two K chunks on two CTAs, the first writing FP32 partial sums
+ * that the second adds before its epilogue.  svgp_create picks kmin from a
+ * cost model; svgp_set_split sets it per kind: kmin > 0 one of the values
+ * svgp_split_candidates lists, 0 no split, < 0 the cost model's choice.  The
+ * full products (SVGP_PROF_VT, SVGP_PROF_LS) accept only 0.  It synchronises
+ * the handle's streams and rewrites the schedule on the device: call it
+ * outside stream capture, and capture again every CUDA graph captured on
+ * this handle before the call (a graph keeps the grid size of the old
+ * schedule; replaying it afterwards gives wrong results).  Results under
+ * different thresholds agree up to the order of the FP32 sums.
+ * SVGP_ERR_UNSUPPORTED for SVGP_FP32
+ * handles.  svgp_get_split returns the kmin in force (-1: not applicable);
+ * svgp_split_candidates writes up to n candidates (0 first) to out and
+ * returns their count. */
+svgp_status svgp_set_split(svgp_handle* h, int kind, int kmin);
+int svgp_get_split(const svgp_handle* h, int kind);
+int svgp_split_candidates(const svgp_handle* h, int kind, int* out, int n);
+
 /* Number of kernel launches the library has issued in this process (all
  * handles; launches captured into a graph are counted once, at capture). */
 long long svgp_launch_count(const svgp_handle* h);

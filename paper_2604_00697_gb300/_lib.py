@@ -247,6 +247,33 @@ def svgp_launch_count(h=None):
     return int(lib.svgp_launch_count(h))
 
 
+EXPORTED += ["svgp_set_split", "svgp_get_split", "svgp_split_candidates"]
+
+
+def svgp_set_split(h, kind, kmin):
+    """Split-K threshold of a contraction kind (see svgp.h); kind: PROF_KINDS index."""
+    lib = load()
+    lib.svgp_set_split.argtypes = [c_void_p, c_int, c_int]
+    lib.svgp_set_split.restype = c_int
+    _check(h, lib.svgp_set_split(h, int(kind), int(kmin)))
+
+
+def svgp_get_split(h, kind):
+    lib = load()
+    lib.svgp_get_split.argtypes = [c_void_p, c_int]
+    lib.svgp_get_split.restype = c_int
+    return int(lib.svgp_get_split(h, int(kind)))
+
+
+def svgp_split_candidates(h, kind):
+    lib = load()
+    lib.svgp_split_candidates.argtypes = [c_void_p, c_int, POINTER(c_int), c_int]
+    lib.svgp_split_candidates.restype = c_int
+    buf = (c_int * 16)()
+    n = lib.svgp_split_candidates(h, int(kind), buf, 16)
+    return [int(buf[i]) for i in range(min(n, 16))]
+
+
 EXPORTED += ["svgp_check_wait_timeout"]
 
 

@@ -43,11 +43,18 @@ template <int NSPLIT, int NI>
 struct WGeo {
   static_assert(NI == 1 || (NI == 2 && NSPLIT == 1), "two row blocks only with BF16 operands");
   static constexpr int NS = NSPLIT == 3 ? 2 : 1;                         // hi (+lo) planes
-  static constexpr int STAGES = (NSPLIT == 3 || NI == 2) ? 2 : 3;
-  // stage: [z k-role coordinate tile CT][P tiles NI*NS*GT][generated Kuf^T tiles NS*GT]
+  // Two rings.  TMA ring, ST stages of [z k-role coordinate tile CT][P tiles
+  // NI*NS*GT]: a stage is refilled once the main MMA of its k-block is done,
+  // so the copies run ST - 1 k-blocks ahead.  Generated ring, SG stages of
+  // Kuf^T tiles NS*GT written by the transform warps: with two, the transform
+  // of k-block g + 1 overlaps the main MMA of k-block g (for split operands
+  // three TMA stages with one generated stage measured slower, 0.186 ->
+  // 0.205 ms at M = 2048, B = 4096, so both rings keep two stages there).
+  static constexpr int ST = (NSPLIT == 3 || NI == 2) ? 2 : 3;
+  static constexpr int SG = 2;
   static constexpr int OFF_P = CT;
-  static constexpr int OFF_G = CT + NI * NS * GT;
-  static constexpr int STAGE = OFF_G + NS * GT;
+  static constexpr int TSTAGE = CT + NI * NS * GT;
+  static constexpr int GSTAGE = NS * GT;
   // static tiles: z rows of the row blocks (row role), x rows of the n-block
   // in row role (generator) and in k role (epilogue exponent)
   static constexpr int OFF_ZR = 0, OFF_XR = NI * GT, OFF_XK = (NI + 1) * GT, STATIC = (NI + 2) * GT;
@@ -55,8 +62,8 @@ struct WGeo {
   // combination of the two column halves (128 x (2 DP + 1))
   static constexpr int EPI_FLOATS = 256 + 128 * 2 * DPMAX;
   static_assert(EPI_FLOATS >= 128 * (2 * DPMAX + 1), "combine buffer");
-  static constexpr int NBAR = 3 * STAGES + 8;
-  static constexpr int SMEM = 1024 + STATIC + STAGES * STAGE + 4 * EPI_FLOATS + 8 * NBAR + 64;
+  static constexpr int NBAR = 2 * ST + 2 * SG + 8;
+  static constexpr int SMEM = 1024 + STATIC + ST * TSTAGE + SG * GSTAGE + 4 * EPI_FLOATS + 8 * NBAR + 64;
   static_assert(SMEM <= 232448, "shared memory budget");
   static constexpr uint32_t TMEM_COLS = 512;
   // TMEM columns: W accumulators [0, 128 NI), generator exponents 2 x 64 after
@@ -87,16 +94,18 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
   unsigned char* sZR = base + G::OFF_ZR;
   unsigned char* sXR = base + G::OFF_XR;
   unsigned char* sXK = base + G::OFF_XK;
-  unsigned char* stg = base + G::STATIC;
-  float* ebuf = reinterpret_cast<float*>(stg + G::STAGES * G::STAGE);
+  unsigned char* stgT = base + G::STATIC;                         // TMA ring
+  unsigned char* stgG = stgT + G::ST * G::TSTAGE;                 // generated ring
+  float* ebuf = reinterpret_cast<float*>(stgG + G::SG * G::GSTAGE);
   uint64_t* bars = reinterpret_cast<uint64_t*>(ebuf + G::EPI_FLOATS);
   volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars + G::NBAR);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   volatile int* consumed = abort_flag + 1;
-  constexpr int S = G::STAGES;
+  constexpr int ST = G::ST, SG = G::SG;
   auto BAR = [&](int idx) { return smem_u32(&bars[idx]); };
-  const int B_ZR = 0, B_TILE = 1, B_LD = 2, B_EMPTY = 2 + S, B_GEN = 2 + 2 * S, B_SFULL = 2 + 3 * S,
-            B_SEMPTY = 4 + 3 * S, B_ACC = 6 + 3 * S, B_EDONE = 7 + 3 * S;
+  // LD / TEMPTY: TMA stage landed / free; GEN / GEMPTY: generated stage written / free
+  const int B_ZR = 0, B_TILE = 1, B_LD = 2, B_TEMPTY = 2 + ST, B_GEN = 2 + 2 * ST, B_GEMPTY = 2 + 2 * ST + SG,
+            B_SFULL = 2 + 2 * ST + 2 * SG, B_SEMPTY = B_SFULL + 2, B_ACC = B_SEMPTY + 2, B_EDONE = B_ACC + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * 128 * NI;
@@ -105,10 +114,13 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
   if (threadIdx.x == 0) {
     mbar_init(BAR(B_ZR), 1);
     mbar_init(BAR(B_TILE), 1);
-    for (int s = 0; s < S; ++s) {
+    for (int s = 0; s < ST; ++s) {
       mbar_init(BAR(B_LD + s), 1);
-      mbar_init(BAR(B_EMPTY + s), 1);
+      mbar_init(BAR(B_TEMPTY + s), 1);
+    }
+    for (int s = 0; s < SG; ++s) {
       mbar_init(BAR(B_GEN + s), NTW);
+      mbar_init(BAR(B_GEMPTY + s), 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(BAR(B_SFULL + b), 1);
@@ -143,9 +155,9 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
       tma_load_2d(smem_u32(sXR), &tmXR, 0, nb * 128, BAR(B_TILE));
       tma_load_2d(smem_u32(sXK), &tmXK, 0, nb * 128, BAR(B_TILE));
       for (int kb = 0; kb < nkb; ++kb, ++g) {
-        const int s = g % S;
-        if (!mbar_wait(BAR(B_EMPTY + s), ((g / S) & 1) ^ 1) || *abort_flag) { ok = false; break; }
-        unsigned char* st = stg + s * G::STAGE;
+        const int s = g % ST;
+        if (!mbar_wait(BAR(B_TEMPTY + s), ((g / ST) & 1) ^ 1) || *abort_flag) { ok = false; break; }
+        unsigned char* st = stgT + s * G::TSTAGE;
         const uint32_t fb = BAR(B_LD + s);
         mbar_expect_tx(fb, CT + NI * G::NS * GT);
         tma_load_2d(smem_u32(st), &tmZK, 0, kb * KB, fb);
@@ -161,7 +173,7 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
     mbar_wait(BAR(B_ZR), 0);
     if (lt > 0) mbar_wait(BAR(B_TILE), (lt - 1) & 1);
     if (*abort_flag) {
-      for (int q = *consumed; q < g; ++q) mbar_wait(BAR(B_LD + q % S), (q / S) & 1);
+      for (int q = *consumed; q < g; ++q) mbar_wait(BAR(B_LD + q % ST), (q / ST) & 1);
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
@@ -182,11 +194,11 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
       while (mn < nkb) {
         bool progressed = false;
         const int gd = g + d, gm = g + mn;
-        if (d < nkb && mbar_try(BAR(B_LD + gd % S), (gd / S) & 1) &&
+        if (d < nkb && mbar_try(BAR(B_LD + gd % ST), (gd / ST) & 1) &&
             mbar_try(BAR(B_SEMPTY + (gd & 1)), ((gd >> 1) & 1) ^ 1)) {
           fence_after();
           *consumed = gd + 1;
-          const uint64_t kd = sw128_desc(smem_u32(stg + (gd % S) * G::STAGE));
+          const uint64_t kd = sw128_desc(smem_u32(stgT + (gd % ST) * G::TSTAGE));
 #pragma unroll
           for (int kk = 0; kk < KB / 16; ++kk) {
             const uint64_t o = (uint64_t)(kk * 2);
@@ -200,11 +212,12 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
         // for that k-block's generated operand, which the transform warps
         // produce only after their epilogue of the previous n-block has read
         // the accumulator and the exponents T.
-        if (mn < d && mbar_try(BAR(B_GEN + gm % S), (gm / S) & 1)) {
+        if (mn < d && mbar_try(BAR(B_GEN + gm % SG), (gm / SG) & 1)) {
           fence_after();
-          unsigned char* st = stg + (gm % S) * G::STAGE;
-          const uint64_t bd = sw128_desc(smem_u32(st + G::OFF_G));
-          const uint64_t bdl = sw128_desc(smem_u32(st + G::OFF_G + GT));
+          unsigned char* st = stgT + (gm % ST) * G::TSTAGE;
+          unsigned char* gs = stgG + (gm % SG) * G::GSTAGE;
+          const uint64_t bd = sw128_desc(smem_u32(gs));
+          const uint64_t bdl = sw128_desc(smem_u32(gs + GT));
 #pragma unroll
           for (int ib = 0; ib < NI; ++ib) {
             const uint64_t ad = sw128_desc(smem_u32(st + G::OFF_P + ib * G::NS * GT));
@@ -219,7 +232,8 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
               }
             }
           }
-          mma_commit(BAR(B_EMPTY + gm % S));
+          mma_commit(BAR(B_TEMPTY + gm % ST));
+          mma_commit(BAR(B_GEMPTY + gm % SG));
           ++mn;
           progressed = true;
         }
@@ -278,7 +292,7 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
       const int n0 = nb * 128;
       for (int kb = 0; kb < nkb; ++kb, ++g) {
         if (*abort_flag) continue;
-        const int s = g % S, b = g & 1;
+        const int s = g % SG, b = g & 1;
         if (!mbar_wait(BAR(B_SFULL + b), (g >> 1) & 1)) { *abort_flag = 1; continue; }
         fence_after();
         float t[32];
@@ -286,10 +300,10 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
         fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(BAR(B_SEMPTY + b));
-        // the generated buffers of stage s are free once the main MMA of g - S finished
-        if (!mbar_wait(BAR(B_EMPTY + s), ((g / S) & 1) ^ 1)) { *abort_flag = 1; continue; }
-        unsigned char* st = stg + s * G::STAGE;
-        gen32<NSPLIT>(t, st + G::OFF_G, st + G::OFF_G + GT, row, kcol0);
+        // generated stage s is free once the main MMA of k-block g - SG finished
+        if (!mbar_wait(BAR(B_GEMPTY + s), ((g / SG) & 1) ^ 1)) { *abort_flag = 1; continue; }
+        unsigned char* gs = stgG + s * G::GSTAGE;
+        gen32<NSPLIT>(t, gs, gs + GT, row, kcol0);
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(BAR(B_GEN + s));

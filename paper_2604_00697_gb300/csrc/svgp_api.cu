@@ -68,6 +68,12 @@ struct svgp_handle {
   double *red, *acc_ell, *resid_tmp;
   int *errword, *done, *iters_tmp;
   GemmCtx gs, gt;   // SIMT and tensor-core tile tables
+  // tensor-core schedule state per table: tiles, split threshold in force,
+  // whether splitting is allowed, workspace slot range, item capacity
+  std::vector<Tile> tc_tiles[TT_COUNT];
+  int tc_kmin[TT_COUNT] = {0};
+  bool may_split[TT_COUNT] = {false};
+  int slot_base[TT_COUNT] = {0}, slot_cap[TT_COUNT] = {0}, item_cap[TT_COUNT] = {0};
   KufTC kt;         // split coordinates for the tensor-core Kuf generator
   bool tc_kuf;      // Psi and W run on the tensor-core Kuf-producer kernels
   std::vector<void*> allocs;
@@ -164,36 +170,59 @@ std::vector<TcTile> split_items(const std::vector<Tile>& v, int kmin, int* slot)
   return out;
 }
 
-// Items of a table for the tensor-core GEMM.  Tables whose tiles have uneven
-// K ranges and few long tiles (the triangular products) get the split
-// threshold with the smallest modelled makespan among a few candidates
-// (ties: fewer splits); the full products keep whole tiles.
-std::vector<TcTile> plan_items(const std::vector<Tile>& v, bool may_split, int nsm, int* slot,
-                               std::vector<int>& off) {
-  int best = 0;
-  long long best_ms = 0;
-  if (may_split) {
-    const int cand[] = {0, 32, 28, 24, 20, 16, 12};
-    for (int kmin : cand) {
-      int tmp = 0;
-      std::vector<int> o;
-      long long ms = 0;
-      lpt_schedule(split_items(v, kmin, &tmp), nsm, o, &ms);
-      if (kmin == 0 || ms < best_ms * 97 / 100) { best = kmin; best_ms = ms; }
-    }
+// Split thresholds a table may take: 0 (no split) or a fraction of its
+// longest tile's k-blocks (1, 7/8, 3/4, 5/8, 1/2, 3/8), at least 2.
+std::vector<int> split_candidates(const std::vector<Tile>& v) {
+  int maxnk = 0;
+  for (const Tile& t : v) maxnk = std::max(maxnk, (t.k1 - t.k0) / 64);
+  std::vector<int> c{0};
+  for (int q : {8, 7, 6, 5, 4, 3}) {
+    const int k = (maxnk * q + 7) / 8;
+    if (k >= 2 && std::find(c.begin(), c.end(), k) == c.end()) c.push_back(k);
   }
-  return lpt_schedule(split_items(v, best, slot), nsm, off, nullptr);
+  return c;
 }
 
-bool upload_sched(svgp_handle* h, const std::vector<Tile>& v, GemmCtx& g, int tab, bool may_split, int* slot) {
+// The candidate with the smallest modelled makespan (ties within 3 %: fewer splits).
+int model_kmin(const std::vector<Tile>& v, int nsm) {
+  int best = 0;
+  long long best_ms = 0;
+  for (int kmin : split_candidates(v)) {
+    int tmp = 0;
+    std::vector<int> o;
+    long long ms = 0;
+    lpt_schedule(split_items(v, kmin, &tmp), nsm, o, &ms);
+    if (kmin == 0 || ms < best_ms * 97 / 100) { best = kmin; best_ms = ms; }
+  }
+  return best;
+}
+
+// Tiles that some candidate threshold would split (the slots a table may need).
+int split_capacity(const std::vector<Tile>& v) {
+  const std::vector<int> c = split_candidates(v);
+  int kmin = 0;
+  for (int k : c)
+    if (k > 0 && (kmin == 0 || k < kmin)) kmin = k;
+  int n = 0;
+  for (const Tile& t : v) n += (kmin > 0 && (t.k1 - t.k0) / 64 >= kmin) ? 1 : 0;
+  return n;
+}
+
+// Tensor-core schedule of table `tab` with split threshold kmin (0: whole
+// tiles), into the table's preallocated item and offset buffers; slots from
+// the table's own range.  Host-synchronous (configuration time only).
+bool schedule_table(svgp_handle* h, int tab, int kmin) {
+  GemmCtx& g = h->gt;
+  int slot = h->slot_base[tab];
   std::vector<int> off;
-  std::vector<TcTile> s = plan_items(v, may_split, tc_num_sms(), slot, off);
-  if (!dalloc(h, &g.tct[tab], sizeof(TcTile) * std::max<size_t>(s.size(), 1))) return false;
-  cudaMemcpy(g.tct[tab], s.data(), sizeof(TcTile) * s.size(), cudaMemcpyHostToDevice);
+  std::vector<TcTile> s = lpt_schedule(split_items(h->tc_tiles[tab], kmin, &slot), tc_num_sms(), off, nullptr);
+  if (slot - h->slot_base[tab] > h->slot_cap[tab] || s.size() > (size_t)h->item_cap[tab]) return false;
+  if (cudaMemcpy(g.tct[tab], s.data(), sizeof(TcTile) * s.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(g.toff[tab], off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return false;
   g.nt[tab] = (int)s.size();
-  if (!dalloc(h, &g.toff[tab], sizeof(int) * off.size())) return false;
-  cudaMemcpy(g.toff[tab], off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice);
   g.ncta[tab] = (int)off.size() - 1;
+  h->tc_kmin[tab] = kmin;
   return true;
 }
 
@@ -208,18 +237,39 @@ bool build_ctx(svgp_handle* h, GemmCtx& g, int BM, int BN, bool sched) {
       make_tiles(Mp, BM, BN, REG_LOWER, K_N0_M1),  make_tiles(Mp, BM, BN, REG_FULL, K_0_M1),
       make_tiles(Mp, BM, BN, REG_LOWER, K_0_N1),   make_tiles(Mp, BM, BN, REG_UPPER, K_ALL),
       make_tiles(Mp, BM, BN, REG_FULL, K_ALL)};
-  // the triangular tables (symmetric and lower outputs) may split long tiles
-  const bool tri[TT_COUNT] = {false, true, true, false, true, false, false};
+  if (!sched) {
+    for (int t = 0; t < TT_COUNT; ++t)
+      if (!upload_tiles(h, tabs[t], &g.tt[t], &g.nt[t])) return false;
+    return true;
+  }
+  // tensor-core schedules: the triangular tables (symmetric and lower
+  // outputs) may split long tiles, with the threshold of the cost model
+  // until svgp_set_split chooses another
   int slot = 0;
   for (int t = 0; t < TT_COUNT; ++t) {
-    const bool ok = (sched && t != TT_PSI) ? upload_sched(h, tabs[t], g, t, tri[t], &slot)
-                                           : upload_tiles(h, tabs[t], &g.tt[t], &g.nt[t]);
-    if (!ok) return false;
+    if (t == TT_PSI) {
+      if (!upload_tiles(h, tabs[t], &g.tt[t], &g.nt[t])) return false;
+      continue;
+    }
+    h->tc_tiles[t] = tabs[t];
+    h->may_split[t] = t == TT_SYM_IN || t == TT_LUPD || t == TT_OUT;
+    h->slot_base[t] = slot;
+    h->slot_cap[t] = h->may_split[t] ? split_capacity(tabs[t]) : 0;
+    h->item_cap[t] = (int)tabs[t].size() + h->slot_cap[t];
+    slot += h->slot_cap[t];
+    if (!dalloc(h, &g.tct[t], sizeof(TcTile) * std::max(h->item_cap[t], 1)) ||
+        !dalloc(h, &g.toff[t], sizeof(int) * (size_t)(tc_num_sms() + 1)))
+      return false;
   }
   g.nslot = slot;
-  if (sched && slot > 0)
-    return dalloc(h, &g.kpart, sizeof(float) * 128 * 128 * (size_t)slot) &&
-           dalloc(h, &g.kflag, sizeof(int) * 2 * (size_t)slot);
+  if (slot > 0 && !(dalloc(h, &g.kpart, sizeof(float) * 128 * 128 * (size_t)slot) &&
+                    dalloc(h, &g.kflag, sizeof(int) * 2 * (size_t)slot)))
+    return false;
+  for (int t = 0; t < TT_COUNT; ++t) {
+    if (t == TT_PSI) continue;
+    const int kmin = h->may_split[t] ? model_kmin(tabs[t], tc_num_sms()) : 0;
+    if (!schedule_table(h, t, kmin)) return false;
+  }
   return true;
 }
 
@@ -228,6 +278,15 @@ bool valid_params(const svgp_handle* h, const svgp_params* p) {
 }
 
 // Brackets one launch with timing events while profiling is enabled.
+// Inside a stream capture the records are external (event-record nodes of
+// the graph, re-recorded at every replay); outside, plain records.
+void prof_record(cudaEvent_t e, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+  else cudaEventRecord(e, st);
+}
+
 struct ProfScope {
   svgp_handle* h; int idx;
   ProfScope(svgp_handle* hh, int kind) : h(hh), idx(-1) {
@@ -236,12 +295,10 @@ struct ProfScope {
     if (2 * n + 1 >= (int)h->ev.size()) return;
     idx = n;
     h->rec_kind.push_back(kind);
-    // External record: inside a stream capture this becomes an event-record
-    // node of the graph, so replays re-record it.
-    cudaEventRecordWithFlags(h->ev[2 * n], h->st, cudaEventRecordExternal);
+    prof_record(h->ev[2 * n], h->st);
   }
   ~ProfScope() {
-    if (idx >= 0) cudaEventRecordWithFlags(h->ev[2 * idx + 1], h->st, cudaEventRecordExternal);
+    if (idx >= 0) prof_record(h->ev[2 * idx + 1], h->st);
   }
 };
 
@@ -820,6 +877,51 @@ svgp_status svgp_adam_step(svgp_handle* h, float* raw, float* constrained, const
     return fail(h, SVGP_ERR_INVALID_ARG, "adam: null pointer");
   k_adam(raw, constrained, grad, m1, m2, step_dev, hyper_dev, zbeta1_dev, h->M, h->D, h->st);
   return check_launch(h, "svgp_adam_step");
+}
+
+namespace {
+// Tile table of a contraction kind (SVGP_PROF_*), or -1.
+int kind_table(int kind) {
+  switch (kind) {
+    case SVGP_PROF_VT: return TT_VT;
+    case SVGP_PROF_SYM: return TT_SYM_IN;
+    case SVGP_PROF_LUPD: return TT_LUPD;
+    case SVGP_PROF_LS: return TT_LS;
+    case SVGP_PROF_OUT: return TT_OUT;
+    default: return -1;
+  }
+}
+}  // namespace
+
+int svgp_split_candidates(const svgp_handle* h, int kind, int* out, int n) {
+  const int t = kind_table(kind);
+  if (!h || t < 0 || h->mode == MODE_F32) return 0;
+  std::vector<int> c = h->may_split[t] ? split_candidates(h->tc_tiles[t]) : std::vector<int>{0};
+  for (int i = 0; i < (int)c.size() && i < n && out; ++i) out[i] = c[i];
+  return (int)c.size();
+}
+
+int svgp_get_split(const svgp_handle* h, int kind) {
+  const int t = kind_table(kind);
+  if (!h || t < 0 || h->mode == MODE_F32) return -1;
+  return h->tc_kmin[t];
+}
+
+svgp_status svgp_set_split(svgp_handle* h, int kind, int kmin) {
+  if (!h) return SVGP_ERR_INVALID_ARG;
+  const int t = kind_table(kind);
+  if (t < 0) return fail(h, SVGP_ERR_INVALID_ARG, "set_split: not a tensor-core contraction kind");
+  if (h->mode == MODE_F32) return fail(h, SVGP_ERR_UNSUPPORTED, "set_split: FP32 handles have no split schedule");
+  if (kmin < 0) kmin = h->may_split[t] ? model_kmin(h->tc_tiles[t], tc_num_sms()) : 0;
+  if (kmin > 0 && !h->may_split[t]) return fail(h, SVGP_ERR_INVALID_ARG, "set_split: this kind keeps whole tiles");
+  // the stream must be idle: an in-flight launch may read the tables
+  if (cudaStreamSynchronize(h->st) != cudaSuccess || cudaStreamSynchronize(h->st_aux) != cudaSuccess)
+    return fail(h, SVGP_ERR_CUDA, "set_split: stream synchronisation failed");
+  if (!schedule_table(h, t, kmin)) {
+    schedule_table(h, t, h->tc_kmin[t]);
+    return fail(h, SVGP_ERR_INVALID_ARG, "set_split: threshold below the smallest candidate");
+  }
+  return SVGP_OK;
 }
 
 svgp_status svgp_check_wait_timeout(svgp_handle* h) {

@@ -194,6 +194,52 @@ class RSVGP:
     def sync_status(self):
         return C.svgp_sync_status(self.h)
 
+    # -- schedule tuning --------------------------------------------------------
+    SPLIT_KINDS = {"sym": 1, "lupd": 2, "out": 4}   # SVGP_PROF_* of the triangular products
+
+    def autotune_split(self, X, y, N, reps=4):
+        """Measured choice of the split-K threshold of each triangular
+        contraction kind (svgp_set_split): for every candidate the library
+        lists, `reps` eager training steps from the same saved state with
+        timing events around each contraction; each kind keeps its fastest
+        candidate.  The state is restored afterwards; graphs captured on this
+        model before the call must be captured again.  Returns
+        {kind: {"kmin": chosen, "ms_per_step": {kmin: ms}}}."""
+        if self.prec == "fp32":
+            return {}
+        state = (self.cons, self.raw, self.L, self.m1, self.m2, self.step)
+        snap = [t.clone() for t in state]
+
+        def restore():
+            for dst, src in zip(state, snap):
+                dst.copy_(src)
+
+        cands = {k: C.svgp_split_candidates(self.h, i) for k, i in self.SPLIT_KINDS.items()}
+        ms = {k: {} for k in self.SPLIT_KINDS}
+        for c in range(max(len(v) for v in cands.values())):
+            pick = {k: v[min(c, len(v) - 1)] for k, v in cands.items()}
+            for k, i in self.SPLIT_KINDS.items():
+                C.svgp_set_split(self.h, i, pick[k])
+            restore()
+            self.train_step(X, y, N)
+            torch.cuda.synchronize()
+            C.svgp_profile_enable(self.h, True)
+            for _ in range(reps):
+                self.train_step(X, y, N)
+            torch.cuda.synchronize()
+            prof = C.svgp_profile_read(self.h)
+            C.svgp_profile_enable(self.h, False)
+            for k in self.SPLIT_KINDS:
+                ms[k][pick[k]] = prof[k][0] / reps
+        out = {}
+        for k, i in self.SPLIT_KINDS.items():
+            best = min(ms[k], key=ms[k].get)
+            C.svgp_set_split(self.h, i, best)
+            out[k] = {"kmin": best, "ms_per_step": {int(a): round(b, 4) for a, b in ms[k].items()}}
+        restore()
+        torch.cuda.synchronize()
+        return out
+
 
 def paper_init(M, D, Z0, sf2=1.0, noise=1.0, ell=1.0, alpha=1e-4, beta=1e-3):
     """Initial state of Appendix S5.3: m~ = 0, s~ = alpha 1, L = beta I."""
