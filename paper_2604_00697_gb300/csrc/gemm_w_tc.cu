@@ -22,7 +22,11 @@
 //     halves the exps per output;
 //   * one more exponent MMA per row block, T[i, n] = log2 Kuf_in for the
 //     epilogue (z rows of the block against the n-block), so Kuf_in is
-//     recomputed exactly as the generator computes it.
+//     recomputed exactly as the generator computes it.  Its operands (z rows
+//     in row role, x of the n-block in k role) are copied, once the n-block's
+//     main MMAs are done, into the generated ring, which is idle then; the
+//     shared memory they would hold through the mainloop goes to the TMA
+//     ring instead.
 // Warp roles (320 threads): 0 TMA producer, 1 TMEM allocator + MMA issuer,
 // 2..9 transform and then epilogue (warp w covers TMEM lanes 32 (w mod 4) ..
 // +31 and one half of the columns).  All waits are bounded; once a wait has
@@ -46,23 +50,28 @@ struct WGeo {
   // Two rings.  TMA ring, ST stages of [z k-role coordinate tile CT][P tiles
   // NI*NS*GT]: a stage is refilled once the main MMA of its k-block is done,
   // so the copies run ST - 1 k-blocks ahead.  Generated ring, SG stages of
-  // Kuf^T tiles NS*GT written by the transform warps: with two, the transform
-  // of k-block g + 1 overlaps the main MMA of k-block g (for split operands
-  // three TMA stages with one generated stage measured slower, 0.186 ->
-  // 0.205 ms at M = 2048, B = 4096, so both rings keep two stages there).
-  static constexpr int ST = (NSPLIT == 3 || NI == 2) ? 2 : 3;
-  static constexpr int SG = 2;
+  // Kuf^T tiles NS*GT written by the transform warps (the transform of k-block
+  // g + 1 overlaps the main MMA of k-block g).  Cycle stamps of the version
+  // with two TMA stages (split operands, M = 2048, B = 4096): one main MMA per
+  // 1630 cycles against 768 of MMA work, paced by the copies (a copy waited
+  // for the main MMA two k-blocks back, then 1400 cycles to the exponent
+  // MMA); one generated stage with three TMA stages measured slower.
+  static constexpr int ST = NSPLIT == 3 ? 3 : (NI == 2 ? 3 : 4);
+  static constexpr int SG = (NSPLIT == 1 && NI == 2) ? 3 : 2;
   static constexpr int OFF_P = CT;
   static constexpr int TSTAGE = CT + NI * NS * GT;
   static constexpr int GSTAGE = NS * GT;
-  // static tiles: z rows of the row blocks (row role), x rows of the n-block
-  // in row role (generator) and in k role (epilogue exponent)
-  static constexpr int OFF_ZR = 0, OFF_XR = NI * GT, OFF_XK = (NI + 1) * GT, STATIC = (NI + 2) * GT;
+  // static tile: x rows of the n-block in row role (generator); the epilogue
+  // exponent's operands -- z rows of the row blocks in row role, then x of the
+  // n-block in k role -- take the start of the generated ring after the
+  // mainloop
+  static constexpr int OFF_XR = 0, STATIC = GT;
+  static_assert(SG * NS * GT >= (NI + 1) * GT, "epilogue exponent operands fit the generated ring");
   // epilogue floats: colbuf[128], gq[128], xq[128][2 DP]; reused for the final
   // combination of the two column halves (128 x (2 DP + 1))
   static constexpr int EPI_FLOATS = 256 + 128 * 2 * DPMAX;
   static_assert(EPI_FLOATS >= 128 * (2 * DPMAX + 1), "combine buffer");
-  static constexpr int NBAR = 2 * ST + 2 * SG + 8;
+  static constexpr int NBAR = 2 * ST + 2 * SG + 9;
   static constexpr int SMEM = 1024 + STATIC + ST * TSTAGE + SG * GSTAGE + 4 * EPI_FLOATS + 8 * NBAR + 64;
   static_assert(SMEM <= 232448, "shared memory budget");
   static constexpr uint32_t TMEM_COLS = 512;
@@ -91,9 +100,7 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
   using G = WGeo<NSPLIT, NI>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sZR = base + G::OFF_ZR;
   unsigned char* sXR = base + G::OFF_XR;
-  unsigned char* sXK = base + G::OFF_XK;
   unsigned char* stgT = base + G::STATIC;                         // TMA ring
   unsigned char* stgG = stgT + G::ST * G::TSTAGE;                 // generated ring
   float* ebuf = reinterpret_cast<float*>(stgG + G::SG * G::GSTAGE);
@@ -103,17 +110,22 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
   volatile int* consumed = abort_flag + 1;
   constexpr int ST = G::ST, SG = G::SG;
   auto BAR = [&](int idx) { return smem_u32(&bars[idx]); };
-  // LD / TEMPTY: TMA stage landed / free; GEN / GEMPTY: generated stage written / free
-  const int B_ZR = 0, B_TILE = 1, B_LD = 2, B_TEMPTY = 2 + ST, B_GEN = 2 + 2 * ST, B_GEMPTY = 2 + 2 * ST + SG,
-            B_SFULL = 2 + 2 * ST + 2 * SG, B_SEMPTY = B_SFULL + 2, B_ACC = B_SEMPTY + 2, B_EDONE = B_ACC + 1;
+  // LD / TEMPTY: TMA stage landed / free; GEN / GEMPTY: generated stage written / free;
+  // MDONE: the n-block's main MMAs completed; ZX: the epilogue exponent's operands landed
+  const int B_ZX = 0, B_TILE = 1, B_LD = 2, B_TEMPTY = 2 + ST, B_GEN = 2 + 2 * ST, B_GEMPTY = 2 + 2 * ST + SG,
+            B_SFULL = 2 + 2 * ST + 2 * SG, B_SEMPTY = B_SFULL + 2, B_ACC = B_SEMPTY + 2, B_EDONE = B_ACC + 1,
+            B_MDONE = B_EDONE + 1;
+  unsigned char* sZR = stgG;                    // after the mainloop of an n-block
+  unsigned char* sXK = stgG + NI * GT;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * 128 * NI;
   const int nkb = wa.nkb;
 
   if (threadIdx.x == 0) {
-    mbar_init(BAR(B_ZR), 1);
+    mbar_init(BAR(B_ZX), 1);
     mbar_init(BAR(B_TILE), 1);
+    mbar_init(BAR(B_MDONE), 1);
     for (int s = 0; s < ST; ++s) {
       mbar_init(BAR(B_LD + s), 1);
       mbar_init(BAR(B_TEMPTY + s), 1);
@@ -143,17 +155,15 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
-    mbar_expect_tx(BAR(B_ZR), NI * GT);
-    for (int ib = 0; ib < NI; ++ib) tma_load_2d(smem_u32(sZR + ib * GT), &tmZR, 0, m0 + 128 * ib, BAR(B_ZR));
-    int g = 0, lt = 0;
+    int g = 0, lt = 0, nzx = 0;
     bool ok = true;
     for (int nb = blockIdx.x; nb < wa.nblk && ok; nb += gridDim.x, ++lt) {
-      // the previous n-block's MMAs (readers of sXR / sXK) have completed
+      // the previous n-block's MMAs (readers of sXR and of the epilogue
+      // exponent's operands) have completed
       if (lt > 0 && !mbar_wait(BAR(B_ACC), (lt - 1) & 1)) { ok = false; break; }
       if (*abort_flag) { ok = false; break; }
-      mbar_expect_tx(BAR(B_TILE), 2 * GT);
+      mbar_expect_tx(BAR(B_TILE), GT);
       tma_load_2d(smem_u32(sXR), &tmXR, 0, nb * 128, BAR(B_TILE));
-      tma_load_2d(smem_u32(sXK), &tmXK, 0, nb * 128, BAR(B_TILE));
       for (int kb = 0; kb < nkb; ++kb, ++g) {
         const int s = g % ST;
         if (!mbar_wait(BAR(B_TEMPTY + s), ((g / ST) & 1) ^ 1) || *abort_flag) { ok = false; break; }
@@ -167,10 +177,18 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
           if (NSPLIT == 3) tma_load_2d(smem_u32(pt + GT), &tmPl, kb * KB, m0 + 128 * ib, fb);
         }
       }
+      if (!ok) break;
+      // the epilogue exponent's operands into the generated ring, once the
+      // n-block's main MMAs (its last readers) are done
+      if (!mbar_wait(BAR(B_MDONE), lt & 1) || *abort_flag) { ok = false; break; }
+      mbar_expect_tx(BAR(B_ZX), (NI + 1) * GT);
+      for (int ib = 0; ib < NI; ++ib) tma_load_2d(smem_u32(sZR + ib * GT), &tmZR, 0, m0 + 128 * ib, BAR(B_ZX));
+      tma_load_2d(smem_u32(sXK), &tmXK, 0, nb * 128, BAR(B_ZX));
+      ++nzx;
     }
     if (!ok) *abort_flag = 1;
     // every copy this thread issued lands before the CTA exits (bounded waits)
-    mbar_wait(BAR(B_ZR), 0);
+    if (nzx > 0) mbar_wait(BAR(B_ZX), (nzx - 1) & 1);
     if (lt > 0) mbar_wait(BAR(B_TILE), (lt - 1) & 1);
     if (*abort_flag) {
       for (int q = *consumed; q < g; ++q) mbar_wait(BAR(B_LD + q % ST), (q / ST) & 1);
@@ -181,7 +199,7 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
     // as soon as its coordinates have landed and its TMEM buffer is free, ahead
     // of the main MMA of earlier k-blocks (which waits for their generated
     // tiles); then the epilogue exponents T.
-    bool ok = mbar_wait(BAR(B_ZR), 0);
+    bool ok = true;
     int g = 0, lt = 0;
     for (int nb = blockIdx.x; nb < wa.nblk && ok; nb += gridDim.x, ++lt) {
       if (!mbar_wait(BAR(B_TILE), lt & 1)) { ok = false; break; }
@@ -242,6 +260,9 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
       }
       g += nkb;
       if (!ok) break;
+      mma_commit(BAR(B_MDONE));                  // arrives when this n-block's main MMAs are done
+      if (!mbar_wait(BAR(B_ZX), lt & 1)) { ok = false; break; }
+      fence_after();
       // epilogue exponents T[i, n] = log2 Kuf_in of each row block
       const uint64_t xd = sw128_desc(smem_u32(sXK));
 #pragma unroll
