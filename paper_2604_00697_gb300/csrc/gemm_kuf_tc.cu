@@ -136,8 +136,8 @@ psi_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // z, row role
     long long idle_since = clock64();
     while (ok && mn < nkb) {
       bool progressed = false;
-      if (d < nkb && mbar_try(BAR(B_LD + d % S), (d / S) & 1) &&
-          mbar_try(BAR(B_SEMPTY + (d & 1)), ((d >> 1) & 1) ^ 1)) {
+      if (d < nkb && mbar_test(BAR(B_LD + d % S), (d / S) & 1) &&
+          mbar_test(BAR(B_SEMPTY + (d & 1)), ((d >> 1) & 1) ^ 1)) {
         fence_after();
         *consumed = d + 1;
         const int b = d & 1;
@@ -152,7 +152,7 @@ psi_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // z, row role
         ++d;
         progressed = true;
       }
-      if (mn < d && mbar_try(BAR(B_GEN + mn % S), (mn / S) & 1)) {
+      if (mn < d && mbar_test(BAR(B_GEN + mn % S), (mn / S) & 1)) {
         fence_after();
         unsigned char* st = stg + (mn % S) * G::STAGE;
         const uint64_t ad = sw128_desc(smem_u32(st + G::OFF_GA));

@@ -5,7 +5,9 @@
 //     W_in) (= G_Kuf o Kuf; h_n = -1/(2 noise) for the Gaussian likelihood,
 //     per point for probit), per row i the sums
 //       S0 = sum_n A_in,  S1_d = sum_n A_in x~_nd,  S2_d = sum_n A_in x~_nd^2
-//     (FP32, x~ and x~^2 staged in shared memory), reported in the
+//     (FP32 in registers; each x~ row staged in shared memory serves a group
+//     of four lanes, which exchange their rows' A values by shuffles and
+//     split the dimensions among them), reported in the
 //     difference form  sum_n A_in e_d = S1_d - z~_id S0  and
 //     sum_n A_in e_d^2 = S2_d - 2 z~_id S1_d + z~_id^2 S0  (e_d = x~_nd - z~_id);
 //   variance mode (colsum != null): colsum[n] += sum_i Kuf_in W_in.
@@ -67,10 +69,10 @@ struct WGeo {
   // mainloop
   static constexpr int OFF_XR = 0, STATIC = GT;
   static_assert(SG * NS * GT >= (NI + 1) * GT, "epilogue exponent operands fit the generated ring");
-  // epilogue floats: colbuf[128], gq[128], xq[128][2 DP]; reused for the final
-  // combination of the two column halves (128 x (2 DP + 1))
-  static constexpr int EPI_FLOATS = 256 + 128 * 2 * DPMAX;
-  static_assert(EPI_FLOATS >= 128 * (2 * DPMAX + 1), "combine buffer");
+  // epilogue floats: colbuf[128], gq[128], xq[128][XW <= DPMAX]; from the
+  // start, the final combination of the two column halves (128 x (2 DP + 1))
+  static constexpr int EPI_FLOATS = 128 * (2 * DPMAX + 1);
+  static_assert(EPI_FLOATS >= 256 + 128 * DPMAX, "x~ staging");
   static constexpr int NBAR = 2 * ST + 2 * SG + 9;
   static constexpr int SMEM = 1024 + STATIC + ST * TSTAGE + SG * GSTAGE + 4 * EPI_FLOATS + 8 * NBAR + 64;
   static_assert(SMEM <= 232448, "shared memory budget");
@@ -212,8 +214,8 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
       while (mn < nkb) {
         bool progressed = false;
         const int gd = g + d, gm = g + mn;
-        if (d < nkb && mbar_try(BAR(B_LD + gd % ST), (gd / ST) & 1) &&
-            mbar_try(BAR(B_SEMPTY + (gd & 1)), ((gd >> 1) & 1) ^ 1)) {
+        if (d < nkb && mbar_test(BAR(B_LD + gd % ST), (gd / ST) & 1) &&
+            mbar_test(BAR(B_SEMPTY + (gd & 1)), ((gd >> 1) & 1) ^ 1)) {
           fence_after();
           *consumed = gd + 1;
           const uint64_t kd = sw128_desc(smem_u32(stgT + (gd % ST) * G::TSTAGE));
@@ -230,7 +232,7 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
         // for that k-block's generated operand, which the transform warps
         // produce only after their epilogue of the previous n-block has read
         // the accumulator and the exponents T.
-        if (mn < d && mbar_try(BAR(B_GEN + gm % SG), (gm / SG) & 1)) {
+        if (mn < d && mbar_test(BAR(B_GEN + gm % SG), (gm / SG) & 1)) {
           fence_after();
           unsigned char* st = stgT + (gm % ST) * G::TSTAGE;
           unsigned char* gs = stgG + (gm % SG) * G::GSTAGE;
@@ -288,7 +290,12 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
     const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
     const int D = we.gen.D, Dp = (D + 3) & ~3, B = we.gen.B;
     const bool grad = wa.rowpart != nullptr;
-    constexpr int XW = 2 * DP;
+    // Row sums in groups of four lanes: lane r (= lane mod 4) of a group
+    // accumulates S1, S2 of the group's four rows for its DQ dimensions
+    // d = r DQ + j, taking the other rows' A values by shuffles; each x~ row is
+    // staged as four lane slots of DQP (>= DQ, even) floats, XW per point.
+    constexpr int DQ = DP / 4, DQP = (DQ + 1) & ~1, XW = 4 * DQP;
+    const int r4 = lane & 3;
     float* colbuf = ebuf;
     float* gq = ebuf + 128;
     float* xq = ebuf + 256;
@@ -299,14 +306,17 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
       cv[ib] = (grad && i < we.gen.M) ? we.c * __ldg(we.v + i) : 0.f;
     }
     if (grad && !we.hn) cn = we.c / *we.noise;          // Gaussian: -2 c h_n = c / noise
-    // row sums as packed FP32 pairs: S1p[ib][j] = (S1_2j, S1_2j+1), likewise S2p
+    // S0 of the thread's own row; S1p[ib][k][j] = (S1, S1) of row 4 (lane / 4)
+    // + (r4 ^ k) at dimensions r4 DQ + 2j, 2j + 1 (packed FP32 pairs), likewise S2p
     float S0[NI];
-    f32x2 S1p[NI][DP / 2], S2p[NI][DP / 2];
+    f32x2 S1p[NI][4][DQP / 2], S2p[NI][4][DQP / 2];
 #pragma unroll
     for (int ib = 0; ib < NI; ++ib) {
       S0[ib] = 0.f;
 #pragma unroll
-      for (int j = 0; j < DP / 2; ++j) { S1p[ib][j] = 0ull; S2p[ib][j] = 0ull; }
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < DQP / 2; ++j) { S1p[ib][k][j] = 0ull; S2p[ib][k][j] = 0ull; }
     }
     int g = 0, lt = 0;
     for (int nb = blockIdx.x; nb < wa.nblk; nb += gridDim.x, ++lt) {
@@ -329,80 +339,108 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
         __syncwarp();
         if (lane == 0) mbar_arrive(BAR(B_GEN + s));
       }
-      // epilogue of this n-block
+      // epilogue of this n-block; its global inputs (x~ rows, g_n, h_n) are
+      // fetched before the wait for the accumulators
+      constexpr int PER = 128 * XW / 256;
+      float xv[PER];
+      float gv = 0.f, hv = 0.f;
+      if (grad) {
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+          const int e = tid + 256 * u, n = e / XW, sl = e - n * XW, j = sl % DQP, d = (sl / DQP) * DQ + j;
+          xv[u] = (n0 + n < B && j < DQ && d < D) ? __ldg(we.gen.Xs + (size_t)(n0 + n) * Dp + d) : 0.f;
+        }
+        if (tid < 128 && n0 + tid < B) {
+          gv = __ldg(we.g + n0 + tid);
+          hv = we.hn ? -2.0f * we.c * __ldg(we.hn + n0 + tid) : cn;
+        }
+      }
       bool ok = !*abort_flag;
       if (ok && !mbar_wait(BAR(B_ACC), lt & 1)) { *abort_flag = 1; ok = false; }
       fence_after();
       if (ok) {
         if (grad) {
-          constexpr int PER = 128 * DP / 256;
-          float xv[PER];
 #pragma unroll
-          for (int u = 0; u < PER; ++u) {
-            const int e = tid + 256 * u, n = e / DP, d = e - n * DP;
-            xv[u] = (n0 + n < B && d < D) ? __ldg(we.gen.Xs + (size_t)(n0 + n) * Dp + d) : 0.f;
-          }
-          const float gv = (tid < 128 && n0 + tid < B) ? __ldg(we.g + n0 + tid) : 0.f;
-#pragma unroll
-          for (int u = 0; u < PER; ++u) {
-            const int e = tid + 256 * u, n = e / DP, d = e - n * DP;
-            xq[n * XW + d] = xv[u];
-          }
+          for (int u = 0; u < PER; ++u) xq[tid + 256 * u] = xv[u];
           if (tid < 128) gq[tid] = gv;
         }
         // gradient mode: colbuf holds -2 c h_n of the n-block; variance mode: the column sums
-        if (tid < 128)
-          colbuf[tid] = (grad && n0 + tid < B) ? (we.hn ? -2.0f * we.c * __ldg(we.hn + n0 + tid) : cn) : 0.f;
+        if (tid < 128) colbuf[tid] = hv;
       }
       asm volatile("bar.sync 1, %0;" ::"n"(32 * NTW) : "memory");
       if (ok) {
-        // 8-column chunks of every row block at once: each x~ row read from
-        // shared memory (a broadcast to all 32 lanes, the cost that dominates
-        // this epilogue) serves the NI row blocks
-        for (int ch = 8 * half; ch < 8 * half + 8; ++ch) {
-          float w[NI][8], tt[NI][8];
+        // CWD-column chunks of every row block at once (accumulator and T
+        // loaded together, one wait); each x~ row read from shared memory
+        // serves the four rows of a lane group and the NI row blocks
+        constexpr int CWD = NI == 1 ? 16 : 8;
+        for (int ch = (64 / CWD) * half; ch < (64 / CWD) * (half + 1); ++ch) {
+          float w[NI][CWD], tt[NI][CWD];
+          if constexpr (NI == 1) {
+            tmem_ld16x2(tmem + lane_off + G::ACC(0) + (uint32_t)(ch * CWD), tmem + lane_off + G::T(0) + (uint32_t)(ch * CWD),
+                        w[0], tt[0]);
+          } else {
+            float v4[4][8];
+            const uint32_t ta[4] = {tmem + lane_off + G::ACC(0) + (uint32_t)(ch * CWD),
+                                    tmem + lane_off + G::T(0) + (uint32_t)(ch * CWD),
+                                    tmem + lane_off + G::ACC(1) + (uint32_t)(ch * CWD),
+                                    tmem + lane_off + G::T(1) + (uint32_t)(ch * CWD)};
+            tmem_ld8x4(ta, v4);
 #pragma unroll
-          for (int ib = 0; ib < NI; ++ib) {
-            tmem_ld8(tmem + lane_off + G::ACC(ib) + (uint32_t)(ch * 8), w[ib]);
-            tmem_ld8(tmem + lane_off + G::T(ib) + (uint32_t)(ch * 8), tt[ib]);
+            for (int q = 0; q < CWD; ++q) {
+              w[0][q] = v4[0][q]; tt[0][q] = v4[1][q];
+              w[NI - 1][q] = v4[2][q]; tt[NI - 1][q] = v4[3][q];
+            }
           }
           if (grad) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const int n = ch * 8 + q;
+            for (int q = 0; q < CWD; ++q) {
+              const int n = ch * CWD + q;
               const float gn = gq[n], hn = colbuf[n];
-              f32x2 a2[NI];
+              // the lane's slot of x~_n (a broadcast to the eight groups) and x~^2
+              f32x2 xp[DQP / 2], xx[DQP / 2];
+              const float* xs = xq + n * XW + r4 * DQP;
+              if (DQP % 4 == 0) {
+#pragma unroll
+                for (int j = 0; j < DQP / 4; ++j) {
+                  const ulonglong2 x = reinterpret_cast<const ulonglong2*>(xs)[j];
+                  xp[2 * j] = x.x;
+                  xp[2 * j + 1] = x.y;
+                }
+              } else {
+#pragma unroll
+                for (int j = 0; j < DQP / 2; ++j) xp[j] = reinterpret_cast<const f32x2*>(xs)[j];
+              }
+#pragma unroll
+              for (int j = 0; j < DQP / 2; ++j) xx[j] = mul2(xp[j], xp[j]);
 #pragma unroll
               for (int ib = 0; ib < NI; ++ib) {
                 const float a = ex2(tt[ib][q]) * fmaf(cv[ib], gn, hn * w[ib][q]);
                 S0[ib] += a;
-                a2[ib] = pack2(a, a);
-              }
-              // x~ from shared memory, x~^2 formed in registers (the broadcast
-              // reads, not the arithmetic, bound this loop)
-              const ulonglong2* xr = reinterpret_cast<const ulonglong2*>(xq + n * XW);
+                float ak[4];
+                ak[0] = a;
+                ak[1] = __shfl_xor_sync(0xffffffffu, a, 1);
+                ak[2] = __shfl_xor_sync(0xffffffffu, a, 2);
+                ak[3] = __shfl_xor_sync(0xffffffffu, a, 3);
 #pragma unroll
-              for (int d4 = 0; d4 < DP / 4; ++d4) {
-                const ulonglong2 x = xr[d4];
-                const f32x2 xx0 = mul2(x.x, x.x), xx1 = mul2(x.y, x.y);
+                for (int k = 0; k < 4; ++k) {
+                  const f32x2 a2 = pack2(ak[k], ak[k]);
 #pragma unroll
-                for (int ib = 0; ib < NI; ++ib) {
-                  fma2(S1p[ib][2 * d4], a2[ib], x.x);
-                  fma2(S1p[ib][2 * d4 + 1], a2[ib], x.y);
-                  fma2(S2p[ib][2 * d4], a2[ib], xx0);
-                  fma2(S2p[ib][2 * d4 + 1], a2[ib], xx1);
+                  for (int j = 0; j < DQP / 2; ++j) {
+                    fma2(S1p[ib][k][j], a2, xp[j]);
+                    fma2(S2p[ib][k][j], a2, xx[j]);
+                  }
                 }
               }
             }
           } else if (we.colsum) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < CWD; ++q) {
               float sv = 0.f;
 #pragma unroll
               for (int ib = 0; ib < NI; ++ib) sv = fmaf(ex2(tt[ib][q]), w[ib][q], sv);
 #pragma unroll
               for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
-              if (lane == 0) atomicAdd(colbuf + ch * 8 + q, sv);
+              if (lane == 0) atomicAdd(colbuf + ch * CWD + q, sv);
             }
           }
         }
@@ -416,31 +454,48 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
     // combine the two column halves and write this CTA's partial rows
     if (grad) {
       constexpr int CW = 2 * DP + 1;
-      float* comb = xq;
+      float* comb = ebuf;                                 // colbuf, gq and xq are done with
 #pragma unroll
       for (int ib = 0; ib < NI; ++ib) {
         const int i = m0 + 128 * ib + row;
         if (ib > 0) asm volatile("bar.sync 1, %0;" ::"n"(32 * NTW) : "memory");   // comb is free again
-        float S1[DP], S2[DP];
+        // the two column halves' partial sums meet in comb[row][2 DP + 1]:
+        // half 1 stores its values, half 0 adds its own, then the rows go out
 #pragma unroll
-        for (int j = 0; j < DP / 2; ++j) {
-          unpack2(S1p[ib][j], S1[2 * j], S1[2 * j + 1]);
-          unpack2(S2p[ib][j], S2[2 * j], S2[2 * j + 1]);
-        }
-        if (half == 1) {
-          comb[row * CW + 2 * DP] = S0[ib];
+        for (int hh = 1; hh >= 0; --hh) {
+          if (half == hh) {
+            if (hh == 1) comb[row * CW + 2 * DP] = S0[ib];
+            else comb[row * CW + 2 * DP] += S0[ib];
 #pragma unroll
-          for (int d = 0; d < DP; ++d) { comb[row * CW + d] = S1[d]; comb[row * CW + DP + d] = S2[d]; }
+            for (int k = 0; k < 4; ++k) {
+              float* cr = comb + (quad * 32 + (lane & ~3) + (r4 ^ k)) * CW;
+#pragma unroll
+              for (int j = 0; j < DQP / 2; ++j) {
+                float a1, b1, a2, b2;
+                unpack2(S1p[ib][k][j], a1, b1);
+                unpack2(S2p[ib][k][j], a2, b2);
+                const int d0 = r4 * DQ + 2 * j;
+                if (2 * j < DQ) {
+                  cr[d0] = hh == 1 ? a1 : cr[d0] + a1;
+                  cr[DP + d0] = hh == 1 ? a2 : cr[DP + d0] + a2;
+                }
+                if (2 * j + 1 < DQ) {
+                  cr[d0 + 1] = hh == 1 ? b1 : cr[d0 + 1] + b1;
+                  cr[DP + d0 + 1] = hh == 1 ? b2 : cr[DP + d0 + 1] + b2;
+                }
+              }
+            }
+          }
+          asm volatile("bar.sync 1, %0;" ::"n"(32 * NTW) : "memory");
         }
-        asm volatile("bar.sync 1, %0;" ::"n"(32 * NTW) : "memory");
         if (half == 0 && !*abort_flag) {
-          const float s0 = S0[ib] + comb[row * CW + 2 * DP];
+          const float s0 = comb[row * CW + 2 * DP];
           const int W = 2 * D + 1;
           float* out = wa.rowpart + (size_t)blockIdx.x * W * wa.Mp + i;
 #pragma unroll
           for (int d = 0; d < DP; ++d) {
             if (d < D) {
-              const float s1 = S1[d] + comb[row * CW + d], s2 = S2[d] + comb[row * CW + DP + d];
+              const float s1 = comb[row * CW + d], s2 = comb[row * CW + DP + d];
               const float z = i < we.gen.M ? __ldg(we.gen.Zs + (size_t)i * Dp + d) : 0.f;
               out[(size_t)d * wa.Mp] = fmaf(-z, s0, s1);
               out[(size_t)(D + d) * wa.Mp] = fmaf(z, fmaf(z, s0, -2.0f * s1), s2);
@@ -477,15 +532,16 @@ void launch_w(dim3 grid, cudaStream_t st, const CUtensorMap (&m)[6], const WArgs
     pdl_launch(w_tc_kernel<NSPLIT, 8, NI>, grid, THREADS, SM, st, m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
   else if (D <= 16)
     pdl_launch(w_tc_kernel<NSPLIT, 16, NI>, grid, THREADS, SM, st, m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
-  else
+  else if constexpr (NI == 1)   // two row blocks only for D <= 16 (w_ni)
     pdl_launch(w_tc_kernel<NSPLIT, 24, NI>, grid, THREADS, SM, st, m[0], m[1], m[2], m[3], m[4], m[5], wa, we);
 }
 
 // Row blocks per CTA: two with BF16 operands when the 128-row blocks pair up
-// and the (row-pair, n-block) units still give every SM a CTA.
-int w_ni(bool split, int Mp, int B) {
+// and the (row-pair, n-block) units still give every SM a CTA (and D <= 16:
+// the register-resident row sums of 24 padded dimensions would spill).
+int w_ni(bool split, int Mp, int B, int D) {
   const int nblk = (B + 127) / 128;
-  return (!split && (Mp / 128) % 2 == 0 && (Mp / 256) * nblk >= tc_num_sms()) ? 2 : 1;
+  return (!split && D <= 16 && (Mp / 128) % 2 == 0 && (Mp / 256) * nblk >= tc_num_sms()) ? 2 : 1;
 }
 
 }  // namespace
@@ -498,15 +554,14 @@ void tc_w_init_attributes() {
   set_w_attr<1, 4, 2>();
   set_w_attr<1, 8, 2>();
   set_w_attr<1, 16, 2>();
-  set_w_attr<1, 24, 2>();
   set_w_attr<3, 4, 1>();
   set_w_attr<3, 8, 1>();
   set_w_attr<3, 16, 1>();
   set_w_attr<3, 24, 1>();
 }
 
-int tc_w_groups(int Mp, int B, bool split) {
-  const int nblk = (B + 127) / 128, rb = Mp / (128 * w_ni(split, Mp, B));
+int tc_w_groups(int Mp, int B, bool split, int D) {
+  const int nblk = (B + 127) / 128, rb = Mp / (128 * w_ni(split, Mp, B, D));
   int gn = tc_num_sms() / rb;
   if (gn < 1) gn = 1;
   if (gn > nblk) gn = nblk;
@@ -527,8 +582,8 @@ int tc_w(const GemmCtx& g, const bf16* P, const KufTC& t, const WEpi& we, float*
   } else {
     m[5] = m[4];
   }
-  const int ni = w_ni(g.split, g.Mp, B);
-  const int gn = tc_w_groups(g.Mp, B, g.split);
+  const int ni = w_ni(g.split, g.Mp, B, we.gen.D);
+  const int gn = tc_w_groups(g.Mp, B, g.split, we.gen.D);
   WArgs wa{g.Mp / KB, Bp / 128, g.Mp, g.err, we.rowacc ? rowpart : nullptr};
   dim3 grid(gn, g.Mp / (128 * ni));
   if (g.split) launch_w<3, 1>(grid, g.st, m, wa, we);

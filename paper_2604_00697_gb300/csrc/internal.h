@@ -90,7 +90,7 @@ bool tc_psi(const GemmCtx& g, const KufGen& kg, const KufTC& t, const bf16* Kk, 
 // writes per-CTA partial rows rowpart[p][k][i] (p < returned count, k < 2D+1,
 // i < Mp) instead of rowacc; variance mode returns 0.  -1: not supported.
 int tc_w(const GemmCtx& g, const bf16* P, const KufTC& t, const WEpi& we, float* rowpart);
-int tc_w_groups(int Mp, int B, bool split);
+int tc_w_groups(int Mp, int B, bool split, int D);
 void tc_w_init_attributes();
 // out[r] = sum_k Kuf(r, k) w_k for r < nrows, k < nk, from the row-role vectors
 // of the row points and the k-role vectors of the k points (kuf_prep); the
