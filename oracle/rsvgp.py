@@ -176,7 +176,14 @@ def bound(p, X, y, N=None, likelihood="gaussian", precond=True, probes=None):
     else:
         tr_KtT, tr_PKuu = hutchinson_traces(p, probes)
     quad = Pm @ Kuu @ Pm
-    sign, logdetT = np.linalg.slogdet(T)
+    # log|T| with T = L L^T: for the lower-triangular L of the parameterisation
+    # (kept lower triangular by the NG update of Prop. 1) the product rule
+    # gives 2 sum_i log|L_ii| exactly; forming T first and factorising it loses
+    # accuracy once cond(T) nears 1/eps (random triangular L at M = 300)
+    if np.all(np.triu(L, 1) == 0.0):
+        logdetT = 2.0 * np.sum(np.log(np.abs(np.diag(L))))
+    else:
+        sign, logdetT = np.linalg.slogdet(T)
     logdetS = np.sum(np.log(p["s"]))
     KL = 0.5 * (-tr_PKuu + tr_KtT - M + quad - logdetT - logdetS)
     return dict(F=E - KL, E=E, KL=KL, tr_PKuu=tr_PKuu, tr_KtT=tr_KtT, quad=quad,

@@ -87,7 +87,8 @@ def test_snelson_like_bound_and_grads(prec, state):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("M,D,B,seed", [(200, 3, 300, 0), (130, 5, 129, 1), (1, 2, 7, 2), (257, 1, 1, 3)])
+@pytest.mark.parametrize("M,D,B,seed", [(200, 3, 300, 0), (130, 5, 129, 1), (1, 2, 7, 2), (257, 1, 1, 3),
+                                        (300, 19, 260, 4)])
 def test_ragged_random_state(prec, M, D, B, seed):
     p, X, y, N = small_case(M, D, B, seed)
     _check_bound_and_grads(f"random/{M}x{D}x{B}", p, X, y, N, prec)

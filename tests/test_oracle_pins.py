@@ -524,6 +524,23 @@ def test_se_ard_special_cases():
     np.testing.assert_allclose(np.diag(O.se_ard(A, A, np.array([0.3]), 1.7)), 1.7)
 
 
+def test_log_det_T_of_triangular_L():
+    """log|T| in the KL bound, T = L L^T: equal to log|det L|^2 computed from L
+    alone (numpy's LU of L), including at M = 300 where cond(T) is near 1e17
+    and factorising the formed T is off by about 0.1; and equal to an
+    extended-precision determinant of the formed T at M = 80."""
+    mpmath = pytest.importorskip("mpmath")
+    X, y = _batch(7, 3, 1)
+    for M in (80, 300):
+        p = S.random_state(M, 3, 4)
+        logdet = O.bound(p, X, y, 70.0)["logdetT"]
+        assert logdet == pytest.approx(2.0 * np.linalg.slogdet(p["L"])[1], abs=1e-9)
+        if M == 80:
+            mpmath.mp.dps = 50
+            Lm = mpmath.matrix(p["L"].tolist())
+            assert logdet == pytest.approx(float(mpmath.log(mpmath.det(Lm * Lm.T))), abs=1e-10)
+
+
 def test_gamma_schedule_endpoints():
     assert O.gamma_schedule(0) == pytest.approx(1e-5)
     assert O.gamma_schedule(5) == pytest.approx(1e-5 ** 0.5)
