@@ -24,15 +24,19 @@ constexpr float SQRT_LOG2E = 1.2011224087864498f;   // sqrt(log2(e))
 template <int NSPLIT>
 struct PsiGeo {
   static constexpr int NS = NSPLIT == 3 ? 2 : 1;                         // hi (+lo) planes
-  static constexpr int STAGES = NSPLIT == 3 ? 2 : 3;
-  // stage: [x coordinate tile CT][generated rows I: NS*GT][generated rows J: NS*GT]
-  static constexpr int OFF_GA = CT;
-  static constexpr int OFF_GB = OFF_GA + NS * GT;
-  static constexpr int STAGE = OFF_GB + NS * GT;
+  // Two rings: the x coordinate tiles (CT each, read by the exponent MMAs, so
+  // a stage frees as soon as they are done and the copies run well ahead)
+  // and the generated tiles [rows I: NS*GT][rows J: NS*GT] (read by the main
+  // MMAs).
+  static constexpr int SC = 6;
+  static constexpr int SG = NSPLIT == 3 ? 2 : 3;
+  static constexpr int OFF_GA = 0;
+  static constexpr int OFF_GB = NS * GT;
+  static constexpr int GSTAGE = 2 * NS * GT;
   static constexpr int STATIC = 2 * GT;                                  // z rows of I and J
-  static_assert(STAGES * STAGE >= NTW * 32 * 33 * 4, "epilogue scratch");
-  static constexpr int NBAR = 3 * STAGES + 6;
-  static constexpr int SMEM = 1024 + STATIC + STAGES * STAGE + 8 * NBAR + 64;
+  static_assert(SG * GSTAGE >= NTW * 32 * 33 * 4, "epilogue scratch");
+  static constexpr int NBAR = 2 * SC + 2 * SG + 6;
+  static constexpr int SMEM = 1024 + STATIC + SC * CT + SG * GSTAGE + 8 * NBAR + 64;
   static_assert(SMEM <= 232448, "shared memory budget");
   static constexpr uint32_t TMEM_COLS = 512;
   // TMEM columns: accumulator [0,128); exponent buffers of 64 columns after it
@@ -63,15 +67,18 @@ psi_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // z, row role
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sRowA = base;                                   // z rows of I
   unsigned char* sRowB = base + GT;                              // z rows of J
-  unsigned char* stg = base + G::STATIC;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(stg + G::STAGES * G::STAGE);
+  unsigned char* cring = base + G::STATIC;                        // coordinate ring
+  unsigned char* stg = cring + G::SC * CT;                        // generated ring
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stg + G::SG * G::GSTAGE);
   volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars + G::NBAR);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   volatile int* consumed = abort_flag + 1;
-  constexpr int S = G::STAGES;
+  constexpr int SC = G::SC, SG = G::SG;
   auto BAR = [&](int idx) { return smem_u32(&bars[idx]); };
-  const int B_STATIC = 0, B_LD = 1, B_EMPTY = 1 + S, B_GEN = 1 + 2 * S, B_SFULL = 1 + 3 * S, B_SEMPTY = 3 + 3 * S,
-            B_ACC = 5 + 3 * S;
+  // LD / TEMPTY: coordinate stage landed / free; GEN / EMPTY: generated stage
+  // written / free
+  const int B_STATIC = 0, B_LD = 1, B_TEMPTY = 1 + SC, B_GEN = 1 + 2 * SC, B_EMPTY = 1 + 2 * SC + SG,
+            B_SFULL = 1 + 2 * SC + 2 * SG, B_SEMPTY = B_SFULL + 2, B_ACC = B_SFULL + 4;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = tiles[blockIdx.x].m0, n0 = tiles[blockIdx.x].n0;
@@ -79,10 +86,13 @@ psi_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // z, row role
 
   if (threadIdx.x == 0) {
     mbar_init(BAR(B_STATIC), 1);
-    for (int s = 0; s < S; ++s) {
+    for (int s = 0; s < SC; ++s) {
       mbar_init(BAR(B_LD + s), 1);
-      mbar_init(BAR(B_EMPTY + s), 1);
+      mbar_init(BAR(B_TEMPTY + s), 1);
+    }
+    for (int s = 0; s < SG; ++s) {
       mbar_init(BAR(B_GEN + s), NTW);
+      mbar_init(BAR(B_EMPTY + s), 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(BAR(B_SFULL + b), 1);
@@ -110,17 +120,17 @@ psi_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // z, row role
     if (!diag) tma_load_2d(smem_u32(sRowB), &tmRow, 0, n0, sb);
     int issued = 0;
     for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % S;
-      if (!mbar_wait(BAR(B_EMPTY + s), ((kb / S) & 1) ^ 1)) { *abort_flag = 1; break; }
+      const int s = kb % SC;
+      if (!mbar_wait(BAR(B_TEMPTY + s), ((kb / SC) & 1) ^ 1)) { *abort_flag = 1; break; }
       if (*abort_flag) break;
       const uint32_t fb = BAR(B_LD + s);
       mbar_expect_tx(fb, CT);
-      tma_load_2d(smem_u32(stg + s * G::STAGE), &tmK, 0, kb * KB, fb);
+      tma_load_2d(smem_u32(cring + s * CT), &tmK, 0, kb * KB, fb);
       issued = kb + 1;
     }
     mbar_wait(sb, 0);
     if (*abort_flag) {
-      for (int kb = *consumed; kb < issued; ++kb) mbar_wait(BAR(B_LD + kb % S), (kb / S) & 1);
+      for (int kb = *consumed; kb < issued; ++kb) mbar_wait(BAR(B_LD + kb % SC), (kb / SC) & 1);
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
@@ -136,12 +146,12 @@ psi_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // z, row role
     long long idle_since = clock64();
     while (ok && mn < nkb) {
       bool progressed = false;
-      if (d < nkb && mbar_test(BAR(B_LD + d % S), (d / S) & 1) &&
+      if (d < nkb && mbar_test(BAR(B_LD + d % SC), (d / SC) & 1) &&
           mbar_test(BAR(B_SEMPTY + (d & 1)), ((d >> 1) & 1) ^ 1)) {
         fence_after();
         *consumed = d + 1;
         const int b = d & 1;
-        const uint64_t kd = sw128_desc(smem_u32(stg + (d % S) * G::STAGE));
+        const uint64_t kd = sw128_desc(smem_u32(cring + (d % SC) * CT));
 #pragma unroll
         for (int kk = 0; kk < KB / 16; ++kk) {
           const uint64_t o = (uint64_t)(kk * 2);
@@ -149,12 +159,13 @@ psi_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // z, row role
           if (!diag) mma_bf16(tmem + G::S_B(b), rb + o, kd + o, ID_DIST, kk != 0);
         }
         mma_commit(BAR(B_SFULL + b));
+        mma_commit(BAR(B_TEMPTY + d % SC));
         ++d;
         progressed = true;
       }
-      if (mn < d && mbar_test(BAR(B_GEN + mn % S), (mn / S) & 1)) {
+      if (mn < d && mbar_test(BAR(B_GEN + mn % SG), (mn / SG) & 1)) {
         fence_after();
-        unsigned char* st = stg + (mn % S) * G::STAGE;
+        unsigned char* st = stg + (mn % SG) * G::GSTAGE;
         const uint64_t ad = sw128_desc(smem_u32(st + G::OFF_GA));
         const uint64_t adl = sw128_desc(smem_u32(st + G::OFF_GA + GT));
         const uint64_t bd = diag ? ad : sw128_desc(smem_u32(st + G::OFF_GB));
@@ -168,7 +179,7 @@ psi_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // z, row role
             mma_bf16(tmem, adl + o, bd + o, ID_MAIN, 1);
           }
         }
-        mma_commit(BAR(B_EMPTY + mn % S));
+        mma_commit(BAR(B_EMPTY + mn % SG));
         ++mn;
         progressed = true;
       }
@@ -185,7 +196,7 @@ psi_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // z, row role
     const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
     for (int kb = 0; kb < nkb; ++kb) {
       if (*abort_flag) break;
-      const int s = kb % S, b = kb & 1;
+      const int s = kb % SG, b = kb & 1;
       if (!mbar_wait(BAR(B_SFULL + b), (kb >> 1) & 1)) { *abort_flag = 1; break; }
       fence_after();
       float sa[32], sbv[32];
@@ -194,9 +205,9 @@ psi_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // z, row role
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(BAR(B_SEMPTY + b));
-      // the generated buffers of stage s are free once the main MMA of kb - S finished
-      if (!mbar_wait(BAR(B_EMPTY + s), ((kb / S) & 1) ^ 1)) { *abort_flag = 1; break; }
-      unsigned char* st = stg + s * G::STAGE;
+      // the generated buffers of stage s are free once the main MMA of kb - SG finished
+      if (!mbar_wait(BAR(B_EMPTY + s), ((kb / SG) & 1) ^ 1)) { *abort_flag = 1; break; }
+      unsigned char* st = stg + s * G::GSTAGE;
       gen32<NSPLIT>(sa, st + G::OFF_GA, st + G::OFF_GA + GT, row, kcol0);
       if (!diag) gen32<NSPLIT>(sbv, st + G::OFF_GB, st + G::OFF_GB + GT, row, kcol0);
       fence_proxy_async();
