@@ -397,84 +397,125 @@ __global__ void gp_assemble_kernel(const float* __restrict__ Kuu, const float* _
 // S2_d = sum_j A_ij z~_jd^2 (two FMAs per dimension and element) and reported
 // as S1_d - z~_id S0 and S2_d - 2 z~_id S1_d + z~_id^2 S0.
 // Block = 32 rows (lane = row i) x a range of JB columns j, split over the 8
-// warps; the host sizes JB so that the grid fills the SMs in one wave.  A is symmetric, so A_ij is read as A[j][i]: a warp reads
-// 32 consecutive floats of row j (eight rows in flight per warp).  z~_j of the
-// range is staged in shared memory and read as broadcasts (their cost bounds
-// the loop, so z~_j^2 is formed in registers).
+// warps; the host sizes JB so that the grid fills the SMs in one wave.  A is
+// symmetric, so A_ij is read as A[j][i]: a warp reads 32 consecutive floats of
+// row j (eight rows in flight per warp).  z~_j of the range is staged in
+// shared memory; the broadcast reads of it bound the loop, so groups of four
+// lanes share them: lane r of a group accumulates S1, S2 of the group's four
+// rows for its quarter of the dimensions (DQ of them), taking the other rows'
+// A_ij by shuffles, and reads only its DQ values of z~_j.
 // Warp partials meet in shared memory; one atomic per row and value per block.
+template <int DP>
+constexpr int kuu_zw() { return 4 * ((DP / 4 + 1) & ~1); }   // staged floats per z~ row (4 lane slots)
+
 template <int DP>
 __global__ void __launch_bounds__(256) kuu_bwd_kernel(const float* __restrict__ GK, const float* __restrict__ Kuu,
                                                      const float* __restrict__ Zs, int M, int Mp, int D,
                                                      float* __restrict__ rowacc, int JB) {
   pdl_enter();
-  constexpr int W = 2 * DP + 1;
   constexpr int U = 8;
-  extern __shared__ __align__(16) float zs[];      // [JB][DP]
-  __shared__ float part[32][W + 1];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int DQ = DP / 4, DQP = (DQ + 1) & ~1, ZW = kuu_zw<DP>();
+  extern __shared__ __align__(16) float zs[];      // [JB][ZW]: lane slot r holds dimensions r DQ .. + DQ
+  __shared__ float part[32][2 * DP + 2];           // raw sums per row: S1 [0, D), S2 [D, 2D), S0 2D
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, r4 = lane & 3;
   const int i = blockIdx.x * 32 + lane;
   const int Dp = (D + 3) & ~3;
   const int jb = blockIdx.y * JB, je = min(M, jb + JB);
-  for (int e = threadIdx.x; e < 32 * (W + 1); e += 256) (&part[0][0])[e] = 0.f;
+  for (int e = threadIdx.x; e < 32 * (2 * DP + 2); e += 256) (&part[0][0])[e] = 0.f;
 #pragma unroll 8
-  for (int e = threadIdx.x; e < JB * DP; e += 256) {
-    const int r = e / DP, d = e - r * DP;
-    const float zv = (jb + r < je && d < Dp) ? __ldg(Zs + (size_t)(jb + r) * Dp + d) : 0.f;
-    zs[r * DP + d] = zv;
+  for (int e = threadIdx.x; e < JB * ZW; e += 256) {
+    const int r = e / ZW, sl = e - r * ZW, jj = sl % DQP, d = (sl / DQP) * DQ + jj;
+    zs[e] = (jb + r < je && jj < DQ && d < Dp) ? __ldg(Zs + (size_t)(jb + r) * Dp + d) : 0.f;
   }
-  // packed FP32 pairs: S1p[j] = (S1_2j, S1_2j+1), likewise S2p
-  f32x2 S1p[DP / 2], S2p[DP / 2];
+  // S1p[k][q] = (S1, S1) of row 4 (lane / 4) + (r4 ^ k) at dimensions r4 DQ + 2q, 2q + 1
+  f32x2 S1p[4][DQP / 2], S2p[4][DQP / 2];
   float S0 = 0.f;
 #pragma unroll
-  for (int j = 0; j < DP / 2; ++j) { S1p[j] = 0ull; S2p[j] = 0ull; }
-  __syncthreads();
-  if (i < M) {
-    for (int j = jb + warp; j < je; j += 8 * U) {
-      float a[U];
+  for (int k = 0; k < 4; ++k)
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int jj = j + 8 * u;
-        a[u] = jj < je ? __ldg(GK + (size_t)jj * Mp + i) * __ldg(Kuu + (size_t)jj * Mp + i) : 0.f;
+    for (int q = 0; q < DQP / 2; ++q) { S1p[k][q] = 0ull; S2p[k][q] = 0ull; }
+  __syncthreads();
+  const bool row_ok = i < M;
+  for (int j = jb + warp; j < je; j += 8 * U) {
+    float a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int jj = j + 8 * u;
+      a[u] = (row_ok && jj < je) ? __ldg(GK + (size_t)jj * Mp + i) * __ldg(Kuu + (size_t)jj * Mp + i) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int jj = min(j + 8 * u, je - 1) - jb;
+      const float* zr = &zs[jj * ZW + r4 * DQP];
+      f32x2 zp[DQP / 2], zq[DQP / 2];
+      if (DQP % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < DQP / 4; ++q) {
+          const ulonglong2 v = reinterpret_cast<const ulonglong2*>(zr)[q];
+          zp[2 * q] = v.x;
+          zp[2 * q + 1] = v.y;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < DQP / 2; ++q) zp[q] = reinterpret_cast<const f32x2*>(zr)[q];
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int jj = min(j + 8 * u, je - 1) - jb;
-        const ulonglong2* zj = reinterpret_cast<const ulonglong2*>(&zs[jj * DP]);
-        S0 += a[u];
-        const f32x2 a2 = pack2(a[u], a[u]);
+      for (int q = 0; q < DQP / 2; ++q) zq[q] = mul2(zp[q], zp[q]);
+      S0 += a[u];
+      float ak[4];
+      ak[0] = a[u];
+      ak[1] = __shfl_xor_sync(0xffffffffu, a[u], 1);
+      ak[2] = __shfl_xor_sync(0xffffffffu, a[u], 2);
+      ak[3] = __shfl_xor_sync(0xffffffffu, a[u], 3);
 #pragma unroll
-        for (int d4 = 0; d4 < DP / 4; ++d4) {
-          const ulonglong2 q = zj[d4];
-          fma2(S1p[2 * d4], a2, q.x);
-          fma2(S1p[2 * d4 + 1], a2, q.y);
-          fma2(S2p[2 * d4], a2, mul2(q.x, q.x));
-          fma2(S2p[2 * d4 + 1], a2, mul2(q.y, q.y));
+      for (int k = 0; k < 4; ++k) {
+        const f32x2 a2 = pack2(ak[k], ak[k]);
+#pragma unroll
+        for (int q = 0; q < DQP / 2; ++q) {
+          fma2(S1p[k][q], a2, zp[q]);
+          fma2(S2p[k][q], a2, zq[q]);
         }
       }
     }
   }
-  const float* zi = Zs + (size_t)(i < M ? i : 0) * Dp;
-  float S1[DP], S2[DP];
+  // raw sums of the eight warps into part
+  atomicAdd(&part[lane][2 * D], S0);
 #pragma unroll
-  for (int j = 0; j < DP / 2; ++j) {
-    unpack2(S1p[j], S1[2 * j], S1[2 * j + 1]);
-    unpack2(S2p[j], S2[2 * j], S2[2 * j + 1]);
-  }
+  for (int k = 0; k < 4; ++k) {
+    const int rr = (lane & ~3) + (r4 ^ k);
 #pragma unroll
-  for (int d = 0; d < DP; ++d) {
-    if (d < D) {
-      const float z = i < M ? __ldg(zi + d) : 0.f;
-      atomicAdd(&part[lane][d], fmaf(-z, S0, S1[d]));
-      atomicAdd(&part[lane][D + d], fmaf(z, fmaf(z, S0, -2.0f * S1[d]), S2[d]));
+    for (int q = 0; q < DQP / 2; ++q) {
+      float s1a, s1b, s2a, s2b;
+      unpack2(S1p[k][q], s1a, s1b);
+      unpack2(S2p[k][q], s2a, s2b);
+      const int d0 = r4 * DQ + 2 * q;
+      if (2 * q < DQ && d0 < D) {
+        atomicAdd(&part[rr][d0], s1a);
+        atomicAdd(&part[rr][D + d0], s2a);
+      }
+      if (2 * q + 1 < DQ && d0 + 1 < D) {
+        atomicAdd(&part[rr][d0 + 1], s1b);
+        atomicAdd(&part[rr][D + d0 + 1], s2b);
+      }
     }
   }
-  atomicAdd(&part[lane][2 * D], S0);
   __syncthreads();
+  // difference form per row, one global atomic per row and value
   const int Wd = 2 * D + 1;
   for (int e = threadIdx.x; e < 32 * Wd; e += 256) {
     const int r = e / Wd, k = e - r * Wd;
     const int ii = blockIdx.x * 32 + r;
-    if (ii < M) atomicAdd(rowacc + (size_t)ii * Wd + k, part[r][k]);
+    if (ii >= M) continue;
+    const float s0 = part[r][2 * D];
+    float v = s0;
+    if (k < D) {
+      v = fmaf(-__ldg(Zs + (size_t)ii * Dp + k), s0, part[r][k]);
+    } else if (k < 2 * D) {
+      const int d = k - D;
+      const float z = __ldg(Zs + (size_t)ii * Dp + d);
+      v = fmaf(z, fmaf(z, s0, -2.0f * part[r][d]), part[r][k]);
+    }
+    atomicAdd(rowacc + (size_t)ii * Wd + k, v);
   }
 }
 
@@ -850,10 +891,11 @@ void k_kuu_bwd(const float* GKuu, const float* Kuu, const float* Zs, int M, int 
   // One wave: blocks per SM x SMs slots, shared out over the row blocks; JB
   // a multiple of 8, the staged z~ with the static partials within 48 KB.
   SVGP_DP_DISPATCH(D, {
-    const int jbmax = std::min(512, 9216 / DP);
+    constexpr int ZW = kuu_zw<DP>();
+    const int jbmax = std::min(512, 9216 / ZW);
     static int occ = 0;
     if (!occ) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kuu_bwd_kernel<DP>, 256, (size_t)jbmax * DP * 4);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kuu_bwd_kernel<DP>, 256, (size_t)jbmax * ZW * 4);
       if (occ < 1) occ = 1;
     }
     const int gx = (M + 31) / 32;
@@ -862,7 +904,7 @@ void k_kuu_bwd(const float* GKuu, const float* Kuu, const float* Zs, int M, int 
     JB = std::max(8, std::min(JB, jbmax));
     dim3 grid(gx, (M + JB - 1) / JB);
     svgp_note_launch();
-    pdl_launch(kuu_bwd_kernel<DP>, grid, 256, (size_t)JB * DP * 4, st, GKuu, Kuu, Zs, M, Mp, D, rowacc_u, JB);
+    pdl_launch(kuu_bwd_kernel<DP>, grid, 256, (size_t)JB * ZW * 4, st, GKuu, Kuu, Zs, M, Mp, D, rowacc_u, JB);
   });
 }
 
