@@ -455,12 +455,13 @@ def constrain(raw):
 
 
 def train(p0, batches, N, steps, lr=5e-3, gamma=None, train_Z=True, eps=0.0,
-          max_ng=1):
+          max_ng=1, ng_counts=None):
     """Alternating optimisation of Section 3.1: NG step(s) on L, then Adam on xi.
 
     ``gamma`` is a callable t -> gamma_t over the global NG counter (default:
     gamma = 1, the fixed-Z setting of Section 3.4).  Returns the final state
-    and the list of bound values recorded after each Adam step.
+    and the list of bound values recorded after each Adam step; the number of
+    NG updates of each step is appended to ``ng_counts`` when given.
     """
     gamma = gamma or (lambda t: 1.0)
     raw = {k: (softplus_inv(p0[k]) if k in _POSITIVE else np.array(p0[k], np.float64))
@@ -473,12 +474,16 @@ def train(p0, batches, N, steps, lr=5e-3, gamma=None, train_Z=True, eps=0.0,
         X, y = batches(step)
         c = constrain(raw)
         _, _, _, Kt = kernel_blocks(c, X[:1])
+        n_ng = 0
         for _ in range(max_ng):
             A = L.T @ Kt @ L
             if eps > 0 and ng_residual(A) < eps:
                 break
             L, _ = ng_step(L, Kt, gamma(t_ng))
             t_ng += 1
+            n_ng += 1
+        if ng_counts is not None:
+            ng_counts.append(n_ng)
         c["L"] = L
         gr = grads(c, X, y, N)
         trace.append(bound(c, X, y, N)["F"])
