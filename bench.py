@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32-plain and single-BF16 comparison lines")
     ap.add_argument("--no-autograd", action="store_true", help="skip the steps/s through the autograd Function")
+    ap.add_argument("--no-hutchinson", action="store_true",
+                    help="skip the timing of the P-free Hutchinson bound at M=8192, B=256")
     ap.add_argument("--no-autotune", action="store_true", help="keep the cost model's split-K thresholds")
     ap.add_argument("--no-validate", action="store_true", help="skip the oracle bound and gradient check")
     ap.add_argument("--validate-single", action="store_true", help="also check the single-BF16 form")
@@ -653,6 +655,8 @@ def run_ours(args):
             m3.close()
     if not args.no_autograd and rank == 0 and ws == 1 and args.workload != "group64":
         line["autograd"] = time_autograd(prec, prob, Xd, yd, max(20, args.steps // 5), args.warmup)
+    if rank == 0 and ws == 1 and args.workload == WORKLOAD and not args.no_hutchinson:
+        line["hutchinson_bound"] = time_hutchinson(prec)
     if not args.no_validate and rank == 0 and ws == 1:
         line["validity"] = validate(prec, prob)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -661,6 +665,45 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.barrier()
+
+
+def time_hutchinson(prec, M=8192, B=256, K=64, D=16, reps=5):
+    """The bound in the paper's B << M regime (Section 3.4): svgp_bound (P
+    formed by the O(M^3) chain) against svgp_bound_hutchinson (no P, traces
+    from K probes, O((B + K) M^2)) on one handle, device ms per evaluation
+    (CUDA events, after two warm-up calls); synthetic GP-sample inputs at
+    s~ = 1e-2, L = 1e-3 I (the cost of either path does not depend on the
+    state)."""
+    import torch
+
+    import svgp_synth as S
+    from paper_2604_00697_gb300.model import RSVGP
+
+    prob = S.gp_sample_regression(M=M, B=B)
+    m = RSVGP(M, D, B, prec=prec)
+    m.set_state(prob.Z0, np.ones(D), 1.0, 1.0, np.zeros(M), np.full(M, 1e-2), 1e-3 * np.eye(M))
+    X, y = prob.batch(0)
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    yd = torch.tensor(y, dtype=torch.float32, device="cuda")
+    probes = torch.tensor(np.where(np.random.default_rng(5).uniform(size=(M, K)) < 0.5, -1.0, 1.0),
+                          dtype=torch.float32, device="cuda")
+    out = {"M": M, "B": B, "K": K, "D": D, "prec": prec}
+    for name, fn in (("bound_ms", lambda: m.bound(Xd, yd, prob.N)),
+                     ("hutchinson_ms", lambda: m.bound_hutchinson(Xd, yd, prob.N, probes))):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = round(e0.elapsed_time(e1) / reps, 3)
+    out["status"] = m.sync_status()
+    out["speedup"] = round(out["bound_ms"] / out["hutchinson_ms"], 2)
+    m.close()
+    return out
 
 
 def validate(prec, prob):

@@ -163,6 +163,13 @@ void k_grad_finalize(const float* rowacc_f, const float* rowacc_u, const float* 
 // red[RED_HX4] for K probes Z (M x K); buffers of M x K floats (hutchinson.cu).
 void k_hutchinson(const float* Lf, const float* Kuu, const float* s, int M, int Mp, const float* Z, int K,
                   float* bufA, float* bufB, float* bufC, double* red, cudaStream_t st);
+// The bound's data-term inputs without P (hutchinson.cu): v = P m~ (m~ when
+// precond is false) and, per point, k_n^T P k_n into colq[n] and summed into
+// red[RED_PPSI], from FP32 products of L and K~ with blocks of at most cmax
+// columns of Kuf (buffers of M x cmax floats).
+void k_hutch_data(const float* Lf, const float* Kuu, const float* s, int M, int Mp, const float* Zs, const float* Xs,
+                  int D, int B, const float* sf2, const float* m, bool precond, float* bufA, float* bufB,
+                  float* bufC, int cmax, float* v, float* colq, double* red, cudaStream_t st);
 // probit: E from red[RED_ELL], dsf2's data part from red[RED_SUMH], dnoise = 0.
 // hutch_K > 0: tr(K~T) and tr(P Kuu) from the Hutchinson sums over hutch_K probes.
 void k_terms_finalize(const double* red, const double* acc_ell, const float* sf2, const float* noise,

@@ -754,9 +754,21 @@ svgp_status svgp_bound_hutchinson(svgp_handle* h, const svgp_params* p, const sv
   svgp_status s = validate_batch(h, b);
   if (s != SVGP_OK) return s;
   prologue(h, p, b->X, b->B, p->L);
-  forward(h, p, b, true);
-  k_hutchinson(h->Lf, h->Kuu_f, p->s, h->M, h->Mp, probes, K, h->hut, h->hut + (size_t)h->M * SVGP_HUTCH_KMAX,
-               h->hut + 2 * (size_t)h->M * SVGP_HUTCH_KMAX, h->red, h->st);
+  // no P and no O(M^3) product: the data term from k_n^T P k_n of the
+  // factored form per point, the two traces from the probes (Section 3.4)
+  cudaStream_t st = h->st;
+  const int M = h->M, Mp = h->Mp;
+  float* bufA = h->hut;
+  float* bufB = h->hut + (size_t)M * SVGP_HUTCH_KMAX;
+  float* bufC = h->hut + 2 * (size_t)M * SVGP_HUTCH_KMAX;
+  k_hutch_data(h->Lf, h->Kuu_f, p->s, M, Mp, h->Zs, h->Xs, h->D, b->B, p->sf2, p->m, !h->unprec, bufA, bufB, bufC,
+               SVGP_HUTCH_KMAX, h->v, h->colsum, h->red, st);
+  k_gemv(h->Kuu_f, Mp, M, h->v, 1.f, nullptr, 0.f, h->w, h->v, h->red + RED_QUAD, st);     // w = Kuu v, v^T w
+  if (!(h->tc_kuf && tc_kuf_gemv(h->kt.XR, b->B, h->kt.ZK, M, h->v, h->mu, true, h->errword, st)))
+    k_mu(h->Zs, h->Xs, M, b->B, h->D, p->sf2, h->v, h->mu, st);                          // mu = Kfu v
+  if (h->probit) k_pointwise_probit(b->y, h->mu, h->colsum, p->sf2, b->B, h->gh, h->g, h->hn, h->red, st);
+  else k_pointwise_gauss(b->y, h->mu, p->noise, b->B, h->g, h->red, st);
+  k_hutchinson(h->Lf, h->Kuu_f, p->s, M, Mp, probes, K, bufA, bufB, bufC, h->red, st);
   k_terms_finalize(h->red, h->acc_ell, p->sf2, p->noise, p->ell, h->M, h->D, b->B, b->N, h->probit, K, terms_dev,
                    nullptr, nullptr, nullptr, h->errword, h->st);
   return check_launch(h, "svgp_bound_hutchinson");

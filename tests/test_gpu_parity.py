@@ -189,6 +189,46 @@ def test_bound_hutchinson_matches_oracle(prec, K):
     m.close()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("lik,precond,B", [("probit", True, 300), ("gaussian", False, 300), ("gaussian", True, 600)])
+def test_bound_hutchinson_likelihoods_and_batches(prec, lik, precond, B):
+    """The P-free bound of Section 3.4 for the probit likelihood, without the
+    mean preconditioner, and for a batch of more than 256 points (three
+    blocks of points, the last one ragged), against the oracle's bound with
+    the same probes."""
+    M, K = 130, 16
+    p, X, y, N = small_case(M, 3, B, 9)
+    if lik == "probit":
+        y = f32((y > np.median(y)).astype(np.float64))
+    probes = np.where(np.random.default_rng([K, 9]).uniform(size=(M, K)) < 0.5, -1.0, 1.0)
+    ref = O.bound(p, X, y, N, likelihood=lik, precond=precond, probes=probes)
+    m = _model(p, M, 3, B, prec, likelihood=lik, precond=precond)
+    t = m.bound_hutchinson(_dev(X), _dev(y), N, torch.tensor(probes, dtype=torch.float32)).cpu().numpy()
+    assert m.sync_status() == 0
+    tb = TOL[prec]["bound"]
+    log_errors(f"hutchinson/{lik}/{'pre' if precond else 'unpre'}/B{B}", prec, {"bound": abs(t[0] - ref["F"]) / abs(ref["F"])})
+    assert abs(t[0] - ref["F"]) <= tb * abs(ref["F"]), (t[0], ref["F"])
+    m.close()
+
+
+def test_bound_hutchinson_exact_terms_agree_with_bound_at_M1024():
+    """At M = 1024 with 200 points, the P-free path's exact terms (sum of
+    squared errors, sum of sigma_n^2, the quadratic term, log-determinants)
+    equal those of svgp_bound, which forms P by the O(M^3) chain (FP32
+    handle: both in FP32 arithmetic)."""
+    M, D, B = 1024, 4, 200
+    p, X, y, N = small_case(M, D, B, 10, state="chol")
+    probes = np.where(np.random.default_rng([3, 10]).uniform(size=(M, 8)) < 0.5, -1.0, 1.0)
+    m = _model(p, M, D, B, "fp32")
+    Xd, yd = _dev(X), _dev(y)
+    t_exact = m.bound(Xd, yd, N).cpu().numpy().copy()
+    t_hut = m.bound_hutchinson(Xd, yd, N, torch.tensor(probes, dtype=torch.float32)).cpu().numpy().copy()
+    assert m.sync_status() == 0
+    for k in (5, 6, 7, 8, 9):              # quad, logdetT, sqerr, sumvar, logdetS
+        assert abs(t_hut[k] - t_exact[k]) <= 1e-4 * max(1.0, abs(t_exact[k])), (k, t_hut[k], t_exact[k])
+    m.close()
+
+
 def test_group_step_matches_separate_models():
     """Several SVGPs of different M stepped together (one CUDA graph with a
     branch per member) give the results of stepping each alone."""
