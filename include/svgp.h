@@ -163,14 +163,18 @@ svgp_status svgp_bound(svgp_handle* h, const svgp_params* p, const svgp_batch* b
  * every other term exact.  probes: device float[M x K] row-major (column k
  * is z_k; entries +-1 for Rademacher probes -- the caller draws them, so the
  * estimate is reproducible), 1 <= K <= SVGP_HUTCH_KMAX.  Nothing of order
- * M^3 is computed and P is never formed: the estimates take FP32 products of
- * the M x M matrices with M x K blocks (about 14 M^2 K flops), and the data
- * term takes k_n^T P k_n = 2 |L^T k_n|^2 - (T k_n)^T K~ (T k_n) per point and
- * v = P m~ from FP32 products of L and K~ with the columns of Kuf (about
- * 6 M^2 B flops, blocks of SVGP_HUTCH_KMAX points) -- O((B + K) M^2) in all,
+ * M^3 is computed and P is never formed: the estimates take products of the
+ * M x M matrices with the M x K probe block (about 14 M^2 K flops), the data
+ * term takes k_n^T P k_n = 2 |L^T k_n|^2 - (T k_n)^T K~ (T k_n) per point from
+ * products of L and K~ with the columns of Kuf (about 6 M^2 B flops), and
+ * v = P m~ comes from FP32 matrix-vector products -- O((B + K) M^2) in all,
  * less than svgp_bound's O(M^3) chain once B + K is well below M.  The
- * terms layout is that of svgp_bound (SVGP_T_TRKT and SVGP_T_TRPKUU hold the
- * estimates). */
+ * products run on the tensor cores in the handle's operand precision (BF16
+ * or hi/lo BF16 handles; FP32 SIMT for SVGP_FP32 handles, and when K exceeds
+ * M rounded up to 128).  The first call, and a call whose B or K changes the
+ * number of 128-column blocks, synchronises the handle's streams to rebuild
+ * the products' schedules: make it outside stream capture.  The terms layout
+ * is that of svgp_bound (SVGP_T_TRKT and SVGP_T_TRPKUU hold the estimates). */
 #define SVGP_HUTCH_KMAX 256
 svgp_status svgp_bound_hutchinson(svgp_handle* h, const svgp_params* p, const svgp_batch* b,
                                   const float* probes, int K, double* terms_dev);

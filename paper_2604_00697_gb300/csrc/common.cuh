@@ -348,6 +348,17 @@ struct EpiStore {
   __device__ void reduce() {}
 };
 
+// Transposed store of a full result, out[j][i] = acc[i][j] (tensor-core
+// path only): the tall-skinny products of the P-free bound keep every M x N
+// factor as its transpose, the K-major operand of the next product.
+template <class OutP>
+struct EpiStoreT {
+  OutP out; int ld;
+  __device__ bool skip() const { return false; }
+  __device__ void begin_tile(int, int) {}
+  __device__ void reduce() {}
+};
+
 // P = Y L^T = L (2I - A1) L^T on the lower region, mirrored; FP32 and
 // low-precision copies; reduces sum_i s_i P_ii and <P, Psi> (Psi may be null).
 template <class OutP>

@@ -38,6 +38,7 @@ template <class OutP, int MODE> struct EpiSmem<EpiSym<OutP, MODE>> {
 };
 template <> struct EpiSmem<EpiLupd> { static constexpr bool input = true; static constexpr int out_slots = 1; };
 template <class OutP> struct EpiSmem<EpiStore<OutP>> { static constexpr bool input = false; static constexpr int out_slots = 1; };
+template <class OutP> struct EpiSmem<EpiStoreT<OutP>> { static constexpr bool input = false; static constexpr int out_slots = 1; };
 template <class OutP> struct EpiSmem<EpiP<OutP>> { static constexpr bool input = true; static constexpr int out_slots = 4; };
 template <> struct EpiSmem<EpiGK> { static constexpr bool input = true; static constexpr int out_slots = 2; };
 
@@ -299,6 +300,24 @@ __device__ __forceinline__ void tc_epi(EpiStore<OutP>&, int i0, int j0, float (&
   staged();
   if (lane == 0) {
     store_out<OutP>(&maps.out[0], out, j0, i0);
+    bulk_commit();
+  }
+}
+
+// Transposed store: the block goes out as its transpose (column stores into
+// the staging slot, as the mirrored blocks of the symmetric results).
+template <class OutP>
+__device__ __forceinline__ bool tc_skip(const EpiStoreT<OutP>&, int, int) { return false; }
+template <class OutP>
+__device__ __forceinline__ bool tc_in(const EpiStoreT<OutP>&, int, int, int&, int&) { return false; }
+template <class OutP>
+__device__ __forceinline__ void tc_epi(EpiStoreT<OutP>&, int i0, int j0, float (&v)[32], int lane,
+                                       const unsigned char*, unsigned char* out, const EpiMaps& maps) {
+#pragma unroll
+  for (int q = 0; q < 32; ++q) Out<OutP>::elem(out, q, lane, v[q]);
+  staged();
+  if (lane == 0) {
+    store_out<OutP>(&maps.out[0], out, i0, j0);
     bulk_commit();
   }
 }

@@ -432,6 +432,10 @@ bool epi_maps(const EpiStore<OutP>& e, etc::EpiMaps& m, int Mp) {
   return e.ld == Mp && out_maps(m.out, e.out, Mp);
 }
 template <class OutP>
+bool epi_maps(const EpiStoreT<OutP>& e, etc::EpiMaps& m, int Mp) {
+  return e.ld == Mp && out_maps(m.out, e.out, Mp);
+}
+template <class OutP>
 bool epi_maps(const EpiP<OutP>& e, etc::EpiMaps& m, int Mp) {
   return e.ld == Mp && (!e.Psi || block_map(&m.in, e.Psi, Mp, true)) && block_map(&m.out[0], e.Pf, Mp, true) &&
          out_maps(m.out + 1, e.Plo, Mp);
@@ -493,6 +497,8 @@ SVGP_TC_INST(EpiStore<SplitPtr>)
 SVGP_TC_INST(EpiP<SplitPtr>)
 SVGP_TC_INST(EpiLupd)
 SVGP_TC_INST(EpiGK)
+SVGP_TC_INST(EpiStoreT<bf16*>)
+SVGP_TC_INST(EpiStoreT<SplitPtr>)
 
 void tc_init_attributes() {
   set_attr_both<EpiVt<bf16*>>();
@@ -509,4 +515,6 @@ void tc_init_attributes() {
   set_attr_both<EpiP<SplitPtr>>();
   set_attr_both<EpiLupd>();
   set_attr_both<EpiGK>();
+  set_attr_both<EpiStoreT<bf16*>>();
+  set_attr_both<EpiStoreT<SplitPtr>>();
 }

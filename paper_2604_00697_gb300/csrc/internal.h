@@ -13,7 +13,12 @@ enum TileTable {
   TT_OUT = 4,     // lower, K [0, n0 + BN)    Y L^T       = L S L^T
   TT_PSI = 5,     // upper, K given at launch Kuf Kuf^T
   TT_FULL = 6,    // full,  K [0, Mp)         general products (Prop. 3 gap)
-  TT_COUNT = 7
+  // tall-skinny products A X of the P-free bound, output columns [0, Np) only
+  // (Np set per call), X stored transposed (one row per column of X)
+  TT_RL = 7,      // K [0, m0 + BM)           A = L
+  TT_RLT = 8,     // K [m0, Mp)               A = L^T
+  TT_RF = 9,      // K [0, Mp)                A = Kuu or K~
+  TT_COUNT = 10
 };
 
 // One work item of the persistent tensor-core GEMM: an output tile and its K
@@ -170,6 +175,17 @@ void k_hutchinson(const float* Lf, const float* Kuu, const float* s, int M, int 
 void k_hutch_data(const float* Lf, const float* Kuu, const float* s, int M, int Mp, const float* Zs, const float* Xs,
                   int D, int B, const float* sf2, const float* m, bool precond, float* bufA, float* bufB,
                   float* bufC, int cmax, float* v, float* colq, double* red, cudaStream_t st);
+// Tensor-core form of the P-free bound (hutchinson.cu): K~ in the operand
+// precision; transposed operands (Np rows of Mp) of Kuf columns c0 .. c0+nc
+// and of the probes; per-row q = 2|U_r|^2 - W_r . V_r; sums of row products.
+template <class OutP> void k_kt_op(const float* Kuu, const float* s, int M, int Mp, OutP out, cudaStream_t st);
+template <class OutP>
+void k_kuf_t(const float* Zs, const float* Xs, int M, int Mp, int D, const float* sf2, int c0, int nc, int Np,
+             OutP out, cudaStream_t st);
+template <class OutP> void k_probes_t(const float* Z, int M, int Mp, int K, int Np, OutP out, cudaStream_t st);
+template <class OutP>
+void k_rowq(OutP U, OutP W, OutP V, int M, int Mp, int nc, float* q, double* dst, cudaStream_t st);
+template <class OutP> void k_tdot(OutP X, OutP Y, int M, int Mp, int n, double* dst, cudaStream_t st);
 // probit: E from red[RED_ELL], dsf2's data part from red[RED_SUMH], dnoise = 0.
 // hutch_K > 0: tr(K~T) and tr(P Kuu) from the Hutchinson sums over hutch_K probes.
 void k_terms_finalize(const double* red, const double* acc_ell, const float* sf2, const float* noise,

@@ -74,6 +74,7 @@ struct svgp_handle {
   int tc_kmin[TT_COUNT] = {0};
   bool may_split[TT_COUNT] = {false};
   int slot_base[TT_COUNT] = {0}, slot_cap[TT_COUNT] = {0}, item_cap[TT_COUNT] = {0};
+  int rect_np[TT_COUNT] = {0};   // output columns of the tall-skinny table's current schedule
   KufTC kt;         // split coordinates for the tensor-core Kuf generator
   bool tc_kuf;      // Psi and W run on the tensor-core Kuf-producer kernels
   std::vector<void*> allocs;
@@ -226,6 +227,33 @@ bool schedule_table(svgp_handle* h, int tab, int kmin) {
   return true;
 }
 
+// Schedule of a tall-skinny table for output columns [0, Np) (whole tiles).
+// Host-synchronous when Np changes: the handle's streams are drained before
+// the device tables are rewritten.
+bool rect_schedule(svgp_handle* h, int tab, int Np) {
+  if (h->rect_np[tab] == Np) return true;
+  if (cudaStreamSynchronize(h->st) != cudaSuccess || cudaStreamSynchronize(h->st_aux) != cudaSuccess) return false;
+  std::vector<Tile> v;
+  for (const Tile& t : h->tc_tiles[tab])
+    if (t.n0 < Np) v.push_back(t);
+  // long K ranges over few output tiles: split where the cost model gains,
+  // within the workspace slots the three tall-skinny tables share (they run
+  // one after another on one stream)
+  const int kmin = (Np / 128) * (h->Mp / 128) <= h->slot_cap[tab] ? model_kmin(v, tc_num_sms()) : 0;
+  int slot = h->slot_base[tab];
+  std::vector<int> off;
+  GemmCtx& g = h->gt;
+  std::vector<TcTile> s = lpt_schedule(split_items(v, kmin, &slot), tc_num_sms(), off, nullptr);
+  if (s.size() > (size_t)h->item_cap[tab] || slot - h->slot_base[tab] > h->slot_cap[tab]) return false;
+  if (cudaMemcpy(g.tct[tab], s.data(), sizeof(TcTile) * s.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(g.toff[tab], off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return false;
+  g.nt[tab] = (int)s.size();
+  g.ncta[tab] = (int)off.size() - 1;
+  h->rect_np[tab] = Np;
+  return true;
+}
+
 bool build_ctx(svgp_handle* h, GemmCtx& g, int BM, int BN, bool sched) {
   int Mp = h->Mp;
   g.Mp = Mp;
@@ -236,7 +264,8 @@ bool build_ctx(svgp_handle* h, GemmCtx& g, int BM, int BN, bool sched) {
       make_tiles(Mp, BM, BN, REG_FULL, K_M0_END),  make_tiles(Mp, BM, BN, REG_UPPER, K_N0_END),
       make_tiles(Mp, BM, BN, REG_LOWER, K_N0_M1),  make_tiles(Mp, BM, BN, REG_FULL, K_0_M1),
       make_tiles(Mp, BM, BN, REG_LOWER, K_0_N1),   make_tiles(Mp, BM, BN, REG_UPPER, K_ALL),
-      make_tiles(Mp, BM, BN, REG_FULL, K_ALL)};
+      make_tiles(Mp, BM, BN, REG_FULL, K_ALL),     make_tiles(Mp, BM, BN, REG_FULL, K_0_M1),
+      make_tiles(Mp, BM, BN, REG_FULL, K_M0_END),  make_tiles(Mp, BM, BN, REG_FULL, K_ALL)};
   if (!sched) {
     for (int t = 0; t < TT_COUNT; ++t)
       if (!upload_tiles(h, tabs[t], &g.tt[t], &g.nt[t])) return false;
@@ -246,6 +275,9 @@ bool build_ctx(svgp_handle* h, GemmCtx& g, int BM, int BN, bool sched) {
   // outputs) may split long tiles, with the threshold of the cost model
   // until svgp_set_split chooses another
   int slot = 0;
+  // the tall-skinny tables share one slot range: split schedules for up to
+  // four output column tiles (Np <= 512)
+  const int rect_cap = (Mp / 128) * std::min(Mp / 128, 4);
   for (int t = 0; t < TT_COUNT; ++t) {
     if (t == TT_PSI) {
       if (!upload_tiles(h, tabs[t], &g.tt[t], &g.nt[t])) return false;
@@ -254,9 +286,9 @@ bool build_ctx(svgp_handle* h, GemmCtx& g, int BM, int BN, bool sched) {
     h->tc_tiles[t] = tabs[t];
     h->may_split[t] = t == TT_SYM_IN || t == TT_LUPD || t == TT_OUT;
     h->slot_base[t] = slot;
-    h->slot_cap[t] = h->may_split[t] ? split_capacity(tabs[t]) : 0;
+    h->slot_cap[t] = h->may_split[t] ? split_capacity(tabs[t]) : (t >= TT_RL ? rect_cap : 0);
     h->item_cap[t] = (int)tabs[t].size() + h->slot_cap[t];
-    slot += h->slot_cap[t];
+    if (t < TT_RL || t == TT_COUNT - 1) slot += h->slot_cap[t];
     if (!dalloc(h, &g.tct[t], sizeof(TcTile) * std::max(h->item_cap[t], 1)) ||
         !dalloc(h, &g.toff[t], sizeof(int) * (size_t)(tc_num_sms() + 1)))
       return false;
@@ -266,7 +298,7 @@ bool build_ctx(svgp_handle* h, GemmCtx& g, int BM, int BN, bool sched) {
                     dalloc(h, &g.kflag, sizeof(int) * 2 * (size_t)slot)))
     return false;
   for (int t = 0; t < TT_COUNT; ++t) {
-    if (t == TT_PSI) continue;
+    if (t == TT_PSI || t >= TT_RL) continue;       // the tall-skinny tables are scheduled per call
     const int kmin = h->may_split[t] ? model_kmin(tabs[t], tc_num_sms()) : 0;
     if (!schedule_table(h, t, kmin)) return false;
   }
@@ -557,6 +589,59 @@ void gap_compute(svgp_handle* h, const int* skip) {
   simt_gemm(h->gs, TT_FULL, h->gapN, h->gapN, EpiDotPsi{h->Psi, Mp, M, h->red + RED_GAPDOT, skip});
 }
 
+// Tall-skinny product of the P-free bound on the tensor cores: out^T =
+// (A X)^T over output columns [0, Np), with X given as X^T (Np rows of Mp).
+template <class OutP>
+bool rect_product(svgp_handle* h, int tab, const bf16* A, const bf16* Bt, OutP outT, int Np) {
+  if (!rect_schedule(h, tab, Np)) return false;
+  return tc_gemm(h->gt, tab, A, Bt, EpiStoreT<OutP>{outT, h->Mp});
+}
+
+// The P-free bound's products (Section 3.4) on the tensor cores in the
+// handle's operand precision: k_n^T P k_n = 2 |L^T k_n|^2 - w^T K~ w with
+// w = T k_n for blocks of up to Mp points, and the three probe chains of
+// the traces.  Factors are kept transposed in the handle's idle M x M operand
+// buffers (Y, V, S, P_lo, GP_lo).  One column count Np for every product of
+// the call (the larger of the point block and the probe block), so that the
+// schedules are rewritten only when B or K changes between calls.
+template <class OutP, class Conv>
+bool hutch_tc(svgp_handle* h, const svgp_params* p, const svgp_batch* b, const float* probes, int K, Conv cv) {
+  cudaStream_t st = h->st;
+  const int M = h->M, Mp = h->Mp;
+  OutP Kt = cv(h->GP_lo), Xt = cv(h->S), Ut = cv(h->Y), Wt = cv(h->V), Zt = cv(h->P_lo);
+  const bf16* Lh = H(h->L_lo);
+  const bf16* Lth = H(h->Lt_lo);
+  const bf16* Kuh = H(h->Kuu_lo);
+  const bf16* Kth = H(h->GP_lo);
+  auto hi = [](void* q) { return reinterpret_cast<const bf16*>(q); };
+  k_kt_op(h->Kuu_f, p->s, M, Mp, Kt, st);
+  const int Np = std::max((std::min(Mp, b->B) + 127) / 128, (K + 127) / 128) * 128;
+  for (int c0 = 0; c0 < b->B; c0 += Mp) {
+    const int nc = std::min(Mp, b->B - c0);
+    k_kuf_t(h->Zs, h->Xs, M, Mp, h->D, p->sf2, c0, nc, Np, Xt, st);
+    if (!rect_product(h, TT_RLT, Lth, hi(h->S), Ut, Np) ||          // u = L^T k
+        !rect_product(h, TT_RL, Lh, hi(h->Y), Wt, Np) ||            // w = L u
+        !rect_product(h, TT_RF, Kth, hi(h->V), Zt, Np))             // K~ w
+      return false;
+    k_rowq(Ut, Wt, Zt, M, Mp, nc, h->colsum + c0, h->red + RED_PPSI, st);
+  }
+  // traces: y = L z, <y, K~ y>;  c = T Kuu z, <z, c>;  f = T K~ c, <z, f>
+  OutP Pt = cv(h->S), Y = cv(h->Y), V = cv(h->V), E = cv(h->P_lo);
+  k_probes_t(probes, M, Mp, K, Np, Pt, st);
+  if (!rect_product(h, TT_RL, Lh, hi(h->S), Y, Np) || !rect_product(h, TT_RF, Kth, hi(h->Y), V, Np))
+    return false;
+  k_tdot(Y, V, M, Mp, K, h->red + RED_HKT, st);
+  if (!rect_product(h, TT_RF, Kuh, hi(h->S), Y, Np) || !rect_product(h, TT_RLT, Lth, hi(h->Y), V, Np) ||
+      !rect_product(h, TT_RL, Lh, hi(h->V), Y, Np))
+    return false;
+  k_tdot(Pt, Y, M, Mp, K, h->red + RED_HW1, st);
+  if (!rect_product(h, TT_RF, Kth, hi(h->Y), V, Np) || !rect_product(h, TT_RLT, Lth, hi(h->V), E, Np) ||
+      !rect_product(h, TT_RL, Lh, hi(h->P_lo), V, Np))
+    return false;
+  k_tdot(Pt, V, M, Mp, K, h->red + RED_HX4, st);
+  return true;
+}
+
 bool valid_ng_args(const svgp_params* p, const float* L_inout, const float* gamma_dev, int max_iters) {
   return p && p->Z && p->ell && p->sf2 && p->s && L_inout && gamma_dev && max_iters >= 0 && max_iters <= 100000;
 }
@@ -761,14 +846,24 @@ svgp_status svgp_bound_hutchinson(svgp_handle* h, const svgp_params* p, const sv
   float* bufA = h->hut;
   float* bufB = h->hut + (size_t)M * SVGP_HUTCH_KMAX;
   float* bufC = h->hut + 2 * (size_t)M * SVGP_HUTCH_KMAX;
-  k_hutch_data(h->Lf, h->Kuu_f, p->s, M, Mp, h->Zs, h->Xs, h->D, b->B, p->sf2, p->m, !h->unprec, bufA, bufB, bufC,
-               SVGP_HUTCH_KMAX, h->v, h->colsum, h->red, st);
+  // v = P m~ from vector products (O(M^2)); the B and K column blocks on
+  // the tensor cores in the handle's operand precision, else FP32 SIMT
+  // (the probe block must fit the transposed M x M buffers: K <= Mp)
+  const bool tc = h->mode != MODE_F32 && (K + 127) / 128 * 128 <= Mp;
+  k_hutch_data(h->Lf, h->Kuu_f, p->s, M, Mp, h->Zs, h->Xs, h->D, tc ? 0 : b->B, p->sf2, p->m, !h->unprec, bufA,
+               bufB, bufC, SVGP_HUTCH_KMAX, h->v, h->colsum, h->red, st);
+  if (tc) {
+    const bool ok = h->mode == MODE_BF16
+                        ? hutch_tc<bf16*>(h, p, b, probes, K, [](void* q) { return H(q); })
+                        : hutch_tc<SplitPtr>(h, p, b, probes, K, [h](void* q) { return SP(h, q); });
+    if (!ok) return fail(h, SVGP_ERR_CUDA, "bound_hutchinson: tall-skinny schedule or launch failed");
+  }
   k_gemv(h->Kuu_f, Mp, M, h->v, 1.f, nullptr, 0.f, h->w, h->v, h->red + RED_QUAD, st);     // w = Kuu v, v^T w
   if (!(h->tc_kuf && tc_kuf_gemv(h->kt.XR, b->B, h->kt.ZK, M, h->v, h->mu, true, h->errword, st)))
     k_mu(h->Zs, h->Xs, M, b->B, h->D, p->sf2, h->v, h->mu, st);                          // mu = Kfu v
   if (h->probit) k_pointwise_probit(b->y, h->mu, h->colsum, p->sf2, b->B, h->gh, h->g, h->hn, h->red, st);
   else k_pointwise_gauss(b->y, h->mu, p->noise, b->B, h->g, h->red, st);
-  k_hutchinson(h->Lf, h->Kuu_f, p->s, M, Mp, probes, K, bufA, bufB, bufC, h->red, st);
+  if (!tc) k_hutchinson(h->Lf, h->Kuu_f, p->s, M, Mp, probes, K, bufA, bufB, bufC, h->red, st);
   k_terms_finalize(h->red, h->acc_ell, p->sf2, p->noise, p->ell, h->M, h->D, b->B, b->N, h->probit, K, terms_dev,
                    nullptr, nullptr, nullptr, h->errword, h->st);
   return check_launch(h, "svgp_bound_hutchinson");
