@@ -269,6 +269,8 @@ KIND_SOURCES = {
 }
 NCU_DRAM_BYTES = {
     ("gp_sample_regression", "bf16x3", "w"): (18827008, "490ebd8a82040285"),
+    ("gp_sample_regression", "bf16x3", "psi"): (824320, "91095c1ba33701de"),
+    ("gp_sample_regression", "bf16x3", "vt"): (43030016, "e76181862f65513f"),
 }
 
 
