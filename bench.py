@@ -268,7 +268,7 @@ KIND_SOURCES = {
     "vt": ["gemm_tc.cu", "epi_tc.cuh", "tc_common.cuh", "common.cuh"],
 }
 NCU_DRAM_BYTES = {
-    ("gp_sample_regression", "bf16x3", "w"): (18827008, "490ebd8a82040285"),
+    ("gp_sample_regression", "bf16x3", "w"): (18850560, "b8360b295b029146"),
     ("gp_sample_regression", "bf16x3", "psi"): (824320, "91095c1ba33701de"),
     ("gp_sample_regression", "bf16x3", "vt"): (43030016, "e76181862f65513f"),
 }

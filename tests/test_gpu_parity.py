@@ -215,6 +215,21 @@ def test_bound_hutchinson_likelihoods_and_batches(prec, lik, precond, B):
     m.close()
 
 
+def test_bound_hutchinson_more_probes_than_padded_rows():
+    """K = 200 probes with M = 100 (padded to 128): the probe block does not
+    fit the transposed M x M buffers, so a BF16X3 handle takes the FP32 path;
+    the result still matches the oracle with the same probes."""
+    M, K = 100, 200
+    p, X, y, N = small_case(M, 3, 150, 11)
+    probes = np.where(np.random.default_rng([K, 11]).uniform(size=(M, K)) < 0.5, -1.0, 1.0)
+    ref = O.bound(p, X, y, N, probes=probes)
+    m = _model(p, M, 3, 150, "bf16x3")
+    t = m.bound_hutchinson(_dev(X), _dev(y), N, torch.tensor(probes, dtype=torch.float32)).cpu().numpy()
+    assert m.sync_status() == 0
+    assert abs(t[0] - ref["F"]) <= TOL["bf16x3"]["bound"] * abs(ref["F"]), (t[0], ref["F"])
+    m.close()
+
+
 def test_bound_hutchinson_exact_terms_agree_with_bound_at_M1024():
     """At M = 1024 with 200 points, the P-free path's exact terms (sum of
     squared errors, sum of sigma_n^2, the quadratic term, log-determinants)
