@@ -268,8 +268,8 @@ KIND_SOURCES = {
     "vt": ["gemm_tc.cu", "epi_tc.cuh", "tc_common.cuh", "common.cuh"],
 }
 NCU_DRAM_BYTES = {
-    ("gp_sample_regression", "bf16x3", "w"): (18850560, "b8360b295b029146"),
-    ("gp_sample_regression", "bf16x3", "psi"): (824320, "91095c1ba33701de"),
+    ("gp_sample_regression", "bf16x3", "w"): (18829824, "d703414dc4f9a8ac"),
+    ("gp_sample_regression", "bf16x3", "psi"): (825344, "2eef7b94d76476ba"),
     ("gp_sample_regression", "bf16x3", "vt"): (43030016, "e76181862f65513f"),
 }
 
@@ -296,6 +296,53 @@ def algorithmic_flops(M, B):
     M3 = float(M) ** 3
     return {"vt": M3, "sym": M3 / 3, "lupd": M3 / 3, "ls": M3, "out": M3 / 3,
             "psi": float(M) * (M + 1) * B, "w": 2.0 * M * M * B}
+
+
+# launches of each contraction kind in one training step (t* = 1, Gaussian)
+STEP_LAUNCHES = {"vt": 3, "sym": 3, "lupd": 1, "ls": 2, "out": 2, "psi": 1, "w": 1}
+
+
+def step_flops(M, B):
+    """Algorithmic FLOPs of the contractions of one training step:
+    7 M^3 + M (M + 1) B + 2 M^2 B."""
+    f = algorithmic_flops(M, B)
+    return sum(f[k] * n for k, n in STEP_LAUNCHES.items())
+
+
+def validate_group(models, batches, Ms, prec):
+    """Relative errors vs the FP64 oracle of one member of each inducing-set
+    size, at the state the timed steps left it in (bound and every gradient
+    block at that member's batch), against the stated tolerances."""
+    import torch
+
+    from oracle import rsvgp as O
+
+    tb, tg = (1e-6, 1e-4) if prec == "fp32" else (1e-3, 1e-2)
+    out = {"tolerance": {"bound": tb, "grad": tg}, "members": {}}
+    ok = True
+    for M in sorted(set(int(v) for v in Ms)):
+        g = int(np.flatnonzero(Ms == M)[0])
+        m = models[g]
+        Xd, yd, N = batches[g]
+        F = float(m.backward(Xd, yd, N)[0])
+        torch.cuda.synchronize()
+        p = {k: m.get(k).double().cpu().numpy() for k in ("Z", "ell", "m", "s")}
+        p["sf2"] = float(m.get("sf2")[0])
+        p["noise"] = float(m.get("noise")[0])
+        p["L"] = m.L.double().cpu().numpy()
+        X, y = Xd.double().cpu().numpy(), yd.double().cpu().numpy()
+        ref = O.bound(p, X, y, N)["F"]
+        gr = O.grads(p, X, y, N)
+        e = {"index": g, "bound": abs(F - ref) / abs(ref), "status": m.sync_status()}
+        ok = ok and e["bound"] <= tb and e["status"] == 0
+        for k in ("Z", "ell", "sf2", "noise", "m", "s"):
+            a = m.grad_of(k).double().cpu().numpy().reshape(np.shape(gr[k]))
+            nb = float(np.linalg.norm(gr[k]))
+            e[k] = float(np.linalg.norm(a - gr[k]) / nb) if nb > 0 else float(np.linalg.norm(a))
+            ok = ok and e[k] <= tg
+        out["members"][str(M)] = e
+    out["meets_gates"] = ok
+    return out
 
 
 def run_group(args):
@@ -354,6 +401,13 @@ def run_group(args):
     tot_ms, value = reduce_timing(tot, args.steps, ws)
     status = group.sync_status()
     wl = WORKLOADS["group64"]
+    # whole-step throughput of the contractions over all members, against the
+    # BF16 burst peak divided by the MMAs per product
+    flops = sum(step_flops(int(M), B) for M in Ms)
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(pk_path)) if os.path.exists(pk_path) else {"bf16_tflops": 1900.0}
+    passes = MMA_PASSES.get(args.prec, {}).get("w", 1)
+    achieved = flops / (tot_ms / args.steps * 1e-3) / 1e12
     line = {"metric": wl["metric"], "value": value, "unit": "group steps/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.prec != "fp32" else "f32",
@@ -361,7 +415,16 @@ def run_group(args):
                                             "M_counts": {int(k): int((Ms == k).sum()) for k in sorted(set(Ms))},
                                             "precision": args.prec, "graph": True,
                                             "l2": "flushed between timed steps"},
-            "clocks": clocks, "device_status": status}
+            "clocks": clocks, "device_status": status,
+            "step_throughput": {"algorithmic_flops_per_step": flops, "achieved_tflops": achieved,
+                                "formula": "sum over members of 7 M^3 + M (M + 1) B + 2 M^2 B"}}
+    if args.prec != "fp32" and peaks.get("bf16_tflops"):
+        peak = peaks["bf16_tflops"] / passes
+        src = "measured burst BF16 (MEASURED_PEAKS.json)" if os.path.exists(pk_path) else "fallback burst BF16"
+        line["step_throughput"].update(peak_tflops=peak, frac=achieved / peak,
+                                       peak_source="%s / %d MMA passes per product" % (src, passes))
+    if not args.no_validate and rank == 0:
+        line["validity"] = validate_group(models, batches, Ms, args.prec)
     if rank == 0:
         print(json.dumps(line), flush=True)
     group.close()

@@ -142,30 +142,16 @@ psi_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // z, row role
     fence_after();
     const uint64_t ra = sw128_desc(smem_u32(sRowA));
     const uint64_t rb = sw128_desc(smem_u32(sRowB));
-    int d = 0, mn = 0;
-    long long idle_since = clock64();
+    // ring positions: the coordinate slot of the next exponent MMA and the
+    // generated slot of the next main MMA (with phases); the main MMA is
+    // polled first, and the time limit and the abort flag every 64 idle polls
+    int d = 0, mn = 0, cs = 0, cph = 0, gsl = 0, gph = 0, idle = 0;
+    long long idle_since = 0;
     while (ok && mn < nkb) {
       bool progressed = false;
-      if (d < nkb && mbar_test(BAR(B_LD + d % SC), (d / SC) & 1) &&
-          mbar_test(BAR(B_SEMPTY + (d & 1)), ((d >> 1) & 1) ^ 1)) {
+      if (mn < d && mbar_test(BAR(B_GEN + gsl), gph)) {
         fence_after();
-        *consumed = d + 1;
-        const int b = d & 1;
-        const uint64_t kd = sw128_desc(smem_u32(cring + (d % SC) * CT));
-#pragma unroll
-        for (int kk = 0; kk < KB / 16; ++kk) {
-          const uint64_t o = (uint64_t)(kk * 2);
-          mma_bf16(tmem + G::S_A(b), ra + o, kd + o, ID_DIST, kk != 0);
-          if (!diag) mma_bf16(tmem + G::S_B(b), rb + o, kd + o, ID_DIST, kk != 0);
-        }
-        mma_commit(BAR(B_SFULL + b));
-        mma_commit(BAR(B_TEMPTY + d % SC));
-        ++d;
-        progressed = true;
-      }
-      if (mn < d && mbar_test(BAR(B_GEN + mn % SG), (mn / SG) & 1)) {
-        fence_after();
-        unsigned char* st = stg + (mn % SG) * G::GSTAGE;
+        unsigned char* st = stg + gsl * G::GSTAGE;
         const uint64_t ad = sw128_desc(smem_u32(st + G::OFF_GA));
         const uint64_t adl = sw128_desc(smem_u32(st + G::OFF_GA + GT));
         const uint64_t bd = diag ? ad : sw128_desc(smem_u32(st + G::OFF_GB));
@@ -179,12 +165,36 @@ psi_tc_kernel(const __grid_constant__ CUtensorMap tmRow,     // z, row role
             mma_bf16(tmem, adl + o, bd + o, ID_MAIN, 1);
           }
         }
-        mma_commit(BAR(B_EMPTY + mn % SG));
+        mma_commit(BAR(B_EMPTY + gsl));
+        if (++gsl == SG) { gsl = 0; gph ^= 1; }
         ++mn;
         progressed = true;
       }
-      if (progressed) idle_since = clock64();
-      else if (clock64() - idle_since > WAIT_CYCLES || *abort_flag) ok = false;
+      if (d < nkb && mbar_test(BAR(B_LD + cs), cph) &&
+          mbar_test(BAR(B_SEMPTY + (d & 1)), ((d >> 1) & 1) ^ 1)) {
+        fence_after();
+        *consumed = d + 1;
+        const int b = d & 1;
+        const uint64_t kd = sw128_desc(smem_u32(cring + cs * CT));
+#pragma unroll
+        for (int kk = 0; kk < KB / 16; ++kk) {
+          const uint64_t o = (uint64_t)(kk * 2);
+          mma_bf16(tmem + G::S_A(b), ra + o, kd + o, ID_DIST, kk != 0);
+          if (!diag) mma_bf16(tmem + G::S_B(b), rb + o, kd + o, ID_DIST, kk != 0);
+        }
+        mma_commit(BAR(B_SFULL + b));
+        mma_commit(BAR(B_TEMPTY + cs));
+        if (++cs == SC) { cs = 0; cph ^= 1; }
+        ++d;
+        progressed = true;
+      }
+      if (progressed) {
+        idle = 0;
+      } else if ((++idle & 63) == 0) {
+        const long long now = clock64();
+        if (idle == 64) idle_since = now;
+        else if (now - idle_since > WAIT_CYCLES || *abort_flag) ok = false;
+      }
     }
     if (!ok) *abort_flag = 1;
     mma_commit(BAR(B_ACC));

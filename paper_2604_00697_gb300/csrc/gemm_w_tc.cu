@@ -200,42 +200,32 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
     // Per n-block an event-driven loop: the exponent MMA of k-block d goes out
     // as soon as its coordinates have landed and its TMEM buffer is free, ahead
     // of the main MMA of earlier k-blocks (which waits for their generated
-    // tiles); then the epilogue exponents T.
+    // tiles); then the epilogue exponents T.  Each poll tries the main MMA
+    // first; the ring positions are running counters (no divisions in the
+    // polling loop, whose speed shows in the launch time).
     bool ok = true;
     int g = 0, lt = 0;
+    // ring positions carried across n-blocks: the exponent MMA's TMA slot,
+    // the main MMA's TMA slot and its generated slot (with phases)
+    int xs = 0, xph = 0, ms = 0, gsl = 0, gph = 0;
     for (int nb = blockIdx.x; nb < wa.nblk && ok; nb += gridDim.x, ++lt) {
       if (!mbar_wait(BAR(B_TILE), lt & 1)) { ok = false; break; }
       // the epilogue of the previous n-block has read the accumulators and T
       if (lt > 0 && !mbar_wait(BAR(B_EDONE), (lt - 1) & 1)) { ok = false; break; }
       fence_after();
       const uint64_t ra = sw128_desc(smem_u32(sXR));
-      int d = 0, mn = 0;
-      long long idle_since = clock64();
+      int d = 0, mn = 0, idle = 0;
+      long long idle_since = 0;
       while (mn < nkb) {
         bool progressed = false;
-        const int gd = g + d, gm = g + mn;
-        if (d < nkb && mbar_test(BAR(B_LD + gd % ST), (gd / ST) & 1) &&
-            mbar_test(BAR(B_SEMPTY + (gd & 1)), ((gd >> 1) & 1) ^ 1)) {
-          fence_after();
-          *consumed = gd + 1;
-          const uint64_t kd = sw128_desc(smem_u32(stgT + (gd % ST) * G::TSTAGE));
-#pragma unroll
-          for (int kk = 0; kk < KB / 16; ++kk) {
-            const uint64_t o = (uint64_t)(kk * 2);
-            mma_bf16(tmem + G::SB(gd & 1), ra + o, kd + o, ID_DIST, kk != 0);
-          }
-          mma_commit(BAR(B_SFULL + (gd & 1)));
-          ++d;
-          progressed = true;
-        }
         // The first main MMA of an n-block overwrites the accumulator: it waits
         // for that k-block's generated operand, which the transform warps
         // produce only after their epilogue of the previous n-block has read
         // the accumulator and the exponents T.
-        if (mn < d && mbar_test(BAR(B_GEN + gm % SG), (gm / SG) & 1)) {
+        if (mn < d && mbar_test(BAR(B_GEN + gsl), gph)) {
           fence_after();
-          unsigned char* st = stgT + (gm % ST) * G::TSTAGE;
-          unsigned char* gs = stgG + (gm % SG) * G::GSTAGE;
+          unsigned char* st = stgT + ms * G::TSTAGE;
+          unsigned char* gs = stgG + gsl * G::GSTAGE;
           const uint64_t bd = sw128_desc(smem_u32(gs));
           const uint64_t bdl = sw128_desc(smem_u32(gs + GT));
 #pragma unroll
@@ -252,13 +242,37 @@ w_tc_kernel(const __grid_constant__ CUtensorMap tmZR, const __grid_constant__ CU
               }
             }
           }
-          mma_commit(BAR(B_TEMPTY + gm % ST));
-          mma_commit(BAR(B_GEMPTY + gm % SG));
+          mma_commit(BAR(B_TEMPTY + ms));
+          mma_commit(BAR(B_GEMPTY + gsl));
+          if (++ms == ST) ms = 0;
+          if (++gsl == SG) { gsl = 0; gph ^= 1; }
           ++mn;
           progressed = true;
         }
-        if (progressed) idle_since = clock64();
-        else if (clock64() - idle_since > WAIT_CYCLES || *abort_flag) { ok = false; break; }
+        const int gd = g + d;
+        if (d < nkb && mbar_test(BAR(B_LD + xs), xph) &&
+            mbar_test(BAR(B_SEMPTY + (gd & 1)), ((gd >> 1) & 1) ^ 1)) {
+          fence_after();
+          *consumed = gd + 1;
+          const uint64_t kd = sw128_desc(smem_u32(stgT + xs * G::TSTAGE));
+#pragma unroll
+          for (int kk = 0; kk < KB / 16; ++kk) {
+            const uint64_t o = (uint64_t)(kk * 2);
+            mma_bf16(tmem + G::SB(gd & 1), ra + o, kd + o, ID_DIST, kk != 0);
+          }
+          mma_commit(BAR(B_SFULL + (gd & 1)));
+          if (++xs == ST) { xs = 0; xph ^= 1; }
+          ++d;
+          progressed = true;
+        }
+        // the time limit and the abort flag are checked every 64 idle polls
+        if (progressed) {
+          idle = 0;
+        } else if ((++idle & 63) == 0) {
+          const long long now = clock64();
+          if (idle == 64) idle_since = now;
+          else if (now - idle_since > WAIT_CYCLES || *abort_flag) { ok = false; break; }
+        }
       }
       g += nkb;
       if (!ok) break;
