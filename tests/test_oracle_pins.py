@@ -557,3 +557,62 @@ def test_training_driver_improves_bound_snelson_like():
     out, trace = O.train(p0, lambda t: (X, y), prob.N, steps=200, lr=5e-3, train_Z=False)
     assert np.all(np.isfinite(trace))
     assert trace[-1] > trace[0] + 50.0
+
+
+def test_softplus_pair_closed_forms():
+    """Positivity transform: softplus(0) = ln 2, softplus(x) -> x for large x
+    (softplus(x) - x = log1p(e^-x)), softplus_inv inverts it, and its
+    derivative (by central differences) is the logistic sigmoid, the factor
+    the Adam chain rule uses."""
+    assert O.softplus(0.0) == pytest.approx(math.log(2.0), abs=1e-15)
+    for x in (20.0, 40.0):
+        assert O.softplus(x) - x == pytest.approx(math.exp(-x), rel=1e-6)
+    x = np.linspace(-12.0, 12.0, 97)
+    np.testing.assert_allclose(O.softplus_inv(O.softplus(x)), x, rtol=1e-10, atol=1e-10)
+    y = np.array([1e-6, 1e-3, 0.5, 1.0, 7.0])
+    np.testing.assert_allclose(O.softplus(O.softplus_inv(y)), y, rtol=1e-12)
+    h = 1e-6
+    fd = (O.softplus(x + h) - O.softplus(x - h)) / (2 * h)
+    np.testing.assert_allclose(fd, 1.0 / (1.0 + np.exp(-x)), rtol=1e-8, atol=1e-10)
+
+
+def test_adam_first_step_has_the_learning_rate_as_its_length():
+    """Kingma & Ba, Section 2.1: with bias correction the first step is
+    lr * g / (|g| + eps), so its length is lr (to eps) whatever the gradient's
+    scale; with a constant gradient every later step has the same length.
+    Ascent: the step follows the gradient's sign."""
+    lr = 1e-2
+    for scale in (1e-4, 1.0, 1e4):
+        g = scale * np.array([1.0, -2.0, 0.5])
+        raw = {"m": np.zeros(3)}
+        st = {}
+        for t in range(1, 6):
+            new = O.adam_update(raw, {"m": g}, st, lr)
+            step = new["m"] - raw["m"]
+            np.testing.assert_allclose(step, lr * np.sign(g), rtol=1e-6 if scale > 1e-3 else 1e-3)
+            raw = new
+
+
+def test_adam_chain_rule_through_softplus_matches_finite_differences():
+    """A positive parameter is optimised in raw (softplus) space: Adam fed
+    with the gradient with respect to the constrained value must take the
+    same steps as Adam on an unconstrained parameter fed with the gradient
+    with respect to the raw value by central differences of F(softplus(raw)).
+    F(c) = -(c - 2)^2 - 0.3 c^3 is maximised from several starting points."""
+    F = lambda c: -(c - 2.0) ** 2 - 0.3 * c ** 3
+    dF = lambda c: -2.0 * (c - 2.0) - 0.9 * c ** 2
+    h = 1e-6
+    for r0 in (-3.0, 0.1, 2.5):
+        a = {"sf2": np.array(r0)}
+        b = {"m": np.array(r0)}
+        sa, sb = {}, {}
+        for t in range(25):
+            ga = {"sf2": dF(O.softplus(a["sf2"]))}
+            gb = {"m": (F(O.softplus(b["m"] + h)) - F(O.softplus(b["m"] - h))) / (2 * h)}
+            a = O.adam_update(a, ga, sa, 5e-2)
+            b = O.adam_update(b, gb, sb, 5e-2)
+            assert float(a["sf2"]) == pytest.approx(float(b["m"]), abs=1e-7)
+        c = float(O.constrain(a)["sf2"])
+        # the iterates approach the maximiser of F on c > 0
+        cstar = (-2.0 + math.sqrt(4.0 + 4 * 0.9 * 4.0)) / (2 * 0.9)
+        assert abs(dF(c)) < abs(dF(O.softplus(r0))) or abs(c - cstar) < 0.05
