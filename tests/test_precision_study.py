@@ -126,3 +126,48 @@ def test_split_bf16_meets_the_gates(converged_case):
 def test_fp8_e4m3_misses_every_gate(converged_case):
     eb, ez, es = _errors(converged_case, _e4m3_rows)
     assert eb > 1e-3 and ez > 0.1 and es > 0.1
+
+
+def _split3(x):
+    x = np.asarray(x, np.float64)
+    h = _bf16(x)
+    lo = _bf16(x - h)
+    return h + lo + _bf16(x - h - lo)
+
+
+def test_kuu_split_dominates_at_an_ill_conditioned_state():
+    """The largest member of the 64-SVGP group workload (M = 2048 inducing
+    points at its own 2048 batch points, D = 8, ell = 1, s~ = 1e-4):
+    cond(K~) is about 3e3 (186 for the headline workload).  At its converged
+    state the hi/lo chain leaves dZ near the 1e-2 gate, and the rounding of
+    Kuu in L^T K~ alone carries almost all of it: with a third BF16 plane for
+    that operand only, dZ drops about six-fold."""
+    import svgp_synth as S
+
+    prob = S.sinusoid_regression(seed=100, B=2048, M=2048, D=8)
+    X, y = prob.batch(0)
+    M, D = 2048, 8
+    s = np.full(M, 1e-4)
+    Kt = O.se_ard(prob.Z0, prob.Z0, np.ones(D), 1.0) + np.diag(s)
+    w = np.linalg.eigvalsh(Kt)
+    assert 2e3 < w[-1] / w[0] < 5e3
+    p = dict(Z=prob.Z0, ell=np.ones(D), sf2=1.0, noise=1.0, m=0.1 * np.random.default_rng(1).normal(size=M),
+             s=s, L=np.linalg.cholesky(np.linalg.inv(Kt)))
+    ref = O.grads(p, X, y, prob.N)
+
+    def dz(site_rnd):
+        cnt = [0]
+
+        def r(a):
+            i = cnt[0]
+            cnt[0] += 1
+            return site_rnd(i, a)
+        return rel(_chain_grads(p, X, y, prob.N, r)[1], ref["Z"])
+
+    # rounding sites in evaluation order: 0 L, 1 Kuu, 2 L^T K~, 3 2I - A1, ...
+    every = dz(lambda i, a: _split(a))
+    kuu_only = dz(lambda i, a: _split(a) if i == 1 else np.asarray(a, np.float64))
+    kuu_3 = dz(lambda i, a: _split3(a) if i == 1 else _split(a))
+    assert 3e-3 < every < 1e-2
+    assert kuu_only > 0.8 * every
+    assert kuu_3 < every / 4
