@@ -65,9 +65,16 @@ typedef enum { SVGP_LIK_GAUSSIAN = 0, SVGP_LIK_BERNOULLI_PROBIT = 1 } svgp_lik;
  * products grows like 2^-9 * cond(K~)).  SVGP_BF16X3: the same tensor-core
  * kernels with every M x M operand held as an unevaluated sum hi + lo of two
  * BF16 matrices and each product formed as hi*hi + hi*lo + lo*hi (three BF16
- * MMAs, FP32 accumulation; error like 2^-17 * cond(K~)).  Scalar reductions
- * are FP64 in every mode. */
-typedef enum { SVGP_FP32 = 0, SVGP_BF16 = 1, SVGP_BF16X3 = 2 } svgp_prec;
+ * MMAs, FP32 accumulation; error like 2^-17 * cond(K~)).  SVGP_BF16X3K:
+ * SVGP_BF16X3 with Kuu held as three BF16 planes (hi + lo + lo2, about 2^-26)
+ * where it is the operand of L^T K~ (the preconditioner's A1 = L^T K~ L of
+ * Section 3.2 and the NG update's A of Eq. (6)), formed as
+ * L_hi (K_hi + K_lo + K_lo2) + L_lo (K_hi + K_lo) (five MMAs).  A1 is close
+ * to I near the fixed point and the rounding of Kuu there dominates the
+ * gradient error once cond(K~) reaches a few thousand; the other products
+ * stay hi/lo.  The handle holds one more M x M BF16 plane.  Scalar
+ * reductions are FP64 in every mode. */
+typedef enum { SVGP_FP32 = 0, SVGP_BF16 = 1, SVGP_BF16X3 = 2, SVGP_BF16X3K = 3 } svgp_prec;
 
 typedef struct {
   int M;              /* number of inducing points, 1 <= M <= 8192              */

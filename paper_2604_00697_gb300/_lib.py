@@ -27,6 +27,7 @@ SVGP_LIK_BERNOULLI_PROBIT = 1
 SVGP_FP32 = 0
 SVGP_BF16 = 1
 SVGP_BF16X3 = 2
+SVGP_BF16X3K = 3
 
 TERMS = ["F", "E", "KL", "trKT", "trPKuu", "quad", "logdetT", "sqerr", "sumvar", "logdetS", "nclamp"]
 SVGP_NTERMS = len(TERMS)

@@ -51,6 +51,12 @@ struct SplitPtr {
   bf16* hi;
   bf16* lo;
 };
+// three planes, x ~ hi + lo + lo2 (rounding about 2^-26 of |x|)
+struct Split3Ptr {
+  bf16* hi;
+  bf16* lo;
+  bf16* lo2;
+};
 
 __device__ __forceinline__ void put(float* p, size_t i, float x) { p[i] = x; }
 __device__ __forceinline__ void put(bf16* p, size_t i, float x) { p[i] = __float2bfloat16_rn(x); }
@@ -58,6 +64,14 @@ __device__ __forceinline__ void put(const SplitPtr& p, size_t i, float x) {
   bf16 h = __float2bfloat16_rn(x);
   p.hi[i] = h;
   p.lo[i] = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+__device__ __forceinline__ void put(const Split3Ptr& p, size_t i, float x) {
+  const bf16 h = __float2bfloat16_rn(x);
+  const float r = x - __bfloat162float(h);
+  const bf16 l = __float2bfloat16_rn(r);
+  p.hi[i] = h;
+  p.lo[i] = l;
+  p.lo2[i] = __float2bfloat16_rn(r - __bfloat162float(l));
 }
 // Four consecutive elements from i (a multiple of 4): one vector store per plane.
 __device__ __forceinline__ void put4(float* p, size_t i, const float (&x)[4]) {

@@ -23,6 +23,8 @@
 
 #include <cstring>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "epi_tc.cuh"
 #include "internal.h"
@@ -37,7 +39,7 @@ constexpr int TILE_BYTES = 128 * BK * 2;    // 16 KB per 128 x 64 operand tile
 constexpr uint32_t TMEM_COLS = 2 * BN;      // two accumulators
 
 // Pipeline geometry per epilogue and operand precision (NSPLIT = 1: BF16,
-// 3: hi/lo pairs).  The mainloop streams operand tiles from L2 and its rate
+// 3: hi/lo pairs, 5: hi/lo A with hi/lo/lo2 B).  The mainloop streams operand tiles from L2 and its rate
 // is set by the bytes in flight, so the ring takes every stage that fits
 // beside the epilogue's own buffers (input slots only where the epilogue
 // reads a matrix, and its staging slots).  An epilogue that reads input
@@ -46,7 +48,7 @@ constexpr uint32_t TMEM_COLS = 2 * BN;      // two accumulators
 // gives it a third: with split operands (64 KB stages) the L^T K~ product
 // then runs 5 % faster (two stages leave the copies waiting for the MMAs).
 template <class Epi, int NSPLIT> struct Geo {
-  static constexpr int NT = NSPLIT == 1 ? 2 : 4;                 // operand tiles per stage
+  static constexpr int NT = NSPLIT == 1 ? 2 : NSPLIT == 3 ? 4 : 5;   // operand tiles per stage
   static constexpr int STAGE_BYTES = NT * TILE_BYTES;
   static constexpr int epi_bytes(int nin) {
     return 4 * ((etc::EpiSmem<Epi>::input ? nin * etc::SLOT : 0) + etc::EpiSmem<Epi>::out_slots * etc::SLOT);
@@ -74,13 +76,13 @@ template <class Epi, int NSPLIT>
 __global__ void __launch_bounds__(192, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmAl, const __grid_constant__ CUtensorMap tmBl,
-               const TcTile* __restrict__ tiles, const int* __restrict__ toff, Epi epi, int* errword,
+               const __grid_constant__ CUtensorMap tmBl2, const TcTile* __restrict__ tiles, const int* __restrict__ toff, Epi epi, int* errword,
                const __grid_constant__ etc::EpiMaps maps, float* __restrict__ kpart, int* kflag) {
   using G = Geo<Epi, NSPLIT>;
   constexpr int S = G::STAGES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  // stage s holds tiles [A_hi, B_hi, (A_lo, B_lo)]
+  // stage s holds tiles [A_hi, B_hi, (A_lo, B_lo, (B_lo2))]
   unsigned char* epi_base = base + S * G::STAGE_BYTES;
   uint64_t* bars = reinterpret_cast<uint64_t*>(epi_base + G::EPI_BYTES);
   // bars: [0,S) full, [S,2S) empty, 2S+b acc_full[b], 2S+2+b acc_empty[b], 2S+4+2w+k epilogue input
@@ -140,10 +142,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         unsigned char* st = base + s * G::STAGE_BYTES;
         tma_load_2d(smem_u32(st), &tmA, k, tl.m0, fb);
         tma_load_2d(smem_u32(st + TILE_BYTES), &tmB, k, tl.n0, fb);
-        if (NSPLIT == 3) {
+        if (NSPLIT >= 3) {
           tma_load_2d(smem_u32(st + 2 * TILE_BYTES), &tmAl, k, tl.m0, fb);
           tma_load_2d(smem_u32(st + 3 * TILE_BYTES), &tmBl, k, tl.n0, fb);
         }
+        if (NSPLIT == 5) tma_load_2d(smem_u32(st + 4 * TILE_BYTES), &tmBl2, k, tl.n0, fb);
       }
     }
     // On abort, wait (bounded) for copies that nobody consumed.
@@ -172,11 +175,17 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         for (int kk = 0; kk < BK / 16; ++kk) {
           const uint64_t o = (uint64_t)(kk * 2);
           mma_bf16(acc, ad + o, bd + o, IDESC, (kb | kk) != 0);
-          if (NSPLIT == 3) {
+          if (NSPLIT >= 3) {
             const uint64_t adl = sw128_desc(smem_u32(st + 2 * TILE_BYTES));
             const uint64_t bdl = sw128_desc(smem_u32(st + 3 * TILE_BYTES));
             mma_bf16(acc, ad + o, bdl + o, IDESC, 1);
             mma_bf16(acc, adl + o, bd + o, IDESC, 1);
+            if (NSPLIT == 5) {
+              // A_hi B_lo2 + A_lo B_lo: B to about 2^-26, A to about 2^-17
+              const uint64_t bdl2 = sw128_desc(smem_u32(st + 4 * TILE_BYTES));
+              mma_bf16(acc, ad + o, bdl2 + o, IDESC, 1);
+              mma_bf16(acc, adl + o, bdl + o, IDESC, 1);
+            }
           }
         }
         mma_commit(BAR(S + s));
@@ -460,29 +469,42 @@ bool tc_available() {
 }
 
 template <class Epi>
-bool tc_gemm(const GemmCtx& g, int tab, const bf16* A, const bf16* B, const Epi& e) {
+bool tc_gemm(const GemmCtx& g, int tab, const bf16* A, const bf16* B, const Epi& e, const bf16* B3) {
   const size_t MM = (size_t)g.Mp * g.Mp;
   const int grid = g.ncta[tab];
-  CUtensorMap ma, mb, mal, mbl;
+  CUtensorMap ma, mb, mal, mbl, mbl2;
   if (!tc_make_map(&ma, A, g.Mp, g.Mp, 128) || !tc_make_map(&mb, B, g.Mp, g.Mp, 128)) return false;
   etc::EpiMaps em;
   memset(&em, 0, sizeof(em));
   if (!epi_maps(e, em, g.Mp)) return false;
-  if (g.split) {
+  if (g.split && B3) {
+    // B's third plane B3 (B + 2 Mp^2): only the L^T K~ product takes it
+    if constexpr (std::is_same<Epi, EpiVt<SplitPtr>>::value) {
+      if (B3 != B + 2 * MM) return false;
+      if (!tc_make_map(&mal, A + MM, g.Mp, g.Mp, 128) || !tc_make_map(&mbl, B + MM, g.Mp, g.Mp, 128) ||
+          !tc_make_map(&mbl2, B3, g.Mp, g.Mp, 128))
+        return false;
+      svgp_note_launch();
+      pdl_launch(tc_gemm_kernel<Epi, 5>, grid, 192, Geo<Epi, 5>::SMEM, g.st, ma, mb, mal, mbl, mbl2, g.tct[tab], g.toff[tab], e,
+                 g.err, em, g.kpart, g.kflag);
+    } else {
+      return false;
+    }
+  } else if (g.split) {
     if (!tc_make_map(&mal, A + MM, g.Mp, g.Mp, 128) || !tc_make_map(&mbl, B + MM, g.Mp, g.Mp, 128)) return false;
     svgp_note_launch();
-    pdl_launch(tc_gemm_kernel<Epi, 3>, grid, 192, Geo<Epi, 3>::SMEM, g.st, ma, mb, mal, mbl, g.tct[tab], g.toff[tab], e, g.err, em,
-               g.kpart, g.kflag);
+    pdl_launch(tc_gemm_kernel<Epi, 3>, grid, 192, Geo<Epi, 3>::SMEM, g.st, ma, mb, mal, mbl, mbl, g.tct[tab], g.toff[tab], e, g.err,
+               em, g.kpart, g.kflag);
   } else {
     svgp_note_launch();
-    pdl_launch(tc_gemm_kernel<Epi, 1>, grid, 192, Geo<Epi, 1>::SMEM, g.st, ma, mb, ma, mb, g.tct[tab], g.toff[tab], e, g.err, em,
-               g.kpart, g.kflag);
+    pdl_launch(tc_gemm_kernel<Epi, 1>, grid, 192, Geo<Epi, 1>::SMEM, g.st, ma, mb, ma, mb, mb, g.tct[tab], g.toff[tab], e, g.err,
+               em, g.kpart, g.kflag);
   }
   return true;
 }
 
 #define SVGP_TC_INST(...) \
-  template bool tc_gemm<__VA_ARGS__>(const GemmCtx&, int, const bf16*, const bf16*, const __VA_ARGS__&);
+  template bool tc_gemm<__VA_ARGS__>(const GemmCtx&, int, const bf16*, const bf16*, const __VA_ARGS__&, const bf16*);
 SVGP_TC_INST(EpiVt<bf16*>)
 SVGP_TC_INST(EpiSym<bf16*, 0>)
 SVGP_TC_INST(EpiSym<bf16*, 1>)
@@ -508,6 +530,7 @@ void tc_init_attributes() {
   set_attr_both<EpiStore<bf16*>>();
   set_attr_both<EpiP<bf16*>>();
   set_attr_both<EpiVt<SplitPtr>>();
+  set_attr<EpiVt<SplitPtr>, 5>();
   set_attr_both<EpiSym<SplitPtr, 0>>();
   set_attr_both<EpiSym<SplitPtr, 1>>();
   set_attr_both<EpiSym<SplitPtr, 2>>();

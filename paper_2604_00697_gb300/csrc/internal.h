@@ -71,7 +71,7 @@ void tc_wait_probe(int* errword, cudaStream_t st);
 int tc_num_sms();
 void tc_init_attributes();
 template <class Epi>
-bool tc_gemm(const GemmCtx& g, int tab, const bf16* A, const bf16* B, const Epi& e);
+bool tc_gemm(const GemmCtx& g, int tab, const bf16* A, const bf16* B, const Epi& e, const bf16* B3 = nullptr);
 
 // Tensor-core Kuf-producer contractions (gemm_kuf_tc.cu): split coordinates
 // of the generator (64 BF16 per point: row role [hi, hi, lo], k role

@@ -740,6 +740,7 @@ void k_kuu(const float* Zs, int M, int Mp, int D, const float* sf2, float* Kf, O
 template void k_kuu<float*>(const float*, int, int, int, const float*, float*, float*, bool, cudaStream_t);
 template void k_kuu<bf16*>(const float*, int, int, int, const float*, float*, bf16*, bool, cudaStream_t);
 template void k_kuu<SplitPtr>(const float*, int, int, int, const float*, float*, SplitPtr, bool, cudaStream_t);
+template void k_kuu<Split3Ptr>(const float*, int, int, int, const float*, float*, Split3Ptr, bool, cudaStream_t);
 
 template <class OutP>
 void k_prep_L(const float* Lin, int M, int Mp, float* Lf, OutP Llo, OutP Ltlo, double* logdet, cudaStream_t st) {

@@ -46,6 +46,7 @@ struct svgp_handle {
   svgp_config cfg;
   int M, Mp, D, Dp, Bmax;
   int mode;       // MODE_F32 / MODE_BF16 / MODE_SPLIT (svgp_prec)
+  bool kuu3 = false;   // SVGP_BF16X3K: Kuu_lo holds a third plane for L^T K~
   cudaStream_t st;
   // second stream for Psi = Kuf Kuf^T, which depends only on the prologue:
   // forked from st after the prologue, joined before the first reader
@@ -344,6 +345,11 @@ bf16* H(void* p) { return reinterpret_cast<bf16*>(p); }
 SplitPtr SP(const svgp_handle* h, void* p) {
   return SplitPtr{reinterpret_cast<bf16*>(p), reinterpret_cast<bf16*>(p) + (size_t)h->Mp * h->Mp};
 }
+Split3Ptr SP3(const svgp_handle* h, void* p) {
+  bf16* b = reinterpret_cast<bf16*>(p);
+  const size_t MM = (size_t)h->Mp * h->Mp;
+  return Split3Ptr{b, b + MM, b + 2 * MM};
+}
 
 // Calls simt_gemm / tc_gemm with the functor built for the handle's mode.
 #define DISPATCH(h, tab, A, B, MAKE)                                                         \
@@ -357,7 +363,10 @@ void run_vt(svgp_handle* h, void* B, const float* s, const int* skip) {
   ProfScope ps(h, SVGP_PROF_VT);
   auto SPH = [h](void* p) { return SP(h, p); };
 #define MK(T, CV) EpiVt<T>{CV(h->V), h->Mp, h->Lf, s, h->M, skip}
-  DISPATCH(h, TT_VT, h->Lt_lo, B, MK);
+  if (h->kuu3 && B == h->Kuu_lo)   // K~ with its third plane: five MMAs per product
+    tc_gemm(h->gt, TT_VT, H(h->Lt_lo), H(B), MK(SplitPtr, SPH), H(B) + 2 * (size_t)h->Mp * h->Mp);
+  else
+    DISPATCH(h, TT_VT, h->Lt_lo, B, MK);
 #undef MK
 }
 
@@ -475,6 +484,7 @@ void prologue(svgp_handle* h, const svgp_params* p, const float* X, int B, const
   if (h->tc_kuf) k_kuf_prep(h->Zs, X ? h->Xs : nullptr, h->M, h->Mp, X ? B : 0, (B + 127) / 128 * 128, h->D, p->sf2, h->kt, st);
   if (h->mode == MODE_F32) k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, (float*)nullptr, false, st);
   else if (h->mode == MODE_BF16) k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, H(h->Kuu_lo), true, st);
+  else if (h->kuu3) k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, SP3(h, h->Kuu_lo), true, st);
   else k_kuu(h->Zs, h->M, h->Mp, h->D, p->sf2, h->Kuu_f, SP(h, h->Kuu_lo), true, st);
   prep_L(h, Lin, logdet_L ? h->red + RED_LOGDETL : nullptr);
 }
@@ -680,7 +690,8 @@ svgp_status svgp_create(const svgp_config* cfg, svgp_handle** out) {
   if (cfg->lik != SVGP_LIK_GAUSSIAN && cfg->lik != SVGP_LIK_BERNOULLI_PROBIT) return SVGP_ERR_INVALID_ARG;
   if (cfg->lik == SVGP_LIK_BERNOULLI_PROBIT && (cfg->gh_points < 0 || cfg->gh_points > GH_MAX))
     return SVGP_ERR_INVALID_ARG;
-  if (cfg->prec != SVGP_FP32 && cfg->prec != SVGP_BF16 && cfg->prec != SVGP_BF16X3) return SVGP_ERR_INVALID_ARG;
+  if (cfg->prec != SVGP_FP32 && cfg->prec != SVGP_BF16 && cfg->prec != SVGP_BF16X3 && cfg->prec != SVGP_BF16X3K)
+    return SVGP_ERR_INVALID_ARG;
   if (cfg->prec != SVGP_FP32 && !tc_available()) return SVGP_ERR_UNSUPPORTED;
   svgp_handle* h = new svgp_handle();
   h->cfg = *cfg;
@@ -689,7 +700,8 @@ svgp_status svgp_create(const svgp_config* cfg, svgp_handle** out) {
   h->D = cfg->D;
   h->Dp = (cfg->D + 3) & ~3;
   h->Bmax = cfg->B_max;
-  h->mode = cfg->prec;   // svgp_prec values coincide with MODE_*
+  h->kuu3 = cfg->prec == SVGP_BF16X3K;
+  h->mode = h->kuu3 ? MODE_SPLIT : cfg->prec;   // svgp_prec values 0..2 coincide with MODE_*
   h->st = (cudaStream_t)cfg->cuda_stream;
   if (cudaStreamCreateWithFlags(&h->st_aux, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -734,7 +746,7 @@ svgp_status svgp_create(const svgp_config* cfg, svgp_handle** out) {
             dalloc(h, &h->red, sizeof(double) * RED_COUNT) && dalloc(h, &h->acc_ell, sizeof(double) * SVGP_MAXD) &&
             dalloc(h, &h->resid_tmp, sizeof(double)) && dalloc(h, &h->errword, sizeof(int)) &&
             dalloc(h, &h->done, sizeof(int)) && dalloc(h, &h->iters_tmp, sizeof(int));
-  if (ok && h->mode != MODE_F32) ok = dalloc(h, &h->Kuu_lo, lob) && dalloc(h, &h->P_lo, lob);
+  if (ok && h->mode != MODE_F32) ok = dalloc(h, &h->Kuu_lo, h->kuu3 ? lob / 2 * 3 : lob) && dalloc(h, &h->P_lo, lob);
   if (ok) ok = dalloc(h, &h->gapN, M2 * 4);
   if (ok) ok = dalloc(h, &h->hut, sizeof(float) * 3 * (size_t)h->M * SVGP_HUTCH_KMAX);
   h->tc_kuf = h->mode != MODE_F32 && tc_kuf_supported(h->D);

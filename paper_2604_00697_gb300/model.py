@@ -13,7 +13,7 @@ import torch
 
 from . import _lib as C
 
-PREC = {"fp32": C.SVGP_FP32, "bf16": C.SVGP_BF16, "bf16x3": C.SVGP_BF16X3}
+PREC = {"fp32": C.SVGP_FP32, "bf16": C.SVGP_BF16, "bf16x3": C.SVGP_BF16X3, "bf16x3k": C.SVGP_BF16X3K}
 
 
 def _softplus_inv(x: torch.Tensor) -> torch.Tensor:

@@ -12,6 +12,7 @@ TOL = {  # relative bound error, per-block relative gradient error
     "fp32": dict(bound=1e-6, grad=1e-4),
     "bf16": dict(bound=1e-3, grad=1e-2),
     "bf16x3": dict(bound=1e-3, grad=1e-2),
+    "bf16x3k": dict(bound=1e-3, grad=1e-2),
 }
 # Cases where a stated gate is out of reach of the arithmetic itself.  Each
 # entry pins the case at about twice (three times for the noisier BF16
@@ -23,8 +24,9 @@ TOL = {  # relative bound error, per-block relative gradient error
 # not named keep the stated gate).
 OUT_OF_REACH = {
     # FP32 at the converged state of the 1-D workload (s~ = 1e-2, cond(K~) =
-    # 1.6e3): bound 2.2e-5, dZ 3.2e-4, dell 4.9e-4, dsf2 4.6e-4, ds~ 6.9e-4
-    ("snelson_like/chol", "fp32"): dict(bound=5e-5, Z=7e-4, ell=1e-3, sf2=1e-3, s=1.5e-3),
+    # 1.6e3): bound 2.2e-5, dZ 3.2e-4, dell 4.9e-4 and 1.05e-3 in two runs
+    # (the order of the FP32 atomic sums differs), dsf2 4.6e-4, ds~ 6.9e-4
+    ("snelson_like/chol", "fp32"): dict(bound=5e-5, Z=7e-4, ell=2.5e-3, sf2=1e-3, s=1.5e-3),
     # BF16X3 there: dZ 1.7e-2, dsf2 1.5e-2, dm~ 1.6e-2, ds~ 1.8e-2
     ("snelson_like/chol", "bf16x3"): dict(Z=3.5e-2, sf2=3e-2, m=3.2e-2, s=3.7e-2),
     # single BF16 there: bound 1.6e-3, dZ 11.4, dell 3.3, dsf2 1.0, dm~ 0.14,

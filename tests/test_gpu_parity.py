@@ -86,7 +86,7 @@ def test_snelson_like_bound_and_grads(prec, state):
     _check_bound_and_grads(f"snelson_like/{state}", p, X, y, N, prec)
 
 
-@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("prec", PRECS + ["bf16x3k"])
 @pytest.mark.parametrize("M,D,B,seed", [(200, 3, 300, 0), (130, 5, 129, 1), (1, 2, 7, 2), (257, 1, 1, 3),
                                         (300, 19, 260, 4)])
 def test_ragged_random_state(prec, M, D, B, seed):
@@ -317,7 +317,7 @@ def test_probit_banana_config(prec, state):
     _check_bound_and_grads(f"banana_like/{state}", p, X, y, N, prec, likelihood="probit")
 
 
-@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("prec", PRECS + ["bf16x3k"])
 @pytest.mark.parametrize("M,D,seed", [(16, 1, 0), (200, 3, 1), (512, 8, 2)])
 def test_ng_step_matches_oracle(prec, M, D, seed):
     p, _, _, _ = small_case(M, D, 4, seed)
@@ -328,7 +328,7 @@ def test_ng_step_matches_oracle(prec, M, D, seed):
     m.ng_update(max_iters=1, eps=0.0, gammas=[0.7])
     torch.cuda.synchronize()
     Lg = m.L.double().cpu().numpy()
-    tol = {"fp32": 1e-5, "bf16": 2e-2, "bf16x3": 1e-4}[prec]
+    tol = {"fp32": 1e-5, "bf16": 2e-2, "bf16x3": 1e-4, "bf16x3k": 1e-4}[prec]
     assert rel(Lg, L1) <= tol
     assert abs(float(m.resid[0]) - r) <= tol * max(r, 1.0)
     assert int(m.iters[0]) == 1
@@ -715,3 +715,44 @@ def test_split_schedules_agree_and_autotune_restores_state():
     _lib.svgp_set_split(m.h, 1, -1)                              # back to the cost model
     assert _lib.svgp_get_split(m.h, 1) in cands["sym"]
     m.close()
+
+
+def _errors_at(p, X, y, N, prec):
+    M, D = p["Z"].shape
+    m = _model(p, M, D, X.shape[0], prec)
+    F = float(m.backward(_dev(X), _dev(y), N)[0])
+    torch.cuda.synchronize()
+    assert m.sync_status() == 0
+    ref = O.bound(p, X, y, N)["F"]
+    g = O.grads(p, X, y, N)
+    out = {"bound": abs(F - ref) / abs(ref)}
+    for k in BLOCKS:
+        out[k] = rel(m.grad_of(k).double().cpu().numpy().reshape(np.shape(g[k])), g[k])
+    m.close()
+    return out
+
+
+def test_three_plane_kuu_at_an_ill_conditioned_state():
+    """SVGP_BF16X3K against SVGP_BF16X3 where the rounding of Kuu in L^T K~
+    dominates dZ: the largest member of the 64-SVGP group workload at its
+    converged state (M = 2048 inducing points at the batch's own points,
+    D = 8, cond(K~) about 3e3).  The CPU rounding study of the chain puts
+    dZ at 7.0e-3 -> 1.2e-3; measured on a GB300, 8.4e-3 -> 2.3e-3 (two
+    runs).  The other gradient blocks are not asserted here: dell is
+    1.6e-2 in both forms, an error the chain's rounding does not explain
+    (the CPU study gives 3.5e-4 for it)."""
+    import svgp_synth as S
+
+    prob = S.sinusoid_regression(seed=100, B=2048, M=2048, D=8)
+    X, y = prob.batch(0)
+    M, D = 2048, 8
+    p = round_state(dict(Z=prob.Z0, ell=np.ones(D), sf2=1.0, noise=1.0,
+                         m=0.1 * np.random.default_rng(1).normal(size=M), s=np.full(M, 1e-4), L=np.eye(M)))
+    p["L"] = f32(chol_inv(p))
+    X, y = f32(X), f32(y)
+    e3 = _errors_at(p, X, y, prob.N, "bf16x3")
+    e5 = _errors_at(p, X, y, prob.N, "bf16x3k")
+    log_errors("group_member_2048/chol", "bf16x3", e3)
+    log_errors("group_member_2048/chol", "bf16x3k", e5)
+    assert e5["bound"] <= 1e-3
+    assert e5["Z"] <= 5e-3 and e5["Z"] < e3["Z"] / 2, (e3, e5)
