@@ -4,4 +4,4 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
 leg may import this package.  The CUDA library neither imports nor links it,
 and the two share no code.
 """
-from . import rsvgp  # noqa: F401
+from . import dgp, rsvgp  # noqa: F401
