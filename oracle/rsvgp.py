@@ -29,9 +29,11 @@ Everything here is plain NumPy in float64, written as the paper states it:
   (NG step then Adam step, Section 3.1; schedule of Section 3.4).
 
 Parity status: every function here is pinned by tests in
-``tests/test_oracle_pins.py`` except ``train`` (the trajectory of the Adam
-driver), whose parity is unpinned beyond monotone progress: the paper prints
-no worked values for it.
+``tests/test_oracle_pins.py``.  For ``train`` the pins fix its two halves
+(with Adam off the NG half reaches the fixed point of Prop. 1; with the NG
+half off one Adam step ascends by the first-order amount) and its progress
+on the 1-D workload; the trajectory as a whole is parity unpinned, since the
+paper prints no worked values for it.
 """
 from __future__ import annotations
 

@@ -616,3 +616,57 @@ def test_adam_chain_rule_through_softplus_matches_finite_differences():
         # the iterates approach the maximiser of F on c > 0
         cstar = (-2.0 + math.sqrt(4.0 + 4 * 0.9 * 4.0)) / (2 * 0.9)
         assert abs(dF(c)) < abs(dF(O.softplus(r0))) or abs(c - cstar) < 0.05
+
+
+def test_training_driver_ng_half_reaches_the_fixed_point():
+    """The alternating driver with its Adam half off (lr = 0): the parameters
+    stay put and the NG half, gamma = 1 from the paper's initial L = 1e-3 I,
+    reaches the fixed point of Prop. 1, chol((Kuu + S~)^-1)."""
+    prob = S.snelson_like()
+    X, y = prob.batch(0)
+    p0 = dict(Z=prob.Z0, ell=np.array([1.0]), sf2=1.0, noise=0.5, m=np.zeros(prob.M),
+              s=np.full(prob.M, 1e-2), L=1e-3 * np.eye(prob.M))
+    out, _ = O.train(p0, lambda t: (X, y), prob.N, steps=60, lr=0.0, gamma=lambda t: 1.0)
+    for k in ("Z", "ell", "m", "s"):
+        np.testing.assert_allclose(out[k], p0[k], rtol=1e-12, atol=1e-12)
+    Kt = O.se_ard(p0["Z"], p0["Z"], p0["ell"], p0["sf2"]) + np.diag(p0["s"])
+    np.testing.assert_allclose(out["L"], np.linalg.cholesky(np.linalg.inv(Kt)), rtol=1e-8, atol=1e-8)
+
+
+def test_training_driver_adam_half_ascends_by_the_first_order_amount():
+    """The alternating driver with its NG half off (gamma = 0): one Adam step
+    of length lr in every raw (softplus) coordinate along the gradient's sign
+    raises the bound by lr * sum_i |dF/draw_i| to first order, the gradient
+    here by central differences of the bound through the positivity
+    transform (independent of the analytic gradients)."""
+    prob = S.snelson_like()
+    X, y = prob.batch(0)
+    M = 5
+    rng = np.random.default_rng(3)
+    p0 = dict(Z=prob.Z0[:M] + 0.1, ell=np.array([0.8]), sf2=1.2, noise=0.4, m=0.3 * rng.normal(size=M),
+              s=np.full(M, 0.05))
+    Kt = O.se_ard(p0["Z"], p0["Z"], p0["ell"], p0["sf2"]) + np.diag(p0["s"])
+    p0["L"] = 0.9 * np.linalg.cholesky(np.linalg.inv(Kt))
+    N, lr, h = 200.0, 1e-6, 1e-6
+    raw = {k: (O.softplus_inv(p0[k]) if k in ("ell", "sf2", "noise", "s") else np.array(p0[k], np.float64))
+           for k in ("Z", "ell", "sf2", "noise", "m", "s")}
+
+    def F(r):
+        c = O.constrain(r)
+        c["L"] = p0["L"]
+        return O.bound(c, X, y, N)["F"]
+
+    l1 = 0.0
+    for k, v in raw.items():
+        v = np.atleast_1d(np.asarray(v, np.float64))
+        for i in range(v.size):
+            rp = {kk: np.array(vv, np.float64) for kk, vv in raw.items()}
+            rm = {kk: np.array(vv, np.float64) for kk, vv in raw.items()}
+            rp[k].reshape(-1)[i] += h
+            rm[k].reshape(-1)[i] -= h
+            l1 += abs(F(rp) - F(rm)) / (2 * h)
+    out, trace = O.train(p0, lambda t: (X, y), N, steps=1, lr=lr, gamma=lambda t: 0.0)
+    np.testing.assert_allclose(out["L"], p0["L"], rtol=0, atol=0)
+    F1 = O.bound(out, X, y, N)["F"]
+    assert trace[0] == pytest.approx(F(raw), rel=1e-12)
+    assert F1 - trace[0] == pytest.approx(lr * l1, rel=2e-3)
