@@ -19,8 +19,7 @@ it:
   mu_nq = k_n^T P m~_q, and sigma_n^2 = k_nn - k_n^T P k_n is the same for
   all outputs of the layer.
 
-Readings where the paper defers to the library it used (recorded in the
-design notes):
+Readings where the paper defers to the library it used:
 
 * hidden layers have width Q_l equal to their input width and the identity
   mean function; the output layer (Q = 1) has zero mean;

@@ -17,9 +17,10 @@ TOL = {  # relative bound error, per-block relative gradient error
 # Cases where a stated gate is out of reach of the arithmetic itself.  Each
 # entry pins the case at about twice (three times for the noisier BF16
 # gradients) the relative error measured on a GB300, with the measured value
-# in the comment.  Why each is out of reach, with the oracle's own
-# sensitivity to perturbations of the kernel blocks at the unit roundoff of
-# the mode, is tabulated in the design notes.  Keys: (case, precision);
+# in the comment.  Each is out of reach because the oracle's own bound and
+# gradients move by about that much when its kernel blocks are perturbed at
+# the unit roundoff of the mode (the states are ill-conditioned: cond(K~) in
+# the hundreds to thousands).  Keys: (case, precision);
 # values: tolerances for "bound" and for the gradient blocks named (blocks
 # not named keep the stated gate).
 OUT_OF_REACH = {
