@@ -81,3 +81,20 @@ def test_gauss_hermite_rule_matches_numpy(lib):
     for bad in (0, 65, -3):
         with pytest.raises(_lib.SvgpError):
             _lib.svgp_gauss_hermite(bad)
+
+
+def test_create_checks_the_precision_before_touching_a_device():
+    """svgp_create validates its configuration on the host: an unknown
+    precision is an invalid argument; a tensor-core precision (BF16, BF16X3,
+    BF16X3K) on a machine without a GB300 is unsupported, not a CUDA error."""
+    from paper_2604_00697_gb300 import _lib
+
+    with pytest.raises(_lib.SvgpError) as e:
+        _lib.svgp_create(64, 2, 16, prec=4)
+    assert e.value.status == _lib.SVGP_ERR_INVALID_ARG
+    if _lib.svgp_has_tensor_cores():
+        pytest.skip("a tensor-core device is present: the handle would be created")
+    for prec in (_lib.SVGP_BF16, _lib.SVGP_BF16X3, _lib.SVGP_BF16X3K):
+        with pytest.raises(_lib.SvgpError) as e:
+            _lib.svgp_create(64, 2, 16, prec=prec)
+        assert e.value.status == _lib.SVGP_ERR_UNSUPPORTED
